@@ -1,0 +1,301 @@
+"""GB300-native PCDN (Parallel Coordinate Descent Newton, arXiv:1306.4080) for L1-regularised
+logistic regression and L2-loss SVM.
+
+This module is a thin ctypes binding of the C ABI declared in ``include/pcdn.h``: every
+function here has the C name, marshals its arguments (numpy host arrays or device pointers
+from PyTorch tensors) and calls ``libpcdn.so``.  All arithmetic of the method runs in that
+library's CUDA kernels.  There is no CPU fallback: if the library is not built, or no GPU is
+present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpcdn.so")
+
+PCDN_OK = 0
+PCDN_EINVAL = -1
+PCDN_ENOMEM = -2
+PCDN_ECUDA = -3
+PCDN_ENUMERIC = -4
+PCDN_ETIMEOUT = -5
+PCDN_ENOTCONVERGED = 1
+
+LOSSES = {"logistic": 0, "l2svm": 1}
+PRECISIONS = {"fp64": 0, "mixed": 1}
+
+SYMBOLS = ["pcdn_default_opts", "pcdn_create", "pcdn_create_device", "pcdn_solve", "pcdn_bundle_step",
+           "pcdn_set_w", "pcdn_get_w", "pcdn_objective", "pcdn_kkt", "pcdn_permutation", "pcdn_memory",
+           "pcdn_destroy", "pcdn_last_error"]
+
+
+class PcdnError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"pcdn error {code}: {msg}")
+        self.code = code
+
+
+class pcdn_csc(ctypes.Structure):
+    _fields_ = [("n_samples", ctypes.c_int64), ("n_features", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("col_ptr", ctypes.c_void_p), ("row_idx", ctypes.c_void_p), ("val", ctypes.c_void_p)]
+
+
+class pcdn_opts(ctypes.Structure):
+    _fields_ = [("sigma", ctypes.c_double), ("beta", ctypes.c_double), ("gamma", ctypes.c_double),
+                ("nu", ctypes.c_double), ("q_max", ctypes.c_int32), ("ls_batch", ctypes.c_int32),
+                ("max_epochs", ctypes.c_int64), ("prec", ctypes.c_int), ("warm_start", ctypes.c_int32),
+                ("grid_ctas", ctypes.c_int32), ("refresh", ctypes.c_int32), ("spin_limit", ctypes.c_uint32)]
+
+
+class pcdn_stats(ctypes.Structure):
+    _fields_ = [("epochs", ctypes.c_int64), ("bundles", ctypes.c_int64), ("coord_updates", ctypes.c_int64),
+                ("ls_steps", ctypes.c_int64), ("ls_cap_hits", ctypes.c_int64), ("ls_passes", ctypes.c_int64),
+                ("nnz_visited", ctypes.c_int64), ("rows_touched", ctypes.c_int64),
+                ("kernel_launches", ctypes.c_int64), ("F_final", ctypes.c_double), ("kkt_rel", ctypes.c_double),
+                ("kkt0", ctypes.c_double), ("wall_s", ctypes.c_double), ("walk_s", ctypes.c_double),
+                ("bytes_model", ctypes.c_double), ("converged", ctypes.c_int32)]
+
+
+class pcdn_trace(ctypes.Structure):
+    _fields_ = [("bundle_cap", ctypes.c_int64), ("q", ctypes.c_void_p), ("alpha", ctypes.c_void_p),
+                ("Delta", ctypes.c_void_p), ("dF", ctypes.c_void_p), ("epoch_cap", ctypes.c_int64),
+                ("epoch_kkt", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def load() -> ctypes.CDLL:
+    """Load ``libpcdn.so`` (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with `python -c \"import __graft_entry__ as g; g.build()\"` "
+                          "or `python paper_1306_4080_gb300/build.py`")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64, d = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    P = ctypes.POINTER
+    lib.pcdn_default_opts.argtypes = [P(pcdn_opts)]
+    lib.pcdn_default_opts.restype = None
+    lib.pcdn_create.argtypes = [P(pcdn_csc), vp, d, ctypes.c_int, P(vp)]
+    lib.pcdn_create.restype = ctypes.c_int
+    lib.pcdn_create_device.argtypes = [P(pcdn_csc), vp, d, ctypes.c_int, vp, P(vp)]
+    lib.pcdn_create_device.restype = ctypes.c_int
+    lib.pcdn_solve.argtypes = [vp, i32, d, ctypes.c_uint64, P(pcdn_opts), vp, P(pcdn_stats), P(pcdn_trace)]
+    lib.pcdn_solve.restype = ctypes.c_int
+    lib.pcdn_bundle_step.argtypes = [vp, vp, vp, i32, P(pcdn_opts), vp, vp, vp, P(d), P(i32), P(d), P(d)]
+    lib.pcdn_bundle_step.restype = ctypes.c_int
+    lib.pcdn_set_w.argtypes = [vp, vp]
+    lib.pcdn_set_w.restype = ctypes.c_int
+    lib.pcdn_get_w.argtypes = [vp, vp]
+    lib.pcdn_get_w.restype = ctypes.c_int
+    lib.pcdn_objective.argtypes = [vp, P(d)]
+    lib.pcdn_objective.restype = ctypes.c_int
+    lib.pcdn_kkt.argtypes = [vp, P(d)]
+    lib.pcdn_kkt.restype = ctypes.c_int
+    lib.pcdn_permutation.argtypes = [vp, ctypes.c_uint64, i64, vp]
+    lib.pcdn_permutation.restype = ctypes.c_int
+    lib.pcdn_memory.argtypes = [vp, P(i64)]
+    lib.pcdn_memory.restype = ctypes.c_int
+    lib.pcdn_destroy.argtypes = [vp]
+    lib.pcdn_destroy.restype = None
+    lib.pcdn_last_error.argtypes = []
+    lib.pcdn_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def pcdn_last_error() -> str:
+    return load().pcdn_last_error().decode()
+
+
+def _check(rc: int, ok=(PCDN_OK,)) -> int:
+    if rc not in ok:
+        raise PcdnError(rc, pcdn_last_error())
+    return rc
+
+
+def pcdn_default_opts(**overrides) -> pcdn_opts:
+    o = pcdn_opts()
+    load().pcdn_default_opts(ctypes.byref(o))
+    for k, v in overrides.items():
+        if k == "prec" and isinstance(v, str):
+            v = PRECISIONS[v]
+        setattr(o, k, v)
+    return o
+
+
+def _host(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def pcdn_create(col_ptr, row_idx, val, y, C: float, loss: str = "logistic") -> int:
+    """Copy host CSC X and labels y to the device; returns an opaque problem handle."""
+    lib = load()
+    cp, ri, vv, yy = _host(col_ptr, np.int64), _host(row_idx, np.int32), _host(val, np.float32), _host(y, np.int8)
+    X = pcdn_csc(int(yy.shape[0]), int(cp.shape[0] - 1), int(ri.shape[0]), cp.ctypes.data, ri.ctypes.data,
+                 vv.ctypes.data)
+    h = ctypes.c_void_p()
+    _check(lib.pcdn_create(ctypes.byref(X), yy.ctypes.data, float(C), LOSSES[loss], ctypes.byref(h)))
+    return h.value
+
+
+def pcdn_create_device(col_ptr, row_idx, val, y, C: float, loss: str = "logistic", stream=None) -> int:
+    """Device-resident inputs (PyTorch CUDA tensors: int64, int32, float32, int8); the caller keeps
+    them alive until pcdn_destroy.  ``stream`` is a torch.cuda.Stream or raw handle (None: own)."""
+    lib = load()
+    n, m, nnz = int(y.shape[0]), int(col_ptr.shape[0] - 1), int(row_idx.shape[0])
+    for t, dt in ((col_ptr, "torch.int64"), (row_idx, "torch.int32"), (val, "torch.float32"), (y, "torch.int8")):
+        if str(t.dtype) != dt or not t.is_cuda or not t.is_contiguous():
+            raise ValueError(f"expected a contiguous CUDA tensor of {dt}, got {t.dtype} on {t.device}")
+    X = pcdn_csc(n, m, nnz, col_ptr.data_ptr(), row_idx.data_ptr(), val.data_ptr())
+    s = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    h = ctypes.c_void_p()
+    _check(lib.pcdn_create_device(ctypes.byref(X), y.data_ptr(), float(C), LOSSES[loss], s, ctypes.byref(h)))
+    return h.value
+
+
+def pcdn_destroy(h: int) -> None:
+    if h:
+        load().pcdn_destroy(h)
+
+
+def pcdn_solve(h: int, P: int, eps: float = 1e-3, seed: int = 0, opts: pcdn_opts | None = None,
+               n_features: int | None = None, want_w: bool = True, trace_bundles: int = 0, trace_epochs: int = 0):
+    """Algorithm 3 to relative KKT ``eps``.  Returns (status, w or None, stats dict, trace dict)."""
+    lib = load()
+    o = opts if opts is not None else pcdn_default_opts()
+    w = None
+    if want_w:
+        if n_features is None:
+            raise ValueError("n_features is needed to receive w")
+        w = np.empty(int(n_features), dtype=np.float64)
+    st = pcdn_stats()
+    tr = None
+    arrs = {}
+    if trace_bundles or trace_epochs:
+        arrs = dict(q=np.zeros(trace_bundles, np.int32), alpha=np.zeros(trace_bundles), Delta=np.zeros(trace_bundles),
+                    dF=np.zeros(trace_bundles), epoch_kkt=np.zeros(trace_epochs))
+        tr = pcdn_trace(trace_bundles, arrs["q"].ctypes.data, arrs["alpha"].ctypes.data, arrs["Delta"].ctypes.data,
+                        arrs["dF"].ctypes.data, trace_epochs, arrs["epoch_kkt"].ctypes.data)
+    rc = lib.pcdn_solve(h, int(P), float(eps), int(seed) & (2**64 - 1), ctypes.byref(o),
+                        w.ctypes.data if w is not None else None, ctypes.byref(st),
+                        ctypes.byref(tr) if tr is not None else None)
+    _check(rc, ok=(PCDN_OK, PCDN_ENOTCONVERGED))
+    stats = {f: getattr(st, f) for f, _ in pcdn_stats._fields_}
+    stats["status"] = rc
+    if arrs:
+        nb = min(int(stats["bundles"]), trace_bundles)
+        arrs = {k: (v[:nb] if k != "epoch_kkt" else v[:min(int(stats["epochs"]), trace_epochs)]) for k, v in arrs.items()}
+    return rc, w, stats, arrs
+
+
+def pcdn_bundle_step(h: int, w_in, bundle, opts: pcdn_opts | None = None):
+    """One inner iteration on ``bundle``; returns a dict of g, h, d, Delta, q, alpha, dF."""
+    lib = load()
+    o = opts if opts is not None else pcdn_default_opts()
+    B = _host(bundle, np.int32)
+    P = int(B.shape[0])
+    wp = None
+    if w_in is not None:
+        wv = _host(w_in, np.float64)
+        wp = wv.ctypes.data
+    g, hh, d = np.empty(P), np.empty(P), np.empty(P)
+    Delta, alpha, dF = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    q = ctypes.c_int32()
+    _check(lib.pcdn_bundle_step(h, wp, B.ctypes.data, P, ctypes.byref(o), g.ctypes.data, hh.ctypes.data, d.ctypes.data,
+                                ctypes.byref(Delta), ctypes.byref(q), ctypes.byref(alpha), ctypes.byref(dF)))
+    return dict(g=g, h=hh, d=d, Delta=Delta.value, q=q.value, alpha=alpha.value, dF=dF.value)
+
+
+def pcdn_set_w(h: int, w) -> None:
+    wv = _host(w, np.float64)
+    _check(load().pcdn_set_w(h, wv.ctypes.data))
+
+
+def pcdn_get_w(h: int, n_features: int) -> np.ndarray:
+    w = np.empty(int(n_features), dtype=np.float64)
+    _check(load().pcdn_get_w(h, w.ctypes.data))
+    return w
+
+
+def pcdn_objective(h: int) -> float:
+    F = ctypes.c_double()
+    _check(load().pcdn_objective(h, ctypes.byref(F)))
+    return F.value
+
+
+def pcdn_kkt(h: int) -> float:
+    k = ctypes.c_double()
+    _check(load().pcdn_kkt(h, ctypes.byref(k)))
+    return k.value
+
+
+def pcdn_permutation(h: int, seed: int, epoch: int, n_features: int) -> np.ndarray:
+    perm = np.empty(int(n_features), dtype=np.int32)
+    _check(load().pcdn_permutation(h, int(seed) & (2**64 - 1), int(epoch), perm.ctypes.data))
+    return perm
+
+
+def pcdn_memory(h: int) -> int:
+    b = ctypes.c_int64()
+    _check(load().pcdn_memory(h, ctypes.byref(b)))
+    return b.value
+
+
+@dataclass
+class Problem:
+    """Owning wrapper of a problem handle (destroyed with the object)."""
+    handle: int
+    n_samples: int
+    n_features: int
+
+    @classmethod
+    def from_csc(cls, col_ptr, row_idx, val, y, C: float, loss: str = "logistic") -> "Problem":
+        return cls(pcdn_create(col_ptr, row_idx, val, y, C, loss), int(len(y)), int(len(col_ptr) - 1))
+
+    @classmethod
+    def from_device(cls, col_ptr, row_idx, val, y, C: float, loss: str = "logistic", stream=None) -> "Problem":
+        return cls(pcdn_create_device(col_ptr, row_idx, val, y, C, loss, stream), int(y.shape[0]),
+                   int(col_ptr.shape[0] - 1))
+
+    def solve(self, P, eps=1e-3, seed=0, opts=None, **kw):
+        return pcdn_solve(self.handle, P, eps, seed, opts, self.n_features, **kw)
+
+    def bundle_step(self, w_in, bundle, opts=None):
+        return pcdn_bundle_step(self.handle, w_in, bundle, opts)
+
+    def set_w(self, w):
+        pcdn_set_w(self.handle, w)
+
+    def get_w(self):
+        return pcdn_get_w(self.handle, self.n_features)
+
+    def objective(self):
+        return pcdn_objective(self.handle)
+
+    def kkt(self):
+        return pcdn_kkt(self.handle)
+
+    def permutation(self, seed, epoch):
+        return pcdn_permutation(self.handle, seed, epoch, self.n_features)
+
+    def memory(self):
+        return pcdn_memory(self.handle)
+
+    def close(self):
+        if self.handle:
+            pcdn_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

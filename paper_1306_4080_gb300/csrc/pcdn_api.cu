@@ -1,0 +1,817 @@
+// C ABI of the GB300 PCDN solver (declared in include/pcdn.h): problem set-up on the device,
+// the outer-iteration loop of Algorithm 3 around the bundle walker, and the single-bundle
+// entry used for parity checks.  All arithmetic of the method runs in the CUDA kernels of
+// pcdn_walk.cu and pcdn_prep.cu; this file validates, allocates, launches and copies.
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "pcdn.h"
+#include "pcdn_internal.cuh"
+#include "pcdn_prep.h"
+
+namespace pcdn {
+cudaError_t launch_walk(int loss, int prec, const WalkParams& p, int grid, cudaStream_t s);
+cudaError_t walk_max_blocks_per_sm(int loss, int prec, int* out);
+}  // namespace pcdn
+
+using namespace pcdn;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define CUDA_TRY(expr)                                                                              \
+  do {                                                                                              \
+    cudaError_t e_ = (expr);                                                                        \
+    if (e_ != cudaSuccess) {                                                                        \
+      if (e_ == cudaErrorMemoryAllocation) return fail(PCDN_ENOMEM, "%s: %s", #expr, cudaGetErrorString(e_)); \
+      return fail(PCDN_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_));                             \
+    }                                                                                               \
+  } while (0)
+
+constexpr uint32_t kDefaultSpin = 1u << 22;  // ~seconds of polling before a wait gives up
+
+template <typename T>
+cudaError_t dalloc(T** p, int64_t count) {
+  *p = nullptr;
+  if (count <= 0) count = 1;
+  return cudaMalloc((void**)p, sizeof(T) * (size_t)count);
+}
+
+}  // namespace
+
+struct pcdn_problem {
+  int64_t n = 0, m = 0, nnz = 0;
+  double c = 1.0;
+  int loss = 0;
+  bool owns_x = true;
+  int device = 0;
+  int sms = 0;
+  // X by columns, labels
+  int64_t* col_ptr = nullptr;
+  int32_t* row_idx = nullptr;
+  float* val = nullptr;
+  int8_t* y = nullptr;
+  // X by rows
+  int64_t* row_ptr = nullptr;
+  int32_t* col_idx = nullptr;
+  float* rval = nullptr;
+  // state
+  double* w = nullptr;
+  double* mq = nullptr;
+  void* rec = nullptr;  // sized for the FP64 pair
+  int rec_prec = 0;
+  double* delta = nullptr;
+  uint32_t* touched = nullptr;
+  int64_t nwords = 0;
+  // identity-order work items (KKT)
+  int32_t* id_perm = nullptr;
+  int64_t* id_item_ptr = nullptr;
+  Item* id_items = nullptr;
+  int64_t n_id_items = 0;
+  // per-epoch partition and items
+  uint64_t* keys0 = nullptr;
+  uint64_t* keys1 = nullptr;
+  int32_t* vals0 = nullptr;
+  int32_t* vals1 = nullptr;
+  int64_t* cnt = nullptr;
+  int64_t* item_ptr = nullptr;
+  Item* items = nullptr;
+  int64_t max_items = 0;
+  int64_t* hist = nullptr;
+  int64_t* scan_ws = nullptr;
+  // bundle scratch
+  int32_t P_cap = 0;
+  double* gk = nullptr;
+  double* hk = nullptr;
+  double* dk = nullptr;
+  uint32_t* col_cnt = nullptr;
+  uint32_t* col_ready = nullptr;
+  double* part = nullptr;
+  // reductions, barriers, flags
+  double* cta_part = nullptr;
+  int max_grid = 1;
+  Decision* decision = nullptr;
+  uint32_t* sync = nullptr;  // [0] bar_count [1] bar_gen [2..4] anynz
+  int* err = nullptr;
+  unsigned long long* counters = nullptr;
+  double* red_part = nullptr;  // block partials
+  double* red_out = nullptr;   // [4]
+  int red_grid = 0;
+  // trace buffers (per epoch)
+  int64_t tr_cap = 0;
+  int32_t* tr_q = nullptr;
+  double* tr_alpha = nullptr;
+  double* tr_Delta = nullptr;
+  double* tr_dF = nullptr;
+  // stream, events
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  uint32_t stamp = 0;
+  int64_t launches = 0;
+  int64_t device_bytes = 0;
+};
+
+namespace {
+
+template <typename T>
+cudaError_t palloc(pcdn_problem* p, T** ptr, int64_t count) {
+  cudaError_t e = dalloc(ptr, count);
+  if (e == cudaSuccess) p->device_bytes += (int64_t)sizeof(T) * (count > 0 ? count : 1);
+  return e;
+}
+
+void free_all(pcdn_problem* p) {
+  auto f = [](void* q) { if (q) cudaFree(q); };
+  if (p->owns_x) {
+    f(p->col_ptr); f(p->row_idx); f(p->val); f(p->y);
+  }
+  f(p->row_ptr); f(p->col_idx); f(p->rval);
+  f(p->w); f(p->mq); f(p->rec); f(p->delta); f(p->touched);
+  f(p->id_perm); f(p->id_item_ptr); f(p->id_items);
+  f(p->keys0); f(p->keys1); f(p->vals0); f(p->vals1); f(p->cnt); f(p->item_ptr); f(p->items);
+  f(p->hist); f(p->scan_ws);
+  f(p->gk); f(p->hk); f(p->dk); f(p->col_cnt); f(p->col_ready); f(p->part);
+  f(p->cta_part); f(p->decision); f(p->sync); f(p->err); f(p->counters); f(p->red_part); f(p->red_out);
+  f(p->tr_q); f(p->tr_alpha); f(p->tr_Delta); f(p->tr_dF);
+  if (p->ev0) cudaEventDestroy(p->ev0);
+  if (p->ev1) cudaEventDestroy(p->ev1);
+  if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
+}
+
+int check_host_csc(const pcdn_csc* X, const int8_t* y) {
+  if (!X || !y) return fail(PCDN_EINVAL, "X and y must be given");
+  if (X->n_samples <= 0 || X->n_features <= 0 || X->nnz < 0)
+    return fail(PCDN_EINVAL, "n_samples and n_features must be positive, nnz >= 0");
+  if (X->n_samples > INT32_MAX || X->n_features > INT32_MAX)
+    return fail(PCDN_EINVAL, "n_samples and n_features must fit int32");
+  if (X->nnz >= INT32_MAX) return fail(PCDN_EINVAL, "nnz must be below 2^31");
+  if (!X->col_ptr || (X->nnz > 0 && (!X->row_idx || !X->val))) return fail(PCDN_EINVAL, "CSC arrays missing");
+  if (X->col_ptr[0] != 0 || X->col_ptr[X->n_features] != X->nnz)
+    return fail(PCDN_EINVAL, "col_ptr must start at 0 and end at nnz");
+  for (int64_t j = 0; j < X->n_features; ++j) {
+    const int64_t a = X->col_ptr[j], b = X->col_ptr[j + 1];
+    if (b < a) return fail(PCDN_EINVAL, "col_ptr decreases at column %lld", (long long)j);
+    for (int64_t e = a; e < b; ++e) {
+      const int32_t r = X->row_idx[e];
+      if (r < 0 || r >= X->n_samples) return fail(PCDN_EINVAL, "row index %d out of range in column %lld", r, (long long)j);
+      if (e > a && r <= X->row_idx[e - 1])
+        return fail(PCDN_EINVAL, "rows not strictly ascending in column %lld", (long long)j);
+      if (!std::isfinite(X->val[e])) return fail(PCDN_EINVAL, "non-finite value in column %lld", (long long)j);
+    }
+  }
+  for (int64_t i = 0; i < X->n_samples; ++i)
+    if (y[i] != 1 && y[i] != -1) return fail(PCDN_EINVAL, "label %d of sample %lld is not +1 or -1", (int)y[i], (long long)i);
+  return PCDN_OK;
+}
+
+// Everything after X and y are on the device: mirror, state, workspaces.
+int finish_create(pcdn_problem* p) {
+  cudaStream_t s = p->stream;
+  const int64_t n = p->n, m = p->m, nnz = p->nnz;
+  CUDA_TRY(cudaGetDevice(&p->device));
+  CUDA_TRY(cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device));
+
+  // ---- row-major mirror: stable sort of the CSC entries by row
+  CUDA_TRY(palloc(p, &p->row_ptr, n + 1));
+  CUDA_TRY(palloc(p, &p->col_idx, nnz));
+  CUDA_TRY(palloc(p, &p->rval, nnz));
+  {
+    int32_t* entry_col = nullptr;
+    uint32_t *k0 = nullptr, *k1 = nullptr;
+    int32_t *v0 = nullptr, *v1 = nullptr;
+    int64_t *hist = nullptr, *ws = nullptr, *counts = nullptr;
+    const int64_t hn = radix_hist_elems(nnz);
+    cudaError_t e = cudaSuccess;
+    auto cleanup = [&]() {
+      cudaFree(entry_col); cudaFree(k0); cudaFree(k1); cudaFree(v0); cudaFree(v1);
+      cudaFree(hist); cudaFree(ws); cudaFree(counts);
+    };
+    if ((e = dalloc(&entry_col, nnz)) || (e = dalloc(&k0, nnz)) || (e = dalloc(&k1, nnz)) || (e = dalloc(&v0, nnz)) ||
+        (e = dalloc(&v1, nnz)) || (e = dalloc(&hist, hn)) ||
+        (e = dalloc(&ws, scan_workspace_elems(hn > n + 1 ? hn : n + 1))) || (e = dalloc(&counts, n + 1))) {
+      cleanup();
+      return fail(e == cudaErrorMemoryAllocation ? PCDN_ENOMEM : PCDN_ECUDA, "mirror workspace: %s", cudaGetErrorString(e));
+    }
+    int key_bits = 1;
+    while ((int64_t(1) << key_bits) < n) ++key_bits;
+    uint32_t* ko = nullptr;
+    int32_t* vo = nullptr;
+    if (nnz > 0) {
+      if ((e = entry_columns(p->col_ptr, m, entry_col, s, &p->launches)) ||
+          (e = copy_keys_u32(p->row_idx, k0, nnz, s, &p->launches)) || (e = iota_i32(v0, nnz, s, &p->launches)) ||
+          (e = radix_sort_u32(k0, v0, k1, v1, nnz, key_bits, hist, ws, &ko, &vo, s, &p->launches)) ||
+          (e = gather_csr(vo, entry_col, p->val, nnz, p->col_idx, p->rval, s, &p->launches))) {
+        cleanup();
+        return fail(PCDN_ECUDA, "mirror build: %s", cudaGetErrorString(e));
+      }
+    }
+    if ((e = cudaMemsetAsync(counts, 0, sizeof(int64_t) * (n + 1), s)) ||
+        (nnz > 0 && (e = row_counts(p->row_idx, nnz, counts, s, &p->launches))) ||
+        (e = scan_exclusive(counts, p->row_ptr, n + 1, ws, s, &p->launches)) || (e = cudaStreamSynchronize(s))) {
+      cleanup();
+      return fail(PCDN_ECUDA, "mirror row pointers: %s", cudaGetErrorString(e));
+    }
+    cleanup();
+  }
+
+  // ---- state
+  p->nwords = (n + 31) / 32;
+  CUDA_TRY(palloc(p, &p->w, m));
+  CUDA_TRY(palloc(p, &p->mq, n));
+  CUDA_TRY(palloc(p, (RecT<0>**)&p->rec, n));
+  CUDA_TRY(palloc(p, &p->delta, n));
+  CUDA_TRY(palloc(p, &p->touched, p->nwords));
+  CUDA_TRY(cudaMemsetAsync(p->w, 0, sizeof(double) * m, s));
+  CUDA_TRY(cudaMemsetAsync(p->delta, 0, sizeof(double) * n, s));
+  CUDA_TRY(cudaMemsetAsync(p->touched, 0, sizeof(uint32_t) * p->nwords, s));
+
+  // ---- workspaces
+  p->max_items = m + nnz / kChunk + 2;
+  const int64_t hm = radix_hist_elems(m);
+  CUDA_TRY(palloc(p, &p->keys0, m));
+  CUDA_TRY(palloc(p, &p->keys1, m));
+  CUDA_TRY(palloc(p, &p->vals0, m));
+  CUDA_TRY(palloc(p, &p->vals1, m));
+  CUDA_TRY(palloc(p, &p->cnt, m + 1));
+  CUDA_TRY(palloc(p, &p->item_ptr, m + 1));
+  CUDA_TRY(palloc(p, &p->items, p->max_items));
+  CUDA_TRY(palloc(p, &p->hist, hm));
+  CUDA_TRY(palloc(p, &p->scan_ws, scan_workspace_elems(hm > m + 1 ? hm : m + 1)));
+  CUDA_TRY(palloc(p, &p->part, 2 * p->max_items));
+  CUDA_TRY(palloc(p, &p->id_perm, m));
+  CUDA_TRY(palloc(p, &p->id_item_ptr, m + 1));
+  CUDA_TRY(palloc(p, &p->id_items, p->max_items));
+  CUDA_TRY(cudaError_t(iota_i32(p->id_perm, m, s, &p->launches)));
+  CUDA_TRY(build_items(p->id_perm, m, p->col_ptr, p->cnt, p->id_item_ptr, p->id_items, p->scan_ws, s, &p->launches));
+  CUDA_TRY(cudaMemcpyAsync(&p->n_id_items, p->id_item_ptr + m, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+
+  int bps = 1;
+  CUDA_TRY(walk_max_blocks_per_sm(p->loss, 0, &bps));
+  int bps1 = 1;
+  CUDA_TRY(walk_max_blocks_per_sm(p->loss, 1, &bps1));
+  if (bps1 < bps) bps = bps1;
+  if (bps > 2) bps = 2;
+  if (bps < 1) return fail(PCDN_ECUDA, "bundle walker cannot be resident on this device");
+  p->max_grid = p->sms * bps;
+  CUDA_TRY(palloc(p, &p->cta_part, (int64_t)p->max_grid * kPartStride));
+  CUDA_TRY(palloc(p, &p->decision, 1));
+  CUDA_TRY(palloc(p, &p->sync, 8));
+  CUDA_TRY(palloc(p, &p->err, 4));
+  CUDA_TRY(palloc(p, &p->counters, 8));
+  p->red_grid = p->sms * 4;
+  CUDA_TRY(palloc(p, &p->red_part, 2 * (int64_t)p->red_grid));
+  CUDA_TRY(palloc(p, &p->red_out, 4));
+  CUDA_TRY(cudaMemsetAsync(p->err, 0, sizeof(int) * 4, s));
+  CUDA_TRY(cudaEventCreate(&p->ev0));
+  CUDA_TRY(cudaEventCreate(&p->ev1));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return PCDN_OK;
+}
+
+int ensure_bundle_scratch(pcdn_problem* p, int32_t P) {
+  if (P <= p->P_cap) return PCDN_OK;
+  auto f = [](void* q) { if (q) cudaFree(q); };
+  f(p->gk); f(p->hk); f(p->dk); f(p->col_cnt); f(p->col_ready);
+  p->gk = p->hk = p->dk = nullptr;
+  p->col_cnt = p->col_ready = nullptr;
+  p->P_cap = 0;
+  CUDA_TRY(palloc(p, &p->gk, P));
+  CUDA_TRY(palloc(p, &p->hk, P));
+  CUDA_TRY(palloc(p, &p->dk, P));
+  CUDA_TRY(palloc(p, &p->col_cnt, P));
+  CUDA_TRY(palloc(p, &p->col_ready, P));
+  CUDA_TRY(cudaMemsetAsync(p->col_cnt, 0, sizeof(uint32_t) * P, p->stream));
+  CUDA_TRY(cudaMemsetAsync(p->col_ready, 0, sizeof(uint32_t) * P, p->stream));
+  p->P_cap = P;
+  return PCDN_OK;
+}
+
+int ensure_trace(pcdn_problem* p, int64_t nb) {
+  if (nb <= p->tr_cap) return PCDN_OK;
+  auto f = [](void* q) { if (q) cudaFree(q); };
+  f(p->tr_q); f(p->tr_alpha); f(p->tr_Delta); f(p->tr_dF);
+  p->tr_q = nullptr;
+  p->tr_alpha = p->tr_Delta = p->tr_dF = nullptr;
+  p->tr_cap = 0;
+  CUDA_TRY(palloc(p, &p->tr_q, nb));
+  CUDA_TRY(palloc(p, &p->tr_alpha, nb));
+  CUDA_TRY(palloc(p, &p->tr_Delta, nb));
+  CUDA_TRY(palloc(p, &p->tr_dF, nb));
+  p->tr_cap = nb;
+  return PCDN_OK;
+}
+
+int device_status(pcdn_problem* p) {
+  int h = 0;
+  CUDA_TRY(cudaMemcpyAsync(&h, p->err, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+  CUDA_TRY(cudaStreamSynchronize(p->stream));
+  if (h & kErrTimeout) return fail(PCDN_ETIMEOUT, "a device-side wait between thread blocks timed out");
+  if (h & kErrNumeric) return fail(PCDN_ENUMERIC, "non-finite value or |w^T x| > 700 in the solve");
+  return PCDN_OK;
+}
+
+// Per-bundle scratch back to its resting state (zero delta, empty bitmap, zero arrival counts):
+// every entry point that starts stepping calls this, so a launch that ended early (a timeout)
+// leaves nothing behind.
+int reset_scratch(pcdn_problem* p) {
+  CUDA_TRY(cudaMemsetAsync(p->delta, 0, sizeof(double) * p->n, p->stream));
+  CUDA_TRY(cudaMemsetAsync(p->touched, 0, sizeof(uint32_t) * p->nwords, p->stream));
+  if (p->P_cap > 0) CUDA_TRY(cudaMemsetAsync(p->col_cnt, 0, sizeof(uint32_t) * p->P_cap, p->stream));
+  return PCDN_OK;
+}
+
+int do_refresh(pcdn_problem* p, int prec, bool write_state, bool with_loss) {
+  CUDA_TRY(refresh(p->loss, prec, p->row_ptr, p->col_idx, p->rval, p->y, p->w, p->n, p->mq, p->rec, write_state,
+                   with_loss ? p->red_part : nullptr, p->red_grid, p->err, p->stream, &p->launches));
+  if (write_state) p->rec_prec = prec;
+  return PCDN_OK;
+}
+
+// ||v||_1 into red_out[slot] (device); the caller copies.
+int do_kkt(pcdn_problem* p, int slot) {
+  CUDA_TRY(kkt_l1(p->rec_prec, p->id_items, p->n_id_items, p->id_item_ptr, p->id_perm, p->m, p->row_idx, p->val, p->rec,
+                  p->w, p->c, p->part, p->red_part, p->red_grid, p->red_out + slot, p->stream, &p->launches));
+  return PCDN_OK;
+}
+
+int do_objective(pcdn_problem* p, int slot) {
+  int rc = do_refresh(p, p->rec_prec, false, true);
+  if (rc) return rc;
+  CUDA_TRY(objective_finish(p->red_part, p->red_grid, p->w, p->m, p->c, p->red_part + p->red_grid, p->red_grid,
+                            p->red_out + slot, p->stream, &p->launches));
+  return PCDN_OK;
+}
+
+int read_double(pcdn_problem* p, int slot, double* out) {
+  CUDA_TRY(cudaMemcpyAsync(out, p->red_out + slot, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+  CUDA_TRY(cudaStreamSynchronize(p->stream));
+  return PCDN_OK;
+}
+
+int check_opts(const pcdn_opts* o) {
+  if (!(o->sigma > 0 && o->sigma < 1)) return fail(PCDN_EINVAL, "sigma must be in (0, 1)");
+  if (!(o->beta > 0 && o->beta < 1)) return fail(PCDN_EINVAL, "beta must be in (0, 1)");
+  if (!(o->gamma >= 0 && o->gamma < 1)) return fail(PCDN_EINVAL, "gamma must be in [0, 1)");
+  if (!(o->nu > 0)) return fail(PCDN_EINVAL, "nu must be positive");
+  if (o->q_max < 1 || o->q_max > 1000) return fail(PCDN_EINVAL, "q_max must be in [1, 1000]");
+  if (o->ls_batch < 0 || o->ls_batch > kMaxK) return fail(PCDN_EINVAL, "ls_batch must be in [0, %d]", kMaxK);
+  if (o->max_epochs < 0) return fail(PCDN_EINVAL, "max_epochs must be >= 0");
+  if (o->prec != PCDN_PREC_FP64 && o->prec != PCDN_PREC_MIXED) return fail(PCDN_EINVAL, "unknown precision");
+  return PCDN_OK;
+}
+
+int pick_grid(const pcdn_problem* p, const pcdn_opts* o, int32_t P) {
+  if (o->grid_ctas > 0) return o->grid_ctas < p->max_grid ? o->grid_ctas : p->max_grid;
+  // One block when a bundle's work fits one SM comfortably; the whole GPU otherwise.
+  const double nnz_per_bundle = (double)p->nnz * (double)P / (double)p->m;
+  if (nnz_per_bundle < 8192.0 && p->n < (1 << 16)) return 1;
+  return p->max_grid;
+}
+
+// Launch the walker over bundles [t0, t1) of the partition held in perm/items.
+int run_walk(pcdn_problem* p, const pcdn_opts* o, const int32_t* perm, int64_t npos, int32_t P, int64_t t0, int64_t t1,
+             int grid, float* ms) {
+  WalkParams w{};
+  w.n = p->n;
+  w.m = p->m;
+  w.col_ptr = p->col_ptr;
+  w.row_idx = p->row_idx;
+  w.val = p->val;
+  w.y = p->y;
+  w.c = p->c;
+  w.w = p->w;
+  w.mq = p->mq;
+  w.rec = p->rec;
+  w.delta = p->delta;
+  w.touched = p->touched;
+  w.nwords = p->nwords;
+  w.perm = perm;
+  w.items = p->items;
+  w.item_ptr = p->item_ptr;
+  w.npos = npos;
+  w.P = P;
+  w.t_begin = t0;
+  w.t_end = t1;
+  w.gk = p->gk;
+  w.hk = p->hk;
+  w.dk = p->dk;
+  w.part = p->part;
+  w.col_cnt = p->col_cnt;
+  w.col_ready = p->col_ready;
+  w.stamp_base = p->stamp;
+  p->stamp += (uint32_t)(t1 + 1);
+  w.anynz = p->sync + 2;
+  w.cta_part = p->cta_part;
+  w.decision = p->decision;
+  w.bar_count = p->sync;
+  w.bar_gen = p->sync + 1;
+  w.spin_limit = o->spin_limit ? o->spin_limit : kDefaultSpin;
+  w.sigma = o->sigma;
+  w.beta = o->beta;
+  w.gamma = o->gamma;
+  w.nu = o->nu;
+  w.q_max = o->q_max;
+  w.K = o->ls_batch > 0 ? o->ls_batch : (o->prec == PCDN_PREC_MIXED ? 8 : 4);
+  w.tr_q = p->tr_q;
+  w.tr_alpha = p->tr_alpha;
+  w.tr_Delta = p->tr_Delta;
+  w.tr_dF = p->tr_dF;
+  w.counters = p->counters;
+  w.err = p->err;
+  CUDA_TRY(cudaMemsetAsync(p->sync, 0, sizeof(uint32_t) * 8, p->stream));
+  CUDA_TRY(cudaEventRecord(p->ev0, p->stream));
+  CUDA_TRY(launch_walk(p->loss, (int)o->prec, w, grid, p->stream));
+  ++p->launches;
+  CUDA_TRY(cudaEventRecord(p->ev1, p->stream));
+  if (ms) {
+    CUDA_TRY(cudaEventSynchronize(p->ev1));
+    CUDA_TRY(cudaEventElapsedTime(ms, p->ev0, p->ev1));
+  }
+  return PCDN_OK;
+}
+
+// The partition of outer iteration `epoch` into p->vals? -> returns the device pointer of perm.
+int make_partition(pcdn_problem* p, uint64_t seed, int64_t epoch, int32_t** perm_out) {
+  CUDA_TRY(perm_keys(seed, epoch, p->m, p->keys0, p->vals0, p->stream, &p->launches));
+  uint64_t* ko = nullptr;
+  int32_t* vo = nullptr;
+  CUDA_TRY(radix_sort_u64(p->keys0, p->vals0, p->keys1, p->vals1, p->m, 64, p->hist, p->scan_ws, &ko, &vo, p->stream,
+                          &p->launches));
+  *perm_out = vo;
+  return PCDN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void pcdn_default_opts(pcdn_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->sigma = 0.01;
+  o->beta = 0.5;
+  o->gamma = 0.0;
+  o->nu = 1e-12;
+  o->q_max = 30;
+  o->ls_batch = 0;
+  o->max_epochs = 1000;
+  o->prec = PCDN_PREC_FP64;
+  o->warm_start = 0;
+  o->grid_ctas = 0;
+  o->refresh = 1;
+  o->spin_limit = 0;
+}
+
+const char* pcdn_last_error(void) { return g_err.c_str(); }
+
+int pcdn_create(const pcdn_csc* X, const int8_t* y, double C, pcdn_loss loss, pcdn_problem** out) {
+  g_err.clear();
+  if (!out) return fail(PCDN_EINVAL, "out must be given");
+  *out = nullptr;
+  if (!(C > 0) || !std::isfinite(C)) return fail(PCDN_EINVAL, "C must be positive and finite");
+  if (loss != PCDN_LOSS_LOGISTIC && loss != PCDN_LOSS_L2SVM) return fail(PCDN_EINVAL, "unknown loss");
+  int rc = check_host_csc(X, y);
+  if (rc) return rc;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return fail(PCDN_ECUDA, "no CUDA device");
+  }
+  pcdn_problem* p = new (std::nothrow) pcdn_problem();
+  if (!p) return fail(PCDN_ENOMEM, "host allocation");
+  p->n = X->n_samples;
+  p->m = X->n_features;
+  p->nnz = X->nnz;
+  p->c = C;
+  p->loss = (int)loss;
+  p->owns_x = true;
+  auto bail = [&](int code) { free_all(p); delete p; return code; };
+  if (cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking) != cudaSuccess)
+    return bail(fail(PCDN_ECUDA, "stream creation failed"));
+  p->own_stream = true;
+  cudaError_t e;
+  if ((e = palloc(p, &p->col_ptr, p->m + 1)) || (e = palloc(p, &p->row_idx, p->nnz)) || (e = palloc(p, &p->val, p->nnz)) ||
+      (e = palloc(p, &p->y, p->n)))
+    return bail(fail(e == cudaErrorMemoryAllocation ? PCDN_ENOMEM : PCDN_ECUDA, "input allocation: %s", cudaGetErrorString(e)));
+  if ((e = cudaMemcpyAsync(p->col_ptr, X->col_ptr, sizeof(int64_t) * (p->m + 1), cudaMemcpyHostToDevice, p->stream)) ||
+      (p->nnz > 0 && (e = cudaMemcpyAsync(p->row_idx, X->row_idx, sizeof(int32_t) * p->nnz, cudaMemcpyHostToDevice, p->stream))) ||
+      (p->nnz > 0 && (e = cudaMemcpyAsync(p->val, X->val, sizeof(float) * p->nnz, cudaMemcpyHostToDevice, p->stream))) ||
+      (e = cudaMemcpyAsync(p->y, y, p->n, cudaMemcpyHostToDevice, p->stream)))
+    return bail(fail(PCDN_ECUDA, "input copy: %s", cudaGetErrorString(e)));
+  rc = finish_create(p);
+  if (rc) return bail(rc);
+  rc = do_refresh(p, 0, true, false);
+  if (!rc) rc = device_status(p);
+  if (rc) return bail(rc);
+  *out = p;
+  return PCDN_OK;
+}
+
+int pcdn_create_device(const pcdn_csc* X, const int8_t* y, double C, pcdn_loss loss, void* stream, pcdn_problem** out) {
+  g_err.clear();
+  if (!out) return fail(PCDN_EINVAL, "out must be given");
+  *out = nullptr;
+  if (!X || !y) return fail(PCDN_EINVAL, "X and y must be given");
+  if (!(C > 0) || !std::isfinite(C)) return fail(PCDN_EINVAL, "C must be positive and finite");
+  if (loss != PCDN_LOSS_LOGISTIC && loss != PCDN_LOSS_L2SVM) return fail(PCDN_EINVAL, "unknown loss");
+  if (X->n_samples <= 0 || X->n_features <= 0 || X->nnz < 0 || X->n_samples > INT32_MAX || X->n_features > INT32_MAX ||
+      X->nnz >= INT32_MAX)
+    return fail(PCDN_EINVAL, "bad sizes");
+  if (!X->col_ptr || (X->nnz > 0 && (!X->row_idx || !X->val))) return fail(PCDN_EINVAL, "CSC arrays missing");
+  pcdn_problem* p = new (std::nothrow) pcdn_problem();
+  if (!p) return fail(PCDN_ENOMEM, "host allocation");
+  p->n = X->n_samples;
+  p->m = X->n_features;
+  p->nnz = X->nnz;
+  p->c = C;
+  p->loss = (int)loss;
+  p->owns_x = false;
+  p->col_ptr = const_cast<int64_t*>(X->col_ptr);
+  p->row_idx = const_cast<int32_t*>(X->row_idx);
+  p->val = const_cast<float*>(X->val);
+  p->y = const_cast<int8_t*>(y);
+  auto bail = [&](int code) { free_all(p); delete p; return code; };
+  if (stream) {
+    p->stream = (cudaStream_t)stream;
+    p->own_stream = false;
+  } else {
+    if (cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking) != cudaSuccess)
+      return bail(fail(PCDN_ECUDA, "stream creation failed"));
+    p->own_stream = true;
+  }
+  cudaError_t e;
+  if ((e = palloc(p, &p->err, 4)) || (e = cudaMemsetAsync(p->err, 0, sizeof(int) * 4, p->stream)))
+    return bail(fail(PCDN_ECUDA, "flag allocation: %s", cudaGetErrorString(e)));
+  if ((e = validate_device(p->col_ptr, p->row_idx, p->val, p->y, p->n, p->m, p->nnz, p->err, p->stream, &p->launches)))
+    return bail(fail(PCDN_ECUDA, "validation launch: %s", cudaGetErrorString(e)));
+  int flag = 0;
+  if ((e = cudaMemcpyAsync(&flag, p->err, sizeof(int), cudaMemcpyDeviceToHost, p->stream)) ||
+      (e = cudaStreamSynchronize(p->stream)))
+    return bail(fail(PCDN_ECUDA, "validation: %s", cudaGetErrorString(e)));
+  if (flag) return bail(fail(PCDN_EINVAL, "device CSC/labels invalid (flags 0x%x)", flag));
+  cudaFree(p->err);
+  p->err = nullptr;
+  int rc = finish_create(p);
+  if (rc) return bail(rc);
+  rc = do_refresh(p, 0, true, false);
+  if (!rc) rc = device_status(p);
+  if (rc) return bail(rc);
+  *out = p;
+  return PCDN_OK;
+}
+
+void pcdn_destroy(pcdn_problem* p) {
+  if (!p) return;
+  if (p->stream) cudaStreamSynchronize(p->stream);
+  free_all(p);
+  delete p;
+}
+
+int pcdn_set_w(pcdn_problem* p, const double* w) {
+  g_err.clear();
+  if (!p || !w) return fail(PCDN_EINVAL, "problem and w must be given");
+  for (int64_t j = 0; j < p->m; ++j)
+    if (!std::isfinite(w[j])) return fail(PCDN_EINVAL, "w[%lld] is not finite", (long long)j);
+  CUDA_TRY(cudaMemcpyAsync(p->w, w, sizeof(double) * p->m, cudaMemcpyHostToDevice, p->stream));
+  CUDA_TRY(cudaMemsetAsync(p->err, 0, sizeof(int), p->stream));
+  int rc = reset_scratch(p);
+  if (rc) return rc;
+  rc = do_refresh(p, p->rec_prec, true, false);
+  if (rc) return rc;
+  return device_status(p);
+}
+
+int pcdn_get_w(pcdn_problem* p, double* w) {
+  g_err.clear();
+  if (!p || !w) return fail(PCDN_EINVAL, "problem and w must be given");
+  CUDA_TRY(cudaMemcpyAsync(w, p->w, sizeof(double) * p->m, cudaMemcpyDeviceToHost, p->stream));
+  CUDA_TRY(cudaStreamSynchronize(p->stream));
+  return PCDN_OK;
+}
+
+int pcdn_objective(pcdn_problem* p, double* F) {
+  g_err.clear();
+  if (!p || !F) return fail(PCDN_EINVAL, "problem and F must be given");
+  int rc = do_objective(p, 0);
+  if (rc) return rc;
+  return read_double(p, 0, F);
+}
+
+int pcdn_kkt(pcdn_problem* p, double* kkt) {
+  g_err.clear();
+  if (!p || !kkt) return fail(PCDN_EINVAL, "problem and kkt must be given");
+  int rc = do_kkt(p, 1);
+  if (rc) return rc;
+  return read_double(p, 1, kkt);
+}
+
+int pcdn_permutation(pcdn_problem* p, uint64_t seed, int64_t epoch, int32_t* perm) {
+  g_err.clear();
+  if (!p || !perm || epoch < 0) return fail(PCDN_EINVAL, "problem, perm and epoch >= 0 must be given");
+  int32_t* dperm = nullptr;
+  int rc = make_partition(p, seed, epoch, &dperm);
+  if (rc) return rc;
+  CUDA_TRY(cudaMemcpyAsync(perm, dperm, sizeof(int32_t) * p->m, cudaMemcpyDeviceToHost, p->stream));
+  CUDA_TRY(cudaStreamSynchronize(p->stream));
+  return PCDN_OK;
+}
+
+int pcdn_memory(pcdn_problem* p, int64_t* bytes) {
+  if (!p || !bytes) return fail(PCDN_EINVAL, "problem and bytes must be given");
+  *bytes = p->device_bytes;
+  return PCDN_OK;
+}
+
+int pcdn_bundle_step(pcdn_problem* p, const double* w_in, const int32_t* bundle, int32_t P, const pcdn_opts* opts,
+                     double* g, double* h, double* d, double* Delta, int32_t* q, double* alpha, double* dF) {
+  g_err.clear();
+  if (!p || !bundle) return fail(PCDN_EINVAL, "problem and bundle must be given");
+  if (P < 1 || P > p->m) return fail(PCDN_EINVAL, "P must be in [1, n_features]");
+  pcdn_opts o;
+  if (opts) o = *opts;
+  else pcdn_default_opts(&o);
+  int rc = check_opts(&o);
+  if (rc) return rc;
+  {
+    std::vector<uint8_t> seen((size_t)p->m, 0);
+    for (int32_t k = 0; k < P; ++k) {
+      const int32_t j = bundle[k];
+      if (j < 0 || j >= p->m) return fail(PCDN_EINVAL, "bundle[%d] = %d out of range", k, j);
+      if (seen[j]) return fail(PCDN_EINVAL, "feature %d repeated in the bundle", j);
+      seen[j] = 1;
+    }
+  }
+  const int prec = (int)o.prec;
+  if (w_in) {
+    for (int64_t j = 0; j < p->m; ++j)
+      if (!std::isfinite(w_in[j])) return fail(PCDN_EINVAL, "w_in[%lld] is not finite", (long long)j);
+    CUDA_TRY(cudaMemcpyAsync(p->w, w_in, sizeof(double) * p->m, cudaMemcpyHostToDevice, p->stream));
+    rc = do_refresh(p, prec, true, false);
+    if (rc) return rc;
+  } else if (p->rec_prec != prec) {
+    CUDA_TRY(rec_from_mq(p->loss, prec, p->mq, p->y, p->n, p->rec, p->stream, &p->launches));
+    p->rec_prec = prec;
+  }
+  rc = ensure_bundle_scratch(p, P);
+  if (rc) return rc;
+  rc = ensure_trace(p, 1);
+  if (rc) return rc;
+  rc = reset_scratch(p);
+  if (rc) return rc;
+  // the bundle is the feature order of a one-bundle walk
+  CUDA_TRY(cudaMemcpyAsync(p->vals1, bundle, sizeof(int32_t) * P, cudaMemcpyHostToDevice, p->stream));
+  CUDA_TRY(build_items(p->vals1, P, p->col_ptr, p->cnt, p->item_ptr, p->items, p->scan_ws, p->stream, &p->launches));
+  CUDA_TRY(cudaMemsetAsync(p->err, 0, sizeof(int), p->stream));
+  CUDA_TRY(cudaMemsetAsync(p->counters, 0, sizeof(unsigned long long) * 8, p->stream));
+  const int grid = pick_grid(p, &o, P);
+  rc = run_walk(p, &o, p->vals1, P, P, 0, 1, grid, nullptr);
+  if (rc) return rc;
+  if (g) CUDA_TRY(cudaMemcpyAsync(g, p->gk, sizeof(double) * P, cudaMemcpyDeviceToHost, p->stream));
+  if (h) CUDA_TRY(cudaMemcpyAsync(h, p->hk, sizeof(double) * P, cudaMemcpyDeviceToHost, p->stream));
+  if (d) CUDA_TRY(cudaMemcpyAsync(d, p->dk, sizeof(double) * P, cudaMemcpyDeviceToHost, p->stream));
+  int32_t hq = 0;
+  double ha = 0, hD = 0, hF = 0;
+  CUDA_TRY(cudaMemcpyAsync(&hq, p->tr_q, sizeof(int32_t), cudaMemcpyDeviceToHost, p->stream));
+  CUDA_TRY(cudaMemcpyAsync(&ha, p->tr_alpha, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+  CUDA_TRY(cudaMemcpyAsync(&hD, p->tr_Delta, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+  CUDA_TRY(cudaMemcpyAsync(&hF, p->tr_dF, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+  rc = device_status(p);
+  if (rc) return rc;
+  if (q) *q = hq;
+  if (alpha) *alpha = ha;
+  if (Delta) *Delta = hD;
+  if (dF) *dF = hF;
+  return PCDN_OK;
+}
+
+int pcdn_solve(pcdn_problem* p, int32_t P, double eps, uint64_t seed, const pcdn_opts* opts, double* w_out,
+               pcdn_stats* stats, pcdn_trace* trace) {
+  g_err.clear();
+  const auto t_start = std::chrono::steady_clock::now();
+  if (!p) return fail(PCDN_EINVAL, "problem must be given");
+  if (P < 1 || P > p->m) return fail(PCDN_EINVAL, "P must be in [1, n_features]");
+  if (!(eps > 0)) return fail(PCDN_EINVAL, "eps must be positive");
+  pcdn_opts o;
+  if (opts) o = *opts;
+  else pcdn_default_opts(&o);
+  int rc = check_opts(&o);
+  if (rc) return rc;
+  const int prec = (int)o.prec;
+  const int64_t nb = (p->m + P - 1) / P;
+  const int64_t launches0 = p->launches;
+  rc = ensure_bundle_scratch(p, P);
+  if (rc) return rc;
+  rc = ensure_trace(p, nb);
+  if (rc) return rc;
+  rc = reset_scratch(p);
+  if (rc) return rc;
+  if (!o.warm_start) CUDA_TRY(cudaMemsetAsync(p->w, 0, sizeof(double) * p->m, p->stream));
+  CUDA_TRY(cudaMemsetAsync(p->err, 0, sizeof(int), p->stream));
+  CUDA_TRY(cudaMemsetAsync(p->counters, 0, sizeof(unsigned long long) * 8, p->stream));
+  rc = do_refresh(p, prec, true, false);
+  if (rc) return rc;
+  rc = do_kkt(p, 2);
+  if (rc) return rc;
+  double kkt0 = 0.0;
+  rc = read_double(p, 2, &kkt0);
+  if (rc) return rc;
+  rc = device_status(p);
+  if (rc) return rc;
+  const int grid = pick_grid(p, &o, P);
+  double kkt_rel = kkt0 > 0 ? 1.0 : 0.0;
+  int converged = kkt0 == 0.0;
+  int64_t epochs = 0;
+  double walk_ms = 0.0;
+  std::vector<int32_t> hq;
+  std::vector<double> ha, hD, hF;
+  for (int64_t k = 0; k < o.max_epochs && !converged; ++k) {
+    int32_t* perm = nullptr;
+    rc = make_partition(p, seed, k, &perm);
+    if (rc) return rc;
+    CUDA_TRY(build_items(perm, p->m, p->col_ptr, p->cnt, p->item_ptr, p->items, p->scan_ws, p->stream, &p->launches));
+    float ms = 0.0f;
+    rc = run_walk(p, &o, perm, p->m, P, 0, nb, grid, &ms);
+    if (rc) return rc;
+    walk_ms += ms;
+    rc = device_status(p);
+    if (rc) return rc;
+    if (trace && (trace->q || trace->alpha || trace->Delta || trace->dF) && k * nb < trace->bundle_cap) {
+      const int64_t cnt = std::min<int64_t>(nb, trace->bundle_cap - k * nb);
+      if (trace->q) CUDA_TRY(cudaMemcpyAsync(trace->q + k * nb, p->tr_q, sizeof(int32_t) * cnt, cudaMemcpyDeviceToHost, p->stream));
+      if (trace->alpha) CUDA_TRY(cudaMemcpyAsync(trace->alpha + k * nb, p->tr_alpha, sizeof(double) * cnt, cudaMemcpyDeviceToHost, p->stream));
+      if (trace->Delta) CUDA_TRY(cudaMemcpyAsync(trace->Delta + k * nb, p->tr_Delta, sizeof(double) * cnt, cudaMemcpyDeviceToHost, p->stream));
+      if (trace->dF) CUDA_TRY(cudaMemcpyAsync(trace->dF + k * nb, p->tr_dF, sizeof(double) * cnt, cudaMemcpyDeviceToHost, p->stream));
+    }
+    if (o.refresh) {
+      rc = do_refresh(p, prec, true, false);
+      if (rc) return rc;
+    }
+    rc = do_kkt(p, 1);
+    if (rc) return rc;
+    double kk = 0.0;
+    rc = read_double(p, 1, &kk);
+    if (rc) return rc;
+    rc = device_status(p);
+    if (rc) return rc;
+    epochs = k + 1;
+    kkt_rel = kkt0 > 0 ? kk / kkt0 : 0.0;
+    if (trace && trace->epoch_kkt && k < trace->epoch_cap) trace->epoch_kkt[k] = kkt_rel;
+    if (kkt_rel <= eps) converged = 1;
+  }
+  double F = 0.0;
+  rc = do_objective(p, 0);
+  if (rc) return rc;
+  rc = read_double(p, 0, &F);
+  if (rc) return rc;
+  if (w_out) {
+    CUDA_TRY(cudaMemcpyAsync(w_out, p->w, sizeof(double) * p->m, cudaMemcpyDeviceToHost, p->stream));
+  }
+  unsigned long long cnt[8] = {0};
+  CUDA_TRY(cudaMemcpyAsync(cnt, p->counters, sizeof(cnt), cudaMemcpyDeviceToHost, p->stream));
+  CUDA_TRY(cudaStreamSynchronize(p->stream));
+  if (stats) {
+    std::memset(stats, 0, sizeof(*stats));
+    stats->epochs = epochs;
+    stats->bundles = (int64_t)cnt[5];
+    stats->coord_updates = (int64_t)cnt[6];
+    stats->ls_steps = (int64_t)cnt[0];
+    stats->ls_cap_hits = (int64_t)cnt[1];
+    stats->ls_passes = (int64_t)cnt[2];
+    stats->nnz_visited = epochs * p->nnz;
+    stats->rows_touched = (int64_t)cnt[4];
+    stats->kernel_launches = p->launches - launches0;
+    stats->F_final = F;
+    stats->kkt_rel = kkt_rel;
+    stats->kkt0 = kkt0;
+    stats->walk_s = walk_ms * 1e-3;
+    stats->bytes_model = 16.0 * (double)stats->nnz_visited + 33.0 * (double)stats->rows_touched +
+                         16.0 * (double)stats->coord_updates;
+    stats->converged = converged;
+    stats->wall_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+  }
+  return converged ? PCDN_OK : PCDN_ENOTCONVERGED;
+}
+
+}  // extern "C"

@@ -1,0 +1,270 @@
+// Internal device-side definitions of the GB300 PCDN solver.
+//
+// Layout in HBM (per problem):
+//   X by columns: col_ptr int64[m+1], row_idx int32[nnz], val f32[nnz]   (read-only)
+//   X by rows (mirror, for z = Xw): row_ptr int64[n+1], col_idx int32[nnz], rval f32[nnz]
+//   y int8[n]; w f64[m]
+//   mq f64[n]        maintained quantity: e^{w^T x_i} (logistic) or b_i = 1 - y_i w^T x_i (L2-SVM)
+//   rec {cg, ch}[n]  per-sample coefficients of the column reductions, derived from mq:
+//                    g_j = c sum_i x_ij cg_i, h_j = c sum_i x_ij^2 ch_i (f64 pairs, or f32 pairs
+//                    in mixed precision).  One 8/16-byte gather per nonzero.
+//   delta f64[n]     d^T x_i of the current bundle; zero outside the bundle step
+//   touched u32[ceil(n/32)]  bit i set when row i received a d_j x_ij != 0 this bundle
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pcdn {
+
+constexpr int kWarp = 32;
+constexpr int kChunk = 2048;       // max nonzeros of one column work item
+constexpr int kMaxK = 8;           // max step sizes per line-search pass
+constexpr int kWalkThreads = 256;  // threads per walker block
+constexpr int kWalkWarps = kWalkThreads / kWarp;
+constexpr int kListCap = 1024;     // touched rows listed per warp per 32 bitmap words
+
+constexpr int kErrTimeout = 1;
+constexpr int kErrNumeric = 2;
+
+// One column work item: nonzeros [start, start+len) of the feature at permutation position pos,
+// chunk `chunk` of `nch` chunks of that column.
+struct Item {
+  int64_t start;
+  int32_t len;
+  int32_t pos;
+  int32_t nch;
+  int32_t chunk;
+};
+
+template <int PREC> struct RecT;
+template <> struct __align__(16) RecT<0> { double cg, ch; };
+template <> struct __align__(8) RecT<1> { float cg, ch; };
+
+// Decision of a line-search pass, written by the last block to arrive.
+enum : int32_t { kDecAccept = 0, kDecContinue = 1, kDecCap = 2 };
+struct Decision {
+  int32_t state;
+  int32_t q;      // accepted q (accept), next q0 (continue), q_max (cap)
+  double alpha;
+  double Delta;
+  double dF;
+};
+
+// Per-block partial record: [0] sum g d, [1] sum h d^2, [2] sum |w+d|-|w|,
+// [3, 3+K) sum |w + a_q d| - |w|, [3+K, 3+2K) line-search sums, [3+2K] touched rows
+constexpr int kPartStride = 3 + 2 * kMaxK + 1;
+
+struct WalkParams {
+  // problem
+  int64_t n, m;
+  const int64_t* col_ptr;
+  const int32_t* row_idx;
+  const float* val;
+  const int8_t* y;
+  double c;
+  // state
+  double* w;
+  double* mq;
+  void* rec;
+  double* delta;
+  uint32_t* touched;
+  int64_t nwords;
+  // partition of this walk
+  const int32_t* perm;      // position -> feature
+  const Item* items;        // work items in position order
+  const int64_t* item_ptr;  // [npos+1] first item of each position
+  int64_t npos;             // number of positions (m for a solve, P for a single bundle)
+  int32_t P;
+  int64_t t_begin, t_end;   // bundles [t_begin, t_end) of this launch
+  // bundle-local scratch, indexed by position within the bundle
+  double* gk;
+  double* hk;
+  double* dk;
+  double* part;             // [2 * items] partial (g, h) of chunks of split columns
+  uint32_t* col_cnt;        // [P] arrivals per split column (reset by the finaliser)
+  uint32_t* col_ready;      // [P] stamp of the bundle whose d is published
+  uint32_t stamp_base;      // stamps of this launch are stamp_base + t + 1
+  uint32_t* anynz;          // [3] any nonzero direction in the bundle, by bundle index mod 3
+  // reductions and barriers
+  double* cta_part;         // [gridDim.x * kPartStride]
+  Decision* decision;
+  uint32_t* bar_count;
+  uint32_t* bar_gen;
+  uint32_t spin_limit;
+  // Armijo
+  double sigma, beta, gamma, nu;
+  int32_t q_max, K;
+  // outputs
+  int32_t* tr_q;            // [t_end] per-bundle records (indexed by bundle)
+  double* tr_alpha;
+  double* tr_Delta;
+  double* tr_dF;
+  unsigned long long* counters;  // [8]: ls_steps, cap_hits, passes, nnz, rows, bundles, coord_updates, nonzero-d bundles
+  int* err;
+};
+
+// ---------------------------------------------------------------- memory-order helpers
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u32(uint32_t* p, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void red_release_add_u32(uint32_t* p, uint32_t v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t atom_acqrel_add_u32(uint32_t* p, uint32_t v) {
+  uint32_t old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ int ld_volatile_int(const int* p) { return *(const volatile int*)p; }
+
+__device__ __forceinline__ void red_add_f64(double* p, double v) {
+  asm volatile("red.global.add.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+}
+__device__ __forceinline__ void red_or_u32(uint32_t* p, uint32_t v) {
+  asm volatile("red.global.or.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Streaming loads of X (ld.global.cs: read about once per bundle step, so evicted first and the
+// per-sample vectors keep their L2 lines).
+__device__ __forceinline__ int32_t ld_stream_i32(const int32_t* p) { return __ldcs(p); }
+__device__ __forceinline__ float ld_stream_f32(const float* p) { return __ldcs(p); }
+
+// ---------------------------------------------------------------- warp reductions (fixed tree)
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ int warp_sum_int(int v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------- direction (Eq. 4 / Eq. 5)
+// argmin_d g d + h d^2/2 + |w + d|; Eq. 5's branch conditions read with the +/-1 terms.
+__device__ __forceinline__ double newton_direction(double g, double h, double w) {
+  if (g + 1.0 <= h * w) return -(g + 1.0) / h;
+  if (g - 1.0 >= h * w) return -(g - 1.0) / h;
+  return -w;
+}
+
+// ---------------------------------------------------------------- per-sample coefficients
+// Logistic (Eq. 11): with E = e^{z}, s = 1/(1+E), p = E/(1+E):
+//   (tau(y z) - 1) y = -s (y = +1) or p (y = -1);  tau (1 - tau) = p s.
+// L2-SVM (Appendix A, proof of Lemma 1(b)): b = 1 - y z; cg = -2 y max(b, 0), ch = 2 [b > 0].
+template <int LOSS, int PREC> struct RowCoef;
+
+template <> struct RowCoef<0, 0> {
+  static __device__ __forceinline__ RecT<0> make(double E, int y) {
+    double s = 1.0 / (1.0 + E);
+    double p = E * s;
+    RecT<0> r;
+    r.cg = y > 0 ? -s : p;
+    r.ch = p * s;
+    return r;
+  }
+};
+template <> struct RowCoef<0, 1> {
+  static __device__ __forceinline__ RecT<1> make(double E, int y) {
+    float e = (float)E;
+    float p, s;
+    if (e <= 1.0f) {
+      s = 1.0f / (1.0f + e);
+      p = e * s;
+    } else {
+      float r = 1.0f / e;  // e may be +inf when E > FLT_MAX: r = 0, p = 1, s = 0
+      p = 1.0f / (1.0f + r);
+      s = r * p;
+    }
+    RecT<1> o;
+    o.cg = y > 0 ? -s : p;
+    o.ch = p * s;
+    return o;
+  }
+};
+template <> struct RowCoef<1, 0> {
+  static __device__ __forceinline__ RecT<0> make(double b, int y) {
+    RecT<0> r;
+    r.cg = b > 0.0 ? -2.0 * (double)y * b : 0.0;
+    r.ch = b > 0.0 ? 2.0 : 0.0;
+    return r;
+  }
+};
+template <> struct RowCoef<1, 1> {
+  static __device__ __forceinline__ RecT<1> make(double b, int y) {
+    RecT<1> r;
+    r.cg = b > 0.0 ? (float)(-2.0 * (double)y * b) : 0.0f;
+    r.ch = b > 0.0 ? 2.0f : 0.0f;
+    return r;
+  }
+};
+
+// Maintained quantity is usable (finite, and for the logistic loss |w^T x| <= 700).
+template <int LOSS>
+__device__ __forceinline__ bool mq_ok(double v) {
+  if (LOSS == 0) return v > 1e-304 && v < 1e304;
+  return isfinite(v);
+}
+
+// ---------------------------------------------------------------- line-search row terms
+// Mixed precision, logistic: the loss change of a row splits into a first-order part (summed
+// exactly as alpha * g^T d over the bundle) and the remainder
+//   R(v; a) = log(1 + a (e^v - 1)) - a v >= 0,  a = min(p, s) in [0, 1/2], v = +/- alpha d^T x_i,
+// the cumulant generating function of a Bernoulli(a) variable minus its first cumulant.  For
+// |v| <= 1/8 it is summed as the cumulant series up to order 7 (truncation below 1e-9 relative);
+// beyond, evaluated directly (cancellation at most a factor 32).
+__device__ __forceinline__ float lr_remainder(float a, float v) {
+  if (a <= 0.0f) return 0.0f;
+  float av = fabsf(v);
+  if (av <= 0.125f) {
+    float b = 1.0f - a, ab = a * b, t = b - a;
+    float k2 = ab, k3 = ab * t, k4 = ab * (1.0f - 6.0f * ab), k5 = ab * t * (1.0f - 12.0f * ab);
+    float k6 = ab * (1.0f - 30.0f * ab + 120.0f * ab * ab);
+    float k7 = ab * t * (1.0f - 60.0f * ab + 360.0f * ab * ab);
+    float s = k6 * (1.0f / 720.0f) + v * (k7 * (1.0f / 5040.0f));
+    s = k5 * (1.0f / 120.0f) + v * s;
+    s = k4 * (1.0f / 24.0f) + v * s;
+    s = k3 * (1.0f / 6.0f) + v * s;
+    s = k2 * 0.5f + v * s;
+    return v * v * s;
+  }
+  float r;
+  if (v > 20.0f) {
+    // 1 + a (e^v - 1) = a e^v (1 + (1 - a) e^{-v} / a)
+    r = v + logf(a) + log1pf((1.0f - a) * expf(-v) / a) - a * v;
+  } else {
+    r = log1pf(a * expm1f(v)) - a * v;
+  }
+  return fmaxf(r, 0.0f);
+}
+
+// Mixed precision, L2-SVM: remainder of max(0, b - v)^2 - max(0, b)^2 after its first-order
+// part 2 max(b, 0) v (summed exactly as alpha g^T d / c).  v = alpha y_i d^T x_i.  The case
+// split compares b with v: FP32 decides unless the rounded values tie, then FP64.
+__device__ __forceinline__ float svm_remainder(double b, double v) {
+  float bf = (float)b, vf = (float)v;
+  bool b_pos = b > 0.0;
+  bool bn_pos = (bf != vf) ? (bf > vf) : (b > v);
+  if (b_pos) return bn_pos ? vf * vf : bf * (2.0f * vf - bf);
+  if (bn_pos) {
+    float t = (float)(b - v);
+    return t * t;
+  }
+  return 0.0f;
+}
+
+__device__ __forceinline__ void kahan_add(float& s, float& comp, float x) {
+  float yv = x - comp;
+  float t = s + yv;
+  comp = (t - s) - yv;
+  s = t;
+}
+
+}  // namespace pcdn

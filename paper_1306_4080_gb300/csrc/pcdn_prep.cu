@@ -1,0 +1,578 @@
+// Preparation, refresh and reduction kernels of the GB300 PCDN solver.
+//
+//   partition of an outer iteration (Eq. 8, Algorithm 3): per-feature splitmix64 keys
+//     (Steele, Lea, Flood 2014) sorted by a stable LSD radix sort, ties by feature index;
+//   column work items: a feature's nonzeros cut into chunks of at most kChunk for the walker;
+//   row-major mirror of X: stable radix sort of the CSC entries by row (columns stay ascending
+//     within each row), so z = Xw sums every row in column order;
+//   refresh: z = Xw by rows, maintained quantity and per-sample coefficients from z;
+//   KKT: fresh gradient of every feature and the l1 norm of the minimum-norm subgradient;
+//   objective: Eq. 1 from z.
+// Every reduction sums in a fixed order (lanes in a tree, warps and blocks in index order).
+
+#include "pcdn_prep.h"
+
+namespace pcdn {
+
+namespace {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;
+constexpr int64_t kScanTile = kScanThreads * kScanItems;  // 4096
+
+constexpr int kSortThreads = 256;
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kSortRounds = 16;
+constexpr int64_t kSortTile = kSortThreads * kSortRounds;  // 4096
+
+constexpr int kRedThreads = 256;
+
+inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+inline cudaError_t post(int64_t* launches) {
+  if (launches) ++*launches;
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------ scan
+__global__ void __launch_bounds__(kScanThreads) scan_tile_kernel(const int64_t* in, int64_t* out, int64_t n,
+                                                                 int64_t* block_sums) {
+  __shared__ int64_t warp_tot[kScanThreads / 32];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)tid * kScanItems;
+  int64_t v[kScanItems];
+  int64_t run = 0;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    const int64_t e = base + i;
+    const int64_t x = e < n ? in[e] : 0;
+    v[i] = run;
+    run += x;
+  }
+  // inclusive scan of thread totals in the warp
+  int64_t incl = run;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int64_t t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) warp_tot[wid] = incl;
+  __syncthreads();
+  if (tid < 32) {
+    int64_t wt = (tid < kScanThreads / 32) ? warp_tot[tid] : 0;
+    int64_t wi = wt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int64_t t = __shfl_up_sync(0xffffffffu, wi, o);
+      if (tid >= o) wi += t;
+    }
+    if (tid < kScanThreads / 32) warp_tot[tid] = wi - wt;  // exclusive warp offsets
+    if (tid == kScanThreads / 32 - 1 && block_sums) block_sums[blockIdx.x] = wi;
+  }
+  __syncthreads();
+  const int64_t off = warp_tot[wid] + incl - run;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    const int64_t e = base + i;
+    if (e < n) out[e] = v[i] + off;
+  }
+}
+
+__global__ void scan_add_kernel(int64_t* out, int64_t n, const int64_t* block_off) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) out[e] += block_off[e / kScanTile];
+}
+
+// ------------------------------------------------------------------------------------ radix sort
+template <typename K>
+__global__ void __launch_bounds__(kSortThreads) sort_hist_kernel(const K* keys, int64_t n, int shift, int64_t nblocks,
+                                                                 int64_t* hist) {
+  __shared__ uint32_t cnt[256];
+  const int tid = threadIdx.x;
+  cnt[tid] = 0;
+  __syncthreads();
+  const int64_t b0 = (int64_t)blockIdx.x * kSortTile;
+  for (int r = 0; r < kSortRounds; ++r) {
+    const int64_t e = b0 + (int64_t)r * kSortThreads + tid;
+    if (e < n) atomicAdd(&cnt[(uint32_t)(keys[e] >> shift) & 255u], 1u);
+  }
+  __syncthreads();
+  hist[(int64_t)tid * nblocks + blockIdx.x] = cnt[tid];
+}
+
+template <typename K>
+__global__ void __launch_bounds__(kSortThreads) sort_scatter_kernel(const K* kin, const int32_t* vin, K* kout,
+                                                                    int32_t* vout, int64_t n, int shift,
+                                                                    int64_t nblocks, const int64_t* offs) {
+  __shared__ int64_t base[256];
+  __shared__ uint32_t running[256];
+  __shared__ uint32_t wcnt[kSortWarps][256];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  base[tid] = offs[(int64_t)tid * nblocks + blockIdx.x];
+  running[tid] = 0;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  const int64_t b0 = (int64_t)blockIdx.x * kSortTile;
+  for (int r = 0; r < kSortRounds; ++r) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) wcnt[wid][lane * 8 + i] = 0;
+    __syncthreads();
+    const int64_t e = b0 + (int64_t)r * kSortThreads + tid;
+    const bool valid = e < n;
+    K key = 0;
+    int32_t val = 0;
+    uint32_t digit = 256u;
+    if (valid) {
+      key = kin[e];
+      val = vin[e];
+      digit = (uint32_t)(key >> shift) & 255u;
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, digit);
+    const int rank = __popc(peers & lt_mask);
+    if (valid && rank == 0) wcnt[wid][digit] = (uint32_t)__popc(peers);
+    __syncthreads();
+    {
+      uint32_t acc = running[tid];
+#pragma unroll
+      for (int wv = 0; wv < kSortWarps; ++wv) {
+        const uint32_t c = wcnt[wv][tid];
+        wcnt[wv][tid] = acc;
+        acc += c;
+      }
+      running[tid] = acc;
+    }
+    __syncthreads();
+    if (valid) {
+      const int64_t pos = base[digit] + (int64_t)wcnt[wid][digit] + rank;
+      kout[pos] = key;
+      vout[pos] = val;
+    }
+    __syncthreads();
+  }
+}
+
+template <typename K>
+cudaError_t radix_sort_impl(K* k0, int32_t* v0, K* k1, int32_t* v1, int64_t n, int key_bits, int64_t* hist,
+                            int64_t* ws, K** k_out, int32_t** v_out, cudaStream_t s, int64_t* launches) {
+  K* ka = k0;
+  K* kb = k1;
+  int32_t* va = v0;
+  int32_t* vb = v1;
+  if (n > 1) {
+    const int64_t nblocks = cdiv(n, kSortTile);
+    for (int shift = 0; shift < key_bits; shift += 8) {
+      sort_hist_kernel<K><<<(unsigned)nblocks, kSortThreads, 0, s>>>(ka, n, shift, nblocks, hist);
+      cudaError_t e = post(launches);
+      if (e != cudaSuccess) return e;
+      e = scan_exclusive(hist, hist, 256 * nblocks, ws, s, launches);
+      if (e != cudaSuccess) return e;
+      sort_scatter_kernel<K><<<(unsigned)nblocks, kSortThreads, 0, s>>>(ka, va, kb, vb, n, shift, nblocks, hist);
+      e = post(launches);
+      if (e != cudaSuccess) return e;
+      K* tk = ka; ka = kb; kb = tk;
+      int32_t* tv = va; va = vb; vb = tv;
+    }
+  }
+  *k_out = ka;
+  *v_out = va;
+  return cudaSuccess;
+}
+
+// ------------------------------------------------------------------------------------ partition
+__device__ __forceinline__ uint64_t sm64_mix(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+__global__ void perm_keys_kernel(uint64_t seed, uint64_t epoch, int64_t m, uint64_t* keys, int32_t* vals) {
+  const uint64_t gamma = 0x9E3779B97F4A7C15ULL;
+  // state of the epoch's stream: first output of the stream started at seed ^ epoch * C
+  const uint64_t s_epoch = sm64_mix((seed ^ (epoch * 0xD1B54A32D192ED03ULL)) + gamma);
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
+    keys[j] = sm64_mix(s_epoch + (uint64_t)(j + 1) * gamma);
+    vals[j] = (int32_t)j;
+  }
+}
+
+// ------------------------------------------------------------------------------------ work items
+__global__ void item_count_kernel(const int32_t* perm, int64_t npos, const int64_t* col_ptr, int64_t* cnt) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k <= npos; k += (int64_t)gridDim.x * blockDim.x) {
+    if (k == npos) { cnt[k] = 0; continue; }
+    const int32_t j = perm[k];
+    const int64_t len = col_ptr[j + 1] - col_ptr[j];
+    cnt[k] = len == 0 ? 1 : (len + kChunk - 1) / kChunk;
+  }
+}
+
+__global__ void item_fill_kernel(const int32_t* perm, int64_t npos, const int64_t* col_ptr, const int64_t* item_ptr,
+                                 Item* items) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < npos; k += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t j = perm[k];
+    const int64_t a = col_ptr[j], len = col_ptr[j + 1] - a;
+    const int64_t first = item_ptr[k];
+    const int32_t nch = (int32_t)(item_ptr[k + 1] - first);
+    for (int32_t c = 0; c < nch; ++c) {
+      Item it;
+      it.start = a + (int64_t)c * kChunk;
+      const int64_t rem = len - (int64_t)c * kChunk;
+      it.len = (int32_t)(rem < kChunk ? (rem > 0 ? rem : 0) : kChunk);
+      it.pos = (int32_t)k;
+      it.nch = nch;
+      it.chunk = c;
+      items[first + c] = it;
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------ mirror
+__global__ void entry_col_kernel(const int64_t* col_ptr, int64_t m, int32_t* entry_col) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
+  for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; j < m; j += warps) {
+    for (int64_t e = col_ptr[j] + lane; e < col_ptr[j + 1]; e += 32) entry_col[e] = (int32_t)j;
+  }
+}
+
+__global__ void row_count_kernel(const int32_t* row_idx, int64_t nnz, unsigned long long* counts) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(counts + row_idx[e], 1ull);
+}
+
+__global__ void iota_kernel(int32_t* v, int64_t n) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    v[e] = (int32_t)e;
+}
+
+__global__ void copy_keys_kernel(const int32_t* src, uint32_t* dst, int64_t n) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    dst[e] = (uint32_t)src[e];
+}
+
+__global__ void gather_csr_kernel(const int32_t* order, const int32_t* entry_col, const float* val, int64_t nnz,
+                                  int32_t* col_idx, float* rval) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t src = order[e];
+    col_idx[e] = entry_col[src];
+    rval[e] = val[src];
+  }
+}
+
+// ------------------------------------------------------------------------------------ validation
+__global__ void validate_kernel(const int64_t* col_ptr, const int32_t* row_idx, const float* val, const int8_t* y,
+                                int64_t n, int64_t m, int64_t nnz, int* flag) {
+  const int64_t tid0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  if (tid0 == 0 && (col_ptr[0] != 0 || col_ptr[m] != nnz)) atomicOr(flag, 1);
+  for (int64_t j = tid0; j < m; j += stride) {
+    const int64_t a = col_ptr[j], b = col_ptr[j + 1];
+    if (b < a || a < 0 || b > nnz) { atomicOr(flag, 1); continue; }
+  }
+  for (int64_t e = tid0; e < nnz; e += stride) {
+    const int32_t r = row_idx[e];
+    if (r < 0 || r >= n || !isfinite(val[e])) atomicOr(flag, 2);
+  }
+  for (int64_t i = tid0; i < n; i += stride)
+    if (y[i] != 1 && y[i] != -1) atomicOr(flag, 4);
+}
+
+// rows strictly ascending within every column (run after the column pointers passed)
+__global__ void validate_order_kernel(const int64_t* col_ptr, const int32_t* row_idx, int64_t m, int* flag) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
+  for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; j < m; j += warps) {
+    for (int64_t e = col_ptr[j] + 1 + lane; e < col_ptr[j + 1]; e += 32)
+      if (row_idx[e] <= row_idx[e - 1]) atomicOr(flag, 8);
+  }
+}
+
+// ------------------------------------------------------------------------------------ refresh
+__device__ __forceinline__ double row_loss(int loss, double z, int y) {
+  const double yz = (double)y * z;
+  if (loss == 0) return yz > 0 ? log1p(exp(-yz)) : (-yz + log1p(exp(yz)));
+  const double b = 1.0 - yz;
+  return b > 0 ? b * b : 0.0;
+}
+
+template <int LOSS, int PREC>
+__global__ void __launch_bounds__(kRedThreads) refresh_kernel(const int64_t* row_ptr, const int32_t* col_idx,
+                                                              const float* rval, const int8_t* y, const double* w,
+                                                              int64_t n, double* mq, void* rec, int write_state,
+                                                              double* loss_part, int* err) {
+  __shared__ double wsum[kRedThreads / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t warps = (int64_t)gridDim.x * (kRedThreads / 32);
+  double lsum = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * (kRedThreads / 32) + wid; i < n; i += warps) {
+    double z = 0.0;
+    for (int64_t e = row_ptr[i] + lane; e < row_ptr[i + 1]; e += 32) {
+      const double wj = w[col_idx[e]];
+      if (wj != 0.0) z = fma((double)rval[e], wj, z);
+    }
+    z = warp_sum(z);
+    if (lane == 0) {
+      const int yi = y[i];
+      if (loss_part) lsum += row_loss(LOSS, z, yi);
+      if (write_state) {
+        double v;
+        if (LOSS == 0) {
+          if (fabs(z) > 700.0) atomicOr(err, kErrNumeric);
+          v = exp(z);
+        } else {
+          v = 1.0 - (double)yi * z;
+        }
+        mq[i] = v;
+        ((RecT<PREC>*)rec)[i] = RowCoef<LOSS, PREC>::make(v, yi);
+      }
+    }
+  }
+  if (loss_part) {
+    if (lane == 0) wsum[wid] = lsum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      for (int k = 0; k < kRedThreads / 32; ++k) s += wsum[k];
+      loss_part[blockIdx.x] = s;
+    }
+  }
+}
+
+template <int LOSS, int PREC>
+__global__ void rec_from_mq_kernel(const double* mq, const int8_t* y, int64_t n, void* rec) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    ((RecT<PREC>*)rec)[i] = RowCoef<LOSS, PREC>::make(mq[i], y[i]);
+}
+
+// ------------------------------------------------------------------------------------ KKT
+template <int PREC>
+__global__ void __launch_bounds__(kRedThreads) kkt_item_kernel(const Item* items, int64_t n_items, const int32_t* row_idx,
+                                                               const float* val, const void* recp, double* gpart) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t warps = (int64_t)gridDim.x * (kRedThreads / 32);
+  const RecT<PREC>* rec = (const RecT<PREC>*)recp;
+  for (int64_t i = (int64_t)blockIdx.x * (kRedThreads / 32) + wid; i < n_items; i += warps) {
+    const Item it = items[i];
+    double g;
+    if constexpr (PREC == 0) {
+      double acc = 0.0;
+      for (int64_t e = it.start + lane; e < it.start + it.len; e += 32) acc = fma((double)val[e], rec[row_idx[e]].cg, acc);
+      g = warp_sum(acc);
+    } else {
+      float acc = 0.0f;
+      for (int64_t e = it.start + lane; e < it.start + it.len; e += 32) acc = fmaf(val[e], rec[row_idx[e]].cg, acc);
+      g = warp_sum((double)acc);
+    }
+    if (lane == 0) gpart[i] = g;
+  }
+}
+
+__global__ void __launch_bounds__(kRedThreads) kkt_col_kernel(const int64_t* item_ptr, const int32_t* perm, int64_t npos,
+                                                              const double* gpart, const double* w, double c,
+                                                              double* block_part) {
+  __shared__ double red[kRedThreads];
+  double acc = 0.0;
+  for (int64_t k = (int64_t)blockIdx.x * kRedThreads + threadIdx.x; k < npos; k += (int64_t)gridDim.x * kRedThreads) {
+    double g = 0.0;
+    for (int64_t i = item_ptr[k]; i < item_ptr[k + 1]; ++i) g += gpart[i];
+    g *= c;
+    const double wj = w[perm[k]];
+    double v;
+    if (wj > 0) v = g + 1.0;
+    else if (wj < 0) v = g - 1.0;
+    else v = fabs(g) > 1.0 ? (g > 0 ? g - 1.0 : g + 1.0) : 0.0;
+    acc += fabs(v);
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = kRedThreads / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) block_part[blockIdx.x] = red[0];
+}
+
+__global__ void abs_sum_kernel(const double* w, int64_t m, double* block_part) {
+  __shared__ double red[kRedThreads];
+  double acc = 0.0;
+  for (int64_t j = (int64_t)blockIdx.x * kRedThreads + threadIdx.x; j < m; j += (int64_t)gridDim.x * kRedThreads)
+    acc += fabs(w[j]);
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = kRedThreads / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) block_part[blockIdx.x] = red[0];
+}
+
+// out = scale * sum(a[0..na)) + sum(b[0..nb)), each sum in index order by one thread of a tree
+__global__ void finish_sum_kernel(const double* a, int na, double scale, const double* b, int nb, double* out) {
+  __shared__ double red[kRedThreads];
+  double sa = 0.0, sb = 0.0;
+  for (int i = threadIdx.x; i < na; i += kRedThreads) sa += a[i];
+  for (int i = threadIdx.x; i < nb; i += kRedThreads) sb += b[i];
+  red[threadIdx.x] = sa;
+  __syncthreads();
+  for (int o = kRedThreads / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  const double ta = red[0];
+  __syncthreads();
+  red[threadIdx.x] = sb;
+  __syncthreads();
+  for (int o = kRedThreads / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = scale * ta + red[0];
+}
+
+inline unsigned grid_for(int64_t n, int threads, int64_t cap = 4096) {
+  int64_t g = cdiv(n > 0 ? n : 1, threads);
+  if (g > cap) g = cap;
+  return (unsigned)g;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------- host API
+int64_t scan_workspace_elems(int64_t n) {
+  int64_t tot = 0;
+  while (n > kScanTile) {
+    n = cdiv(n, kScanTile);
+    tot += n + 8;
+  }
+  return tot + 8;
+}
+
+cudaError_t scan_exclusive(const int64_t* in, int64_t* out, int64_t n, int64_t* ws, cudaStream_t s, int64_t* launches) {
+  if (n <= 0) return cudaSuccess;
+  const int64_t nb = cdiv(n, kScanTile);
+  if (nb == 1) {
+    scan_tile_kernel<<<1, kScanThreads, 0, s>>>(in, out, n, nullptr);
+    return post(launches);
+  }
+  int64_t* sums = ws;
+  scan_tile_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, sums);
+  cudaError_t e = post(launches);
+  if (e != cudaSuccess) return e;
+  e = scan_exclusive(sums, sums, nb, ws + nb + 8, s, launches);
+  if (e != cudaSuccess) return e;
+  scan_add_kernel<<<(unsigned)cdiv(n, 256), 256, 0, s>>>(out, n, sums);
+  return post(launches);
+}
+
+int64_t radix_hist_elems(int64_t n) { return 256 * cdiv(n > 0 ? n : 1, kSortTile); }
+
+cudaError_t radix_sort_u64(uint64_t* k0, int32_t* v0, uint64_t* k1, int32_t* v1, int64_t n, int key_bits,
+                           int64_t* hist, int64_t* ws, uint64_t** k_out, int32_t** v_out, cudaStream_t s,
+                           int64_t* launches) {
+  return radix_sort_impl<uint64_t>(k0, v0, k1, v1, n, key_bits, hist, ws, k_out, v_out, s, launches);
+}
+cudaError_t radix_sort_u32(uint32_t* k0, int32_t* v0, uint32_t* k1, int32_t* v1, int64_t n, int key_bits,
+                           int64_t* hist, int64_t* ws, uint32_t** k_out, int32_t** v_out, cudaStream_t s,
+                           int64_t* launches) {
+  return radix_sort_impl<uint32_t>(k0, v0, k1, v1, n, key_bits, hist, ws, k_out, v_out, s, launches);
+}
+
+cudaError_t perm_keys(uint64_t seed, int64_t epoch, int64_t m, uint64_t* keys, int32_t* vals, cudaStream_t s,
+                      int64_t* launches) {
+  perm_keys_kernel<<<grid_for(m, 256), 256, 0, s>>>(seed, (uint64_t)epoch, m, keys, vals);
+  return post(launches);
+}
+
+cudaError_t build_items(const int32_t* perm, int64_t npos, const int64_t* col_ptr, int64_t* cnt_ws, int64_t* item_ptr,
+                        Item* items, int64_t* scan_ws, cudaStream_t s, int64_t* launches) {
+  item_count_kernel<<<grid_for(npos + 1, 256), 256, 0, s>>>(perm, npos, col_ptr, cnt_ws);
+  cudaError_t e = post(launches);
+  if (e != cudaSuccess) return e;
+  e = scan_exclusive(cnt_ws, item_ptr, npos + 1, scan_ws, s, launches);
+  if (e != cudaSuccess) return e;
+  item_fill_kernel<<<grid_for(npos, 256), 256, 0, s>>>(perm, npos, col_ptr, item_ptr, items);
+  return post(launches);
+}
+
+cudaError_t entry_columns(const int64_t* col_ptr, int64_t m, int32_t* entry_col, cudaStream_t s, int64_t* launches) {
+  entry_col_kernel<<<grid_for(m * 32, 256), 256, 0, s>>>(col_ptr, m, entry_col);
+  return post(launches);
+}
+
+cudaError_t row_counts(const int32_t* row_idx, int64_t nnz, int64_t* counts, cudaStream_t s, int64_t* launches) {
+  row_count_kernel<<<grid_for(nnz, 256), 256, 0, s>>>(row_idx, nnz, (unsigned long long*)counts);
+  return post(launches);
+}
+
+cudaError_t iota_i32(int32_t* v, int64_t n, cudaStream_t s, int64_t* launches) {
+  iota_kernel<<<grid_for(n, 256), 256, 0, s>>>(v, n);
+  return post(launches);
+}
+
+cudaError_t copy_keys_u32(const int32_t* src, uint32_t* dst, int64_t n, cudaStream_t s, int64_t* launches) {
+  copy_keys_kernel<<<grid_for(n, 256), 256, 0, s>>>(src, dst, n);
+  return post(launches);
+}
+
+cudaError_t gather_csr(const int32_t* order, const int32_t* entry_col, const float* val, int64_t nnz, int32_t* col_idx,
+                       float* rval, cudaStream_t s, int64_t* launches) {
+  gather_csr_kernel<<<grid_for(nnz, 256), 256, 0, s>>>(order, entry_col, val, nnz, col_idx, rval);
+  return post(launches);
+}
+
+cudaError_t validate_device(const int64_t* col_ptr, const int32_t* row_idx, const float* val, const int8_t* y, int64_t n,
+                            int64_t m, int64_t nnz, int* flag, cudaStream_t s, int64_t* launches) {
+  validate_kernel<<<grid_for(nnz > n ? nnz : n, 256), 256, 0, s>>>(col_ptr, row_idx, val, y, n, m, nnz, flag);
+  cudaError_t e = post(launches);
+  if (e != cudaSuccess) return e;
+  validate_order_kernel<<<grid_for(m * 32, 256), 256, 0, s>>>(col_ptr, row_idx, m, flag);
+  return post(launches);
+}
+
+cudaError_t refresh(int loss, int prec, const int64_t* row_ptr, const int32_t* col_idx, const float* rval,
+                    const int8_t* y, const double* w, int64_t n, double* mq, void* rec, bool write_state,
+                    double* loss_part, int grid, int* err, cudaStream_t s, int64_t* launches) {
+  const int ws = write_state ? 1 : 0;
+  if (loss == 0 && prec == 0)
+    refresh_kernel<0, 0><<<grid, kRedThreads, 0, s>>>(row_ptr, col_idx, rval, y, w, n, mq, rec, ws, loss_part, err);
+  else if (loss == 0)
+    refresh_kernel<0, 1><<<grid, kRedThreads, 0, s>>>(row_ptr, col_idx, rval, y, w, n, mq, rec, ws, loss_part, err);
+  else if (prec == 0)
+    refresh_kernel<1, 0><<<grid, kRedThreads, 0, s>>>(row_ptr, col_idx, rval, y, w, n, mq, rec, ws, loss_part, err);
+  else
+    refresh_kernel<1, 1><<<grid, kRedThreads, 0, s>>>(row_ptr, col_idx, rval, y, w, n, mq, rec, ws, loss_part, err);
+  return post(launches);
+}
+
+cudaError_t rec_from_mq(int loss, int prec, const double* mq, const int8_t* y, int64_t n, void* rec, cudaStream_t s,
+                        int64_t* launches) {
+  const unsigned g = grid_for(n, 256);
+  if (loss == 0 && prec == 0) rec_from_mq_kernel<0, 0><<<g, 256, 0, s>>>(mq, y, n, rec);
+  else if (loss == 0) rec_from_mq_kernel<0, 1><<<g, 256, 0, s>>>(mq, y, n, rec);
+  else if (prec == 0) rec_from_mq_kernel<1, 0><<<g, 256, 0, s>>>(mq, y, n, rec);
+  else rec_from_mq_kernel<1, 1><<<g, 256, 0, s>>>(mq, y, n, rec);
+  return post(launches);
+}
+
+cudaError_t kkt_l1(int prec, const Item* items, int64_t n_items, const int64_t* item_ptr, const int32_t* perm,
+                   int64_t npos, const int32_t* row_idx, const float* val, const void* rec, const double* w, double c,
+                   double* gpart, double* block_part, int grid, double* out, cudaStream_t s, int64_t* launches) {
+  if (prec == 0) kkt_item_kernel<0><<<grid, kRedThreads, 0, s>>>(items, n_items, row_idx, val, rec, gpart);
+  else kkt_item_kernel<1><<<grid, kRedThreads, 0, s>>>(items, n_items, row_idx, val, rec, gpart);
+  cudaError_t e = post(launches);
+  if (e != cudaSuccess) return e;
+  kkt_col_kernel<<<grid, kRedThreads, 0, s>>>(item_ptr, perm, npos, gpart, w, c, block_part);
+  e = post(launches);
+  if (e != cudaSuccess) return e;
+  finish_sum_kernel<<<1, kRedThreads, 0, s>>>(block_part, grid, 1.0, nullptr, 0, out);
+  return post(launches);
+}
+
+cudaError_t objective_finish(const double* loss_part, int nb, const double* w, int64_t m, double c, double* block_part,
+                             int grid, double* out, cudaStream_t s, int64_t* launches) {
+  abs_sum_kernel<<<grid, kRedThreads, 0, s>>>(w, m, block_part);
+  cudaError_t e = post(launches);
+  if (e != cudaSuccess) return e;
+  finish_sum_kernel<<<1, kRedThreads, 0, s>>>(loss_part, nb, c, block_part, grid, out);
+  return post(launches);
+}
+
+}  // namespace pcdn

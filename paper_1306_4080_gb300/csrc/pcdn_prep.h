@@ -1,0 +1,68 @@
+// Host-side launchers of the preparation, refresh and reduction kernels (pcdn_prep.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pcdn_internal.cuh"
+
+namespace pcdn {
+
+// ---- scan --------------------------------------------------------------------------------
+// Exclusive prefix sum of n int64 values (in-place allowed).  Workspace from scan_workspace().
+int64_t scan_workspace_elems(int64_t n);
+cudaError_t scan_exclusive(const int64_t* in, int64_t* out, int64_t n, int64_t* ws, cudaStream_t s, int64_t* launches);
+
+// ---- stable LSD radix sort of (key, value) pairs, 8-bit digits ------------------------------
+// Sorts the low `key_bits` bits; result in (*k_out, *v_out), which point at either the input or
+// the alternate buffers.  hist must hold radix_hist_elems(n) int64; ws scan_workspace_elems(that).
+int64_t radix_hist_elems(int64_t n);
+cudaError_t radix_sort_u64(uint64_t* k0, int32_t* v0, uint64_t* k1, int32_t* v1, int64_t n, int key_bits,
+                           int64_t* hist, int64_t* ws, uint64_t** k_out, int32_t** v_out, cudaStream_t s,
+                           int64_t* launches);
+cudaError_t radix_sort_u32(uint32_t* k0, int32_t* v0, uint32_t* k1, int32_t* v1, int64_t n, int key_bits,
+                           int64_t* hist, int64_t* ws, uint32_t** k_out, int32_t** v_out, cudaStream_t s,
+                           int64_t* launches);
+
+// ---- partition of one outer iteration (Eq. 8) ------------------------------------------------
+// perm_keys: key_j = splitmix64 output j+1 of the stream of (seed, epoch); values j.
+cudaError_t perm_keys(uint64_t seed, int64_t epoch, int64_t m, uint64_t* keys, int32_t* vals, cudaStream_t s,
+                      int64_t* launches);
+
+// ---- column work items ------------------------------------------------------------------------
+// For positions [0, npos) of `perm`: item_ptr[npos+1] and items[] (chunks of <= kChunk nonzeros).
+cudaError_t build_items(const int32_t* perm, int64_t npos, const int64_t* col_ptr, int64_t* cnt_ws,
+                        int64_t* item_ptr, Item* items, int64_t* scan_ws, cudaStream_t s, int64_t* launches);
+
+// ---- row-major mirror -------------------------------------------------------------------------
+cudaError_t entry_columns(const int64_t* col_ptr, int64_t m, int32_t* entry_col, cudaStream_t s, int64_t* launches);
+cudaError_t row_counts(const int32_t* row_idx, int64_t nnz, int64_t* counts, cudaStream_t s, int64_t* launches);
+cudaError_t iota_i32(int32_t* v, int64_t n, cudaStream_t s, int64_t* launches);
+cudaError_t copy_keys_u32(const int32_t* src, uint32_t* dst, int64_t n, cudaStream_t s, int64_t* launches);
+cudaError_t gather_csr(const int32_t* order, const int32_t* entry_col, const float* val, int64_t nnz,
+                       int32_t* col_idx, float* rval, cudaStream_t s, int64_t* launches);
+
+// ---- validation (device-resident input) -------------------------------------------------------
+cudaError_t validate_device(const int64_t* col_ptr, const int32_t* row_idx, const float* val, const int8_t* y,
+                            int64_t n, int64_t m, int64_t nnz, int* flag, cudaStream_t s, int64_t* launches);
+
+// ---- maintained quantities --------------------------------------------------------------------
+// z = Xw by rows; mq and rec from z (write_state), optional per-block loss partial sums.
+cudaError_t refresh(int loss, int prec, const int64_t* row_ptr, const int32_t* col_idx, const float* rval,
+                    const int8_t* y, const double* w, int64_t n, double* mq, void* rec, bool write_state,
+                    double* loss_part, int grid, int* err, cudaStream_t s, int64_t* launches);
+// rec from the current mq (precision switch without recomputing z).
+cudaError_t rec_from_mq(int loss, int prec, const double* mq, const int8_t* y, int64_t n, void* rec, cudaStream_t s,
+                        int64_t* launches);
+
+// ---- reductions -------------------------------------------------------------------------------
+// Minimum-norm subgradient l1 norm from the coefficients in rec, over work items of all columns.
+cudaError_t kkt_l1(int prec, const Item* items, int64_t n_items, const int64_t* item_ptr, const int32_t* perm,
+                   int64_t npos, const int32_t* row_idx, const float* val, const void* rec, const double* w,
+                   double c, double* gpart, double* block_part, int grid, double* out, cudaStream_t s,
+                   int64_t* launches);
+// out = c * sum(loss_part[0..nb)) + sum_j |w_j|
+cudaError_t objective_finish(const double* loss_part, int nb, const double* w, int64_t m, double c,
+                             double* block_part, int grid, double* out, cudaStream_t s, int64_t* launches);
+
+}  // namespace pcdn

@@ -1,0 +1,112 @@
+"""The C-ABI library: loads, exports every function include/pcdn.h declares, rejects bad input on
+the host (no GPU needed for any of these)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def pk():
+    from paper_1306_4080_gb300 import build
+    build.build()
+    import paper_1306_4080_gb300 as m
+    m.load()
+    return m
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "pcdn.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(pcdn_[a-z_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(pk):
+    names = declared_functions()
+    assert len(names) >= 13
+    out = subprocess.run(["nm", "-D", "--defined-only", pk.LIB_PATH], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (pcdn_\w+)", out))
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    lib = ctypes.CDLL(pk.LIB_PATH)
+    for n in names:
+        assert hasattr(lib, n)
+    assert sorted(pk.SYMBOLS) == names
+
+
+def test_default_opts(pk):
+    o = pk.pcdn_default_opts()
+    assert (o.sigma, o.beta, o.gamma, o.nu) == (0.01, 0.5, 0.0, 1e-12)
+    assert o.q_max == 30 and o.max_epochs == 1000 and o.prec == 0 and o.refresh == 1
+
+
+def _good():
+    col_ptr = np.array([0, 2, 3, 3, 5], dtype=np.int64)
+    row_idx = np.array([0, 2, 1, 0, 2], dtype=np.int32)
+    val = np.array([1.0, 0.5, -2.0, 0.25, 1.0], dtype=np.float32)
+    y = np.array([1, -1, 1], dtype=np.int8)
+    return col_ptr, row_idx, val, y
+
+
+@pytest.mark.parametrize("case", ["col_ptr_start", "col_ptr_decreasing", "row_out_of_range", "rows_not_ascending",
+                                  "nan_value", "bad_label", "bad_C", "bad_loss"])
+def test_create_rejects_bad_input_on_host(pk, case):
+    col_ptr, row_idx, val, y = _good()
+    C, loss = 1.0, "logistic"
+    if case == "col_ptr_start":
+        col_ptr = col_ptr.copy(); col_ptr[0] = 1
+    elif case == "col_ptr_decreasing":
+        col_ptr = np.array([0, 3, 2, 3, 5], dtype=np.int64)
+    elif case == "row_out_of_range":
+        row_idx = row_idx.copy(); row_idx[1] = 3
+    elif case == "rows_not_ascending":
+        row_idx = np.array([2, 0, 1, 0, 2], dtype=np.int32)
+    elif case == "nan_value":
+        val = val.copy(); val[2] = np.nan
+    elif case == "bad_label":
+        y = np.array([1, 0, 1], dtype=np.int8)
+    elif case == "bad_C":
+        C = 0.0
+    elif case == "bad_loss":
+        loss = None
+    if case == "bad_loss":
+        lib = pk.load()
+        X = pk.pcdn_csc(3, 4, 5, col_ptr.ctypes.data, row_idx.ctypes.data, val.ctypes.data)
+        h = ctypes.c_void_p()
+        rc = lib.pcdn_create(ctypes.byref(X), y.ctypes.data, 1.0, 7, ctypes.byref(h))
+        assert rc == pk.PCDN_EINVAL and h.value is None
+        return
+    with pytest.raises(pk.PcdnError) as ei:
+        pk.pcdn_create(col_ptr, row_idx, val, y, C, loss)
+    assert ei.value.code == pk.PCDN_EINVAL
+    assert pk.pcdn_last_error()
+
+
+def test_null_arguments_are_errors(pk):
+    lib = pk.load()
+    assert lib.pcdn_solve(None, 1, 1e-3, 0, None, None, None, None) == pk.PCDN_EINVAL
+    assert lib.pcdn_set_w(None, None) == pk.PCDN_EINVAL
+    lib.pcdn_destroy(None)
+
+
+def test_no_device_is_reported(pk, has_cuda):
+    if has_cuda:
+        pytest.skip("a CUDA device is present")
+    col_ptr, row_idx, val, y = _good()
+    with pytest.raises(pk.PcdnError) as ei:
+        pk.pcdn_create(col_ptr, row_idx, val, y, 1.0, "logistic")
+    assert ei.value.code == pk.PCDN_ECUDA
+
+
+def test_product_path_does_not_import_the_oracle():
+    pkg = os.path.join(ROOT, "paper_1306_4080_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in txt and "from oracle" not in txt and "pcdn_oracle" not in txt, f

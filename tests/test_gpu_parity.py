@@ -1,0 +1,242 @@
+"""GPU path vs the FP64 oracle, through the C ABI, on identical seeded inputs and partitions.
+
+Tolerances (spec bar: per-bundle d and step size within 1e-5 relative, final objective
+within 1e-6 relative):
+  FP64 mode   g, h, d, Delta within 1e-9 of the bundle's largest magnitude; q and alpha equal;
+              dF within 1e-7 relative (different reduction order over up to 10^5 rows).
+  mixed mode  g, h, d within 1e-5 of the bundle's largest magnitude; q and alpha equal unless
+              the oracle's Armijo margin is within 1e-5 of the compared quantities.
+"""
+import numpy as np
+import pytest
+
+import datagen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pk():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1306_4080_gb300 import build
+    build.build()
+    import paper_1306_4080_gb300 as m
+    m.load()
+    return m
+
+
+_CACHE = {}
+
+
+def problem(name):
+    if name in _CACHE:
+        return _CACHE[name]
+    if name == "ragged_lr":
+        wl = datagen.Workload("ragged_lr", datagen.Spec(333, 1001, "uniform", density=0.02, values="halfnormal",
+                                                        wstar_nnz=20, flip_frac=0.05, seed=7), "logistic", 2.0, 100)
+    elif name == "ragged_svm":
+        wl = datagen.Workload("ragged_svm", datagen.Spec(4000, 3001, "zipf", row_mean=30.0, zipf_s=1.1,
+                                                         values="tfidf", wstar_nnz=40, flip_frac=0.05, seed=8),
+                              "l2svm", 1.0, 97)
+    else:
+        wl = datagen.workload(name)
+    p = datagen.generate(wl.spec)
+    _CACHE[name] = (wl, p)
+    return wl, p
+
+
+def rel_err(a, b):
+    scale = max(float(np.max(np.abs(b))) if np.size(b) else 0.0, 1e-300)
+    return float(np.max(np.abs(np.asarray(a) - np.asarray(b)))) / scale if np.size(b) else 0.0
+
+
+def margin_small(orc, w, ro, bundle, q_gpu, q_or, armijo, tol):
+    """True when, at every step size between the two accepted ones, the oracle's objective change
+    F(w + a d) - F(w) is within tol of the Armijo threshold sigma a Delta (Eq. 6)."""
+    F0 = orc.objective(w)
+    for q in range(min(q_gpu, q_or), max(q_gpu, q_or) + 1):
+        a = armijo.beta ** q
+        wt = w.copy()
+        wt[bundle] += a * ro["d"]
+        dF = orc.objective(wt) - F0
+        thr = armijo.sigma * a * ro["Delta"]
+        if abs(dF - thr) <= tol * (abs(dF) + abs(thr)):
+            return True
+    return False
+
+
+@pytest.mark.parametrize("name", ["lr_2k_10k", "svm_20k_100k", "ragged_lr", "ragged_svm"])
+def test_permutation_bitwise(pk, name):
+    wl, p = problem(name)
+    P = pk.Problem.from_csc(p.col_ptr, p.row_idx, p.val, p.y, wl.C, wl.loss)
+    try:
+        for seed, epoch in [(0, 0), (0, 1), (wl.solver_seed + 99, 5), (2**64 - 1, 2)]:
+            np.testing.assert_array_equal(P.permutation(seed, epoch), oracle.permutation(seed, epoch, p.n_features))
+    finally:
+        P.close()
+
+
+CASES = [("lr_2k_10k", 64), ("svm_20k_100k", 1024), ("svm_20k_100k", 8), ("ragged_lr", 100), ("ragged_svm", 97)]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("grid", [1, 0])
+@pytest.mark.parametrize("name,Pb", CASES)
+def test_bundle_step_parity(pk, name, Pb, grid, prec):
+    wl, p = problem(name)
+    orc = oracle.Oracle.from_problem(p, wl.C, wl.loss)
+    P = pk.Problem.from_csc(p.col_ptr, p.row_idx, p.val, p.y, wl.C, wl.loss)
+    opts = pk.pcdn_default_opts(prec=prec, grid_ctas=(grid if grid else 100000))
+    armijo = oracle.Armijo()
+    tol = 1e-9 if prec == "fp64" else 1e-5
+    try:
+        # states: w = 0, and w after part of an outer iteration of the oracle
+        w1, _ = orc.solve(Pb, eps=1e-12, seed=3, max_epochs=2, bundle_limit=max(1, (p.n_features // Pb) // 2))
+        rng = np.random.default_rng(11)
+        for w in (np.zeros(p.n_features), w1):
+            mq = orc.maintained(w)
+            for trial in range(3):
+                B = rng.choice(p.n_features, size=Pb, replace=False).astype(np.int32)
+                r = P.bundle_step(w, B, opts)
+                _, _, ro = orc.bundle_step(w, mq, B, armijo=armijo)
+                assert rel_err(r["g"], ro["g"]) <= tol, ("g", rel_err(r["g"], ro["g"]))
+                assert rel_err(r["h"], ro["h"]) <= tol, ("h", rel_err(r["h"], ro["h"]))
+                assert rel_err(r["d"], ro["d"]) <= tol, ("d", rel_err(r["d"], ro["d"]))
+                assert abs(r["Delta"] - ro["Delta"]) <= tol * max(abs(ro["Delta"]), 1e-300) + 1e-300
+                if r["q"] != ro["q"]:
+                    assert prec == "mixed" and margin_small(orc, w, ro, B, r["q"], ro["q"], armijo, 1e-5), \
+                        (r["q"], ro["q"], r["dF"], ro["dF"])
+                    continue
+                assert r["alpha"] == ro["alpha"]
+                if ro["dF"] != 0.0:
+                    dtol = 1e-7 if prec == "fp64" else 1e-4
+                    assert abs(r["dF"] - ro["dF"]) <= dtol * abs(ro["dF"]) + 1e-12 * abs(ro["Delta"]), (r["dF"], ro["dF"])
+                else:
+                    assert r["dF"] == 0.0
+    finally:
+        P.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("name,Pb,grid", [("lr_2k_10k", 64, 0), ("lr_2k_10k", 64, 100000), ("svm_20k_100k", 256, 0),
+                                          ("svm_20k_100k", 1024, 0), ("ragged_svm", 97, 100000)])
+def test_solve_parity(pk, name, Pb, grid, prec):
+    wl, p = problem(name)
+    orc = oracle.Oracle.from_problem(p, wl.C, wl.loss)
+    wo, so = orc.solve(Pb, eps=wl.eps, seed=wl.solver_seed, trace=True, max_epochs=200)
+    P = pk.Problem.from_csc(p.col_ptr, p.row_idx, p.val, p.y, wl.C, wl.loss)
+    try:
+        opts = pk.pcdn_default_opts(prec=prec, grid_ctas=grid, max_epochs=200)
+        nb = so["bundles"] + 8
+        rc, w, st, tr = P.solve(Pb, wl.eps, wl.solver_seed, opts, trace_bundles=int(nb), trace_epochs=200)
+        assert st["converged"] and so["converged"]
+        assert abs(st["F_final"] - so["F_final"]) <= 1e-6 * abs(so["F_final"]), (st["F_final"], so["F_final"])
+        if prec == "fp64":
+            # same trajectory: same epochs, same accepted steps, same relative KKT per epoch
+            assert st["epochs"] == so["epochs"]
+            n = min(len(tr["q"]), len(so["q"]))
+            assert n == so["bundles"]
+            assert np.mean(tr["q"][:n] == so["q"][:n]) >= 0.999
+            np.testing.assert_allclose(tr["epoch_kkt"], so["epoch_kkt"], rtol=1e-6)
+            np.testing.assert_allclose(w, wo, rtol=0, atol=1e-7 * max(1.0, np.abs(wo).max()))
+        else:
+            assert abs(st["epochs"] - so["epochs"]) <= 1
+        assert st["bundles"] == so["bundles"] or prec == "mixed"
+        # F is non-increasing bundle by bundle (Lemma 1(c)) on the GPU as well
+        assert np.all(tr["dF"] <= 1e-9 * abs(so["F_final"]))
+        assert st["kernel_launches"] > 0
+    finally:
+        P.close()
+
+
+@pytest.mark.parametrize("name", ["lr_2k_10k", "svm_20k_100k"])
+def test_objective_and_kkt(pk, name):
+    wl, p = problem(name)
+    orc = oracle.Oracle.from_problem(p, wl.C, wl.loss)
+    P = pk.Problem.from_csc(p.col_ptr, p.row_idx, p.val, p.y, wl.C, wl.loss)
+    try:
+        rng = np.random.default_rng(2)
+        for _ in range(3):
+            w = rng.normal(0, 0.5, p.n_features) * (rng.random(p.n_features) < 0.05)
+            P.set_w(w)
+            np.testing.assert_array_equal(P.get_w(), w)
+            assert P.objective() == pytest.approx(orc.objective(w), rel=1e-12)
+            assert P.kkt() == pytest.approx(orc.kkt_l1(w), rel=1e-10)
+    finally:
+        P.close()
+
+
+def test_device_pointer_create_matches_host_create(pk):
+    import torch
+    wl, p = problem("svm_20k_100k")
+    dev = torch.device("cuda:0")
+    t = [torch.from_numpy(a).to(dev) for a in (p.col_ptr, p.row_idx, p.val, p.y)]
+    s = torch.cuda.Stream()
+    Pd = pk.Problem.from_device(*t, wl.C, wl.loss, stream=s)
+    Ph = pk.Problem.from_csc(p.col_ptr, p.row_idx, p.val, p.y, wl.C, wl.loss)
+    try:
+        _, wd, sd, _ = Pd.solve(wl.P, wl.eps, 0)
+        _, wh, sh, _ = Ph.solve(wl.P, wl.eps, 0)
+        assert sd["epochs"] == sh["epochs"]
+        assert sd["F_final"] == pytest.approx(sh["F_final"], rel=1e-12)
+        np.testing.assert_allclose(wd, wh, atol=1e-9)
+    finally:
+        Pd.close()
+        Ph.close()
+
+
+@pytest.mark.parametrize("loss", ["logistic", "l2svm"])
+def test_p1_and_pm(pk, loss):
+    # P = 1 (CDN, Algorithm 1) and P = m (one bundle per outer iteration)
+    wl, p = problem("ragged_lr")
+    orc = oracle.Oracle.from_problem(p, wl.C, loss)
+    P = pk.Problem.from_csc(p.col_ptr, p.row_idx, p.val, p.y, wl.C, loss)
+    try:
+        for Pb in (1, p.n_features):
+            wo, so = orc.solve(Pb, eps=1e-4, seed=5, max_epochs=500)
+            _, w, st, _ = P.solve(Pb, 1e-4, 5, pk.pcdn_default_opts(max_epochs=500))
+            assert st["epochs"] == so["epochs"]
+            assert st["F_final"] == pytest.approx(so["F_final"], rel=1e-9)
+    finally:
+        P.close()
+
+
+def test_zero_direction_bundle(pk):
+    # at w = 0 a feature with |g_j| <= 1 keeps d_j = 0; a bundle of only such features changes nothing
+    wl, p = problem("lr_2k_10k")
+    orc = oracle.Oracle.from_problem(p, 1e-3, wl.loss)  # tiny c: every |g_j| < 1
+    P = pk.Problem.from_csc(p.col_ptr, p.row_idx, p.val, p.y, 1e-3, wl.loss)
+    try:
+        B = np.arange(64, dtype=np.int32)
+        r = P.bundle_step(np.zeros(p.n_features), B)
+        assert np.all(r["d"] == 0) and r["q"] == 0 and r["alpha"] == 1.0 and r["dF"] == 0.0 and r["Delta"] == 0.0
+        np.testing.assert_array_equal(P.get_w(), 0.0)
+        _, _, ro = orc.bundle_step(np.zeros(p.n_features), orc.maintained(np.zeros(p.n_features)), B)
+        assert np.all(ro["d"] == 0)
+    finally:
+        P.close()
+
+
+def test_errors_and_bounded_wait(pk):
+    wl, p = problem("svm_20k_100k")
+    P = pk.Problem.from_csc(p.col_ptr, p.row_idx, p.val, p.y, wl.C, wl.loss)
+    try:
+        with pytest.raises(pk.PcdnError) as ei:
+            P.bundle_step(None, np.array([1, 2, 1], dtype=np.int32))
+        assert ei.value.code == pk.PCDN_EINVAL
+        with pytest.raises(pk.PcdnError) as ei:
+            P.solve(0, 1e-3, 0)
+        assert ei.value.code == pk.PCDN_EINVAL
+        # a wait between blocks that gives up at once: the launch ends with PCDN_ETIMEOUT and the
+        # context stays usable
+        opts = pk.pcdn_default_opts(grid_ctas=100000, spin_limit=1, max_epochs=1)
+        with pytest.raises(pk.PcdnError) as ei:
+            P.solve(1024, 1e-3, 0, opts)
+        assert ei.value.code == pk.PCDN_ETIMEOUT
+        rc, w, st, _ = P.solve(wl.P, wl.eps, 0)
+        assert st["converged"]
+    finally:
+        P.close()
