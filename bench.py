@@ -1,0 +1,358 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 PCDN solver: time to relative KKT 1e-3 on the 2M x 3M logistic workload.
+
+One step = one full solve from w = 0 (Algorithm 3 with Algorithm 4, every bundle step, the
+per-outer-iteration refresh and KKT test) to relative minimum-norm subgradient <= 1e-3.
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Prints one JSON line.  `value` is seconds per solve (lower is better) with the inputs resident in
+HBM, timed by CUDA events on the library's stream; `e2e` is the same through the C ABI from host
+buffers (host->device copy of X and y, device set-up, solve, copy of w back).  `roofline` reports
+the bundle walker (the dominant kernel): algorithmic bytes of its bundle steps (16 nnz_B +
+33 |U_B| + 16 P per bundle) over its CUDA-event time, against the measured HBM copy bandwidth.
+`cpu_baseline` times the FP64 CPU oracle on a bounded sample of the same workload and projects it
+to a whole solve.  Under torchrun each rank solves its own replica (no collective on the data
+path); `value` is then the slowest rank's time divided by the number of solves in flight.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-eps (KKT 1e-3) & bundle-step HBM GB/s vs peak; batched/served vs plain"
+UNIT = "s"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="lr_2m_3m")
+    ap.add_argument("--scale", type=float, default=1.0, help="scale n and m of the workload (profiling runs)")
+    ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--also-fp64", type=int, default=1, help="also time the FP64 mode (reported under 'fp64')")
+    ap.add_argument("--max-epochs", type=int, default=1000)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--cpu-bundles", type=int, default=0, help="oracle sample size in bundles (0 = auto)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--grid", type=int, default=0)
+    return ap.parse_args()
+
+
+def workload(args):
+    import datagen
+    if args.scale != 1.0:
+        return datagen.scaled(args.workload, args.scale)
+    return datagen.workload(args.workload)
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def walker_traffic():
+    """DRAM bytes per walker launch from the committed ncu summary, if it was taken on the
+    current walker source; else None."""
+    path = os.path.join(ROOT, "profiles", "walk_traffic.json")
+    src = os.path.join(ROOT, "paper_1306_4080_gb300", "csrc", "pcdn_walk.cu")
+    try:
+        d = json.load(open(path))
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if d.get("walk_source_sha256_16") != h:
+            return None
+        return d
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    Q = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is None:
+            return
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        rows = []
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 10:
+                continue
+            if self.uuid and self.uuid not in f[1]:
+                continue
+            rows.append(f)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[6 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def gpu_uuid(dev):
+    import torch
+    try:
+        u = torch.cuda.get_device_properties(dev).uuid
+        s = str(u)
+        return s if s.startswith("GPU-") else "GPU-" + s
+    except Exception:
+        return None
+
+
+def cpu_sample(prob, wl, bundles_total, epochs_total, n_bundles):
+    """The FP64 oracle as it stands, single-threaded: the set-up of a solve (refresh + KKT at w = 0,
+    which is also the per-outer-iteration cost) and the first n_bundles bundle steps, projected to a
+    whole solve of bundles_total bundles over epochs_total outer iterations."""
+    import oracle
+    o = oracle.Oracle.from_problem(prob, wl.C, wl.loss)
+    t0 = time.perf_counter()
+    o.solve(wl.P, eps=wl.eps, seed=wl.solver_seed, bundle_limit=0)
+    t_setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    o.solve(wl.P, eps=wl.eps, seed=wl.solver_seed, bundle_limit=n_bundles)
+    t_run = time.perf_counter() - t0
+    per_bundle = max(0.0, t_run - t_setup) / n_bundles
+    projected = t_setup * (epochs_total + 1) + per_bundle * bundles_total
+    return dict(value=projected, unit=UNIT, cores=1, kind="oracle",
+                sample=f"oracle (1 thread, FP64) on {n_bundles} bundles of outer iteration 0 plus one solve set-up "
+                       f"(refresh + KKT) of this workload, projected to {bundles_total} bundles and "
+                       f"{epochs_total} outer iterations: per bundle {per_bundle * 1e3:.3f} ms, per outer-iteration "
+                       f"refresh+KKT {t_setup:.3f} s; sample wall {t_setup + t_run:.1f} s",
+                per_bundle_s=per_bundle, setup_s=t_setup)
+
+
+def oracle_record(name):
+    path = os.path.join(ROOT, "tests", "golden", "oracle_records.json")
+    try:
+        return json.load(open(path))[name]
+    except Exception:
+        return None
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if rank != 0:
+        return 0
+    import datagen
+    wl = workload(args)
+    prob = datagen.generate(wl.spec, with_csr=False)
+    rec = oracle_record(wl.name)
+    if rec is not None:
+        bundles_total, epochs_total, basis = rec["bundles"], rec["epochs"], "oracle's own full solve (recorded)"
+    else:
+        nb = (prob.n_features + wl.P - 1) // wl.P
+        bundles_total, epochs_total, basis = nb * 10, 10, "assumed 10 outer iterations"
+    nbun = args.cpu_bundles or max(8, min(200, (prob.n_features + wl.P - 1) // wl.P))
+    vals = []
+    last = None
+    for i in range(args.warmup + args.steps):
+        last = cpu_sample(prob, wl, bundles_total, epochs_total, nbun)
+        if i >= args.warmup:
+            vals.append(last["value"])
+    v = statistics.mean(vals)
+    cb = {k: last[k] for k in ("kind", "cores", "sample")}
+    cb["value"] = v
+    cb["unit"] = UNIT
+    cb["projection_basis"] = basis
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_of(wl, prob, "fp64"), "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config_of(wl, prob, prec):
+    return {"workload": f"{wl.name}: L1 {wl.loss}, n_samples={prob.n_samples}, n_features={prob.n_features}, "
+                        f"nnz={prob.nnz}, Zipf {wl.spec.zipf_s} columns, tf-idf rows L2-normalised, C={wl.C}, "
+                        f"P={wl.P}, eps={wl.eps}",
+            "n_samples": prob.n_samples, "n_features": prob.n_features, "nnz": prob.nnz, "loss": wl.loss,
+            "C": wl.C, "P": wl.P, "eps": wl.eps, "precision": prec,
+            "cache": "inputs larger than L2 (X alone is %.2f GB)" % (prob.nnz * 8 / 1e9)}
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import datagen
+    import paper_1306_4080_gb300 as pk
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pk.load()
+
+    wl = workload(args)
+    prob = datagen.generate(wl.spec, with_csr=False)
+    stream = torch.cuda.Stream(device=dev)
+    t_cp = torch.from_numpy(prob.col_ptr).to(dev)
+    t_ri = torch.from_numpy(prob.row_idx).to(dev)
+    t_v = torch.from_numpy(prob.val).to(dev)
+    t_y = torch.from_numpy(prob.y).to(dev)
+    torch.cuda.synchronize()
+    P = pk.Problem.from_device(t_cp, t_ri, t_v, t_y, wl.C, wl.loss, stream=stream)
+
+    def timed(prec, steps, warmup):
+        opts = pk.pcdn_default_opts(prec=prec, max_epochs=args.max_epochs, grid_ctas=args.grid)
+        for _ in range(warmup):
+            P.solve(wl.P, wl.eps, wl.solver_seed, opts, want_w=False)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        sts = []
+        with ClockSampler(gpu_uuid(dev)) as clk:
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            for _ in range(steps):
+                _, _, st, _ = P.solve(wl.P, wl.eps, wl.solver_seed, opts, want_w=False)
+                sts.append(st)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / steps
+        if dist:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+            dist.barrier()
+        return ms, sts, clk.summary()
+
+    ms, sts, clocks = timed(args.prec, args.steps, args.warmup)
+    st0 = sts[-1]
+    walk_s = sum(s["walk_s"] for s in sts)
+    walk_launches = sum(s["epochs"] for s in sts)
+    bytes_model = sum(s["bytes_model"] for s in sts)
+    launches = sum(s["kernel_launches"] for s in sts)
+    peak, peak_src = measured_peak()
+    achieved = bytes_model / walk_s / 1e9 if walk_s > 0 else 0.0
+    tr = walker_traffic()
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": (tr["dram_bytes_per_launch"] * (bytes_model / walk_launches) / tr["bytes_model_per_launch"])
+            if tr else None,
+            "kernel": "pcdn::walk_kernel (one launch per outer iteration)",
+            "peak_source": f"{peak_src} HBM copy bandwidth",
+            "bytes_per_launch": bytes_model / walk_launches, "ms_per_launch": walk_s / walk_launches * 1e3,
+            "walk_share_of_step": walk_s / (ms * 1e-3 * len(sts))}
+    if tr:
+        roof["traffic_source"] = tr.get("source")
+
+    extra = {}
+    if args.also_fp64 and args.prec != "fp64":
+        ms64, sts64, clk64 = timed("fp64", max(1, min(args.steps, 3)), 1)
+        s64 = sts64[-1]
+        extra["fp64"] = {"value": ms64 * 1e-3 / world, "ms_per_step": ms64, "epochs": s64["epochs"],
+                         "F_final": s64["F_final"], "kkt_rel": s64["kkt_rel"],
+                         "walk_ms_per_launch": sum(s["walk_s"] for s in sts64) / sum(s["epochs"] for s in sts64) * 1e3,
+                         "achieved_GBps": sum(s["bytes_model"] for s in sts64) / sum(s["walk_s"] for s in sts64) / 1e9,
+                         "clocks": clk64}
+
+    e2e = None
+    if not args.no_e2e:
+        cp, ri, vv, yy = prob.col_ptr, prob.row_idx, prob.val, prob.y
+        pin = [torch.from_numpy(a).pin_memory().numpy() for a in (cp, ri, vv, yy)]
+        opts = pk.pcdn_default_opts(prec=args.prec, max_epochs=args.max_epochs, grid_ctas=args.grid)
+        times = []
+        for i in range(args.e2e_steps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            h = pk.pcdn_create(*pin, wl.C, wl.loss)
+            _, w, _, _ = pk.pcdn_solve(h, wl.P, wl.eps, wl.solver_seed, opts, prob.n_features)
+            pk.pcdn_destroy(h)
+            t1 = time.perf_counter()
+            if i > 0:
+                times.append(t1 - t0)
+        h2d = cp.nbytes + ri.nbytes + vv.nbytes + yy.nbytes
+        e2e = {"value": statistics.mean(times) / world, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(8 * prob.n_features + 8), "steps": len(times),
+               "includes": "pcdn_create from pinned host CSC + row-mirror build + solve + w to host + destroy"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        nbun = args.cpu_bundles or max(8, min(200, (prob.n_features + wl.P - 1) // wl.P))
+        cpu = cpu_sample(prob, wl, int(st0["bundles"]), int(st0["epochs"]), nbun)
+        cpu.pop("per_bundle_s", None)
+        cpu.pop("setup_s", None)
+
+    P.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": ms * 1e-3 / world, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32/f64 mixed" if args.prec == "mixed" else "f64",
+                "data": "synthetic (seeded generator, shapes of the paper's sparse text workloads)",
+                "config": config_of(wl, prob, args.prec), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(launches), "clocks": clocks,
+                "solve": {"epochs": st0["epochs"], "bundles": st0["bundles"], "F_final": st0["F_final"],
+                          "kkt_rel": st0["kkt_rel"], "coord_updates_per_s": st0["coord_updates"] / (ms * 1e-3),
+                          "ls_steps": st0["ls_steps"], "ls_cap_hits": st0["ls_cap_hits"],
+                          "rows_touched": st0["rows_touched"]}}
+        line.update(extra)
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -22,6 +22,7 @@
 namespace pcdn {
 cudaError_t launch_walk(int loss, int prec, const WalkParams& p, int grid, cudaStream_t s);
 cudaError_t walk_max_blocks_per_sm(int loss, int prec, int* out);
+cudaError_t walk_configure(int loss, int prec);
 }  // namespace pcdn
 
 using namespace pcdn;
@@ -78,6 +79,7 @@ struct pcdn_problem {
   float* rval = nullptr;
   // state
   double* w = nullptr;
+  double* w_pos = nullptr;  // w in the walk's position order
   double* mq = nullptr;
   void* rec = nullptr;  // sized for the FP64 pair
   int rec_prec = 0;
@@ -100,6 +102,10 @@ struct pcdn_problem {
   int64_t max_items = 0;
   int64_t* hist = nullptr;
   int64_t* scan_ws = nullptr;
+  int64_t* item_len = nullptr;  // [max_items + 1]
+  int64_t* item_off = nullptr;  // [max_items + 1]
+  int64_t* plan = nullptr;
+  int64_t plan_cap = 0;
   // bundle scratch
   int32_t P_cap = 0;
   double* gk = nullptr;
@@ -148,7 +154,8 @@ void free_all(pcdn_problem* p) {
     f(p->col_ptr); f(p->row_idx); f(p->val); f(p->y);
   }
   f(p->row_ptr); f(p->col_idx); f(p->rval);
-  f(p->w); f(p->mq); f(p->rec); f(p->delta); f(p->touched);
+  f(p->w); f(p->w_pos); f(p->mq); f(p->rec); f(p->delta); f(p->touched);
+  f(p->item_len); f(p->item_off); f(p->plan);
   f(p->id_perm); f(p->id_item_ptr); f(p->id_items);
   f(p->keys0); f(p->keys1); f(p->vals0); f(p->vals1); f(p->cnt); f(p->item_ptr); f(p->items);
   f(p->hist); f(p->scan_ws);
@@ -239,6 +246,7 @@ int finish_create(pcdn_problem* p) {
   // ---- state
   p->nwords = (n + 31) / 32;
   CUDA_TRY(palloc(p, &p->w, m));
+  CUDA_TRY(palloc(p, &p->w_pos, m));
   CUDA_TRY(palloc(p, &p->mq, n));
   CUDA_TRY(palloc(p, (RecT<0>**)&p->rec, n));
   CUDA_TRY(palloc(p, &p->delta, n));
@@ -258,8 +266,14 @@ int finish_create(pcdn_problem* p) {
   CUDA_TRY(palloc(p, &p->item_ptr, m + 1));
   CUDA_TRY(palloc(p, &p->items, p->max_items));
   CUDA_TRY(palloc(p, &p->hist, hm));
-  CUDA_TRY(palloc(p, &p->scan_ws, scan_workspace_elems(hm > m + 1 ? hm : m + 1)));
+  {
+    int64_t scan_n = hm > m + 1 ? hm : m + 1;
+    if (p->max_items + 1 > scan_n) scan_n = p->max_items + 1;
+    CUDA_TRY(palloc(p, &p->scan_ws, scan_workspace_elems(scan_n)));
+  }
   CUDA_TRY(palloc(p, &p->part, 2 * p->max_items));
+  CUDA_TRY(palloc(p, &p->item_len, p->max_items + 1));
+  CUDA_TRY(palloc(p, &p->item_off, p->max_items + 1));
   CUDA_TRY(palloc(p, &p->id_perm, m));
   CUDA_TRY(palloc(p, &p->id_item_ptr, m + 1));
   CUDA_TRY(palloc(p, &p->id_items, p->max_items));
@@ -305,6 +319,16 @@ int ensure_bundle_scratch(pcdn_problem* p, int32_t P) {
   CUDA_TRY(cudaMemsetAsync(p->col_cnt, 0, sizeof(uint32_t) * P, p->stream));
   CUDA_TRY(cudaMemsetAsync(p->col_ready, 0, sizeof(uint32_t) * P, p->stream));
   p->P_cap = P;
+  return PCDN_OK;
+}
+
+int ensure_plan(pcdn_problem* p, int64_t entries) {
+  if (entries <= p->plan_cap) return PCDN_OK;
+  if (p->plan) cudaFree(p->plan);
+  p->plan = nullptr;
+  p->plan_cap = 0;
+  CUDA_TRY(palloc(p, &p->plan, entries));
+  p->plan_cap = entries;
   return PCDN_OK;
 }
 
@@ -383,11 +407,19 @@ int check_opts(const pcdn_opts* o) {
 }
 
 int pick_grid(const pcdn_problem* p, const pcdn_opts* o, int32_t P) {
-  if (o->grid_ctas > 0) return o->grid_ctas < p->max_grid ? o->grid_ctas : p->max_grid;
-  // One block when a bundle's work fits one SM comfortably; the whole GPU otherwise.
-  const double nnz_per_bundle = (double)p->nnz * (double)P / (double)p->m;
-  if (nnz_per_bundle < 8192.0 && p->n < (1 << 16)) return 1;
-  return p->max_grid;
+  int g;
+  if (o->grid_ctas > 0) {
+    g = o->grid_ctas < p->max_grid ? o->grid_ctas : p->max_grid;
+  } else {
+    // One block when a bundle's work fits one SM comfortably; the whole GPU otherwise.
+    const double nnz_per_bundle = (double)p->nnz * (double)P / (double)p->m;
+    g = (nnz_per_bundle < 8192.0 && p->n < (1 << 16)) ? 1 : p->max_grid;
+  }
+  // the block plan holds (bundles) x (blocks + 1) entries; keep it under 2^26
+  const int64_t nb = (p->m + P - 1) / P;
+  const int64_t cap = (int64_t(1) << 26) / (nb > 0 ? nb : 1) - 1;
+  if (cap < g) g = cap < 1 ? 1 : (int)cap;
+  return g;
 }
 
 // Launch the walker over bundles [t0, t1) of the partition held in perm/items.
@@ -401,7 +433,7 @@ int run_walk(pcdn_problem* p, const pcdn_opts* o, const int32_t* perm, int64_t n
   w.val = p->val;
   w.y = p->y;
   w.c = p->c;
-  w.w = p->w;
+  w.w_pos = p->w_pos;
   w.mq = p->mq;
   w.rec = p->rec;
   w.delta = p->delta;
@@ -410,6 +442,7 @@ int run_walk(pcdn_problem* p, const pcdn_opts* o, const int32_t* perm, int64_t n
   w.perm = perm;
   w.items = p->items;
   w.item_ptr = p->item_ptr;
+  w.plan = p->plan;
   w.npos = npos;
   w.P = P;
   w.t_begin = t0;
@@ -440,11 +473,19 @@ int run_walk(pcdn_problem* p, const pcdn_opts* o, const int32_t* perm, int64_t n
   w.tr_dF = p->tr_dF;
   w.counters = p->counters;
   w.err = p->err;
+  const int64_t nb = (npos + P - 1) / P;
+  int rc = ensure_plan(p, nb * (grid + 1));
+  if (rc) return rc;
+  w.plan = p->plan;
+  CUDA_TRY(build_plan(p->items, p->max_items, p->item_ptr, npos, P, nb, grid, p->item_len, p->item_off, p->plan,
+                      p->scan_ws, p->stream, &p->launches));
+  CUDA_TRY(gather_w(p->w, perm, npos, p->w_pos, p->stream, &p->launches));
   CUDA_TRY(cudaMemsetAsync(p->sync, 0, sizeof(uint32_t) * 8, p->stream));
   CUDA_TRY(cudaEventRecord(p->ev0, p->stream));
   CUDA_TRY(launch_walk(p->loss, (int)o->prec, w, grid, p->stream));
   ++p->launches;
   CUDA_TRY(cudaEventRecord(p->ev1, p->stream));
+  CUDA_TRY(scatter_w(p->w_pos, perm, npos, p->w, p->stream, &p->launches));
   if (ms) {
     CUDA_TRY(cudaEventSynchronize(p->ev1));
     CUDA_TRY(cudaEventElapsedTime(ms, p->ev0, p->ev1));

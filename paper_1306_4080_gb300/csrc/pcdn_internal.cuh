@@ -23,6 +23,8 @@ constexpr int kMaxK = 8;           // max step sizes per line-search pass
 constexpr int kWalkThreads = 256;  // threads per walker block
 constexpr int kWalkWarps = kWalkThreads / kWarp;
 constexpr int kListCap = 1024;     // touched rows listed per warp per 32 bitmap words
+constexpr int kICap = 256;         // work items staged per batch of the column pass
+constexpr int kECap = 2048;        // nonzeros staged per batch (= 8 per thread)
 
 constexpr int kErrTimeout = 1;
 constexpr int kErrNumeric = 2;
@@ -64,7 +66,7 @@ struct WalkParams {
   const int8_t* y;
   double c;
   // state
-  double* w;
+  double* w_pos;            // w in position order (the partition's order) during the walk
   double* mq;
   void* rec;
   double* delta;
@@ -74,6 +76,7 @@ struct WalkParams {
   const int32_t* perm;      // position -> feature
   const Item* items;        // work items in position order
   const int64_t* item_ptr;  // [npos+1] first item of each position
+  const int64_t* plan;      // [(t_end) * (gridDim.x + 1)] first item of each block in each bundle
   int64_t npos;             // number of positions (m for a solve, P for a single bundle)
   int32_t P;
   int64_t t_begin, t_end;   // bundles [t_begin, t_end) of this launch

@@ -224,6 +224,53 @@ __global__ void item_fill_kernel(const int32_t* perm, int64_t npos, const int64_
   }
 }
 
+// ------------------------------------------------------------------------------------ block plan
+// lengths of items [0, cap]; entries past the walk's real item count (item_ptr[npos]) are 0
+__global__ void item_len_kernel(const Item* items, int64_t cap, const int64_t* item_ptr, int64_t npos, int64_t* len) {
+  const int64_t n_real = item_ptr[npos];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= cap; i += (int64_t)gridDim.x * blockDim.x)
+    len[i] = i < n_real ? (int64_t)items[i].len : 0;
+}
+
+__global__ void plan_kernel(const int64_t* item_ptr, const int64_t* item_off, int64_t npos, int32_t P, int64_t nb, int G,
+                            int64_t* plan) {
+  const int64_t total = nb * (int64_t)(G + 1);
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t t = idx / (G + 1);
+    const int c = (int)(idx - t * (G + 1));
+    const int64_t lo = t * (int64_t)P;
+    const int64_t hi = lo + P < npos ? lo + P : npos;
+    const int64_t ib = item_ptr[lo], ie = item_ptr[hi];
+    int64_t r;
+    if (c == 0) {
+      r = ib;
+    } else if (c == G) {
+      r = ie;
+    } else {
+      const int64_t z0 = item_off[ib], z = item_off[ie] - z0;
+      const int64_t target = z0 + (int64_t)(((__int128)z * c) / G);
+      int64_t a = ib, b = ie;  // first i in [ib, ie) with item_off[i] >= target (ie if none)
+      while (a < b) {
+        const int64_t mid = a + (b - a) / 2;
+        if (item_off[mid] < target) a = mid + 1;
+        else b = mid;
+      }
+      r = a;
+    }
+    plan[idx] = r;
+  }
+}
+
+__global__ void gather_w_kernel(const double* w, const int32_t* perm, int64_t npos, double* w_pos) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < npos; k += (int64_t)gridDim.x * blockDim.x)
+    w_pos[k] = w[perm[k]];
+}
+
+__global__ void scatter_w_kernel(const double* w_pos, const int32_t* perm, int64_t npos, double* w) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < npos; k += (int64_t)gridDim.x * blockDim.x)
+    w[perm[k]] = w_pos[k];
+}
+
 // ------------------------------------------------------------------------------------ mirror
 __global__ void entry_col_kernel(const int64_t* col_ptr, int64_t m, int32_t* entry_col) {
   const int lane = threadIdx.x & 31;
@@ -489,6 +536,28 @@ cudaError_t build_items(const int32_t* perm, int64_t npos, const int64_t* col_pt
   e = scan_exclusive(cnt_ws, item_ptr, npos + 1, scan_ws, s, launches);
   if (e != cudaSuccess) return e;
   item_fill_kernel<<<grid_for(npos, 256), 256, 0, s>>>(perm, npos, col_ptr, item_ptr, items);
+  return post(launches);
+}
+
+cudaError_t build_plan(const Item* items, int64_t n_items, const int64_t* item_ptr, int64_t npos, int32_t P, int64_t nb,
+                       int G, int64_t* len_ws, int64_t* item_off, int64_t* plan, int64_t* scan_ws, cudaStream_t s,
+                       int64_t* launches) {
+  item_len_kernel<<<grid_for(n_items + 1, 256), 256, 0, s>>>(items, n_items, item_ptr, npos, len_ws);
+  cudaError_t e = post(launches);
+  if (e != cudaSuccess) return e;
+  e = scan_exclusive(len_ws, item_off, n_items + 1, scan_ws, s, launches);
+  if (e != cudaSuccess) return e;
+  plan_kernel<<<grid_for(nb * (G + 1), 256), 256, 0, s>>>(item_ptr, item_off, npos, P, nb, G, plan);
+  return post(launches);
+}
+
+cudaError_t gather_w(const double* w, const int32_t* perm, int64_t npos, double* w_pos, cudaStream_t s, int64_t* launches) {
+  gather_w_kernel<<<grid_for(npos, 256), 256, 0, s>>>(w, perm, npos, w_pos);
+  return post(launches);
+}
+
+cudaError_t scatter_w(const double* w_pos, const int32_t* perm, int64_t npos, double* w, cudaStream_t s, int64_t* launches) {
+  scatter_w_kernel<<<grid_for(npos, 256), 256, 0, s>>>(w_pos, perm, npos, w);
   return post(launches);
 }
 

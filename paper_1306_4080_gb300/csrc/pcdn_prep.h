@@ -34,6 +34,17 @@ cudaError_t perm_keys(uint64_t seed, int64_t epoch, int64_t m, uint64_t* keys, i
 cudaError_t build_items(const int32_t* perm, int64_t npos, const int64_t* col_ptr, int64_t* cnt_ws,
                         int64_t* item_ptr, Item* items, int64_t* scan_ws, cudaStream_t s, int64_t* launches);
 
+// Block plan of a walk: item_off = exclusive prefix of item lengths over [0, n_items] (n_items
+// may exceed the walk's real count item_ptr[npos]; the excess counts as empty); for bundle t and
+// block c in [0, G], plan[t*(G+1)+c] = first item of block c (nonzeros balanced over blocks;
+// an item never splits between blocks).
+cudaError_t build_plan(const Item* items, int64_t n_items, const int64_t* item_ptr, int64_t npos, int32_t P, int64_t nb,
+                       int G, int64_t* len_ws, int64_t* item_off, int64_t* plan, int64_t* scan_ws, cudaStream_t s,
+                       int64_t* launches);
+// w in position order for a walk, and back.
+cudaError_t gather_w(const double* w, const int32_t* perm, int64_t npos, double* w_pos, cudaStream_t s, int64_t* launches);
+cudaError_t scatter_w(const double* w_pos, const int32_t* perm, int64_t npos, double* w, cudaStream_t s, int64_t* launches);
+
 // ---- row-major mirror -------------------------------------------------------------------------
 cudaError_t entry_columns(const int64_t* col_ptr, int64_t m, int32_t* entry_col, cudaStream_t s, int64_t* launches);
 cudaError_t row_counts(const int32_t* row_idx, int64_t nnz, int64_t* counts, cudaStream_t s, int64_t* launches);
