@@ -88,6 +88,8 @@ def _load(path: str | None = None):
             lib.or_solve.argtypes = [P(_Problem), P(_Armijo), i64, d, ctypes.c_uint64, i64, i32, i64, vp,
                                      P(_Stats), i64, vp, vp, vp, vp, i64, vp, vp]
             lib.or_solve.restype = i32
+            lib.or_loss_change.argtypes = [P(_Problem), d, i32, d]
+            lib.or_loss_change.restype = d
             lib.or_cdn_epoch.argtypes = [P(_Problem), P(_Armijo), ctypes.c_uint64, i64, vp, vp]
             lib.or_cdn_epoch.restype = i32
             _libs[key] = lib
@@ -151,6 +153,10 @@ class Oracle:
         g, h = ctypes.c_double(), ctypes.c_double()
         self.lib.or_grad_hess(ctypes.byref(self._p), _ptr(mq), int(j), float(nu), ctypes.byref(g), ctypes.byref(h))
         return g.value, h.value
+
+    def row_loss_change(self, mq_i: float, y_i: int, u: float) -> float:
+        """Loss change of one sample with maintained quantity mq_i when w^T x_i moves by u."""
+        return float(self.lib.or_loss_change(ctypes.byref(self._p), float(mq_i), int(y_i), float(u)))
 
     def kkt_l1(self, w, mq=None, nu: float = 1e-12) -> float:
         w = np.ascontiguousarray(w, dtype=np.float64)

@@ -217,19 +217,38 @@ double or_kkt_l1(const or_problem* p, const double* w, const double* mq, double 
 }
 
 /* Loss change of sample i when w moves by a d (maintained form, Eq. 10 for
- * the logistic loss; the SVM analogue for Eq. 3).  Eq. 10's logarithm
- * log((E e^u + 1) / (E e^u + e^u)) equals log1p(expm1(-u) / (1 + E)); the
- * latter is evaluated to avoid forming a ratio close to one. */
+ * the logistic loss; the SVM analogue for Eq. 3).  Section 3.1 states that
+ * Eq. 10 is the objective change of Eq. 6 itself; its logarithm
+ * log((E e^u + 1) / (E e^u + e^u)) + [y = -1] u is evaluated here in forms
+ * that do not cancel.  With p = E/(1+E) and s = 1/(1+E) the per-sample
+ * change is log(p e^u + s) - [y = +1] u, written as
+ *   log1p(p expm1(u)) - [y = +1] u   when E <= 1 (the log1p argument >= -1/2),
+ *   log1p(s expm1(-u)) + [y = -1] u  when E > 1  (the same bound),
+ * and, when |u| is too large for expm1, as a log-sum-exp of log p + u and
+ * log s.  (Eq. 10's log-ratio taken literally loses every digit once
+ * |w^T x_i| exceeds about 37: the ratio rounds to 0 or 1.) */
 static double row_loss_change(const or_problem* p, double mq_i, int8_t y_i, double u /* a d^T x_i */) {
   if (p->loss == OR_LOSS_LOGISTIC) {
-    double t = log1p(expm1(-u) / (1.0 + mq_i));
-    return t + (y_i < 0 ? u : 0.0);
+    const double E = mq_i;
+    if (fabs(u) < 700.0) {
+      if (E <= 1.0) return log1p(E / (1.0 + E) * expm1(u)) - (y_i > 0 ? u : 0.0);
+      return log1p(expm1(-u) / (1.0 + E)) + (y_i < 0 ? u : 0.0);
+    }
+    const double lp = log(E) - log1p(E), ls = -log1p(E);
+    const double a = lp + u, b = ls;
+    const double m = a > b ? a : b;
+    return m + log1p(exp(-fabs(a - b))) - (y_i > 0 ? u : 0.0);
   } else {
     double bn = mq_i - (double)y_i * u;
     double a = bn > 0 ? bn * bn : 0.0;
     double b = mq_i > 0 ? mq_i * mq_i : 0.0;
     return a - b;
   }
+}
+
+/* The per-sample loss change above, exported for its pin tests. */
+double or_loss_change(const or_problem* p, double mq_i, int y_i, double u) {
+  return row_loss_change(p, mq_i, (int8_t)y_i, u);
 }
 
 /*

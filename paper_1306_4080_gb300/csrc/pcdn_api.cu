@@ -118,7 +118,7 @@ struct pcdn_problem {
   double* cta_part = nullptr;
   int max_grid = 1;
   Decision* decision = nullptr;
-  uint32_t* sync = nullptr;  // [0] bar_count [1] bar_gen [2..4] anynz
+  uint32_t* sync = nullptr;  // [0] bar_count [1] bar_gen [4..5] barrier-1 counter (64-bit)
   int* err = nullptr;
   unsigned long long* counters = nullptr;
   double* red_part = nullptr;  // block partials
@@ -352,7 +352,9 @@ int device_status(pcdn_problem* p) {
   CUDA_TRY(cudaMemcpyAsync(&h, p->err, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
   CUDA_TRY(cudaStreamSynchronize(p->stream));
   if (h & kErrTimeout) return fail(PCDN_ETIMEOUT, "a device-side wait between thread blocks timed out");
-  if (h & kErrNumeric) return fail(PCDN_ENUMERIC, "non-finite value or |w^T x| > 700 in the solve");
+  if (h & kErrNumeric) return fail(PCDN_ENUMERIC, "non-finite gradient, Hessian diagonal or direction");
+  if (h & kErrRange) return fail(PCDN_ENUMERIC, "maintained quantity out of range after an update (|w^T x| > 700)");
+  if (h & kErrRefresh) return fail(PCDN_ENUMERIC, "|w^T x| > 700 when recomputing from z = Xw");
   return PCDN_OK;
 }
 
@@ -455,7 +457,8 @@ int run_walk(pcdn_problem* p, const pcdn_opts* o, const int32_t* perm, int64_t n
   w.col_ready = p->col_ready;
   w.stamp_base = p->stamp;
   p->stamp += (uint32_t)(t1 + 1);
-  w.anynz = p->sync + 2;
+  w.anynz = nullptr;
+  w.bar1 = reinterpret_cast<unsigned long long*>(p->sync + 4);
   w.cta_part = p->cta_part;
   w.decision = p->decision;
   w.bar_count = p->sync;

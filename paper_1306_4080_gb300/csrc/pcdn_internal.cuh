@@ -27,7 +27,9 @@ constexpr int kICap = 256;         // work items staged per batch of the column 
 constexpr int kECap = 2048;        // nonzeros staged per batch (= 8 per thread)
 
 constexpr int kErrTimeout = 1;
-constexpr int kErrNumeric = 2;
+constexpr int kErrNumeric = 2;       // non-finite g, h or d
+constexpr int kErrRange = 4;         // maintained quantity out of range after an update
+constexpr int kErrRefresh = 8;       // |w^T x| > 700 when recomputing from z = Xw
 
 // One column work item: nonzeros [start, start+len) of the feature at permutation position pos,
 // chunk `chunk` of `nch` chunks of that column.
@@ -88,7 +90,7 @@ struct WalkParams {
   uint32_t* col_cnt;        // [P] arrivals per split column (reset by the finaliser)
   uint32_t* col_ready;      // [P] stamp of the bundle whose d is published
   uint32_t stamp_base;      // stamps of this launch are stamp_base + t + 1
-  uint32_t* anynz;          // [3] any nonzero direction in the bundle, by bundle index mod 3
+  uint32_t* anynz;          // unused
   // reductions and barriers
   double* cta_part;         // [gridDim.x * kPartStride]
   Decision* decision;
@@ -104,6 +106,7 @@ struct WalkParams {
   double* tr_Delta;
   double* tr_dF;
   unsigned long long* counters;  // [8]: ls_steps, cap_hits, passes, nnz, rows, bundles, coord_updates, nonzero-d bundles
+  unsigned long long* bar1;      // barrier 1: low 32 bits arrivals, high 32 bits blocks with a nonzero direction
   int* err;
 };
 
@@ -125,6 +128,14 @@ __device__ __forceinline__ uint32_t atom_acqrel_add_u32(uint32_t* p, uint32_t v)
   return old;
 }
 __device__ __forceinline__ int ld_volatile_int(const int* p) { return *(const volatile int*)p; }
+__device__ __forceinline__ uint64_t ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void red_release_add_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
 
 __device__ __forceinline__ void red_add_f64(double* p, double v) {
   asm volatile("red.global.add.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
@@ -226,6 +237,7 @@ __device__ __forceinline__ bool mq_ok(double v) {
 __device__ __forceinline__ float lr_remainder(float a, float v) {
   if (a <= 0.0f) return 0.0f;
   float av = fabsf(v);
+  if (!(av <= 3.0e38f)) return __int_as_float(0x7f800000);  // an infinite trial step: +inf, rejected
   if (av <= 0.125f) {
     float b = 1.0f - a, ab = a * b, t = b - a;
     float k2 = ab, k3 = ab * t, k4 = ab * (1.0f - 6.0f * ab), k5 = ab * t * (1.0f - 12.0f * ab);
@@ -251,16 +263,64 @@ __device__ __forceinline__ float lr_remainder(float a, float v) {
 // Mixed precision, L2-SVM: remainder of max(0, b - v)^2 - max(0, b)^2 after its first-order
 // part 2 max(b, 0) v (summed exactly as alpha g^T d / c).  v = alpha y_i d^T x_i.  The case
 // split compares b with v: FP32 decides unless the rounded values tie, then FP64.
-__device__ __forceinline__ float svm_remainder(double b, double v) {
-  float bf = (float)b, vf = (float)v;
-  bool b_pos = b > 0.0;
-  bool bn_pos = (bf != vf) ? (bf > vf) : (b > v);
+// b_pos = (b > 0) decided once per row in FP64; v = alpha y_i d^T x_i formed in FP32 (alpha is a
+// power of two for beta = 1/2, so the product is exact); ties of the rounded b and v fall back to
+// an FP64 comparison.
+__device__ __forceinline__ float svm_remainder(double b, float bf, bool b_pos, float vf, double alpha, double yd) {
+  const bool bn_pos = (bf != vf) ? (bf > vf) : (b > alpha * yd);
   if (b_pos) return bn_pos ? vf * vf : bf * (2.0f * vf - bf);
   if (bn_pos) {
-    float t = (float)(b - v);
+    const float t = bf - vf;
     return t * t;
   }
   return 0.0f;
+}
+
+// ---------------------------------------------------------------- double-float sums
+// A sum carried as an unevaluated pair hi + lo of FP32 numbers (error-free TwoSum, Knuth), about
+// 48 significant bits.  GB300 runs FP32 at many times its FP64 rate, so the mixed-precision path
+// accumulates its FP64-grade sums in this form.
+struct dfloat {
+  float hi, lo;
+};
+__device__ __forceinline__ dfloat df_make(double v) {
+  dfloat r;
+  r.hi = (float)v;
+  r.lo = (float)(v - (double)r.hi);
+  return r;
+}
+__device__ __forceinline__ dfloat df_add(dfloat a, dfloat b) {
+  const float s = a.hi + b.hi;
+  const float bb = s - a.hi;
+  const float err = (a.hi - (s - bb)) + (b.hi - bb);
+  const float lo = err + a.lo + b.lo;
+  dfloat r;
+  r.hi = s + lo;
+  r.lo = lo - (r.hi - s);
+  return r;
+}
+__device__ __forceinline__ dfloat df_add_f(dfloat a, float b) {
+  dfloat t;
+  t.hi = b;
+  t.lo = 0.0f;
+  return df_add(a, t);
+}
+__device__ __forceinline__ double df_value(dfloat a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ dfloat df_shfl_xor(dfloat a, int o) {
+  dfloat r;
+  r.hi = __shfl_xor_sync(0xffffffffu, a.hi, o);
+  r.lo = __shfl_xor_sync(0xffffffffu, a.lo, o);
+  return r;
+}
+__device__ __forceinline__ dfloat df_warp_sum(dfloat a) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) a = df_add(a, df_shfl_xor(a, o));
+  return a;
+}
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
 }
 
 __device__ __forceinline__ void kahan_add(float& s, float& comp, float x) {

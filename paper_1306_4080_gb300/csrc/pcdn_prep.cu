@@ -362,7 +362,7 @@ __global__ void __launch_bounds__(kRedThreads) refresh_kernel(const int64_t* row
       if (write_state) {
         double v;
         if (LOSS == 0) {
-          if (fabs(z) > 700.0) atomicOr(err, kErrNumeric);
+          if (fabs(z) > 700.0) atomicOr(err, kErrRefresh);
           v = exp(z);
         } else {
           v = 1.0 - (double)yi * z;

@@ -6,22 +6,28 @@
 //      long column) are split over the blocks in contiguous runs of balanced nonzero count (the
 //      plan).  A block stages a batch of items: item records and w_j (one wave of loads), then the
 //      batch's row indices and values and, for each, the row's coefficient pair (two waves, every
-//      load of a wave in flight at once), all into shared memory.  One warp per item then reduces
-//      g_j, h_j (Eq. 11 / generalised Hessian) from shared memory, computes d_j (Eq. 5) and
-//      scatters d_j x_ij into delta (red.add.f64) from the staged copy, setting the row's touched
-//      bit.  Chunks of one column combine through a per-column arrival counter: the last chunk in
-//      computes d_j and publishes it; the other chunks scatter once it is published.
-//   -- barrier 1
+//      load of a wave in flight at once), all into shared memory.  One warp per item reduces
+//      g_j, h_j (Eq. 11 / generalised Hessian) from shared memory; one thread per item then forms
+//      d_j (Eq. 5); one warp per item scatters d_j x_ij into delta (red.add.f64) from the staged
+//      copy and sets the row's touched bit.  Chunks of one column combine through a per-column
+//      arrival counter: the last chunk in computes d_j and publishes it; the other chunks scatter
+//      once it is published.
+//   -- barrier 1 (its counter also carries "some block has a nonzero direction")
 //   B  line search: every warp walks a fixed range of the touched-row bitmap, lists the touched
-//      rows and sums the loss change of each for K step sizes beta^q (Eq. 10); every block also
-//      sums Delta's parts (Eq. 7) and the L1 change of each step over a fixed slice of the
-//      bundle.  Partial sums per block.
+//      rows and sums the loss change of each for K step sizes beta^q (Eq. 10); a block also sums
+//      Delta's parts (Eq. 7) and the L1 change of each step over a fixed slice of the bundle.
+//      Partial sums per block.
 //   -- barrier 2 (the last block to arrive reduces the partials in block order and decides
 //      accept / next K step sizes / cap; Eq. 6)
 //   C  update: w_B += alpha d; each warp updates the maintained quantity and coefficients of
 //      the rows it evaluated (Algorithm 4), clears delta and the bitmap.
 //   -- barrier 3
 // A bundle whose directions are all zero ends after barrier 1.
+//
+// Precision.  FP64 mode sums in FP64 throughout.  Mixed mode does its per-nonzero and per-row
+// arithmetic in FP32 and carries every sum that feeds the Armijo test (Delta's parts, the L1
+// change of each step, the line-search remainders) as double-float pairs: about 48 significant
+// bits on the FP32 pipe, because GB300's FP64 rate is a small fraction of its FP32 rate.
 //
 // Every wait between blocks is a bounded spin; at the bound the block records kErrTimeout
 // and the launch ends (the host reports PCDN_ETIMEOUT).  With one block the barriers are
@@ -36,6 +42,9 @@ struct StageA {
   Item items[kICap];
   int32_t ioff[kICap + 1];
   double wpos[kICap];
+  double g[kICap];
+  double h[kICap];
+  double d[kICap];
   int32_t row[kECap];
   float x[kECap];
   RecT<PREC> rec[kECap];
@@ -45,6 +54,7 @@ template <int PREC>
 struct SharedWalk {
   int abort;
   int last;
+  int has_nz;
   int nonzero;
   int scan_tot[kWalkWarps];
   Decision dec;
@@ -56,10 +66,44 @@ struct SharedWalk {
   } u;
 };
 
+// A partial sum slot: FP64 mode stores a double, mixed mode a double-float pair in the same 8 bytes.
+template <int PREC> struct Acc;
+template <> struct Acc<0> {
+  double v = 0.0;
+  __device__ __forceinline__ void add(double x) { v += x; }
+  __device__ __forceinline__ void add_acc(const Acc& o) { v += o.v; }
+  __device__ __forceinline__ void warp_reduce() { v = warp_sum(v); }
+  __device__ __forceinline__ double store() const { return v; }
+  __device__ __forceinline__ static Acc load(double s) { Acc a; a.v = s; return a; }
+  __device__ __forceinline__ double value() const { return v; }
+};
+template <> struct Acc<1> {
+  dfloat v = {0.0f, 0.0f};
+  __device__ __forceinline__ void add(double x) { v = df_add(v, df_make(x)); }
+  __device__ __forceinline__ void add_acc(const Acc& o) { v = df_add(v, o.v); }
+  __device__ __forceinline__ void warp_reduce() { v = df_warp_sum(v); }
+  __device__ __forceinline__ double store() const {
+    double s;
+    float2 f = make_float2(v.hi, v.lo);
+    memcpy(&s, &f, sizeof(s));
+    return s;
+  }
+  __device__ __forceinline__ static Acc load(double s) {
+    float2 f;
+    memcpy(&f, &s, sizeof(f));
+    Acc a;
+    a.v.hi = f.x;
+    a.v.lo = f.y;
+    return a;
+  }
+  __device__ __forceinline__ double value() const { return df_value(v); }
+};
+
 // ---------------------------------------------------------------- barriers
 __device__ __forceinline__ bool err_set(const WalkParams& p) { return ld_volatile_int(p.err) != 0; }
 
-// Plain barrier over the grid.  Returns false when the launch must end.
+// Plain barrier over the grid.  Returns false when the launch must end (a wait gave up, or a
+// block recorded an error while this one waited).
 template <class SH>
 __device__ bool grid_barrier(const WalkParams& p, uint32_t& idx, SH& sh) {
   __syncthreads();
@@ -73,12 +117,41 @@ __device__ bool grid_barrier(const WalkParams& p, uint32_t& idx, SH& sh) {
         if (++spins > p.spin_limit) { atomicOr(p.err, kErrTimeout); abort = 1; break; }
         if ((spins & 1023u) == 0 && err_set(p)) { abort = 1; break; }
       }
-      sh.abort = abort || err_set(p);
+      sh.abort = abort;
     }
-  } else if (threadIdx.x == 0) {
-    sh.abort = err_set(p);
   }
   ++idx;
+  __syncthreads();
+  return !sh.abort;
+}
+
+// Barrier 1: each block adds 1 (arrival) + (has_nz << 32); the waiters also learn whether any
+// block found a nonzero direction.  `seen` is the high word at the previous barrier 1.
+template <class SH>
+__device__ bool grid_barrier_flag(const WalkParams& p, uint32_t& n1, uint32_t& seen, SH& sh) {
+  __syncthreads();
+  if (gridDim.x > 1) {
+    if (threadIdx.x == 0) {
+      const uint64_t target = (uint64_t)(n1 + 1) * gridDim.x;
+      red_release_add_u64(p.bar1, 1ull + ((unsigned long long)(sh.has_nz ? 1 : 0) << 32));
+      uint32_t spins = 0;
+      int abort = 0;
+      uint64_t v;
+      while (((v = ld_acquire_u64(p.bar1)) & 0xffffffffull) < target) {
+        if (++spins > p.spin_limit) { atomicOr(p.err, kErrTimeout); abort = 1; break; }
+        if ((spins & 1023u) == 0 && err_set(p)) { abort = 1; break; }
+      }
+      const uint32_t hi = (uint32_t)(v >> 32);
+      sh.nonzero = hi != seen;
+      sh.abort = abort;
+      sh.scan_tot[0] = (int)hi;
+    }
+    __syncthreads();
+    seen = (uint32_t)sh.scan_tot[0];
+  } else {
+    if (threadIdx.x == 0) sh.nonzero = sh.has_nz;
+  }
+  ++n1;
   __syncthreads();
   return !sh.abort;
 }
@@ -100,7 +173,6 @@ __device__ bool grid_barrier_reduce(const WalkParams& p, uint32_t& idx, SH& sh, 
       if (threadIdx.x == 0) {
         __threadfence();
         st_release_u32(p.bar_gen, idx + 1);
-        sh.abort = err_set(p);
       }
     } else if (threadIdx.x == 0) {
       uint32_t spins = 0;
@@ -109,12 +181,10 @@ __device__ bool grid_barrier_reduce(const WalkParams& p, uint32_t& idx, SH& sh, 
         if (++spins > p.spin_limit) { atomicOr(p.err, kErrTimeout); abort = 1; break; }
         if ((spins & 1023u) == 0 && err_set(p)) { abort = 1; break; }
       }
-      sh.abort = abort || err_set(p);
+      sh.abort = abort;
     }
   } else {
     fn();
-    __syncthreads();
-    if (threadIdx.x == 0) sh.abort = err_set(p);
   }
   ++idx;
   __syncthreads();
@@ -131,8 +201,10 @@ template <> struct ColAcc<0> {
     g = fma(xd, r.cg, g);
     h = fma(xd * xd, r.ch, h);
   }
-  __device__ __forceinline__ double gsum() const { return warp_sum(g); }
-  __device__ __forceinline__ double hsum() const { return warp_sum(h); }
+  __device__ __forceinline__ void reduce(double& go, double& ho) const {
+    go = warp_sum(g);
+    ho = warp_sum(h);
+  }
 };
 template <> struct ColAcc<1> {
   float g = 0.0f, h = 0.0f;
@@ -140,8 +212,10 @@ template <> struct ColAcc<1> {
     g = fmaf(x, r.cg, g);
     h = fmaf(x * x, r.ch, h);
   }
-  __device__ __forceinline__ double gsum() const { return warp_sum((double)g); }
-  __device__ __forceinline__ double hsum() const { return warp_sum((double)h); }
+  __device__ __forceinline__ void reduce(double& go, double& ho) const {
+    go = (double)warp_sum_f(g);
+    ho = (double)warp_sum_f(h);
+  }
 };
 
 template <int PREC>
@@ -165,18 +239,16 @@ __device__ __forceinline__ void item_scatter_global(const WalkParams& p, const I
   for (int64_t e = it.start + lane; e < end; e += kWarp) scatter_one(p, p.row_idx[e], scatter_value<PREC>(d, p.val[e]));
 }
 
-// g, h -> d for bundle position kl (lane 0 writes; returns d to all lanes).
+// g, h (sums without the factor c) -> d for bundle position kl; writes gk, hk, dk.
 __device__ __forceinline__ double finalize_column(const WalkParams& p, int32_t kl, double g, double h, double wj) {
   g *= p.c;
   h *= p.c;
   if (h <= 0.0) h = p.nu;
   const double d = newton_direction(g, h, wj);
-  if ((threadIdx.x & 31) == 0) {
-    p.gk[kl] = g;
-    p.hk[kl] = h;
-    p.dk[kl] = d;
-    if (!isfinite(g) || !isfinite(h) || !isfinite(d)) atomicOr(p.err, kErrNumeric);
-  }
+  p.gk[kl] = g;
+  p.hk[kl] = h;
+  p.dk[kl] = d;
+  if (!isfinite(g) || !isfinite(h) || !isfinite(d)) atomicOr(p.err, kErrNumeric);
   return d;
 }
 
@@ -201,7 +273,7 @@ __device__ __forceinline__ int block_scan_incl(SH& sh, int v) {
 // Phase A for this block: items [i0, i1) of the bundle whose positions start at lo.
 template <int LOSS, int PREC>
 __device__ void column_pass(const WalkParams& p, SharedWalk<PREC>& sh, int64_t lo, int64_t i0, int64_t i1,
-                            uint32_t stamp, uint32_t* anynz) {
+                            uint32_t stamp) {
   const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
   StageA<PREC>& st = sh.u.a;
   const RecT<PREC>* rec = (const RecT<PREC>*)p.rec;
@@ -253,52 +325,71 @@ __device__ void column_pass(const WalkParams& p, SharedWalk<PREC>& sh, int64_t l
       }
     }
     __syncthreads();
-    // one warp per item: reduce, direction, scatter
+    // one warp per item: the reduction; chunks of split columns combine here
     for (int j = wib; j < nb; j += kWalkWarps) {
       const Item it = st.items[j];
       const int a = st.ioff[j], b = st.ioff[j + 1];
       ColAcc<PREC> acc;
       for (int v = a + lane; v < b; v += kWarp) acc.add(st.x[v], st.rec[v]);
-      const double g = acc.gsum(), h = acc.hsum();
-      const int32_t kl = (int32_t)(it.pos - lo);
+      double g, h;
+      acc.reduce(g, h);
       if (it.nch == 1) {
-        const double d = finalize_column(p, kl, g, h, st.wpos[j]);
-        if (d != 0.0) {
-          if (lane == 0) red_or_u32(anynz, 1u);
-          for (int v = a + lane; v < b; v += kWarp) scatter_one(p, st.row[v], scatter_value<PREC>(d, st.x[v]));
-        }
-      } else {
-        const int64_t gi = i + j;  // global item index
-        int last = 0;
         if (lane == 0) {
-          p.part[2 * gi] = g;
-          p.part[2 * gi + 1] = h;
-          __threadfence();
-          const uint32_t old = atomicAdd(p.col_cnt + kl, 1u);
-          last = (old == (uint32_t)it.nch - 1u);
-          if (last) __threadfence();
+          st.g[j] = g;
+          st.h[j] = h;
         }
-        last = __shfl_sync(0xffffffffu, last, 0);
-        __syncwarp();
-        if (last) {
-          // fixed-order combine of the column's chunks: lane l sums chunks l, l+32, ..., then a tree
-          const int64_t first = gi - it.chunk;
-          double gs = 0.0, hs = 0.0;
-          for (int cch = lane; cch < it.nch; cch += kWarp) {
-            gs += p.part[2 * (first + cch)];
-            hs += p.part[2 * (first + cch) + 1];
-          }
-          gs = warp_sum(gs);
-          hs = warp_sum(hs);
+        continue;
+      }
+      const int32_t kl = (int32_t)(it.pos - lo);
+      const int64_t gi = i + j;  // global item index
+      int last = 0;
+      if (lane == 0) {
+        p.part[2 * gi] = g;
+        p.part[2 * gi + 1] = h;
+        __threadfence();
+        const uint32_t old = atomicAdd(p.col_cnt + kl, 1u);
+        last = (old == (uint32_t)it.nch - 1u);
+        if (last) __threadfence();
+      }
+      last = __shfl_sync(0xffffffffu, last, 0);
+      __syncwarp();
+      if (last) {
+        // fixed-order combine of the column's chunks: lane l sums chunks l, l+32, ..., then a tree
+        const int64_t first = gi - it.chunk;
+        double gs = 0.0, hs = 0.0;
+        for (int cch = lane; cch < it.nch; cch += kWarp) {
+          gs += p.part[2 * (first + cch)];
+          hs += p.part[2 * (first + cch) + 1];
+        }
+        gs = warp_sum(gs);
+        hs = warp_sum(hs);
+        if (lane == 0) {
           const double d = finalize_column(p, kl, gs, hs, st.wpos[j]);
-          if (lane == 0) {
-            if (d != 0.0) red_or_u32(anynz, 1u);
-            p.col_cnt[kl] = 0u;
-            __threadfence();
-            st_release_u32(p.col_ready + kl, stamp);
-          }
+          if (d != 0.0) sh.has_nz = 1;
+          p.col_cnt[kl] = 0u;
+          __threadfence();
+          st_release_u32(p.col_ready + kl, stamp);
         }
       }
+    }
+    __syncthreads();
+    // one thread per item: the direction (Eq. 5)
+    if (tid < nb) {
+      const Item it = st.items[tid];
+      double d = 0.0;
+      if (it.nch == 1) {
+        d = finalize_column(p, (int32_t)(it.pos - lo), st.g[tid], st.h[tid], st.wpos[tid]);
+        if (d != 0.0) sh.has_nz = 1;
+      }
+      st.d[tid] = d;
+    }
+    __syncthreads();
+    // one warp per item: scatter from the staged copy
+    for (int j = wib; j < nb; j += kWalkWarps) {
+      const double d = st.d[j];
+      if (d == 0.0) continue;
+      for (int v = st.ioff[j] + lane; v < st.ioff[j + 1]; v += kWarp)
+        scatter_one(p, st.row[v], scatter_value<PREC>(d, st.x[v]));
     }
     __syncthreads();  // the staging area is reused by the next batch
     i += nb;
@@ -329,7 +420,16 @@ __device__ void column_pass(const WalkParams& p, SharedWalk<PREC>& sh, int64_t l
 template <int LOSS, int PREC>
 struct LsAcc;
 
-// FP64: direct loss change per row (Eq. 10 rewritten with log1p/expm1; Eq. 3 for the SVM).
+// FP64: direct loss change per row.  Logistic: Eq. 10 in cancellation-free form, log(p e^u + s) -
+// [y = +1] u with p = E/(1+E), s = 1/(1+E): log1p(p expm1(u)) - [y = +1] u for E <= 1,
+// log1p(s expm1(-u)) + [y = -1] u for E > 1, a log-sum-exp when |u| >= 700.  L2-SVM: Eq. 3.
+__device__ __forceinline__ double lr_change_lse(double E, int y, double u) {
+  const double lp = log(E) - log1p(E), ls = -log1p(E);
+  const double a = lp + u, b = ls;
+  const double m = a > b ? a : b;
+  return m + log1p(exp(-fabs(a - b))) - (y > 0 ? u : 0.0);
+}
+
 template <int LOSS>
 struct LsAcc<LOSS, 0> {
   double s[kMaxK];
@@ -337,20 +437,28 @@ struct LsAcc<LOSS, 0> {
 #pragma unroll
     for (int q = 0; q < kMaxK; ++q) s[q] = 0.0;
   }
-  __device__ __forceinline__ void row(const WalkParams& p, int32_t r, const double* alpha, int K, bool halving) {
+  __device__ __forceinline__ void row(const WalkParams& p, int32_t r, const double* alpha, const float*, int K,
+                                      bool halving) {
     const double dl = p.delta[r];
     const double mq = p.mq[r];
     const int y = p.y[r];
     if constexpr (LOSS == 0) {
-      const double sinv = 1.0 / (1.0 + mq);
+      // form A (E <= 1): coefficient p, expm1(+u), label term -[y=+1] u
+      // form B (E > 1):  coefficient s, expm1(-u), label term +[y=-1] u
+      const bool fa = mq <= 1.0;
+      const double coef = fa ? mq / (1.0 + mq) : 1.0 / (1.0 + mq);
+      const double sg = fa ? 1.0 : -1.0;
       if (halving) {
-        // alpha_q = 2 alpha_{q+1}: expm1(-2u) = m (m + 2) with m = expm1(-u)
-        double m = expm1(-alpha[K - 1] * dl);
+        // alpha_q = 2 alpha_{q+1}: expm1(2v) = m (m + 2) with m = expm1(v)
+        double m = expm1(sg * alpha[K - 1] * dl);
 #pragma unroll
         for (int q = kMaxK - 1; q >= 0; --q) {
           if (q < K) {
             const double u = alpha[q] * dl;
-            s[q] += log1p(m * sinv) + (y < 0 ? u : 0.0);
+            double l;
+            if (fabs(u) < 700.0) l = fa ? log1p(coef * m) - (y > 0 ? u : 0.0) : log1p(m * coef) + (y < 0 ? u : 0.0);
+            else l = lr_change_lse(mq, y, u);
+            s[q] += l;
             m = m * (m + 2.0);
           }
         }
@@ -359,7 +467,10 @@ struct LsAcc<LOSS, 0> {
         for (int q = 0; q < kMaxK; ++q) {
           if (q < K) {
             const double u = alpha[q] * dl;
-            s[q] += log1p(expm1(-u) * sinv) + (y < 0 ? u : 0.0);
+            double l;
+            if (fabs(u) < 700.0) l = fa ? log1p(coef * expm1(u)) - (y > 0 ? u : 0.0) : log1p(expm1(-u) * coef) + (y < 0 ? u : 0.0);
+            else l = lr_change_lse(mq, y, u);
+            s[q] += l;
           }
         }
       }
@@ -375,7 +486,7 @@ struct LsAcc<LOSS, 0> {
       }
     }
   }
-  __device__ __forceinline__ double get(int q) const { return s[q]; }
+  __device__ __forceinline__ Acc<0> get(int q) const { Acc<0> a; a.v = s[q]; return a; }
 };
 
 // Mixed: FP32 remainder terms (non-negative), compensated FP32 sums per lane.
@@ -386,32 +497,39 @@ struct LsAcc<LOSS, 1> {
 #pragma unroll
     for (int q = 0; q < kMaxK; ++q) { s[q] = 0.0f; cmp[q] = 0.0f; }
   }
-  __device__ __forceinline__ void row(const WalkParams& p, int32_t r, const double* alpha, int K, bool) {
+  __device__ __forceinline__ void row(const WalkParams& p, int32_t r, const double* alpha, const float* alpha_f, int K,
+                                      bool) {
     const double dl = p.delta[r];
     const double mq = p.mq[r];
     const int y = p.y[r];
+    const float dlf = (float)dl;
     if constexpr (LOSS == 0) {
       float e = (float)mq, pp, ss;
       if (e <= 1.0f) { ss = 1.0f / (1.0f + e); pp = e * ss; }
       else { const float rr = 1.0f / e; pp = 1.0f / (1.0f + rr); ss = rr * pp; }
       const bool use_p = pp <= ss;
       const float a = use_p ? pp : ss;
+      const float vf = use_p ? dlf : -dlf;
 #pragma unroll
-      for (int q = 0; q < kMaxK; ++q) {
-        if (q < K) {
-          const float u = (float)(alpha[q] * dl);
-          kahan_add(s[q], cmp[q], lr_remainder(a, use_p ? u : -u));
-        }
-      }
+      for (int q = 0; q < kMaxK; ++q)
+        if (q < K) kahan_add(s[q], cmp[q], lr_remainder(a, alpha_f[q] * vf));
     } else {
-      const double v = (double)y * dl;
+      const double yd = (double)y * dl;
+      const float ydf = (float)yd;
+      const float bf = (float)mq;
+      const bool b_pos = mq > 0.0;
 #pragma unroll
-      for (int q = 0; q < kMaxK; ++q) {
-        if (q < K) kahan_add(s[q], cmp[q], svm_remainder(mq, alpha[q] * v));
-      }
+      for (int q = 0; q < kMaxK; ++q)
+        if (q < K) kahan_add(s[q], cmp[q], svm_remainder(mq, bf, b_pos, alpha_f[q] * ydf, alpha[q], yd));
     }
   }
-  __device__ __forceinline__ double get(int q) const { return (double)s[q] - (double)cmp[q]; }
+  __device__ __forceinline__ Acc<1> get(int q) const {
+    Acc<1> a;
+    a.v.hi = s[q];
+    a.v.lo = -cmp[q];
+    a.v = df_add(a.v, dfloat{0.0f, 0.0f});
+    return a;
+  }
 };
 
 // Update of one touched row after acceptance with step alpha (Algorithm 4).
@@ -421,49 +539,102 @@ __device__ __forceinline__ void row_update(const WalkParams& p, int32_t r, doubl
   double mq = p.mq[r];
   const int y = p.y[r];
   if constexpr (LOSS == 0) {
-    if constexpr (PREC == 0) mq = mq * exp(alpha * dl);
-    else mq = fma(mq, (double)expm1f((float)(alpha * dl)), mq);
+    if constexpr (PREC == 0) {
+      mq = mq * exp(alpha * dl);
+    } else {
+      // E e^u = E + E (e^u - 1) with FP32 expm1 where that is accurate to FP32 relative to e^u
+      // (u >= -1/2, so 1 + expm1(u) >= 0.6, and below FP32 overflow); FP64 exp elsewhere
+      const float uf = (float)alpha * (float)dl;
+      if (uf >= -0.5f && uf < 80.0f) mq = fma(mq, (double)expm1f(uf), mq);
+      else mq = mq * exp(alpha * dl);
+    }
   } else {
     mq = mq - alpha * (double)y * dl;
   }
-  if (!mq_ok<LOSS>(mq)) atomicOr(p.err, kErrNumeric);
+  if (!mq_ok<LOSS>(mq)) atomicOr(p.err, kErrRange);
   p.mq[r] = mq;
   ((RecT<PREC>*)p.rec)[r] = RowCoef<LOSS, PREC>::make(mq, y);
 }
 
-// Walk this warp's bitmap range: list touched rows 32 words at a time, call fn(row) per row.
-template <class Fn>
-__device__ __forceinline__ void for_touched_rows(const WalkParams& p, int32_t* list, bool clear, Fn&& fn) {
-  const int lane = threadIdx.x & 31;
+// The touched rows of this warp's fixed bitmap range.  When the range is at most 32 words the
+// listing made in phase B is kept (in shared memory and the lane's word) for phase C.
+struct WarpRows {
+  int64_t w0, w1;
+  bool single;
+  uint32_t word;  // the lane's bitmap word (single range)
+  int total;      // rows listed (single range)
+};
+
+__device__ __forceinline__ WarpRows warp_rows_range(const WalkParams& p) {
   const int wib = threadIdx.x >> 5;
   const int64_t W = (int64_t)gridDim.x * kWalkWarps;
   const int64_t gw = (int64_t)blockIdx.x * kWalkWarps + wib;
   const int64_t per = (p.nwords + W - 1) / W;
-  const int64_t w0 = gw * per;
-  const int64_t w1 = min(p.nwords, w0 + per);
-  for (int64_t base = w0; base < w1; base += kWarp) {
-    const int64_t wi = base + lane;
-    const uint32_t word = (wi < w1) ? p.touched[wi] : 0u;
-    if (__ballot_sync(0xffffffffu, word != 0u) == 0u) continue;
-    const int cnt = __popc(word);
-    int off = cnt;
+  WarpRows wr;
+  wr.w0 = gw * per;
+  wr.w1 = min(p.nwords, wr.w0 + per);
+  wr.single = per <= kWarp;
+  wr.word = 0u;
+  wr.total = 0;
+  return wr;
+}
+
+// List the touched rows of words [base, base+32) into `list`; returns the count (all lanes).
+__device__ __forceinline__ int list_group(const WalkParams& p, int64_t base, int64_t w1, int32_t* list, uint32_t& word) {
+  const int lane = threadIdx.x & 31;
+  const int64_t wi = base + lane;
+  word = (wi < w1) ? p.touched[wi] : 0u;
+  if (__ballot_sync(0xffffffffu, word != 0u) == 0u) return 0;
+  const int cnt = __popc(word);
+  int off = cnt;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int t = __shfl_up_sync(0xffffffffu, off, o);
-      if (lane >= o) off += t;
-    }
-    const int total = __shfl_sync(0xffffffffu, off, 31);
-    off -= cnt;
-    uint32_t bits = word;
-    while (bits) {
-      const int b = __ffs(bits) - 1;
-      bits &= bits - 1;
-      list[off++] = (int32_t)(wi * 32 + b);
-    }
-    __syncwarp();
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, off, o);
+    if (lane >= o) off += t;
+  }
+  const int total = __shfl_sync(0xffffffffu, off, 31);
+  off -= cnt;
+  uint32_t bits = word;
+  while (bits) {
+    const int b = __ffs(bits) - 1;
+    bits &= bits - 1;
+    list[off++] = (int32_t)(wi * 32 + b);
+  }
+  __syncwarp();
+  return total;
+}
+
+// Phase B walk: fn(row) for every touched row of the warp's range (list kept when single).
+template <class Fn>
+__device__ __forceinline__ void rows_phase_b(const WalkParams& p, WarpRows& wr, int32_t* list, Fn&& fn) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t base = wr.w0; base < wr.w1; base += kWarp) {
+    uint32_t word;
+    const int total = list_group(p, base, wr.w1, list, word);
     for (int i = lane; i < total; i += kWarp) fn(list[i]);
     __syncwarp();
-    if (clear && word != 0u) p.touched[wi] = 0u;
+    if (wr.single) {
+      wr.word = word;
+      wr.total = total;
+    }
+  }
+}
+
+// Phase C walk: fn(row) for every touched row, then the warp's bitmap words are cleared.
+template <class Fn>
+__device__ __forceinline__ void rows_phase_c(const WalkParams& p, const WarpRows& wr, int32_t* list, Fn&& fn) {
+  const int lane = threadIdx.x & 31;
+  if (wr.single) {
+    for (int i = lane; i < wr.total; i += kWarp) fn(list[i]);
+    if (wr.word != 0u) p.touched[wr.w0 + lane] = 0u;
+    return;
+  }
+  for (int64_t base = wr.w0; base < wr.w1; base += kWarp) {
+    uint32_t word;
+    const int total = list_group(p, base, wr.w1, list, word);
+    for (int i = lane; i < total; i += kWarp) fn(list[i]);
+    __syncwarp();
+    if (word != 0u) p.touched[base + lane] = 0u;
   }
 }
 
@@ -477,8 +648,11 @@ __global__ void __launch_bounds__(kWalkThreads) walk_kernel(WalkParams p) {
   const int wib = tid >> 5;
   const int K = p.K;
   const int G = (int)gridDim.x;
-  uint32_t bar = 0;
-  if (tid == 0) sh.abort = 0;
+  uint32_t bar = 0, n1 = 0, seen = 0;
+  if (tid == 0) {
+    sh.abort = 0;
+    sh.has_nz = 0;
+  }
   __syncthreads();
 
   for (int64_t t = p.t_begin; t < p.t_end; ++t) {
@@ -486,20 +660,14 @@ __global__ void __launch_bounds__(kWalkThreads) walk_kernel(WalkParams p) {
     const int64_t hi = min(p.npos, lo + (int64_t)p.P);
     const int32_t Pt = (int32_t)(hi - lo);
     const uint32_t stamp = p.stamp_base + (uint32_t)(t + 1);
-    uint32_t* anynz = p.anynz + (t % 3);
-    // The flag of bundle t+1 was last read (as bundle t-2's) before barrier 1 of bundle t-1, and
-    // is next written after barrier 1 of bundle t: clear it in between.
-    if (blockIdx.x == 0 && tid == 0) p.anynz[(t + 1) % 3] = 0u;
 
     // ---------------- A: column reductions, directions, scatter
     {
       const int64_t* pl = p.plan + t * (int64_t)(G + 1) + blockIdx.x;
-      column_pass<LOSS, PREC>(p, sh, lo, pl[0], pl[1], stamp, anynz);
+      column_pass<LOSS, PREC>(p, sh, lo, pl[0], pl[1], stamp);
     }
-    if (!grid_barrier(p, bar, sh)) return;
-
-    if (tid == 0) sh.nonzero = (int)*(volatile uint32_t*)anynz;
-    __syncthreads();
+    if (!grid_barrier_flag(p, n1, seen, sh)) return;
+    if (tid == 0) sh.has_nz = 0;  // read by the barrier above; next written in the next column pass
     if (!sh.nonzero) {
       if (blockIdx.x == 0 && tid == 0) {
         if (p.tr_q) p.tr_q[t] = 0;
@@ -517,15 +685,20 @@ __global__ void __launch_bounds__(kWalkThreads) walk_kernel(WalkParams p) {
     Decision dec;
     const int64_t kpb = (Pt + G - 1) / G;  // bundle positions per block
     const int64_t k0 = min((int64_t)Pt, (int64_t)blockIdx.x * kpb), k1 = min((int64_t)Pt, k0 + kpb);
+    // warps that sum the bundle-position terms (about 128 positions each)
+    const int pos_warps = (int)min((int64_t)kWalkWarps, max((int64_t)1, (k1 - k0 + 127) / 128));
     int32_t* list = sh.u.list[wib];
+    WarpRows wr = warp_rows_range(p);
     for (;;) {
       double alpha[kMaxK];
+      float alpha_f[kMaxK];
       {
         double a = 1.0;
         for (int q = 0; q < q0; ++q) a *= p.beta;
 #pragma unroll
         for (int q = 0; q < kMaxK; ++q) {
           alpha[q] = a;
+          alpha_f[q] = (float)a;
           a *= p.beta;
         }
       }
@@ -533,59 +706,95 @@ __global__ void __launch_bounds__(kWalkThreads) walk_kernel(WalkParams p) {
       LsAcc<LOSS, PREC> acc;
       acc.zero();
       int nrows = 0;
-      for_touched_rows(p, list, false, [&](int32_t r) {
-        acc.row(p, r, alpha, K, halving);
+      rows_phase_b(p, wr, list, [&](int32_t r) {
+        acc.row(p, r, alpha, alpha_f, K, halving);
         ++nrows;
       });
-      // bundle-position terms of this block (Eq. 7 parts and the L1 change of each step)
-      double pgd = 0.0, phd = 0.0, pl1 = 0.0, pq[kMaxK];
-#pragma unroll
-      for (int q = 0; q < kMaxK; ++q) pq[q] = 0.0;
-      for (int64_t kl = k0 + tid; kl < k1; kl += kWalkThreads) {
-        const double d = p.dk[kl];
-        if (d == 0.0) continue;
-        const double wj = p.w_pos[lo + kl];
-        pgd += p.gk[kl] * d;
-        phd += p.hk[kl] * d * d;
-        pl1 += fabs(wj + d) - fabs(wj);
-#pragma unroll
-        for (int q = 0; q < kMaxK; ++q)
-          if (q < K) pq[q] += fabs(wj + alpha[q] * d) - fabs(wj);
-      }
-      // block reduction in fixed order: lanes (tree), then warps
+      // line-search sums of this warp
       {
-        double v[kPartStride];
-        v[0] = warp_sum(pgd);
-        v[1] = warp_sum(phd);
-        v[2] = warp_sum(pl1);
+        nrows = warp_sum_int(nrows);
 #pragma unroll
         for (int q = 0; q < kMaxK; ++q) {
-          v[3 + q] = (q < K) ? warp_sum(pq[q]) : 0.0;
-          v[3 + kMaxK + q] = (q < K) ? warp_sum(acc.get(q)) : 0.0;
+          if (q < K) {
+            Acc<PREC> a = acc.get(q);
+            a.warp_reduce();
+            if (lane == 0) sh.red[wib][3 + kMaxK + q] = a.store();
+          }
         }
-        v[3 + 2 * kMaxK] = (double)warp_sum_int(nrows);
-        if (lane == 0) {
+      }
+      // bundle-position terms (Eq. 7 parts and the L1 change of each step)
+      if (wib < pos_warps) {
+        Acc<PREC> pgd, phd, pl1, pq[kMaxK];
+        for (int64_t kl = k0 + wib * 32 + lane; kl < k1; kl += 32 * pos_warps) {
+          const double d = p.dk[kl];
+          if (d == 0.0) continue;
+          const double wj = p.w_pos[lo + kl];
+          pgd.add(p.gk[kl] * d);
+          phd.add(p.hk[kl] * d * d);
+          pl1.add(fabs(wj + d) - fabs(wj));
 #pragma unroll
-          for (int f = 0; f < kPartStride; ++f) sh.red[wib][f] = v[f];
+          for (int q = 0; q < kMaxK; ++q)
+            if (q < K) pq[q].add(fabs(wj + alpha[q] * d) - fabs(wj));
         }
-        __syncthreads();
-        if (tid < kPartStride) {
+        pgd.warp_reduce();
+        phd.warp_reduce();
+        pl1.warp_reduce();
+        if (lane == 0) {
+          sh.red[wib][0] = pgd.store();
+          sh.red[wib][1] = phd.store();
+          sh.red[wib][2] = pl1.store();
+        }
+#pragma unroll
+        for (int q = 0; q < kMaxK; ++q) {
+          if (q < K) {
+            pq[q].warp_reduce();
+            if (lane == 0) sh.red[wib][3 + q] = pq[q].store();
+          }
+        }
+      }
+      if (lane == 0) sh.red[wib][3 + 2 * kMaxK] = (double)nrows;
+      __syncthreads();
+      // block total of each field, warps in order
+      if (tid < kPartStride) {
+        const int f = tid;
+        double out;
+        if (f == 3 + 2 * kMaxK) {
           double s = 0.0;
-          for (int wv = 0; wv < kWalkWarps; ++wv) s += sh.red[wv][tid];
-          p.cta_part[(int64_t)blockIdx.x * kPartStride + tid] = s;
+          for (int wv = 0; wv < kWalkWarps; ++wv) s += sh.red[wv][f];
+          out = s;
+        } else {
+          Acc<PREC> s;
+          const bool posf = f < 3 + kMaxK;
+          const int nw = posf ? pos_warps : kWalkWarps;
+          if ((f >= 3 && f < 3 + kMaxK && f - 3 >= K) || (f >= 3 + kMaxK && f - 3 - kMaxK >= K)) {
+            out = s.store();
+          } else {
+            for (int wv = 0; wv < nw; ++wv) s.add_acc(Acc<PREC>::load(sh.red[wv][f]));
+            out = s.store();
+          }
         }
+        p.cta_part[(int64_t)blockIdx.x * kPartStride + f] = out;
       }
       const int qbase = q0;
       const bool ok = grid_barrier_reduce(p, bar, sh, [&]() {
-        // block-order reduction of all partials, then the Armijo decision (Eq. 6)
-        double* tot = sh.tot;
-        if (tid < kPartStride) {
-          double s = 0.0;
-          for (int b = 0; b < G; ++b) s += __ldcg(p.cta_part + (int64_t)b * kPartStride + tid);
-          tot[tid] = s;
+        // block-order reduction of all partials: warp w takes fields w, w+8, ...; lanes stride
+        // over the blocks; then a fixed lane tree.  Then the Armijo decision (Eq. 6).
+        for (int f = wib; f < kPartStride; f += kWalkWarps) {
+          if (f == 3 + 2 * kMaxK) {
+            double s = 0.0;
+            for (int b = lane; b < G; b += kWarp) s += __ldcg(p.cta_part + (int64_t)b * kPartStride + f);
+            s = warp_sum(s);
+            if (lane == 0) sh.tot[f] = s;
+          } else {
+            Acc<PREC> s;
+            for (int b = lane; b < G; b += kWarp) s.add_acc(Acc<PREC>::load(__ldcg(p.cta_part + (int64_t)b * kPartStride + f)));
+            s.warp_reduce();
+            if (lane == 0) sh.tot[f] = s.value();
+          }
         }
         __syncthreads();
         if (tid == 0) {
+          const double* tot = sh.tot;
           const double gd = tot[0], hdd = tot[1], l1 = tot[2];
           const double Delta = gd + p.gamma * hdd + l1;
           Decision dd;
@@ -599,7 +808,7 @@ __global__ void __launch_bounds__(kWalkThreads) walk_kernel(WalkParams p) {
             double dF;
             if constexpr (PREC == 0) dF = p.c * tot[3 + kMaxK + q] + tot[3 + q];
             else dF = a * gd + p.c * tot[3 + kMaxK + q] + tot[3 + q];
-            if (!(dF == dF)) atomicOr(p.err, kErrNumeric);
+            // a NaN change (an overflowing trial step) fails the test, as in Eq. 6 read literally
             if (dF <= p.sigma * a * Delta) {
               dd.state = kDecAccept;
               dd.q = qbase + q;
@@ -625,19 +834,22 @@ __global__ void __launch_bounds__(kWalkThreads) walk_kernel(WalkParams p) {
             if (p.tr_Delta) p.tr_Delta[t] = Delta;
             if (p.tr_dF) p.tr_dF[t] = dd.dF;
           }
-          *p.decision = dd;
+          if (G > 1) *p.decision = dd;
+          sh.dec = dd;
         }
       });
       if (!ok) return;
-      if (tid == 0) {
-        const volatile Decision* vd = p.decision;
-        sh.dec.state = vd->state;
-        sh.dec.q = vd->q;
-        sh.dec.alpha = vd->alpha;
-        sh.dec.Delta = vd->Delta;
-        sh.dec.dF = vd->dF;
+      if (G > 1 && !sh.last) {
+        if (tid == 0) {
+          const volatile Decision* vd = p.decision;
+          sh.dec.state = vd->state;
+          sh.dec.q = vd->q;
+          sh.dec.alpha = vd->alpha;
+          sh.dec.Delta = vd->Delta;
+          sh.dec.dF = vd->dF;
+        }
+        __syncthreads();
       }
-      __syncthreads();
       dec = sh.dec;
       if (dec.state != kDecContinue) break;
       q0 = dec.q;
@@ -652,7 +864,7 @@ __global__ void __launch_bounds__(kWalkThreads) walk_kernel(WalkParams p) {
         if (d != 0.0) p.w_pos[lo + kl] += a * d;
       }
     }
-    for_touched_rows(p, list, true, [&](int32_t r) {
+    rows_phase_c(p, wr, list, [&](int32_t r) {
       if (accept) row_update<LOSS, PREC>(p, r, a);
       p.delta[r] = 0.0;
     });

@@ -245,6 +245,47 @@ def test_maintained_line_search_equals_direct(loss):
             np.testing.assert_allclose(mq1, o.maintained(w1), rtol=1e-12, atol=1e-12)
 
 
+@pytest.mark.parametrize("scale", [30.0, 80.0, 400.0])
+def test_maintained_line_search_exact_at_extreme_margins(scale):
+    # Section 3.1: Eq. 10 is the objective change of Eq. 6.  With |w^T x_i| in the tens or hundreds
+    # (saturated samples), the maintained value must still equal the objective difference from the
+    # definition, and no ascent step may be accepted (Lemma 1(c)).
+    p, X, y = tiny("logistic", n=60, m=16, seed=31, density=0.5)
+    o = oracle.Oracle.from_problem(p, 1.0, "logistic")
+    rng = np.random.default_rng(int(scale))
+    accepted = 0
+    for trial in range(12):
+        w = rand_w(p.n_features, rng, frac=0.8, scale=scale / 4)
+        z = X @ w
+        if np.abs(z).max() > 700:
+            continue
+        mq = o.maintained(w)
+        B = rng.choice(p.n_features, size=8, replace=False)
+        w1, _, r = o.bundle_step(w, mq, B)
+        if r["status"] != 0:
+            continue
+        F0 = D.F(X, y, w, 1.0, "logistic")
+        dF_def = D.F(X, y, w1, 1.0, "logistic") - F0
+        assert r["dF"] == pytest.approx(dF_def, rel=1e-9, abs=1e-9 * max(1.0, abs(F0)))
+        assert dF_def <= 1e-9 * max(1.0, abs(F0))
+        accepted += 1
+    assert accepted >= 4
+
+
+def test_row_loss_change_against_the_definition():
+    # one sample: the line search's loss change against phi(z0 + u) - phi(z0) from Eq. 2 evaluated
+    # with log-sum-exp, for margins up to |z0| = 600 and steps of either sign up to 900
+    X = np.array([[1.0]])
+    cp, ri, vv = D.dense_to_csc(X)
+    for ysign in (1, -1):
+        o = oracle.Oracle(cp, ri, vv, np.array([ysign], dtype=np.int8), 1.0, "logistic")
+        for z0 in (-600.0, -60.0, -1.0, 0.0, 3.0, 60.0, 600.0):
+            for u in (-900.0, -50.0, -1.0, -1e-6, 1e-6, 1.0, 50.0, 900.0):
+                ref = float(np.logaddexp(0, -ysign * (z0 + u)) - np.logaddexp(0, -ysign * z0))
+                got = o.row_loss_change(np.exp(z0), ysign, u)
+                assert got == pytest.approx(ref, rel=1e-11, abs=1e-12 * max(1.0, abs(z0))), (ysign, z0, u, got, ref)
+
+
 @pytest.mark.parametrize("loss,theta", [("logistic", 0.25), ("l2svm", 2.0)])
 def test_delta_bound_descent_and_step_lower_bound(loss, theta):
     # Lemma 1(c), Eq. 14-15: Delta <= (gamma - 1) d^T H d <= 0 and F(w + a d) - F(w) <= sigma a Delta <= 0.

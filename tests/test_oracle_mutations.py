@@ -25,7 +25,8 @@ MUTANTS = [
      "if (dF <= a * Delta) { accepted = 1; break; }"),
     ("update_drops_alpha", "if (p->loss == OR_LOSS_LOGISTIC) mq[i] *= exp(alpha * dx[i]);",
      "if (p->loss == OR_LOSS_LOGISTIC) mq[i] *= exp(dx[i]);"),
-    ("lr_label_term", "return t + (y_i < 0 ? u : 0.0);", "return t + (y_i > 0 ? u : 0.0);"),
+    ("lr_label_term", "return log1p(expm1(-u) / (1.0 + E)) + (y_i < 0 ? u : 0.0);",
+     "return log1p(expm1(-u) / (1.0 + E)) + (y_i > 0 ? u : 0.0);"),
     ("dx_overwrites", "dx[p->row_idx[e]] += d[k] * (double)p->val[e];", "dx[p->row_idx[e]] = d[k] * (double)p->val[e];"),
     ("kkt_branch_swap", "else v = fabs(g) > 1.0 ? (g > 0 ? g - 1.0 : g + 1.0) : 0.0;",
      "else v = fabs(g) > 1.0 ? (g > 0 ? g + 1.0 : g - 1.0) : 0.0;"),
@@ -34,6 +35,8 @@ MUTANTS = [
     ("perm_key_index", "return or_splitmix64_output(s_epoch, (uint64_t)j + 1);",
      "return or_splitmix64_output(s_epoch, (uint64_t)j);"),
     ("nu_ignored", "if (h <= 0.0) h = nu;", "if (h < 0.0) h = nu;"),
+    # Eq. 10's log-ratio taken literally for every sample (cancels at large margins)
+    ("eq10_literal", "      if (E <= 1.0) return log1p(E / (1.0 + E) * expm1(u)) - (y_i > 0 ? u : 0.0);\n", ""),
 ]
 
 
@@ -49,6 +52,8 @@ def _pins():
         ("lr_hess", T.test_logistic_hessian_matches_second_differences),
         ("svm_hess", T.test_svm_generalised_hessian_matches_second_differences),
         ("nu", T.test_nu_replaces_zero_hessian),
+        ("loss_change", T.test_row_loss_change_against_the_definition),
+        ("extreme", lambda: T.test_maintained_line_search_exact_at_extreme_margins(80.0)),
     ]
     for loss in ("logistic", "l2svm"):
         out += [
