@@ -469,7 +469,8 @@ int run_walk(pcdn_problem* p, const pcdn_opts* o, const int32_t* perm, int64_t n
   w.gamma = o->gamma;
   w.nu = o->nu;
   w.q_max = o->q_max;
-  w.K = o->ls_batch > 0 ? o->ls_batch : (o->prec == PCDN_PREC_MIXED ? 8 : 4);
+  // step sizes per pass: most bundles accept q = 0, and a further pass costs one barrier
+  w.K = o->ls_batch > 0 ? o->ls_batch : 2;
   w.tr_q = p->tr_q;
   w.tr_alpha = p->tr_alpha;
   w.tr_Delta = p->tr_Delta;

@@ -18,13 +18,14 @@
 namespace pcdn {
 
 constexpr int kWarp = 32;
-constexpr int kChunk = 2048;       // max nonzeros of one column work item
+constexpr int kChunk = 1024;       // max nonzeros of one column work item
 constexpr int kMaxK = 8;           // max step sizes per line-search pass
 constexpr int kWalkThreads = 256;  // threads per walker block
 constexpr int kWalkWarps = kWalkThreads / kWarp;
 constexpr int kListCap = 1024;     // touched rows listed per warp per 32 bitmap words
 constexpr int kICap = 256;         // work items staged per batch of the column pass
 constexpr int kECap = 2048;        // nonzeros staged per batch (= 8 per thread)
+constexpr int kSplitCap = 64;      // chunks of split columns a block remembers for its deferred scatter
 
 constexpr int kErrTimeout = 1;
 constexpr int kErrNumeric = 2;       // non-finite g, h or d
@@ -306,6 +307,10 @@ __device__ __forceinline__ dfloat df_add_f(dfloat a, float b) {
   return df_add(a, t);
 }
 __device__ __forceinline__ double df_value(dfloat a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ dfloat df_neg(dfloat a) { return dfloat{-a.hi, -a.lo}; }
+__device__ __forceinline__ dfloat df_abs(dfloat a) { return (a.hi < 0.0f || (a.hi == 0.0f && a.lo < 0.0f)) ? df_neg(a) : a; }
+// scaling by a power of two is exact
+__device__ __forceinline__ dfloat df_scale(dfloat a, float s) { return dfloat{a.hi * s, a.lo * s}; }
 __device__ __forceinline__ dfloat df_shfl_xor(dfloat a, int o) {
   dfloat r;
   r.hi = __shfl_xor_sync(0xffffffffu, a.hi, o);

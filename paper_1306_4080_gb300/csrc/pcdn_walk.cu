@@ -56,6 +56,10 @@ struct SharedWalk {
   int last;
   int has_nz;
   int nonzero;
+  int n_split;
+  int split_ok;
+  double split_d;
+  int64_t split_items[kSplitCap];
   int scan_tot[kWalkWarps];
   Decision dec;
   double tot[kPartStride];
@@ -277,6 +281,8 @@ __device__ void column_pass(const WalkParams& p, SharedWalk<PREC>& sh, int64_t l
   const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
   StageA<PREC>& st = sh.u.a;
   const RecT<PREC>* rec = (const RecT<PREC>*)p.rec;
+  if (tid == 0) sh.n_split = 0;
+  __syncthreads();
   for (int64_t i = i0; i < i1;) {
     const int nload = (int)min((int64_t)kICap, i1 - i);
     // wave 1: item records and w_j
@@ -293,6 +299,11 @@ __device__ void column_pass(const WalkParams& p, SharedWalk<PREC>& sh, int64_t l
     int nb = __syncthreads_count(tid < nload && incl <= kECap);  // the fitting items are a prefix
     if (nb == 0) nb = 1;  // an item never exceeds kECap (kChunk <= kECap)
     const int eb = st.ioff[nb];
+    // chunks of split columns processed by this batch, for the deferred scatter
+    if (tid < nb && st.items[tid].nch > 1) {
+      const int k = atomicAdd(&sh.n_split, 1);
+      if (k < kSplitCap) sh.split_items[k] = i + tid;
+    }
     // waves 2 and 3: row indices and values, then the rows' coefficient pairs
     {
       int32_t rr[kECap / kWalkThreads];
@@ -354,12 +365,23 @@ __device__ void column_pass(const WalkParams& p, SharedWalk<PREC>& sh, int64_t l
       last = __shfl_sync(0xffffffffu, last, 0);
       __syncwarp();
       if (last) {
-        // fixed-order combine of the column's chunks: lane l sums chunks l, l+32, ..., then a tree
+        // fixed-order combine of the column's chunks: lane l sums chunks l, l+32, ... (eight loads
+        // in flight per lane), then a tree
         const int64_t first = gi - it.chunk;
         double gs = 0.0, hs = 0.0;
-        for (int cch = lane; cch < it.nch; cch += kWarp) {
-          gs += p.part[2 * (first + cch)];
-          hs += p.part[2 * (first + cch) + 1];
+        for (int base = 0; base < it.nch; base += 8 * kWarp) {
+          double gv[8], hv[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int cch = base + u * kWarp + lane;
+            gv[u] = cch < it.nch ? __ldcg(p.part + 2 * (first + cch)) : 0.0;
+            hv[u] = cch < it.nch ? __ldcg(p.part + 2 * (first + cch) + 1) : 0.0;
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            gs += gv[u];
+            hs += hv[u];
+          }
         }
         gs = warp_sum(gs);
         hs = warp_sum(hs);
@@ -394,25 +416,48 @@ __device__ void column_pass(const WalkParams& p, SharedWalk<PREC>& sh, int64_t l
     __syncthreads();  // the staging area is reused by the next batch
     i += nb;
   }
-  // chunks of split columns scatter once their column's direction is published
-  for (int64_t i = i0 + wib; i < i1; i += kWalkWarps) {
-    const Item it = p.items[i];
-    if (it.nch == 1) continue;
+  // chunks of split columns scatter once their column's direction is published: the whole block
+  // takes one chunk at a time, eight loads in flight per thread.  The chunks are the ones listed
+  // during the batches, or, when there were more than kSplitCap, every split chunk of [i0, i1).
+  __syncthreads();
+  const int ns = sh.n_split;
+  const bool listed = ns <= kSplitCap;
+  const int64_t n_iter = listed ? (int64_t)ns : (i1 - i0);
+  for (int64_t k = 0; k < n_iter; ++k) {
+    const int64_t gi = listed ? sh.split_items[k] : i0 + k;
+    const Item it = p.items[gi];
+    if (it.nch == 1) continue;  // only on the unlisted path
     const int32_t kl = (int32_t)(it.pos - lo);
-    int ok = 1;
-    double d = 0.0;
-    if (lane == 0) {
+    if (tid == 0) {
       uint32_t spins = 0;
+      int ok = 1;
       while (ld_acquire_u32(p.col_ready + kl) != stamp) {
         if (++spins > p.spin_limit) { atomicOr(p.err, kErrTimeout); ok = 0; break; }
         if ((spins & 1023u) == 0 && err_set(p)) { ok = 0; break; }
       }
-      if (ok) d = p.dk[kl];
+      sh.split_ok = ok;
+      sh.split_d = ok ? __ldcg(p.dk + kl) : 0.0;
     }
-    ok = __shfl_sync(0xffffffffu, ok, 0);
-    d = __shfl_sync(0xffffffffu, d, 0);
+    __syncthreads();
+    const int ok = sh.split_ok;
+    const double d = sh.split_d;
+    __syncthreads();
     if (!ok) break;
-    if (d != 0.0) item_scatter_global<PREC>(p, it, d);
+    if (d == 0.0) continue;
+    int32_t rr[kChunk / kWalkThreads];
+    float xx[kChunk / kWalkThreads];
+#pragma unroll
+    for (int u = 0; u < kChunk / kWalkThreads; ++u) {
+      const int v = tid + u * kWalkThreads;
+      rr[u] = -1;
+      if (v < it.len) {
+        rr[u] = p.row_idx[it.start + v];
+        xx[u] = p.val[it.start + v];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kChunk / kWalkThreads; ++u)
+      if (rr[u] >= 0) scatter_one(p, rr[u], scatter_value<PREC>(d, xx[u]));
   }
 }
 
@@ -732,9 +777,17 @@ __global__ void __launch_bounds__(kWalkThreads) walk_kernel(WalkParams p) {
           pgd.add(p.gk[kl] * d);
           phd.add(p.hk[kl] * d * d);
           pl1.add(fabs(wj + d) - fabs(wj));
+          if constexpr (PREC == 0) {
 #pragma unroll
-          for (int q = 0; q < kMaxK; ++q)
-            if (q < K) pq[q].add(fabs(wj + alpha[q] * d) - fabs(wj));
+            for (int q = 0; q < kMaxK; ++q)
+              if (q < K) pq[q].add(fabs(wj + alpha[q] * d) - fabs(wj));
+          } else {
+            // |w + a d| - |w| in double-float arithmetic (a is a power of two when beta = 1/2)
+            const dfloat wd = df_make(wj), dd = df_make(d), aw = df_neg(df_abs(wd));
+#pragma unroll
+            for (int q = 0; q < kMaxK; ++q)
+              if (q < K) pq[q].v = df_add(pq[q].v, df_add(df_abs(df_add(wd, df_scale(dd, alpha_f[q]))), aw));
+          }
         }
         pgd.warp_reduce();
         phd.warp_reduce();
@@ -780,14 +833,27 @@ __global__ void __launch_bounds__(kWalkThreads) walk_kernel(WalkParams p) {
         // block-order reduction of all partials: warp w takes fields w, w+8, ...; lanes stride
         // over the blocks; then a fixed lane tree.  Then the Armijo decision (Eq. 6).
         for (int f = wib; f < kPartStride; f += kWalkWarps) {
-          if (f == 3 + 2 * kMaxK) {
-            double s = 0.0;
-            for (int b = lane; b < G; b += kWarp) s += __ldcg(p.cta_part + (int64_t)b * kPartStride + f);
-            s = warp_sum(s);
-            if (lane == 0) sh.tot[f] = s;
+          const bool rows_f = f == 3 + 2 * kMaxK;
+          if ((f >= 3 + K && f < 3 + kMaxK) || (f >= 3 + kMaxK + K && !rows_f)) continue;  // unused step sizes
+          double rs = 0.0;
+          Acc<PREC> s;
+          for (int base = 0; base < G; base += 8 * kWarp) {
+            double v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              const int b = base + u * kWarp + lane;
+              v[u] = b < G ? __ldcg(p.cta_part + (int64_t)b * kPartStride + f) : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              if (rows_f) rs += v[u];
+              else if (base + u * kWarp + lane < G) s.add_acc(Acc<PREC>::load(v[u]));
+            }
+          }
+          if (rows_f) {
+            rs = warp_sum(rs);
+            if (lane == 0) sh.tot[f] = rs;
           } else {
-            Acc<PREC> s;
-            for (int b = lane; b < G; b += kWarp) s.add_acc(Acc<PREC>::load(__ldcg(p.cta_part + (int64_t)b * kPartStride + f)));
             s.warp_reduce();
             if (lane == 0) sh.tot[f] = s.value();
           }
