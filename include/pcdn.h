@@ -161,6 +161,28 @@ int pcdn_permutation(pcdn_problem* prob, uint64_t seed, int64_t epoch, int32_t* 
 /* Device-resident sizes (bytes) held by the problem. */
 int pcdn_memory(pcdn_problem* prob, int64_t* bytes);
 
+/* Objective without allocation.
+ *
+ * For callers that may not allocate device memory (an application that owns all GPU memory
+ * through its own pool or budget, or a request loop that allows no allocator calls): the
+ * objective F(w) = C * sum_i phi(w; x_i, y_i) + ||w||_1 from the caller's device buffers,
+ * with no cudaMalloc, cudaFree or other allocating call.  The paper has no counterpart; the
+ * value equals pcdn_objective's for the same X, y, C, loss and w (up to summation order).
+ *
+ * X's arrays, y (n_samples labels in {-1, +1}), w (n_features doubles) and F (one double,
+ * written) are device pointers; the call only enqueues work on `stream` (a cudaStream_t, NULL =
+ * the legacy default stream) and returns: F is ready once that stream has reached this work.
+ * Its scratch (z = Xw and per-block partial sums) is one fixed array of about 2 MiB inside the
+ * library, held on every GPU that loads the library until the process exits; hence
+ * n_samples <= PCDN_NOALLOC_MAX_SAMPLES, larger problems return PCDN_EINVAL.  The first call
+ * on a device looks up that array's device address (cudaGetSymbolAddress) and keeps it: make
+ * that first call before any stream capture.  All calls share the array, so calls that may
+ * run at the same time on the GPU race: order them (one stream, or events).  A row index
+ * outside [0, n_samples) makes F NaN.  Errors: PCDN_EINVAL, PCDN_ECUDA. */
+#define PCDN_NOALLOC_MAX_SAMPLES 262144
+int pcdn_objective_noalloc(const pcdn_csc* X, const int8_t* y, double C, pcdn_loss loss, const double* w,
+                           double* F, void* stream);
+
 void pcdn_destroy(pcdn_problem* prob);
 /* Message of the last failed call on this thread ("" if none). */
 const char* pcdn_last_error(void);

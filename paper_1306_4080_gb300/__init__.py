@@ -31,7 +31,8 @@ PRECISIONS = {"fp64": 0, "mixed": 1}
 
 SYMBOLS = ["pcdn_default_opts", "pcdn_create", "pcdn_create_device", "pcdn_solve", "pcdn_bundle_step",
            "pcdn_set_w", "pcdn_get_w", "pcdn_objective", "pcdn_kkt", "pcdn_permutation", "pcdn_memory",
-           "pcdn_destroy", "pcdn_last_error"]
+           "pcdn_destroy", "pcdn_last_error", "pcdn_objective_noalloc"]
+PCDN_NOALLOC_MAX_SAMPLES = 262144
 
 
 class PcdnError(RuntimeError):
@@ -107,6 +108,8 @@ def load() -> ctypes.CDLL:
     lib.pcdn_destroy.restype = None
     lib.pcdn_last_error.argtypes = []
     lib.pcdn_last_error.restype = ctypes.c_char_p
+    lib.pcdn_objective_noalloc.argtypes = [P(pcdn_csc), vp, d, ctypes.c_int, vp, vp, vp]
+    lib.pcdn_objective_noalloc.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -241,6 +244,17 @@ def pcdn_permutation(h: int, seed: int, epoch: int, n_features: int) -> np.ndarr
     perm = np.empty(int(n_features), dtype=np.int32)
     _check(load().pcdn_permutation(h, int(seed) & (2**64 - 1), int(epoch), perm.ctypes.data))
     return perm
+
+
+def pcdn_objective_noalloc(col_ptr, row_idx, val, y, C: float, loss: str, w, F, stream=None) -> None:
+    """F(w) into the one-element device tensor F from device tensors, allocating nothing on the
+    device (see include/pcdn.h).  Enqueues on ``stream`` (torch.cuda.Stream, raw handle or None)."""
+    lib = load()
+    X = pcdn_csc(int(y.shape[0]), int(col_ptr.shape[0] - 1), int(row_idx.shape[0]), col_ptr.data_ptr(),
+                 row_idx.data_ptr(), val.data_ptr())
+    s = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    _check(lib.pcdn_objective_noalloc(ctypes.byref(X), y.data_ptr(), float(C), LOSSES[loss], w.data_ptr(),
+                                      F.data_ptr(), s))
 
 
 def pcdn_memory(h: int) -> int:

@@ -31,6 +31,14 @@ namespace {
 
 thread_local std::string g_err;
 
+}  // namespace
+
+namespace pcdn {
+void set_last_error(const char* msg) { g_err = msg; }
+}  // namespace pcdn
+
+namespace {
+
 int fail(int code, const char* fmt, ...) {
   char buf[512];
   va_list ap;
