@@ -340,46 +340,56 @@ __device__ __forceinline__ double row_loss(int loss, double z, int y) {
   return b > 0 ? b * b : 0.0;
 }
 
+// One lane per row; each lane walks its row in column order with eight loads in flight, using a
+// separate multiply and add per nonzero (the same rounding as a column-by-column accumulation).
 template <int LOSS, int PREC>
 __global__ void __launch_bounds__(kRedThreads) refresh_kernel(const int64_t* row_ptr, const int32_t* col_idx,
                                                               const float* rval, const int8_t* y, const double* w,
                                                               int64_t n, double* mq, void* rec, int write_state,
                                                               double* loss_part, int* err) {
-  __shared__ double wsum[kRedThreads / 32];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int64_t warps = (int64_t)gridDim.x * (kRedThreads / 32);
+  __shared__ double wsum[kRedThreads];
   double lsum = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * (kRedThreads / 32) + wid; i < n; i += warps) {
+  for (int64_t i = (int64_t)blockIdx.x * kRedThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kRedThreads) {
+    const int64_t a = row_ptr[i], b = row_ptr[i + 1];
     double z = 0.0;
-    for (int64_t e = row_ptr[i] + lane; e < row_ptr[i + 1]; e += 32) {
-      const double wj = w[col_idx[e]];
-      if (wj != 0.0) z = fma((double)rval[e], wj, z);
-    }
-    z = warp_sum(z);
-    if (lane == 0) {
-      const int yi = y[i];
-      if (loss_part) lsum += row_loss(LOSS, z, yi);
-      if (write_state) {
-        double v;
-        if (LOSS == 0) {
-          if (fabs(z) > 700.0) atomicOr(err, kErrRefresh);
-          v = exp(z);
-        } else {
-          v = 1.0 - (double)yi * z;
-        }
-        mq[i] = v;
-        ((RecT<PREC>*)rec)[i] = RowCoef<LOSS, PREC>::make(v, yi);
+    for (int64_t e0 = a; e0 < b; e0 += 8) {
+      int32_t c[8];
+      float v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int64_t e = e0 + u;
+        c[u] = e < b ? col_idx[e] : -1;
+        v[u] = e < b ? rval[e] : 0.0f;
       }
+      double wv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) wv[u] = c[u] >= 0 ? w[c[u]] : 0.0;
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (wv[u] != 0.0) z = __dadd_rn(z, __dmul_rn((double)v[u], wv[u]));
+    }
+    const int yi = y[i];
+    if (loss_part) lsum += row_loss(LOSS, z, yi);
+    if (write_state) {
+      double v;
+      if (LOSS == 0) {
+        if (fabs(z) > 700.0) atomicOr(err, kErrRefresh);
+        v = exp(z);
+      } else {
+        v = 1.0 - (double)yi * z;
+      }
+      mq[i] = v;
+      ((RecT<PREC>*)rec)[i] = RowCoef<LOSS, PREC>::make(v, yi);
     }
   }
   if (loss_part) {
-    if (lane == 0) wsum[wid] = lsum;
+    wsum[threadIdx.x] = lsum;
     __syncthreads();
-    if (threadIdx.x == 0) {
-      double s = 0.0;
-      for (int k = 0; k < kRedThreads / 32; ++k) s += wsum[k];
-      loss_part[blockIdx.x] = s;
+    for (int o = kRedThreads / 2; o > 0; o >>= 1) {
+      if (threadIdx.x < o) wsum[threadIdx.x] += wsum[threadIdx.x + o];
+      __syncthreads();
     }
+    if (threadIdx.x == 0) loss_part[blockIdx.x] = wsum[0];
   }
 }
 

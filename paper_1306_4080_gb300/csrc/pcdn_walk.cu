@@ -482,11 +482,8 @@ struct LsAcc<LOSS, 0> {
 #pragma unroll
     for (int q = 0; q < kMaxK; ++q) s[q] = 0.0;
   }
-  __device__ __forceinline__ void row(const WalkParams& p, int32_t r, const double* alpha, const float*, int K,
+  __device__ __forceinline__ void row(double dl, double mq, int y, const double* alpha, const float*, int K,
                                       bool halving) {
-    const double dl = p.delta[r];
-    const double mq = p.mq[r];
-    const int y = p.y[r];
     if constexpr (LOSS == 0) {
       // form A (E <= 1): coefficient p, expm1(+u), label term -[y=+1] u
       // form B (E > 1):  coefficient s, expm1(-u), label term +[y=-1] u
@@ -542,11 +539,8 @@ struct LsAcc<LOSS, 1> {
 #pragma unroll
     for (int q = 0; q < kMaxK; ++q) { s[q] = 0.0f; cmp[q] = 0.0f; }
   }
-  __device__ __forceinline__ void row(const WalkParams& p, int32_t r, const double* alpha, const float* alpha_f, int K,
+  __device__ __forceinline__ void row(double dl, double mq, int y, const double* alpha, const float* alpha_f, int K,
                                       bool) {
-    const double dl = p.delta[r];
-    const double mq = p.mq[r];
-    const int y = p.y[r];
     const float dlf = (float)dl;
     if constexpr (LOSS == 0) {
       float e = (float)mq, pp, ss;
@@ -579,10 +573,7 @@ struct LsAcc<LOSS, 1> {
 
 // Update of one touched row after acceptance with step alpha (Algorithm 4).
 template <int LOSS, int PREC>
-__device__ __forceinline__ void row_update(const WalkParams& p, int32_t r, double alpha) {
-  const double dl = p.delta[r];
-  double mq = p.mq[r];
-  const int y = p.y[r];
+__device__ __forceinline__ void row_update(const WalkParams& p, int32_t r, double dl, double mq, int y, double alpha) {
   if constexpr (LOSS == 0) {
     if constexpr (PREC == 0) {
       mq = mq * exp(alpha * dl);
@@ -649,14 +640,40 @@ __device__ __forceinline__ int list_group(const WalkParams& p, int64_t base, int
   return total;
 }
 
-// Phase B walk: fn(row) for every touched row of the warp's range (list kept when single).
+// fn(row, d^T x, maintained, label) for listed rows [0, total), four rows per lane in flight.
+template <class Fn>
+__device__ __forceinline__ void for_listed_rows(const WalkParams& p, const int32_t* list, int total, Fn&& fn) {
+  const int lane = threadIdx.x & 31;
+  for (int i0 = lane; i0 < total; i0 += 4 * kWarp) {
+    int32_t r[4];
+    double dl[4], mq[4];
+    int yv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = i0 + u * kWarp;
+      r[u] = i < total ? list[i] : -1;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (r[u] >= 0) {
+        dl[u] = p.delta[r[u]];
+        mq[u] = p.mq[r[u]];
+        yv[u] = p.y[r[u]];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (r[u] >= 0) fn(r[u], dl[u], mq[u], yv[u]);
+  }
+}
+
+// Phase B walk over the warp's range (the listing is kept when the range is one group).
 template <class Fn>
 __device__ __forceinline__ void rows_phase_b(const WalkParams& p, WarpRows& wr, int32_t* list, Fn&& fn) {
-  const int lane = threadIdx.x & 31;
   for (int64_t base = wr.w0; base < wr.w1; base += kWarp) {
     uint32_t word;
     const int total = list_group(p, base, wr.w1, list, word);
-    for (int i = lane; i < total; i += kWarp) fn(list[i]);
+    for_listed_rows(p, list, total, fn);
     __syncwarp();
     if (wr.single) {
       wr.word = word;
@@ -665,19 +682,19 @@ __device__ __forceinline__ void rows_phase_b(const WalkParams& p, WarpRows& wr, 
   }
 }
 
-// Phase C walk: fn(row) for every touched row, then the warp's bitmap words are cleared.
+// Phase C walk: every touched row, then the warp's bitmap words are cleared.
 template <class Fn>
 __device__ __forceinline__ void rows_phase_c(const WalkParams& p, const WarpRows& wr, int32_t* list, Fn&& fn) {
   const int lane = threadIdx.x & 31;
   if (wr.single) {
-    for (int i = lane; i < wr.total; i += kWarp) fn(list[i]);
+    for_listed_rows(p, list, wr.total, fn);
     if (wr.word != 0u) p.touched[wr.w0 + lane] = 0u;
     return;
   }
   for (int64_t base = wr.w0; base < wr.w1; base += kWarp) {
     uint32_t word;
     const int total = list_group(p, base, wr.w1, list, word);
-    for (int i = lane; i < total; i += kWarp) fn(list[i]);
+    for_listed_rows(p, list, total, fn);
     __syncwarp();
     if (word != 0u) p.touched[base + lane] = 0u;
   }
@@ -751,8 +768,8 @@ __global__ void __launch_bounds__(kWalkThreads) walk_kernel(WalkParams p) {
       LsAcc<LOSS, PREC> acc;
       acc.zero();
       int nrows = 0;
-      rows_phase_b(p, wr, list, [&](int32_t r) {
-        acc.row(p, r, alpha, alpha_f, K, halving);
+      rows_phase_b(p, wr, list, [&](int32_t, double dl, double mq, int y) {
+        acc.row(dl, mq, y, alpha, alpha_f, K, halving);
         ++nrows;
       });
       // line-search sums of this warp
@@ -930,8 +947,8 @@ __global__ void __launch_bounds__(kWalkThreads) walk_kernel(WalkParams p) {
         if (d != 0.0) p.w_pos[lo + kl] += a * d;
       }
     }
-    rows_phase_c(p, wr, list, [&](int32_t r) {
-      if (accept) row_update<LOSS, PREC>(p, r, a);
+    rows_phase_c(p, wr, list, [&](int32_t r, double dl, double mq, int y) {
+      if (accept) row_update<LOSS, PREC>(p, r, dl, mq, y, a);
       p.delta[r] = 0.0;
     });
     if (!grid_barrier(p, bar, sh)) return;
