@@ -64,7 +64,7 @@ typedef struct {
   double gamma;       /* weight of d^T H d in Delta, Eq. 7 (default 0, Section 5.1) */
   double nu;          /* replaces a Hessian diagonal <= 0 (default 1e-12, Appendix A, proof of Lemma 1(b)) */
   int32_t q_max;      /* backtracking cap; at the cap the bundle is left unchanged (default 30) */
-  int32_t ls_batch;   /* step sizes beta^q evaluated per pass over the touched samples (1..8; 0 = default, 2) */
+  int32_t ls_batch;   /* step sizes beta^q evaluated per pass over the touched samples (1..8; 0 = default: 1 on the first pass, 4 after) */
   int64_t max_epochs; /* outer-iteration cap (default 1000) */
   pcdn_precision prec;
   int32_t warm_start; /* 0: the solve starts from w = 0 (Algorithm 3); 1: from the problem's current w */

@@ -125,7 +125,6 @@ struct pcdn_problem {
   // reductions, barriers, flags
   double* cta_part = nullptr;
   int max_grid = 1;
-  Decision* decision = nullptr;
   uint32_t* sync = nullptr;  // [0] bar_count [1] bar_gen [4..5] barrier-1 counter (64-bit)
   int* err = nullptr;
   unsigned long long* counters = nullptr;
@@ -168,7 +167,7 @@ void free_all(pcdn_problem* p) {
   f(p->keys0); f(p->keys1); f(p->vals0); f(p->vals1); f(p->cnt); f(p->item_ptr); f(p->items);
   f(p->hist); f(p->scan_ws);
   f(p->gk); f(p->hk); f(p->dk); f(p->col_cnt); f(p->col_ready); f(p->part);
-  f(p->cta_part); f(p->decision); f(p->sync); f(p->err); f(p->counters); f(p->red_part); f(p->red_out);
+  f(p->cta_part); f(p->sync); f(p->err); f(p->counters); f(p->red_part); f(p->red_out);
   f(p->tr_q); f(p->tr_alpha); f(p->tr_Delta); f(p->tr_dF);
   if (p->ev0) cudaEventDestroy(p->ev0);
   if (p->ev1) cudaEventDestroy(p->ev1);
@@ -286,7 +285,8 @@ int finish_create(pcdn_problem* p) {
   CUDA_TRY(palloc(p, &p->id_item_ptr, m + 1));
   CUDA_TRY(palloc(p, &p->id_items, p->max_items));
   CUDA_TRY(cudaError_t(iota_i32(p->id_perm, m, s, &p->launches)));
-  CUDA_TRY(build_items(p->id_perm, m, p->col_ptr, p->cnt, p->id_item_ptr, p->id_items, p->scan_ws, s, &p->launches));
+  CUDA_TRY(build_items(p->id_perm, m, p->col_ptr, nullptr, p->cnt, p->id_item_ptr, p->id_items, p->scan_ws, s,
+                       &p->launches));
   CUDA_TRY(cudaMemcpyAsync(&p->n_id_items, p->id_item_ptr + m, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
 
   int bps = 1;
@@ -297,8 +297,7 @@ int finish_create(pcdn_problem* p) {
   if (bps > 2) bps = 2;
   if (bps < 1) return fail(PCDN_ECUDA, "bundle walker cannot be resident on this device");
   p->max_grid = p->sms * bps;
-  CUDA_TRY(palloc(p, &p->cta_part, (int64_t)p->max_grid * kPartStride));
-  CUDA_TRY(palloc(p, &p->decision, 1));
+  CUDA_TRY(palloc(p, &p->cta_part, 2 * (int64_t)p->max_grid * kPartStride));
   CUDA_TRY(palloc(p, &p->sync, 8));
   CUDA_TRY(palloc(p, &p->err, 4));
   CUDA_TRY(palloc(p, &p->counters, 8));
@@ -468,7 +467,6 @@ int run_walk(pcdn_problem* p, const pcdn_opts* o, const int32_t* perm, int64_t n
   w.anynz = nullptr;
   w.bar1 = reinterpret_cast<unsigned long long*>(p->sync + 4);
   w.cta_part = p->cta_part;
-  w.decision = p->decision;
   w.bar_count = p->sync;
   w.bar_gen = p->sync + 1;
   w.spin_limit = o->spin_limit ? o->spin_limit : kDefaultSpin;
@@ -477,8 +475,10 @@ int run_walk(pcdn_problem* p, const pcdn_opts* o, const int32_t* perm, int64_t n
   w.gamma = o->gamma;
   w.nu = o->nu;
   w.q_max = o->q_max;
-  // step sizes per pass: most bundles accept q = 0, and a further pass costs one barrier
-  w.K = o->ls_batch > 0 ? o->ls_batch : 2;
+  // step sizes per pass: almost every bundle accepts q = 0, so the first pass tests that alone;
+  // a further pass (one more barrier) tests four
+  w.K1 = o->ls_batch > 0 ? o->ls_batch : 1;
+  w.K = o->ls_batch > 0 ? o->ls_batch : 4;
   w.tr_q = p->tr_q;
   w.tr_alpha = p->tr_alpha;
   w.tr_Delta = p->tr_Delta;
@@ -735,7 +735,8 @@ int pcdn_bundle_step(pcdn_problem* p, const double* w_in, const int32_t* bundle,
   if (rc) return rc;
   // the bundle is the feature order of a one-bundle walk
   CUDA_TRY(cudaMemcpyAsync(p->vals1, bundle, sizeof(int32_t) * P, cudaMemcpyHostToDevice, p->stream));
-  CUDA_TRY(build_items(p->vals1, P, p->col_ptr, p->cnt, p->item_ptr, p->items, p->scan_ws, p->stream, &p->launches));
+  CUDA_TRY(build_items(p->vals1, P, p->col_ptr, p->w, p->cnt, p->item_ptr, p->items, p->scan_ws, p->stream,
+                       &p->launches));
   CUDA_TRY(cudaMemsetAsync(p->err, 0, sizeof(int), p->stream));
   CUDA_TRY(cudaMemsetAsync(p->counters, 0, sizeof(unsigned long long) * 8, p->stream));
   const int grid = pick_grid(p, &o, P);
@@ -803,7 +804,8 @@ int pcdn_solve(pcdn_problem* p, int32_t P, double eps, uint64_t seed, const pcdn
     int32_t* perm = nullptr;
     rc = make_partition(p, seed, k, &perm);
     if (rc) return rc;
-    CUDA_TRY(build_items(perm, p->m, p->col_ptr, p->cnt, p->item_ptr, p->items, p->scan_ws, p->stream, &p->launches));
+    CUDA_TRY(build_items(perm, p->m, p->col_ptr, p->w, p->cnt, p->item_ptr, p->items, p->scan_ws, p->stream,
+                         &p->launches));
     float ms = 0.0f;
     rc = run_walk(p, &o, perm, p->m, P, 0, nb, grid, &ms);
     if (rc) return rc;

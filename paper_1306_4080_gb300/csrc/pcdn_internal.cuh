@@ -34,12 +34,15 @@ constexpr int kErrRefresh = 8;       // |w^T x| > 700 when recomputing from z = 
 
 // One column work item: nonzeros [start, start+len) of the feature at permutation position pos,
 // chunk `chunk` of `nch` chunks of that column.
+// w is the feature's weight when the items are built: a bundle's own weights change only in its
+// own step, so this is the value its column pass needs.
 struct Item {
   int64_t start;
   int32_t len;
   int32_t pos;
   int32_t nch;
   int32_t chunk;
+  double w;
 };
 
 template <int PREC> struct RecT;
@@ -93,14 +96,14 @@ struct WalkParams {
   uint32_t stamp_base;      // stamps of this launch are stamp_base + t + 1
   uint32_t* anynz;          // unused
   // reductions and barriers
-  double* cta_part;         // [gridDim.x * kPartStride]
-  Decision* decision;
+  double* cta_part;         // [2][gridDim.x][kPartStride], by line-search pass parity
   uint32_t* bar_count;
   uint32_t* bar_gen;
   uint32_t spin_limit;
   // Armijo
   double sigma, beta, gamma, nu;
-  int32_t q_max, K;
+  int32_t q_max, K;         // K step sizes per line-search pass after the first
+  int32_t K1;               // step sizes in the first pass
   // outputs
   int32_t* tr_q;            // [t_end] per-bundle records (indexed by bundle)
   double* tr_alpha;

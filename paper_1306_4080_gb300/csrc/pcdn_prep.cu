@@ -205,7 +205,7 @@ __global__ void item_count_kernel(const int32_t* perm, int64_t npos, const int64
 }
 
 __global__ void item_fill_kernel(const int32_t* perm, int64_t npos, const int64_t* col_ptr, const int64_t* item_ptr,
-                                 Item* items) {
+                                 const double* w, Item* items) {
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < npos; k += (int64_t)gridDim.x * blockDim.x) {
     const int32_t j = perm[k];
     const int64_t a = col_ptr[j], len = col_ptr[j + 1] - a;
@@ -219,6 +219,7 @@ __global__ void item_fill_kernel(const int32_t* perm, int64_t npos, const int64_
       it.pos = (int32_t)k;
       it.nch = nch;
       it.chunk = c;
+      it.w = w ? w[j] : 0.0;
       items[first + c] = it;
     }
   }
@@ -538,14 +539,14 @@ cudaError_t perm_keys(uint64_t seed, int64_t epoch, int64_t m, uint64_t* keys, i
   return post(launches);
 }
 
-cudaError_t build_items(const int32_t* perm, int64_t npos, const int64_t* col_ptr, int64_t* cnt_ws, int64_t* item_ptr,
-                        Item* items, int64_t* scan_ws, cudaStream_t s, int64_t* launches) {
+cudaError_t build_items(const int32_t* perm, int64_t npos, const int64_t* col_ptr, const double* w, int64_t* cnt_ws,
+                        int64_t* item_ptr, Item* items, int64_t* scan_ws, cudaStream_t s, int64_t* launches) {
   item_count_kernel<<<grid_for(npos + 1, 256), 256, 0, s>>>(perm, npos, col_ptr, cnt_ws);
   cudaError_t e = post(launches);
   if (e != cudaSuccess) return e;
   e = scan_exclusive(cnt_ws, item_ptr, npos + 1, scan_ws, s, launches);
   if (e != cudaSuccess) return e;
-  item_fill_kernel<<<grid_for(npos, 256), 256, 0, s>>>(perm, npos, col_ptr, item_ptr, items);
+  item_fill_kernel<<<grid_for(npos, 256), 256, 0, s>>>(perm, npos, col_ptr, item_ptr, w, items);
   return post(launches);
 }
 

@@ -30,8 +30,9 @@ cudaError_t perm_keys(uint64_t seed, int64_t epoch, int64_t m, uint64_t* keys, i
                       int64_t* launches);
 
 // ---- column work items ------------------------------------------------------------------------
-// For positions [0, npos) of `perm`: item_ptr[npos+1] and items[] (chunks of <= kChunk nonzeros).
-cudaError_t build_items(const int32_t* perm, int64_t npos, const int64_t* col_ptr, int64_t* cnt_ws,
+// For positions [0, npos) of `perm`: item_ptr[npos+1] and items[] (chunks of <= kChunk nonzeros),
+// each carrying its feature's current weight (w may be NULL: 0).
+cudaError_t build_items(const int32_t* perm, int64_t npos, const int64_t* col_ptr, const double* w, int64_t* cnt_ws,
                         int64_t* item_ptr, Item* items, int64_t* scan_ws, cudaStream_t s, int64_t* launches);
 
 // Block plan of a walk: item_off = exclusive prefix of item lengths over [0, n_items] (n_items

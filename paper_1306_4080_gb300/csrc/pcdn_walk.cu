@@ -17,8 +17,8 @@
 //      rows and sums the loss change of each for K step sizes beta^q (Eq. 10); a block also sums
 //      Delta's parts (Eq. 7) and the L1 change of each step over a fixed slice of the bundle.
 //      Partial sums per block.
-//   -- barrier 2 (the last block to arrive reduces the partials in block order and decides
-//      accept / next K step sizes / cap; Eq. 6)
+//   -- barrier 2; then every block reduces all partials in block order and takes the same
+//      decision: accept / next step sizes / cap (Eq. 6)
 //   C  update: w_B += alpha d; each warp updates the maintained quantity and coefficients of
 //      the rows it evaluated (Algorithm 4), clears delta and the bitmap.
 //   -- barrier 3
@@ -53,7 +53,6 @@ struct StageA {
 template <int PREC>
 struct SharedWalk {
   int abort;
-  int last;
   int has_nz;
   int nonzero;
   int n_split;
@@ -160,41 +159,6 @@ __device__ bool grid_barrier_flag(const WalkParams& p, uint32_t& n1, uint32_t& s
   return !sh.abort;
 }
 
-// Barrier whose last arriving block runs `fn` (the whole block) before releasing the others.
-template <class SH, class Fn>
-__device__ bool grid_barrier_reduce(const WalkParams& p, uint32_t& idx, SH& sh, Fn&& fn) {
-  __syncthreads();
-  if (gridDim.x > 1) {
-    if (threadIdx.x == 0) {
-      __threadfence();
-      const uint32_t old = atom_acqrel_add_u32(p.bar_count, 1u);
-      sh.last = (old == (idx + 1) * gridDim.x - 1);
-    }
-    __syncthreads();
-    if (sh.last) {
-      fn();
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        __threadfence();
-        st_release_u32(p.bar_gen, idx + 1);
-      }
-    } else if (threadIdx.x == 0) {
-      uint32_t spins = 0;
-      int abort = 0;
-      while (ld_acquire_u32(p.bar_gen) < idx + 1) {
-        if (++spins > p.spin_limit) { atomicOr(p.err, kErrTimeout); abort = 1; break; }
-        if ((spins & 1023u) == 0 && err_set(p)) { abort = 1; break; }
-      }
-      sh.abort = abort;
-    }
-  } else {
-    fn();
-  }
-  ++idx;
-  __syncthreads();
-  return !sh.abort;
-}
-
 // ---------------------------------------------------------------- phase A helpers
 template <int PREC>
 struct ColAcc;
@@ -228,8 +192,9 @@ __device__ __forceinline__ double scatter_value(double d, float x) {
   else return (double)((float)d * x);
 }
 
+// delta_r += v and mark row r (r < 0: nothing).
 __device__ __forceinline__ void scatter_one(const WalkParams& p, int32_t r, double v) {
-  if (v != 0.0) {
+  if (r >= 0 && v != 0.0) {
     red_add_f64(p.delta + r, v);
     red_or_u32(p.touched + (r >> 5), 1u << (r & 31));
   }
@@ -240,7 +205,11 @@ template <int PREC>
 __device__ __forceinline__ void item_scatter_global(const WalkParams& p, const Item& it, double d) {
   const int lane = threadIdx.x & 31;
   const int64_t end = it.start + it.len;
-  for (int64_t e = it.start + lane; e < end; e += kWarp) scatter_one(p, p.row_idx[e], scatter_value<PREC>(d, p.val[e]));
+  for (int64_t e0 = it.start; e0 < end; e0 += kWarp) {
+    const int64_t e = e0 + lane;
+    if (e < end) scatter_one(p, p.row_idx[e], scatter_value<PREC>(d, p.val[e]));
+    else scatter_one(p, -1, 0.0);
+  }
 }
 
 // g, h (sums without the factor c) -> d for bundle position kl; writes gk, hk, dk.
@@ -290,7 +259,7 @@ __device__ void column_pass(const WalkParams& p, SharedWalk<PREC>& sh, int64_t l
     if (tid < nload) {
       const Item it = p.items[i + tid];
       st.items[tid] = it;
-      st.wpos[tid] = p.w_pos[it.pos];
+      st.wpos[tid] = it.w;
       len = it.len;
     }
     const int incl = block_scan_incl(sh, len);
@@ -410,8 +379,12 @@ __device__ void column_pass(const WalkParams& p, SharedWalk<PREC>& sh, int64_t l
     for (int j = wib; j < nb; j += kWalkWarps) {
       const double d = st.d[j];
       if (d == 0.0) continue;
-      for (int v = st.ioff[j] + lane; v < st.ioff[j + 1]; v += kWarp)
-        scatter_one(p, st.row[v], scatter_value<PREC>(d, st.x[v]));
+      const int b = st.ioff[j + 1];
+      for (int v0 = st.ioff[j]; v0 < b; v0 += kWarp) {
+        const int v = v0 + lane;
+        if (v < b) scatter_one(p, st.row[v], scatter_value<PREC>(d, st.x[v]));
+        else scatter_one(p, -1, 0.0);
+      }
     }
     __syncthreads();  // the staging area is reused by the next batch
     i += nb;
@@ -457,7 +430,7 @@ __device__ void column_pass(const WalkParams& p, SharedWalk<PREC>& sh, int64_t l
     }
 #pragma unroll
     for (int u = 0; u < kChunk / kWalkThreads; ++u)
-      if (rr[u] >= 0) scatter_one(p, rr[u], scatter_value<PREC>(d, xx[u]));
+      scatter_one(p, rr[u], rr[u] >= 0 ? scatter_value<PREC>(d, xx[u]) : 0.0);
   }
 }
 
@@ -640,30 +613,13 @@ __device__ __forceinline__ int list_group(const WalkParams& p, int64_t base, int
   return total;
 }
 
-// fn(row, d^T x, maintained, label) for listed rows [0, total), four rows per lane in flight.
+// fn(row, d^T x, maintained, label) for listed rows [0, total).
 template <class Fn>
 __device__ __forceinline__ void for_listed_rows(const WalkParams& p, const int32_t* list, int total, Fn&& fn) {
   const int lane = threadIdx.x & 31;
-  for (int i0 = lane; i0 < total; i0 += 4 * kWarp) {
-    int32_t r[4];
-    double dl[4], mq[4];
-    int yv[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int i = i0 + u * kWarp;
-      r[u] = i < total ? list[i] : -1;
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      if (r[u] >= 0) {
-        dl[u] = p.delta[r[u]];
-        mq[u] = p.mq[r[u]];
-        yv[u] = p.y[r[u]];
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-      if (r[u] >= 0) fn(r[u], dl[u], mq[u], yv[u]);
+  for (int i = lane; i < total; i += kWarp) {
+    const int32_t r = list[i];
+    fn(r, p.delta[r], p.mq[r], (int)p.y[r]);
   }
 }
 
@@ -702,15 +658,14 @@ __device__ __forceinline__ void rows_phase_c(const WalkParams& p, const WarpRows
 
 // ---------------------------------------------------------------- the walker
 template <int LOSS, int PREC>
-__global__ void __launch_bounds__(kWalkThreads) walk_kernel(WalkParams p) {
+__global__ void __launch_bounds__(kWalkThreads, 2) walk_kernel(WalkParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SharedWalk<PREC>& sh = *reinterpret_cast<SharedWalk<PREC>*>(smem_raw);
   const int tid = threadIdx.x;
   const int lane = tid & 31;
   const int wib = tid >> 5;
-  const int K = p.K;
   const int G = (int)gridDim.x;
-  uint32_t bar = 0, n1 = 0, seen = 0;
+  uint32_t bar = 0, n1 = 0, seen = 0, npass = 0;
   if (tid == 0) {
     sh.abort = 0;
     sh.has_nz = 0;
@@ -752,6 +707,8 @@ __global__ void __launch_bounds__(kWalkThreads) walk_kernel(WalkParams p) {
     int32_t* list = sh.u.list[wib];
     WarpRows wr = warp_rows_range(p);
     for (;;) {
+      // step sizes of this pass: K1 on the first pass, K on later ones
+      const int K = q0 == 0 ? p.K1 : p.K;
       double alpha[kMaxK];
       float alpha_f[kMaxK];
       {
@@ -843,36 +800,60 @@ __global__ void __launch_bounds__(kWalkThreads) walk_kernel(WalkParams p) {
             out = s.store();
           }
         }
-        p.cta_part[(int64_t)blockIdx.x * kPartStride + f] = out;
+        p.cta_part[((int64_t)(npass & 1) * G + blockIdx.x) * kPartStride + f] = out;
       }
       const int qbase = q0;
-      const bool ok = grid_barrier_reduce(p, bar, sh, [&]() {
-        // block-order reduction of all partials: warp w takes fields w, w+8, ...; lanes stride
-        // over the blocks; then a fixed lane tree.  Then the Armijo decision (Eq. 6).
-        for (int f = wib; f < kPartStride; f += kWalkWarps) {
-          const bool rows_f = f == 3 + 2 * kMaxK;
-          if ((f >= 3 + K && f < 3 + kMaxK) || (f >= 3 + kMaxK + K && !rows_f)) continue;  // unused step sizes
-          double rs = 0.0;
-          Acc<PREC> s;
-          for (int base = 0; base < G; base += 8 * kWarp) {
-            double v[8];
+      // barrier 2; then every block reduces all partials in the same fixed order and takes the same
+      // decision (no block waits for another's reduction).  The partials alternate between two
+      // buffers by pass parity: a block writes the next pass's partials only after the next
+      // barrier, which every block reaches after reading this pass's.
+      if (!grid_barrier(p, bar, sh)) return;
+      {
+        const double* part = p.cta_part + (int64_t)(npass & 1) * G * kPartStride;
+        // reduction of all partials in a fixed order: warp w takes blocks [w G/8, (w+1) G/8), lane l
+        // the blocks l, l+32, ... of that range with every used field of a block loaded at once; a lane
+        // tree per field; then the warps in order.
+        {
+          const int b0 = (int)((int64_t)wib * G / kWalkWarps), b1 = (int)((int64_t)(wib + 1) * G / kWalkWarps);
+          Acc<PREC> fa[3 + 2 * kMaxK];
+          double rows = 0.0;
+          for (int b = b0 + lane; b < b1; b += kWarp) {
+            const double* cp = part + (int64_t)b * kPartStride;
+            double v[kPartStride];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-              const int b = base + u * kWarp + lane;
-              v[u] = b < G ? __ldcg(p.cta_part + (int64_t)b * kPartStride + f) : 0.0;
+            for (int f = 0; f < kPartStride; ++f) {
+              const bool used = f < 3 || (f < 3 + kMaxK && f - 3 < K) || (f >= 3 + kMaxK && f < 3 + 2 * kMaxK && f - 3 - kMaxK < K) ||
+                                f == 3 + 2 * kMaxK;
+              v[f] = used ? __ldcg(cp + f) : 0.0;
             }
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-              if (rows_f) rs += v[u];
-              else if (base + u * kWarp + lane < G) s.add_acc(Acc<PREC>::load(v[u]));
+            for (int f = 0; f < 3 + 2 * kMaxK; ++f) fa[f].add_acc(Acc<PREC>::load(v[f]));
+            rows += v[3 + 2 * kMaxK];
+          }
+#pragma unroll
+          for (int f = 0; f < 3 + 2 * kMaxK; ++f) {
+            const bool used = f < 3 || (f < 3 + kMaxK && f - 3 < K) || (f >= 3 + kMaxK && f - 3 - kMaxK < K);
+            if (used) {
+              fa[f].warp_reduce();
+              if (lane == 0) sh.red[wib][f] = fa[f].store();
             }
           }
-          if (rows_f) {
-            rs = warp_sum(rs);
-            if (lane == 0) sh.tot[f] = rs;
-          } else {
-            s.warp_reduce();
-            if (lane == 0) sh.tot[f] = s.value();
+          rows = warp_sum(rows);
+          if (lane == 0) sh.red[wib][3 + 2 * kMaxK] = rows;
+          __syncthreads();
+          if (tid < kPartStride) {
+            const int f = tid;
+            if (f == 3 + 2 * kMaxK) {
+              double r = 0.0;
+              for (int wv = 0; wv < kWalkWarps; ++wv) r += sh.red[wv][f];
+              sh.tot[f] = r;
+            } else {
+              const bool used = f < 3 || (f < 3 + kMaxK && f - 3 < K) || (f >= 3 + kMaxK && f - 3 - kMaxK < K);
+              Acc<PREC> a;
+              if (used)
+                for (int wv = 0; wv < kWalkWarps; ++wv) a.add_acc(Acc<PREC>::load(sh.red[wv][f]));
+              sh.tot[f] = a.value();
+            }
           }
         }
         __syncthreads();
@@ -904,9 +885,9 @@ __global__ void __launch_bounds__(kWalkThreads) walk_kernel(WalkParams p) {
             dd.state = kDecContinue;
             dd.q = qbase + K;
           }
-          atomicAdd(p.counters + 2, 1ull);
-          if (qbase == 0) atomicAdd(p.counters + 4, (unsigned long long)tot[3 + 2 * kMaxK]);
-          if (dd.state != kDecContinue) {
+          if (blockIdx.x == 0) atomicAdd(p.counters + 2, 1ull);
+          if (blockIdx.x == 0 && qbase == 0) atomicAdd(p.counters + 4, (unsigned long long)tot[3 + 2 * kMaxK]);
+          if (blockIdx.x == 0 && dd.state != kDecContinue) {
             atomicAdd(p.counters + 0, (unsigned long long)(dd.state == kDecAccept ? dd.q + 1 : p.q_max));
             if (dd.state == kDecCap) atomicAdd(p.counters + 1, 1ull);
             atomicAdd(p.counters + 5, 1ull);
@@ -917,22 +898,11 @@ __global__ void __launch_bounds__(kWalkThreads) walk_kernel(WalkParams p) {
             if (p.tr_Delta) p.tr_Delta[t] = Delta;
             if (p.tr_dF) p.tr_dF[t] = dd.dF;
           }
-          if (G > 1) *p.decision = dd;
           sh.dec = dd;
-        }
-      });
-      if (!ok) return;
-      if (G > 1 && !sh.last) {
-        if (tid == 0) {
-          const volatile Decision* vd = p.decision;
-          sh.dec.state = vd->state;
-          sh.dec.q = vd->q;
-          sh.dec.alpha = vd->alpha;
-          sh.dec.Delta = vd->Delta;
-          sh.dec.dF = vd->dF;
         }
         __syncthreads();
       }
+      ++npass;
       dec = sh.dec;
       if (dec.state != kDecContinue) break;
       q0 = dec.q;
