@@ -120,7 +120,6 @@ struct pcdn_problem {
   double* hk = nullptr;
   double* dk = nullptr;
   uint32_t* col_cnt = nullptr;
-  uint32_t* col_ready = nullptr;
   double* part = nullptr;
   // reductions, barriers, flags
   double* cta_part = nullptr;
@@ -141,7 +140,6 @@ struct pcdn_problem {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-  uint32_t stamp = 0;
   int64_t launches = 0;
   int64_t device_bytes = 0;
 };
@@ -166,7 +164,7 @@ void free_all(pcdn_problem* p) {
   f(p->id_perm); f(p->id_item_ptr); f(p->id_items);
   f(p->keys0); f(p->keys1); f(p->vals0); f(p->vals1); f(p->cnt); f(p->item_ptr); f(p->items);
   f(p->hist); f(p->scan_ws);
-  f(p->gk); f(p->hk); f(p->dk); f(p->col_cnt); f(p->col_ready); f(p->part);
+  f(p->gk); f(p->hk); f(p->dk); f(p->col_cnt); f(p->part);
   f(p->cta_part); f(p->sync); f(p->err); f(p->counters); f(p->red_part); f(p->red_out);
   f(p->tr_q); f(p->tr_alpha); f(p->tr_Delta); f(p->tr_dF);
   if (p->ev0) cudaEventDestroy(p->ev0);
@@ -314,17 +312,15 @@ int finish_create(pcdn_problem* p) {
 int ensure_bundle_scratch(pcdn_problem* p, int32_t P) {
   if (P <= p->P_cap) return PCDN_OK;
   auto f = [](void* q) { if (q) cudaFree(q); };
-  f(p->gk); f(p->hk); f(p->dk); f(p->col_cnt); f(p->col_ready);
+  f(p->gk); f(p->hk); f(p->dk); f(p->col_cnt);
   p->gk = p->hk = p->dk = nullptr;
-  p->col_cnt = p->col_ready = nullptr;
+  p->col_cnt = nullptr;
   p->P_cap = 0;
   CUDA_TRY(palloc(p, &p->gk, P));
   CUDA_TRY(palloc(p, &p->hk, P));
   CUDA_TRY(palloc(p, &p->dk, P));
-  CUDA_TRY(palloc(p, &p->col_cnt, P));
-  CUDA_TRY(palloc(p, &p->col_ready, P));
-  CUDA_TRY(cudaMemsetAsync(p->col_cnt, 0, sizeof(uint32_t) * P, p->stream));
-  CUDA_TRY(cudaMemsetAsync(p->col_ready, 0, sizeof(uint32_t) * P, p->stream));
+  CUDA_TRY(palloc(p, &p->col_cnt, 2 * P));
+  CUDA_TRY(cudaMemsetAsync(p->col_cnt, 0, sizeof(uint32_t) * 2 * P, p->stream));
   p->P_cap = P;
   return PCDN_OK;
 }
@@ -371,7 +367,7 @@ int device_status(pcdn_problem* p) {
 int reset_scratch(pcdn_problem* p) {
   CUDA_TRY(cudaMemsetAsync(p->delta, 0, sizeof(double) * p->n, p->stream));
   CUDA_TRY(cudaMemsetAsync(p->touched, 0, sizeof(uint32_t) * p->nwords, p->stream));
-  if (p->P_cap > 0) CUDA_TRY(cudaMemsetAsync(p->col_cnt, 0, sizeof(uint32_t) * p->P_cap, p->stream));
+  if (p->P_cap > 0) CUDA_TRY(cudaMemsetAsync(p->col_cnt, 0, sizeof(uint32_t) * 2 * p->P_cap, p->stream));
   return PCDN_OK;
 }
 
@@ -461,9 +457,6 @@ int run_walk(pcdn_problem* p, const pcdn_opts* o, const int32_t* perm, int64_t n
   w.dk = p->dk;
   w.part = p->part;
   w.col_cnt = p->col_cnt;
-  w.col_ready = p->col_ready;
-  w.stamp_base = p->stamp;
-  p->stamp += (uint32_t)(t1 + 1);
   w.anynz = nullptr;
   w.bar1 = reinterpret_cast<unsigned long long*>(p->sync + 4);
   w.cta_part = p->cta_part;

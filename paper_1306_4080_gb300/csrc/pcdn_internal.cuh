@@ -91,9 +91,7 @@ struct WalkParams {
   double* hk;
   double* dk;
   double* part;             // [2 * items] partial (g, h) of chunks of split columns
-  uint32_t* col_cnt;        // [P] arrivals per split column (reset by the finaliser)
-  uint32_t* col_ready;      // [P] stamp of the bundle whose d is published
-  uint32_t stamp_base;      // stamps of this launch are stamp_base + t + 1
+  uint32_t* col_cnt;        // [2][P] chunks of a split column that published sums, by bundle parity
   uint32_t* anynz;          // unused
   // reductions and barriers
   double* cta_part;         // [2][gridDim.x][kPartStride], by line-search pass parity

@@ -76,6 +76,10 @@ template <> struct Acc<0> {
   __device__ __forceinline__ void add(double x) { v += x; }
   __device__ __forceinline__ void add_acc(const Acc& o) { v += o.v; }
   __device__ __forceinline__ void warp_reduce() { v = warp_sum(v); }
+  // sum over aligned groups of T lanes (T a power of two, at most 32)
+  __device__ __forceinline__ void group_reduce(int T) {
+    for (int o = T >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  }
   __device__ __forceinline__ double store() const { return v; }
   __device__ __forceinline__ static Acc load(double s) { Acc a; a.v = s; return a; }
   __device__ __forceinline__ double value() const { return v; }
@@ -85,6 +89,9 @@ template <> struct Acc<1> {
   __device__ __forceinline__ void add(double x) { v = df_add(v, df_make(x)); }
   __device__ __forceinline__ void add_acc(const Acc& o) { v = df_add(v, o.v); }
   __device__ __forceinline__ void warp_reduce() { v = df_warp_sum(v); }
+  __device__ __forceinline__ void group_reduce(int T) {
+    for (int o = T >> 1; o > 0; o >>= 1) v = df_add(v, df_shfl_xor(v, o));
+  }
   __device__ __forceinline__ double store() const {
     double s;
     float2 f = make_float2(v.hi, v.lo);
@@ -212,12 +219,17 @@ __device__ __forceinline__ void item_scatter_global(const WalkParams& p, const I
   }
 }
 
-// g, h (sums without the factor c) -> d for bundle position kl; writes gk, hk, dk.
-__device__ __forceinline__ double finalize_column(const WalkParams& p, int32_t kl, double g, double h, double wj) {
+// g, h (sums without the factor c) -> the scaled g, h and d (Eq. 5; h <= 0 replaced by nu).
+__device__ __forceinline__ double column_direction(const WalkParams& p, double& g, double& h, double wj) {
   g *= p.c;
   h *= p.c;
   if (h <= 0.0) h = p.nu;
-  const double d = newton_direction(g, h, wj);
+  return newton_direction(g, h, wj);
+}
+
+// As column_direction, and writes gk, hk, dk of bundle position kl.
+__device__ __forceinline__ double finalize_column(const WalkParams& p, int32_t kl, double g, double h, double wj) {
+  const double d = column_direction(p, g, h, wj);
   p.gk[kl] = g;
   p.hk[kl] = h;
   p.dk[kl] = d;
@@ -246,12 +258,14 @@ __device__ __forceinline__ int block_scan_incl(SH& sh, int v) {
 // Phase A for this block: items [i0, i1) of the bundle whose positions start at lo.
 template <int LOSS, int PREC>
 __device__ void column_pass(const WalkParams& p, SharedWalk<PREC>& sh, int64_t lo, int64_t i0, int64_t i1,
-                            uint32_t stamp) {
+                            uint32_t* col_cnt) {
   const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
   StageA<PREC>& st = sh.u.a;
   const RecT<PREC>* rec = (const RecT<PREC>*)p.rec;
   if (tid == 0) sh.n_split = 0;
   __syncthreads();
+  int64_t last_i = i0;  // the batch still staged in shared memory
+  int last_nb = 0;
   for (int64_t i = i0; i < i1;) {
     const int nload = (int)min((int64_t)kICap, i1 - i);
     // wave 1: item records and w_j
@@ -268,10 +282,14 @@ __device__ void column_pass(const WalkParams& p, SharedWalk<PREC>& sh, int64_t l
     int nb = __syncthreads_count(tid < nload && incl <= kECap);  // the fitting items are a prefix
     if (nb == 0) nb = 1;  // an item never exceeds kECap (kChunk <= kECap)
     const int eb = st.ioff[nb];
-    // chunks of split columns processed by this batch, for the deferred scatter
-    if (tid < nb && st.items[tid].nch > 1) {
-      const int k = atomicAdd(&sh.n_split, 1);
-      if (k < kSplitCap) sh.split_items[k] = i + tid;
+    // chunks of split columns processed by this batch, listed in item order for the deferred
+    // scatter (n_split counts them all, also beyond kSplitCap)
+    {
+      const int is_split = (tid < nb && st.items[tid].nch > 1) ? 1 : 0;
+      const int base = sh.n_split;
+      const int at = base + block_scan_incl(sh, is_split) - is_split;
+      if (is_split && at < kSplitCap) sh.split_items[at] = i + tid;
+      if (tid == kWalkThreads - 1) sh.n_split = at + is_split;  // every thread read it before the scan's barriers
     }
     // waves 2 and 3: row indices and values, then the rows' coefficient pairs
     {
@@ -320,47 +338,13 @@ __device__ void column_pass(const WalkParams& p, SharedWalk<PREC>& sh, int64_t l
         }
         continue;
       }
-      const int32_t kl = (int32_t)(it.pos - lo);
-      const int64_t gi = i + j;  // global item index
-      int last = 0;
+      // a chunk of a split column: publish its partial sums; the column is combined after the
+      // batches by every block that holds one of its chunks
       if (lane == 0) {
+        const int64_t gi = i + j;  // global item index
         p.part[2 * gi] = g;
         p.part[2 * gi + 1] = h;
-        __threadfence();
-        const uint32_t old = atomicAdd(p.col_cnt + kl, 1u);
-        last = (old == (uint32_t)it.nch - 1u);
-        if (last) __threadfence();
-      }
-      last = __shfl_sync(0xffffffffu, last, 0);
-      __syncwarp();
-      if (last) {
-        // fixed-order combine of the column's chunks: lane l sums chunks l, l+32, ... (eight loads
-        // in flight per lane), then a tree
-        const int64_t first = gi - it.chunk;
-        double gs = 0.0, hs = 0.0;
-        for (int base = 0; base < it.nch; base += 8 * kWarp) {
-          double gv[8], hv[8];
-#pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            const int cch = base + u * kWarp + lane;
-            gv[u] = cch < it.nch ? __ldcg(p.part + 2 * (first + cch)) : 0.0;
-            hv[u] = cch < it.nch ? __ldcg(p.part + 2 * (first + cch) + 1) : 0.0;
-          }
-#pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            gs += gv[u];
-            hs += hv[u];
-          }
-        }
-        gs = warp_sum(gs);
-        hs = warp_sum(hs);
-        if (lane == 0) {
-          const double d = finalize_column(p, kl, gs, hs, st.wpos[j]);
-          if (d != 0.0) sh.has_nz = 1;
-          p.col_cnt[kl] = 0u;
-          __threadfence();
-          st_release_u32(p.col_ready + kl, stamp);
-        }
+        red_release_add_u32(col_cnt + (int32_t)(it.pos - lo), 1u);
       }
     }
     __syncthreads();
@@ -387,36 +371,84 @@ __device__ void column_pass(const WalkParams& p, SharedWalk<PREC>& sh, int64_t l
       }
     }
     __syncthreads();  // the staging area is reused by the next batch
+    last_i = i;
+    last_nb = nb;
     i += nb;
   }
-  // chunks of split columns scatter once their column's direction is published: the whole block
-  // takes one chunk at a time, eight loads in flight per thread.  The chunks are the ones listed
+  // Chunks of split columns.  Once all chunks of a column have published their sums, the block
+  // combines them itself, in a fixed order that every block holding a chunk of the column repeats
+  // bit for bit (the block holding chunk 0 writes gk, hk, dk), and scatters its chunks: from the
+  // staged copy when the chunk is in the last batch, else reloaded.  The chunks are the ones listed
   // during the batches, or, when there were more than kSplitCap, every split chunk of [i0, i1).
   __syncthreads();
   const int ns = sh.n_split;
   const bool listed = ns <= kSplitCap;
   const int64_t n_iter = listed ? (int64_t)ns : (i1 - i0);
+  int32_t kl_prev = -1;
+  double d = 0.0;
   for (int64_t k = 0; k < n_iter; ++k) {
     const int64_t gi = listed ? sh.split_items[k] : i0 + k;
     const Item it = p.items[gi];
     if (it.nch == 1) continue;  // only on the unlisted path
     const int32_t kl = (int32_t)(it.pos - lo);
-    if (tid == 0) {
-      uint32_t spins = 0;
-      int ok = 1;
-      while (ld_acquire_u32(p.col_ready + kl) != stamp) {
-        if (++spins > p.spin_limit) { atomicOr(p.err, kErrTimeout); ok = 0; break; }
-        if ((spins & 1023u) == 0 && err_set(p)) { ok = 0; break; }
+    if (kl != kl_prev) {
+      if (tid == 0) {
+        uint32_t spins = 0;
+        int ok = 1;
+        while (ld_acquire_u32(col_cnt + kl) != (uint32_t)it.nch) {
+          if (++spins > p.spin_limit) { atomicOr(p.err, kErrTimeout); ok = 0; break; }
+          if ((spins & 1023u) == 0 && err_set(p)) { ok = 0; break; }
+        }
+        sh.split_ok = ok;
       }
-      sh.split_ok = ok;
-      sh.split_d = ok ? __ldcg(p.dk + kl) : 0.0;
+      __syncthreads();
+      if (!sh.split_ok) break;  // uniform: every thread read the flag after the barrier
+      // thread t sums chunks t, t + 256, ... (eight loads in flight), then warps, then in warp order
+      const int64_t first = gi - it.chunk;
+      double gs = 0.0, hs = 0.0;
+      for (int base = 0; base < it.nch; base += 8 * kWalkThreads) {
+        double2 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int c = base + u * kWalkThreads + tid;
+          v[u] = c < it.nch ? __ldcg((const double2*)(p.part + 2 * (first + c))) : make_double2(0.0, 0.0);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          gs += v[u].x;
+          hs += v[u].y;
+        }
+      }
+      gs = warp_sum(gs);
+      hs = warp_sum(hs);
+      if (lane == 0) {
+        sh.red[wib][0] = gs;
+        sh.red[wib][1] = hs;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        double gt = 0.0, ht = 0.0;
+        for (int wv = 0; wv < kWalkWarps; ++wv) {
+          gt += sh.red[wv][0];
+          ht += sh.red[wv][1];
+        }
+        const double wj = it.w;
+        const double dj = it.chunk == 0 ? finalize_column(p, kl, gt, ht, wj) : column_direction(p, gt, ht, wj);
+        if (dj != 0.0) sh.has_nz = 1;
+        sh.split_d = dj;
+      }
+      __syncthreads();
+      d = sh.split_d;
+      kl_prev = kl;
     }
-    __syncthreads();
-    const int ok = sh.split_ok;
-    const double d = sh.split_d;
-    __syncthreads();
-    if (!ok) break;
     if (d == 0.0) continue;
+    if (gi >= last_i && gi < last_i + last_nb) {
+      StageA<PREC>& st = sh.u.a;
+      const int j = (int)(gi - last_i);
+      const int b = st.ioff[j + 1];
+      for (int v = st.ioff[j] + tid; v < b; v += kWalkThreads) scatter_one(p, st.row[v], scatter_value<PREC>(d, st.x[v]));
+      continue;
+    }
     int32_t rr[kChunk / kWalkThreads];
     float xx[kChunk / kWalkThreads];
 #pragma unroll
@@ -676,15 +708,19 @@ __global__ void __launch_bounds__(kWalkThreads, 2) walk_kernel(WalkParams p) {
     const int64_t lo = t * (int64_t)p.P;
     const int64_t hi = min(p.npos, lo + (int64_t)p.P);
     const int32_t Pt = (int32_t)(hi - lo);
-    const uint32_t stamp = p.stamp_base + (uint32_t)(t + 1);
 
     // ---------------- A: column reductions, directions, scatter
     {
       const int64_t* pl = p.plan + t * (int64_t)(G + 1) + blockIdx.x;
-      column_pass<LOSS, PREC>(p, sh, lo, pl[0], pl[1], stamp);
+      column_pass<LOSS, PREC>(p, sh, lo, pl[0], pl[1], p.col_cnt + (t & 1) * (int64_t)p.P);
     }
     if (!grid_barrier_flag(p, n1, seen, sh)) return;
     if (tid == 0) sh.has_nz = 0;  // read by the barrier above; next written in the next column pass
+    const int64_t kpb = (Pt + G - 1) / G;  // bundle positions per block
+    const int64_t k0 = min((int64_t)Pt, (int64_t)blockIdx.x * kpb), k1 = min((int64_t)Pt, k0 + kpb);
+    // chunk counts of this bundle's split columns, last read before barrier 1; the next bundle
+    // counts in the other half, and the one after it only after the next barrier 1
+    for (int64_t kl = k0 + tid; kl < k1; kl += kWalkThreads) p.col_cnt[(t & 1) * (int64_t)p.P + kl] = 0u;
     if (!sh.nonzero) {
       if (blockIdx.x == 0 && tid == 0) {
         if (p.tr_q) p.tr_q[t] = 0;
@@ -700,8 +736,6 @@ __global__ void __launch_bounds__(kWalkThreads, 2) walk_kernel(WalkParams p) {
     // ---------------- B: line search passes
     int q0 = 0;
     Decision dec;
-    const int64_t kpb = (Pt + G - 1) / G;  // bundle positions per block
-    const int64_t k0 = min((int64_t)Pt, (int64_t)blockIdx.x * kpb), k1 = min((int64_t)Pt, k0 + kpb);
     // warps that sum the bundle-position terms (about 128 positions each)
     const int pos_warps = (int)min((int64_t)kWalkWarps, max((int64_t)1, (k1 - k0 + 127) / 128));
     int32_t* list = sh.u.list[wib];
@@ -781,15 +815,18 @@ __global__ void __launch_bounds__(kWalkThreads, 2) walk_kernel(WalkParams p) {
       }
       if (lane == 0) sh.red[wib][3 + 2 * kMaxK] = (double)nrows;
       __syncthreads();
-      // block total of each field, warps in order
+      // block total of each field, warps in order; the partials are stored field-major so that the
+      // reduction below reads each field of all blocks contiguously
       if (tid < kPartStride) {
         const int f = tid;
-        double out;
         if (f == 3 + 2 * kMaxK) {
-          double s = 0.0;
-          for (int wv = 0; wv < kWalkWarps; ++wv) s += sh.red[wv][f];
-          out = s;
+          if (q0 == 0) {  // rows touched by this bundle, a statistic
+            double s = 0.0;
+            for (int wv = 0; wv < kWalkWarps; ++wv) s += sh.red[wv][f];
+            atomicAdd(p.counters + 4, (unsigned long long)s);
+          }
         } else {
+          double out;
           Acc<PREC> s;
           const bool posf = f < 3 + kMaxK;
           const int nw = posf ? pos_warps : kWalkWarps;
@@ -799,8 +836,8 @@ __global__ void __launch_bounds__(kWalkThreads, 2) walk_kernel(WalkParams p) {
             for (int wv = 0; wv < nw; ++wv) s.add_acc(Acc<PREC>::load(sh.red[wv][f]));
             out = s.store();
           }
+          p.cta_part[((int64_t)(npass & 1) * kPartStride + f) * G + blockIdx.x] = out;
         }
-        p.cta_part[((int64_t)(npass & 1) * G + blockIdx.x) * kPartStride + f] = out;
       }
       const int qbase = q0;
       // barrier 2; then every block reduces all partials in the same fixed order and takes the same
@@ -809,96 +846,91 @@ __global__ void __launch_bounds__(kWalkThreads, 2) walk_kernel(WalkParams p) {
       // barrier, which every block reaches after reading this pass's.
       if (!grid_barrier(p, bar, sh)) return;
       {
-        const double* part = p.cta_part + (int64_t)(npass & 1) * G * kPartStride;
-        // reduction of all partials in a fixed order: warp w takes blocks [w G/8, (w+1) G/8), lane l
-        // the blocks l, l+32, ... of that range with every used field of a block loaded at once; a lane
-        // tree per field; then the warps in order.
+        const double* part = p.cta_part + (int64_t)(npass & 1) * kPartStride * G;
+        // reduction of all partials in a fixed order: the 3 + 2K used fields (gd, hdd, l1, K L1
+        // changes, K loss changes) get T threads each; thread s of a field sums blocks s, s + T, ...
+        // (coalesced over the T threads, all loads in flight at once), then a lane tree over the T.
         {
-          const int b0 = (int)((int64_t)wib * G / kWalkWarps), b1 = (int)((int64_t)(wib + 1) * G / kWalkWarps);
-          Acc<PREC> fa[3 + 2 * kMaxK];
-          double rows = 0.0;
-          for (int b = b0 + lane; b < b1; b += kWarp) {
-            const double* cp = part + (int64_t)b * kPartStride;
-            double v[kPartStride];
+          const int nf = 3 + 2 * K;
+          const int T = nf <= 8 ? 32 : (nf <= 16 ? 16 : 8);
+          const int fi = tid / T, s = tid & (T - 1);
+          const int f = fi < 3 + K ? fi : fi - K + kMaxK;
+          Acc<PREC> fa;
+          if (fi < nf) {
+            const double* pf = part + (int64_t)f * G;
+            constexpr int kLd = 24;
+            for (int bb = s; bb < G; bb += kLd * T) {
+              double v[kLd];
 #pragma unroll
-            for (int f = 0; f < kPartStride; ++f) {
-              const bool used = f < 3 || (f < 3 + kMaxK && f - 3 < K) || (f >= 3 + kMaxK && f < 3 + 2 * kMaxK && f - 3 - kMaxK < K) ||
-                                f == 3 + 2 * kMaxK;
-              v[f] = used ? __ldcg(cp + f) : 0.0;
-            }
+              for (int u = 0; u < kLd; ++u) {
+                const int b = bb + u * T;
+                v[u] = b < G ? __ldcg(pf + b) : 0.0;
+              }
 #pragma unroll
-            for (int f = 0; f < 3 + 2 * kMaxK; ++f) fa[f].add_acc(Acc<PREC>::load(v[f]));
-            rows += v[3 + 2 * kMaxK];
-          }
-#pragma unroll
-          for (int f = 0; f < 3 + 2 * kMaxK; ++f) {
-            const bool used = f < 3 || (f < 3 + kMaxK && f - 3 < K) || (f >= 3 + kMaxK && f - 3 - kMaxK < K);
-            if (used) {
-              fa[f].warp_reduce();
-              if (lane == 0) sh.red[wib][f] = fa[f].store();
+              for (int u = 0; u < kLd; ++u)
+                if (bb + u * T < G) fa.add_acc(Acc<PREC>::load(v[u]));
             }
           }
-          rows = warp_sum(rows);
-          if (lane == 0) sh.red[wib][3 + 2 * kMaxK] = rows;
-          __syncthreads();
-          if (tid < kPartStride) {
-            const int f = tid;
-            if (f == 3 + 2 * kMaxK) {
-              double r = 0.0;
-              for (int wv = 0; wv < kWalkWarps; ++wv) r += sh.red[wv][f];
-              sh.tot[f] = r;
-            } else {
-              const bool used = f < 3 || (f < 3 + kMaxK && f - 3 < K) || (f >= 3 + kMaxK && f - 3 - kMaxK < K);
-              Acc<PREC> a;
-              if (used)
-                for (int wv = 0; wv < kWalkWarps; ++wv) a.add_acc(Acc<PREC>::load(sh.red[wv][f]));
-              sh.tot[f] = a.value();
-            }
-          }
+          fa.group_reduce(T);
+          if (fi < nf && s == 0) sh.tot[f] = fa.value();
         }
         __syncthreads();
-        if (tid == 0) {
+        // the decision (Eq. 6): lane q of warp 0 tests step size alpha_q, the first passing one wins
+        if (wib == 0) {
           const double* tot = sh.tot;
           const double gd = tot[0], hdd = tot[1], l1 = tot[2];
           const double Delta = gd + p.gamma * hdd + l1;
-          Decision dd;
-          dd.state = kDecCap;
-          dd.q = p.q_max;
-          dd.alpha = 0.0;
-          dd.Delta = Delta;
-          dd.dF = 0.0;
-          for (int q = 0; q < K && qbase + q < p.q_max; ++q) {
-            const double a = alpha[q];
-            double dF;
-            if constexpr (PREC == 0) dF = p.c * tot[3 + kMaxK + q] + tot[3 + q];
-            else dF = a * gd + p.c * tot[3 + kMaxK + q] + tot[3 + q];
+          double a = alpha[0];
+#pragma unroll
+          for (int q = 1; q < kMaxK; ++q)
+            if (lane == q) a = alpha[q];
+          double dF = 0.0;
+          bool pass = false;
+          if (lane < K && qbase + lane < p.q_max) {
+            if constexpr (PREC == 0) dF = p.c * tot[3 + kMaxK + lane] + tot[3 + lane];
+            else dF = a * gd + p.c * tot[3 + kMaxK + lane] + tot[3 + lane];
             // a NaN change (an overflowing trial step) fails the test, as in Eq. 6 read literally
-            if (dF <= p.sigma * a * Delta) {
+            pass = dF <= p.sigma * a * Delta;
+          }
+          const uint32_t m = __ballot_sync(0xffffffffu, pass);
+          const int qa = m ? __ffs(m) - 1 : 0;
+          const double dFa = __shfl_sync(0xffffffffu, dF, qa);
+          const double aa = __shfl_sync(0xffffffffu, a, qa);
+          if (lane == 0) {
+            Decision dd;
+            dd.Delta = Delta;
+            if (m) {
               dd.state = kDecAccept;
-              dd.q = qbase + q;
-              dd.alpha = a;
-              dd.dF = dF;
-              break;
+              dd.q = qbase + qa;
+              dd.alpha = aa;
+              dd.dF = dFa;
+            } else if (qbase + K < p.q_max) {
+              dd.state = kDecContinue;
+              dd.q = qbase + K;
+              dd.alpha = 0.0;
+              dd.dF = 0.0;
+            } else {
+              dd.state = kDecCap;
+              dd.q = p.q_max;
+              dd.alpha = 0.0;
+              dd.dF = 0.0;
             }
+            if (blockIdx.x == 0) {
+              atomicAdd(p.counters + 2, 1ull);
+              if (dd.state != kDecContinue) {
+                atomicAdd(p.counters + 0, (unsigned long long)(dd.state == kDecAccept ? dd.q + 1 : p.q_max));
+                if (dd.state == kDecCap) atomicAdd(p.counters + 1, 1ull);
+                atomicAdd(p.counters + 5, 1ull);
+                atomicAdd(p.counters + 6, (unsigned long long)Pt);
+                atomicAdd(p.counters + 7, 1ull);
+                if (p.tr_q) p.tr_q[t] = dd.q;
+                if (p.tr_alpha) p.tr_alpha[t] = dd.alpha;
+                if (p.tr_Delta) p.tr_Delta[t] = Delta;
+                if (p.tr_dF) p.tr_dF[t] = dd.dF;
+              }
+            }
+            sh.dec = dd;
           }
-          if (dd.state != kDecAccept && qbase + K < p.q_max) {
-            dd.state = kDecContinue;
-            dd.q = qbase + K;
-          }
-          if (blockIdx.x == 0) atomicAdd(p.counters + 2, 1ull);
-          if (blockIdx.x == 0 && qbase == 0) atomicAdd(p.counters + 4, (unsigned long long)tot[3 + 2 * kMaxK]);
-          if (blockIdx.x == 0 && dd.state != kDecContinue) {
-            atomicAdd(p.counters + 0, (unsigned long long)(dd.state == kDecAccept ? dd.q + 1 : p.q_max));
-            if (dd.state == kDecCap) atomicAdd(p.counters + 1, 1ull);
-            atomicAdd(p.counters + 5, 1ull);
-            atomicAdd(p.counters + 6, (unsigned long long)Pt);
-            atomicAdd(p.counters + 7, 1ull);
-            if (p.tr_q) p.tr_q[t] = dd.q;
-            if (p.tr_alpha) p.tr_alpha[t] = dd.alpha;
-            if (p.tr_Delta) p.tr_Delta[t] = Delta;
-            if (p.tr_dF) p.tr_dF[t] = dd.dF;
-          }
-          sh.dec = dd;
         }
         __syncthreads();
       }
