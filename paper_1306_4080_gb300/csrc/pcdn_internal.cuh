@@ -151,6 +151,27 @@ __device__ __forceinline__ void red_or_u32(uint32_t* p, uint32_t v) {
 __device__ __forceinline__ int32_t ld_stream_i32(const int32_t* p) { return __ldcs(p); }
 __device__ __forceinline__ float ld_stream_f32(const float* p) { return __ldcs(p); }
 
+// ---------------------------------------------------------------- asynchronous copies to shared memory
+// cp.async (global -> shared without registers); each thread waits for its own copies, a block
+// barrier then makes all of them visible.  X goes through with an evict-first L2 policy.
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ uint64_t l2_evict_first_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ void cp_async4_stream(void* dst, const void* src, uint64_t pol) {
+  asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], 4, %2;" ::"r"(smem_u32(dst)), "l"(src), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // ---------------------------------------------------------------- warp reductions (fixed tree)
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll

@@ -37,18 +37,16 @@
 
 namespace pcdn {
 
+// Phase A scratch that phases B and C reuse for their row lists.
 template <int PREC>
 struct StageA {
-  Item items[kICap];
-  int32_t ioff[kICap + 1];
-  double wpos[kICap];
   double g[kICap];
   double h[kICap];
   double d[kICap];
-  int32_t row[kECap];
-  float x[kECap];
   RecT<PREC> rec[kECap];
 };
+
+constexpr int kAlphaTab = 64;
 
 template <int PREC>
 struct SharedWalk {
@@ -63,6 +61,14 @@ struct SharedWalk {
   Decision dec;
   double tot[kPartStride];
   double red[kWalkWarps][kPartStride];
+  // the batch of work items and their nonzeros; the next bundle's first batch is copied in during
+  // phases B and C (pf_ready), since X does not change
+  int pf_ready, pf_nb, pf_eb;
+  double atab[kAlphaTab];  // beta^q as the running product 1, beta, beta*beta, ... (q < kAlphaTab)
+  __align__(16) Item items[kICap];  // 16-byte halves are copied asynchronously
+  int32_t ioff[kICap + 1];
+  int32_t row[kECap];
+  float x[kECap];
   union {
     StageA<PREC> a;
     int32_t list[kWalkWarps][kListCap];
@@ -129,6 +135,29 @@ __device__ bool grid_barrier(const WalkParams& p, uint32_t& idx, SH& sh) {
       }
       sh.abort = abort;
     }
+  }
+  ++idx;
+  __syncthreads();
+  return !sh.abort;
+}
+
+// Split-phase form of grid_barrier: work between arrive and wait must neither write what other
+// blocks read after the barrier nor read what they write before it.
+__device__ __forceinline__ void grid_arrive(const WalkParams& p) {
+  __syncthreads();
+  if (gridDim.x > 1 && threadIdx.x == 0) red_release_add_u32(p.bar_count, 1u);
+}
+template <class SH>
+__device__ bool grid_wait(const WalkParams& p, uint32_t& idx, SH& sh) {
+  if (gridDim.x > 1 && threadIdx.x == 0) {
+    const uint32_t target = (idx + 1) * gridDim.x;
+    uint32_t spins = 0;
+    int abort = 0;
+    while (ld_acquire_u32(p.bar_count) < target) {
+      if (++spins > p.spin_limit) { atomicOr(p.err, kErrTimeout); abort = 1; break; }
+      if ((spins & 1023u) == 0 && err_set(p)) { abort = 1; break; }
+    }
+    sh.abort = abort;
   }
   ++idx;
   __syncthreads();
@@ -255,6 +284,47 @@ __device__ __forceinline__ int block_scan_incl(SH& sh, int v) {
   return x + off;
 }
 
+// Asynchronous copy of items [i, i + n) (n <= kICap) into sh.items, two 16-byte halves each.
+template <class SH>
+__device__ __forceinline__ void stage_items_async(const WalkParams& p, SH& sh, int64_t i, int n) {
+  for (int k = threadIdx.x; k < 2 * n; k += kWalkThreads)
+    cp_async16(reinterpret_cast<char*>(&sh.items[k >> 1]) + 16 * (k & 1),
+               reinterpret_cast<const char*>(p.items + i + (k >> 1)) + 16 * (k & 1));
+  cp_async_commit();
+}
+
+// With the n staged items visible: the batch is the longest prefix of them whose nonzeros fit in
+// kECap (at least one item; kChunk <= kECap).  Writes sh.ioff; returns the item and nonzero counts.
+template <class SH>
+__device__ __forceinline__ void plan_batch(SH& sh, int n, int& nb, int& eb) {
+  const int tid = threadIdx.x;
+  const int len = tid < n ? sh.items[tid].len : 0;
+  const int incl = block_scan_incl(sh, len);
+  if (tid < n) sh.ioff[tid + 1] = incl;
+  if (tid == 0) sh.ioff[0] = 0;
+  nb = __syncthreads_count(tid < n && incl <= kECap);
+  if (nb == 0) nb = 1;
+  eb = sh.ioff[nb];
+}
+
+// Asynchronous copy of the batch's row indices and values into sh.row, sh.x.
+template <class SH>
+__device__ __forceinline__ void stage_entries_async(const WalkParams& p, SH& sh, int nb, int eb) {
+  const uint64_t pol = l2_evict_first_policy();
+  for (int v = threadIdx.x; v < eb; v += kWalkThreads) {
+    int a = 0, b = nb - 1;  // largest j < nb with ioff[j] <= v
+    while (a < b) {
+      const int mid = (a + b + 1) >> 1;
+      if (sh.ioff[mid] <= v) a = mid;
+      else b = mid - 1;
+    }
+    const int64_t e = sh.items[a].start + (v - sh.ioff[a]);
+    cp_async4_stream(&sh.row[v], p.row_idx + e, pol);
+    cp_async4_stream(&sh.x[v], p.val + e, pol);
+  }
+  cp_async_commit();
+}
+
 // Phase A for this block: items [i0, i1) of the bundle whose positions start at lo.
 template <int LOSS, int PREC>
 __device__ void column_pass(const WalkParams& p, SharedWalk<PREC>& sh, int64_t lo, int64_t i0, int64_t i1,
@@ -267,68 +337,47 @@ __device__ void column_pass(const WalkParams& p, SharedWalk<PREC>& sh, int64_t l
   int64_t last_i = i0;  // the batch still staged in shared memory
   int last_nb = 0;
   for (int64_t i = i0; i < i1;) {
-    const int nload = (int)min((int64_t)kICap, i1 - i);
-    // wave 1: item records and w_j
-    int len = 0;
-    if (tid < nload) {
-      const Item it = p.items[i + tid];
-      st.items[tid] = it;
-      st.wpos[tid] = it.w;
-      len = it.len;
+    // items and nonzeros of the batch: prefetched for the first batch, else copied now
+    int nb, eb;
+    if (i == i0 && sh.pf_ready) {
+      cp_async_wait_all();
+      __syncthreads();
+      nb = sh.pf_nb;
+      eb = sh.pf_eb;
+    } else {
+      const int nload = (int)min((int64_t)kICap, i1 - i);
+      stage_items_async(p, sh, i, nload);
+      cp_async_wait_all();
+      __syncthreads();
+      plan_batch(sh, nload, nb, eb);
+      stage_entries_async(p, sh, nb, eb);
+      cp_async_wait_all();
+      __syncthreads();
     }
-    const int incl = block_scan_incl(sh, len);
-    if (tid < nload) st.ioff[tid + 1] = incl;
-    if (tid == 0) st.ioff[0] = 0;
-    int nb = __syncthreads_count(tid < nload && incl <= kECap);  // the fitting items are a prefix
-    if (nb == 0) nb = 1;  // an item never exceeds kECap (kChunk <= kECap)
-    const int eb = st.ioff[nb];
+    // the rows' coefficient pairs
+    for (int v = tid; v < eb; v += kWalkThreads) {
+      if constexpr (PREC == 0) cp_async16(&st.rec[v], rec + sh.row[v]);
+      else cp_async8(&st.rec[v], rec + sh.row[v]);
+    }
+    cp_async_commit();
     // chunks of split columns processed by this batch, listed in item order for the deferred
     // scatter (n_split counts them all, also beyond kSplitCap)
     {
-      const int is_split = (tid < nb && st.items[tid].nch > 1) ? 1 : 0;
+      const int is_split = (tid < nb && sh.items[tid].nch > 1) ? 1 : 0;
       const int base = sh.n_split;
       const int at = base + block_scan_incl(sh, is_split) - is_split;
       if (is_split && at < kSplitCap) sh.split_items[at] = i + tid;
       if (tid == kWalkThreads - 1) sh.n_split = at + is_split;  // every thread read it before the scan's barriers
+      if (tid == 0) sh.pf_ready = 0;                           // read before the scan's barriers too
     }
-    // waves 2 and 3: row indices and values, then the rows' coefficient pairs
-    {
-      int32_t rr[kECap / kWalkThreads];
-      float xx[kECap / kWalkThreads];
-#pragma unroll
-      for (int u = 0; u < kECap / kWalkThreads; ++u) {
-        const int v = tid + u * kWalkThreads;
-        rr[u] = -1;
-        xx[u] = 0.0f;
-        if (v < eb) {
-          int a = 0, b = nb - 1;  // largest j < nb with ioff[j] <= v
-          while (a < b) {
-            const int mid = (a + b + 1) >> 1;
-            if (st.ioff[mid] <= v) a = mid;
-            else b = mid - 1;
-          }
-          const int64_t e = st.items[a].start + (v - st.ioff[a]);
-          rr[u] = ld_stream_i32(p.row_idx + e);
-          xx[u] = ld_stream_f32(p.val + e);
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < kECap / kWalkThreads; ++u) {
-        const int v = tid + u * kWalkThreads;
-        if (rr[u] >= 0) {
-          st.rec[v] = rec[rr[u]];
-          st.row[v] = rr[u];
-          st.x[v] = xx[u];
-        }
-      }
-    }
+    cp_async_wait_all();
     __syncthreads();
     // one warp per item: the reduction; chunks of split columns combine here
     for (int j = wib; j < nb; j += kWalkWarps) {
-      const Item it = st.items[j];
-      const int a = st.ioff[j], b = st.ioff[j + 1];
+      const Item it = sh.items[j];
+      const int a = sh.ioff[j], b = sh.ioff[j + 1];
       ColAcc<PREC> acc;
-      for (int v = a + lane; v < b; v += kWarp) acc.add(st.x[v], st.rec[v]);
+      for (int v = a + lane; v < b; v += kWarp) acc.add(sh.x[v], st.rec[v]);
       double g, h;
       acc.reduce(g, h);
       if (it.nch == 1) {
@@ -350,10 +399,10 @@ __device__ void column_pass(const WalkParams& p, SharedWalk<PREC>& sh, int64_t l
     __syncthreads();
     // one thread per item: the direction (Eq. 5)
     if (tid < nb) {
-      const Item it = st.items[tid];
+      const Item it = sh.items[tid];
       double d = 0.0;
       if (it.nch == 1) {
-        d = finalize_column(p, (int32_t)(it.pos - lo), st.g[tid], st.h[tid], st.wpos[tid]);
+        d = finalize_column(p, (int32_t)(it.pos - lo), st.g[tid], st.h[tid], sh.items[tid].w);
         if (d != 0.0) sh.has_nz = 1;
       }
       st.d[tid] = d;
@@ -363,10 +412,10 @@ __device__ void column_pass(const WalkParams& p, SharedWalk<PREC>& sh, int64_t l
     for (int j = wib; j < nb; j += kWalkWarps) {
       const double d = st.d[j];
       if (d == 0.0) continue;
-      const int b = st.ioff[j + 1];
-      for (int v0 = st.ioff[j]; v0 < b; v0 += kWarp) {
+      const int b = sh.ioff[j + 1];
+      for (int v0 = sh.ioff[j]; v0 < b; v0 += kWarp) {
         const int v = v0 + lane;
-        if (v < b) scatter_one(p, st.row[v], scatter_value<PREC>(d, st.x[v]));
+        if (v < b) scatter_one(p, sh.row[v], scatter_value<PREC>(d, sh.x[v]));
         else scatter_one(p, -1, 0.0);
       }
     }
@@ -443,10 +492,9 @@ __device__ void column_pass(const WalkParams& p, SharedWalk<PREC>& sh, int64_t l
     }
     if (d == 0.0) continue;
     if (gi >= last_i && gi < last_i + last_nb) {
-      StageA<PREC>& st = sh.u.a;
       const int j = (int)(gi - last_i);
-      const int b = st.ioff[j + 1];
-      for (int v = st.ioff[j] + tid; v < b; v += kWalkThreads) scatter_one(p, st.row[v], scatter_value<PREC>(d, st.x[v]));
+      const int b = sh.ioff[j + 1];
+      for (int v = sh.ioff[j] + tid; v < b; v += kWalkThreads) scatter_one(p, sh.row[v], scatter_value<PREC>(d, sh.x[v]));
       continue;
     }
     int32_t rr[kChunk / kWalkThreads];
@@ -701,6 +749,12 @@ __global__ void __launch_bounds__(kWalkThreads, 2) walk_kernel(WalkParams p) {
   if (tid == 0) {
     sh.abort = 0;
     sh.has_nz = 0;
+    sh.pf_ready = 0;
+    double a = 1.0;
+    for (int q = 0; q < kAlphaTab; ++q) {
+      sh.atab[q] = a;
+      a *= p.beta;
+    }
   }
   __syncthreads();
 
@@ -709,12 +763,20 @@ __global__ void __launch_bounds__(kWalkThreads, 2) walk_kernel(WalkParams p) {
     const int64_t hi = min(p.npos, lo + (int64_t)p.P);
     const int32_t Pt = (int32_t)(hi - lo);
 
+    // the next bundle's item range (its first batch is copied in during phases B and C)
+    int64_t nx0 = 0, nx1 = 0;
+    if (t + 1 < p.t_end) {
+      const int64_t* pn = p.plan + (t + 1) * (int64_t)(G + 1) + blockIdx.x;
+      nx0 = pn[0];
+      nx1 = pn[1];
+    }
+
     // ---------------- A: column reductions, directions, scatter
     {
       const int64_t* pl = p.plan + t * (int64_t)(G + 1) + blockIdx.x;
       column_pass<LOSS, PREC>(p, sh, lo, pl[0], pl[1], p.col_cnt + (t & 1) * (int64_t)p.P);
     }
-    if (!grid_barrier_flag(p, n1, seen, sh)) return;
+    if (!grid_barrier_flag(p, n1, seen, sh)) return;  // no copies in flight: the column pass waited
     if (tid == 0) sh.has_nz = 0;  // read by the barrier above; next written in the next column pass
     const int64_t kpb = (Pt + G - 1) / G;  // bundle positions per block
     const int64_t k0 = min((int64_t)Pt, (int64_t)blockIdx.x * kpb), k1 = min((int64_t)Pt, k0 + kpb);
@@ -733,6 +795,10 @@ __global__ void __launch_bounds__(kWalkThreads, 2) walk_kernel(WalkParams p) {
       continue;  // nothing changed; the next bundle may start
     }
 
+    // the next bundle's first batch: its items now, its nonzeros inside barrier 3
+    const int nx_load = (int)min((int64_t)kICap, nx1 - nx0);
+    if (nx_load > 0) stage_items_async(p, sh, nx0, nx_load);
+
     // ---------------- B: line search passes
     int q0 = 0;
     Decision dec;
@@ -745,16 +811,20 @@ __global__ void __launch_bounds__(kWalkThreads, 2) walk_kernel(WalkParams p) {
       const int K = q0 == 0 ? p.K1 : p.K;
       double alpha[kMaxK];
       float alpha_f[kMaxK];
-      {
+      if (q0 + kMaxK <= kAlphaTab) {
+#pragma unroll
+        for (int q = 0; q < kMaxK; ++q) alpha[q] = sh.atab[q0 + q];
+      } else {
         double a = 1.0;
         for (int q = 0; q < q0; ++q) a *= p.beta;
 #pragma unroll
         for (int q = 0; q < kMaxK; ++q) {
           alpha[q] = a;
-          alpha_f[q] = (float)a;
           a *= p.beta;
         }
       }
+#pragma unroll
+      for (int q = 0; q < kMaxK; ++q) alpha_f[q] = (float)alpha[q];
       const bool halving = (p.beta == 0.5);
       LsAcc<LOSS, PREC> acc;
       acc.zero();
@@ -844,7 +914,10 @@ __global__ void __launch_bounds__(kWalkThreads, 2) walk_kernel(WalkParams p) {
       // decision (no block waits for another's reduction).  The partials alternate between two
       // buffers by pass parity: a block writes the next pass's partials only after the next
       // barrier, which every block reaches after reading this pass's.
-      if (!grid_barrier(p, bar, sh)) return;
+      if (!grid_barrier(p, bar, sh)) {
+        cp_async_wait_all();  // the next bundle's item copies
+        return;
+      }
       {
         const double* part = p.cta_part + (int64_t)(npass & 1) * kPartStride * G;
         // reduction of all partials in a fixed order: the 3 + 2K used fields (gd, hdd, l1, K L1
@@ -953,7 +1026,25 @@ __global__ void __launch_bounds__(kWalkThreads, 2) walk_kernel(WalkParams p) {
       if (accept) row_update<LOSS, PREC>(p, r, dl, mq, y, a);
       p.delta[r] = 0.0;
     });
-    if (!grid_barrier(p, bar, sh)) return;
+    // barrier 3, with the next bundle's first batch planned and its nonzero copies issued between
+    // arriving and waiting (X and the plan are read-only)
+    grid_arrive(p);
+    if (nx_load > 0) {
+      cp_async_wait_all();
+      __syncthreads();
+      int nb, eb;
+      plan_batch(sh, nx_load, nb, eb);
+      stage_entries_async(p, sh, nb, eb);
+      if (tid == 0) {
+        sh.pf_nb = nb;
+        sh.pf_eb = eb;
+        sh.pf_ready = 1;
+      }
+    }
+    if (!grid_wait(p, bar, sh)) {
+      cp_async_wait_all();  // the next bundle's nonzero copies
+      return;
+    }
   }
 }
 
