@@ -26,6 +26,7 @@ constexpr int kListCap = 1024;     // touched rows listed per warp per 32 bitmap
 constexpr int kICap = 256;         // work items staged per batch of the column pass
 constexpr int kECap = 2048;        // nonzeros staged per batch (= 8 per thread)
 constexpr int kSplitCap = 64;      // chunks of split columns a block remembers for its deferred scatter
+constexpr int kWarpChunks = 256;   // split columns of at most this many chunks are combined by one warp
 
 constexpr int kErrTimeout = 1;
 constexpr int kErrNumeric = 2;       // non-finite g, h or d

@@ -57,6 +57,12 @@ struct SharedWalk {
   int split_ok;
   double split_d;
   int64_t split_items[kSplitCap];
+  // the listed split chunks: column position, chunk count, chunk index, w_j, length, start, column
+  // index among the block's split columns; and each column's d
+  int32_t s_kl[kSplitCap], s_nch[kSplitCap], s_chunk[kSplitCap], s_len[kSplitCap], s_col[kSplitCap];
+  double s_w[kSplitCap];
+  int64_t s_start[kSplitCap];
+  double s_d[kSplitCap];
   int scan_tot[kWalkWarps];
   Decision dec;
   double tot[kPartStride];
@@ -284,6 +290,114 @@ __device__ __forceinline__ int block_scan_incl(SH& sh, int v) {
   return x + off;
 }
 
+// ---------------------------------------------------------------- split columns
+// A column longer than kChunk is cut into chunks whose partial sums (g, h) go to part[2 gi],
+// part[2 gi + 1]; col_cnt counts the chunks that published.
+
+// Waits (one thread) until all nch chunks of a column have published; false on timeout or another
+// block's error.
+__device__ __forceinline__ bool split_wait(const WalkParams& p, const uint32_t* cnt, int nch) {
+  uint32_t spins = 0;
+  while (ld_acquire_u32(cnt) != (uint32_t)nch) {
+    if (++spins > p.spin_limit) { atomicOr(p.err, kErrTimeout); return false; }
+    if ((spins & 1023u) == 0 && err_set(p)) return false;
+  }
+  return true;
+}
+
+// split_wait by lane 0 of a whole (converged) warp; every lane gets the result.
+__device__ __forceinline__ bool split_wait_warp(const WalkParams& p, const uint32_t* cnt, int nch) {
+  int ok = 1;
+  if ((threadIdx.x & 31) == 0) ok = split_wait(p, cnt, nch) ? 1 : 0;
+  return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
+// Canonical sum of the nch <= kWarpChunks chunk partials of a column, by one warp: lane l sums
+// chunks l, l + 32, ... in order (all loads in flight at once), then the lane tree.
+__device__ __forceinline__ void split_combine_warp(const double* part, int nch, double& g, double& h) {
+  const int lane = threadIdx.x & 31;
+  double2 v[kWarpChunks / kWarp];
+#pragma unroll
+  for (int u = 0; u < kWarpChunks / kWarp; ++u) {
+    const int c = u * kWarp + lane;
+    v[u] = c < nch ? __ldcg(reinterpret_cast<const double2*>(part) + c) : make_double2(0.0, 0.0);
+  }
+  g = v[0].x;
+  h = v[0].y;
+  const int nu = (nch + kWarp - 1) / kWarp;  // FP64 adds are costly on this part: only loaded rounds
+#pragma unroll
+  for (int u = 1; u < kWarpChunks / kWarp; ++u) {
+    if (u < nu) {
+      g += v[u].x;
+      h += v[u].y;
+    }
+  }
+  g = warp_sum(g);
+  h = warp_sum(h);
+}
+
+// Canonical sum for nch > kWarpChunks, by the whole block: thread s sums chunks s, s + 256, ...,
+// then each warp's lane tree, then the warps in order (result in thread 0).
+template <class SH>
+__device__ __forceinline__ void split_combine_block(const double* part, int nch, SH& sh, double& g, double& h) {
+  const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
+  double gs = 0.0, hs = 0.0;
+  for (int base = 0; base < nch; base += 8 * kWalkThreads) {
+    double2 v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int c = base + u * kWalkThreads + tid;
+      v[u] = c < nch ? __ldcg(reinterpret_cast<const double2*>(part) + c) : make_double2(0.0, 0.0);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      if (base + u * kWalkThreads < nch) {
+        gs += v[u].x;
+        hs += v[u].y;
+      }
+    }
+  }
+  gs = warp_sum(gs);
+  hs = warp_sum(hs);
+  if (lane == 0) {
+    sh.red[wib][0] = gs;
+    sh.red[wib][1] = hs;
+  }
+  __syncthreads();
+  g = h = 0.0;
+  if (tid == 0) {
+    for (int wv = 0; wv < kWalkWarps; ++wv) {
+      g += sh.red[wv][0];
+      h += sh.red[wv][1];
+    }
+  }
+}
+
+// d of a combined split column; the holder of chunk 0 also writes gk, hk, dk.
+__device__ __forceinline__ double split_finalize(const WalkParams& p, int32_t kl, bool chunk0, double g, double h, double wj) {
+  return chunk0 ? finalize_column(p, kl, g, h, wj) : column_direction(p, g, h, wj);
+}
+
+// Scatter d x_ij of a chunk reloaded from X, the whole block (eight loads in flight per thread).
+template <int PREC>
+__device__ __forceinline__ void scatter_chunk_global(const WalkParams& p, int64_t start, int len, double d) {
+  int32_t rr[kChunk / kWalkThreads];
+  float xx[kChunk / kWalkThreads];
+#pragma unroll
+  for (int u = 0; u < kChunk / kWalkThreads; ++u) {
+    const int v = threadIdx.x + u * kWalkThreads;
+    rr[u] = -1;
+    xx[u] = 0.0f;
+    if (v < len) {
+      rr[u] = ld_stream_i32(p.row_idx + start + v);
+      xx[u] = ld_stream_f32(p.val + start + v);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < kChunk / kWalkThreads; ++u)
+    scatter_one(p, rr[u], rr[u] >= 0 ? scatter_value<PREC>(d, xx[u]) : 0.0);
+}
+
 // Asynchronous copy of items [i, i + n) (n <= kICap) into sh.items, two 16-byte halves each.
 template <class SH>
 __device__ __forceinline__ void stage_items_async(const WalkParams& p, SH& sh, int64_t i, int n) {
@@ -424,65 +538,100 @@ __device__ void column_pass(const WalkParams& p, SharedWalk<PREC>& sh, int64_t l
     last_nb = nb;
     i += nb;
   }
-  // Chunks of split columns.  Once all chunks of a column have published their sums, the block
-  // combines them itself, in a fixed order that every block holding a chunk of the column repeats
-  // bit for bit (the block holding chunk 0 writes gk, hk, dk), and scatters its chunks: from the
-  // staged copy when the chunk is in the last batch, else reloaded.  The chunks are the ones listed
-  // during the batches, or, when there were more than kSplitCap, every split chunk of [i0, i1).
+  // Chunks of split columns.  Once all chunks of a column have published their sums, each block
+  // holding one of them combines the column itself (split_combine: an order fixed by the chunk count
+  // alone, so every holder gets the same bits; the holder of chunk 0 writes gk, hk, dk), then
+  // scatters its chunks, from the staged copy when the chunk is in the last batch, else reloaded.
   __syncthreads();
   const int ns = sh.n_split;
-  const bool listed = ns <= kSplitCap;
-  const int64_t n_iter = listed ? (int64_t)ns : (i1 - i0);
+  if (ns == 0) return;
+  if (ns <= kSplitCap) {
+    // the listed chunks (item order): their columns, one warp per column of at most kWarpChunks
+    // chunks, then the block for each larger one
+    if (tid < ns) {
+      const Item it = p.items[sh.split_items[tid]];
+      sh.s_kl[tid] = (int32_t)(it.pos - lo);
+      sh.s_nch[tid] = it.nch;
+      sh.s_chunk[tid] = it.chunk;
+      sh.s_w[tid] = it.w;
+      sh.s_len[tid] = it.len;
+      sh.s_start[tid] = it.start;
+    }
+    if (tid == 0) sh.split_ok = 1;
+    __syncthreads();
+    if (tid < ns) {  // column index of each listed chunk: the number of column starts before it
+      int c = 0;
+      for (int k = 1; k <= tid; ++k) c += sh.s_kl[k] != sh.s_kl[k - 1];
+      sh.s_col[tid] = c;
+    }
+    __syncthreads();
+    for (int k = wib; k < ns; k += kWalkWarps) {  // a column start per warp, small columns
+      const bool start = k == 0 || sh.s_kl[k] != sh.s_kl[k - 1];
+      if (!start || sh.s_nch[k] > kWarpChunks) continue;
+      double g, h;
+      if (!split_wait_warp(p, col_cnt + sh.s_kl[k], sh.s_nch[k])) {
+        if (lane == 0) sh.split_ok = 0;
+        continue;
+      }
+      split_combine_warp(p.part + 2 * (sh.split_items[k] - sh.s_chunk[k]), sh.s_nch[k], g, h);
+      if (lane == 0) {
+        const double dj = split_finalize(p, sh.s_kl[k], sh.s_chunk[k] == 0, g, h, sh.s_w[k]);
+        if (dj != 0.0) sh.has_nz = 1;
+        sh.s_d[sh.s_col[k]] = dj;
+      }
+    }
+    for (int k = 0; k < ns; ++k) {  // large columns, the whole block each
+      const bool start = k == 0 || sh.s_kl[k] != sh.s_kl[k - 1];
+      if (!start || sh.s_nch[k] <= kWarpChunks) continue;
+      __syncthreads();
+      if (tid == 0 && !split_wait(p, col_cnt + sh.s_kl[k], sh.s_nch[k])) sh.split_ok = 0;
+      __syncthreads();
+      if (!sh.split_ok) break;
+      double g, h;
+      split_combine_block(p.part + 2 * (sh.split_items[k] - sh.s_chunk[k]), sh.s_nch[k], sh, g, h);
+      if (tid == 0) {
+        const double dj = split_finalize(p, sh.s_kl[k], sh.s_chunk[k] == 0, g, h, sh.s_w[k]);
+        if (dj != 0.0) sh.has_nz = 1;
+        sh.s_d[sh.s_col[k]] = dj;
+      }
+    }
+    __syncthreads();
+    if (!sh.split_ok) return;
+    // scatter every listed chunk, no barriers in between
+    for (int k = 0; k < ns; ++k) {
+      const double d = sh.s_d[sh.s_col[k]];
+      if (d == 0.0) continue;
+      const int64_t gi = sh.split_items[k];
+      if (gi >= last_i && gi < last_i + last_nb) {
+        const int j = (int)(gi - last_i);
+        const int b = sh.ioff[j + 1];
+        for (int v = sh.ioff[j] + tid; v < b; v += kWalkThreads) scatter_one(p, sh.row[v], scatter_value<PREC>(d, sh.x[v]));
+      } else {
+        scatter_chunk_global<PREC>(p, sh.s_start[k], sh.s_len[k], d);
+      }
+    }
+    return;
+  }
+  // more split chunks than listed: every split chunk of [i0, i1) in item order, one at a time
   int32_t kl_prev = -1;
   double d = 0.0;
-  for (int64_t k = 0; k < n_iter; ++k) {
-    const int64_t gi = listed ? sh.split_items[k] : i0 + k;
+  for (int64_t gi = i0; gi < i1; ++gi) {
     const Item it = p.items[gi];
-    if (it.nch == 1) continue;  // only on the unlisted path
+    if (it.nch == 1) continue;
     const int32_t kl = (int32_t)(it.pos - lo);
     if (kl != kl_prev) {
-      if (tid == 0) {
-        uint32_t spins = 0;
-        int ok = 1;
-        while (ld_acquire_u32(col_cnt + kl) != (uint32_t)it.nch) {
-          if (++spins > p.spin_limit) { atomicOr(p.err, kErrTimeout); ok = 0; break; }
-          if ((spins & 1023u) == 0 && err_set(p)) { ok = 0; break; }
-        }
-        sh.split_ok = ok;
-      }
       __syncthreads();
-      if (!sh.split_ok) break;  // uniform: every thread read the flag after the barrier
-      // thread t sums chunks t, t + 256, ... (eight loads in flight), then warps, then in warp order
-      const int64_t first = gi - it.chunk;
-      double gs = 0.0, hs = 0.0;
-      for (int base = 0; base < it.nch; base += 8 * kWalkThreads) {
-        double2 v[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int c = base + u * kWalkThreads + tid;
-          v[u] = c < it.nch ? __ldcg((const double2*)(p.part + 2 * (first + c))) : make_double2(0.0, 0.0);
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          gs += v[u].x;
-          hs += v[u].y;
-        }
-      }
-      gs = warp_sum(gs);
-      hs = warp_sum(hs);
-      if (lane == 0) {
-        sh.red[wib][0] = gs;
-        sh.red[wib][1] = hs;
-      }
+      if (tid == 0) sh.split_ok = split_wait(p, col_cnt + kl, it.nch) ? 1 : 0;
       __syncthreads();
+      if (!sh.split_ok) return;
+      double g, h;
+      if (it.nch <= kWarpChunks) {
+        if (wib == 0) split_combine_warp(p.part + 2 * (gi - it.chunk), it.nch, g, h);
+      } else {
+        split_combine_block(p.part + 2 * (gi - it.chunk), it.nch, sh, g, h);
+      }
       if (tid == 0) {
-        double gt = 0.0, ht = 0.0;
-        for (int wv = 0; wv < kWalkWarps; ++wv) {
-          gt += sh.red[wv][0];
-          ht += sh.red[wv][1];
-        }
-        const double wj = it.w;
-        const double dj = it.chunk == 0 ? finalize_column(p, kl, gt, ht, wj) : column_direction(p, gt, ht, wj);
+        const double dj = split_finalize(p, kl, it.chunk == 0, g, h, it.w);
         if (dj != 0.0) sh.has_nz = 1;
         sh.split_d = dj;
       }
@@ -490,27 +639,7 @@ __device__ void column_pass(const WalkParams& p, SharedWalk<PREC>& sh, int64_t l
       d = sh.split_d;
       kl_prev = kl;
     }
-    if (d == 0.0) continue;
-    if (gi >= last_i && gi < last_i + last_nb) {
-      const int j = (int)(gi - last_i);
-      const int b = sh.ioff[j + 1];
-      for (int v = sh.ioff[j] + tid; v < b; v += kWalkThreads) scatter_one(p, sh.row[v], scatter_value<PREC>(d, sh.x[v]));
-      continue;
-    }
-    int32_t rr[kChunk / kWalkThreads];
-    float xx[kChunk / kWalkThreads];
-#pragma unroll
-    for (int u = 0; u < kChunk / kWalkThreads; ++u) {
-      const int v = tid + u * kWalkThreads;
-      rr[u] = -1;
-      if (v < it.len) {
-        rr[u] = p.row_idx[it.start + v];
-        xx[u] = p.val[it.start + v];
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < kChunk / kWalkThreads; ++u)
-      scatter_one(p, rr[u], rr[u] >= 0 ? scatter_value<PREC>(d, xx[u]) : 0.0);
+    if (d != 0.0) scatter_chunk_global<PREC>(p, it.start, it.len, d);
   }
 }
 
