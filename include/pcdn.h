@@ -91,6 +91,7 @@ typedef struct {
   double walk_s;         /* device time of the bundle-walker launches (CUDA events) */
   double bytes_model;    /* algorithmic bytes of the bundle steps: sum of 16 nnz_B + 33 |U_B| + 16 P */
   int32_t converged;     /* kkt_rel <= eps */
+  int32_t walk_grid;     /* thread blocks of the bundle walker (last launch) */
 } pcdn_stats;
 
 /* Optional per-bundle / per-epoch record of a solve (caller-owned host arrays,

@@ -59,7 +59,7 @@ class pcdn_stats(ctypes.Structure):
                 ("nnz_visited", ctypes.c_int64), ("rows_touched", ctypes.c_int64),
                 ("kernel_launches", ctypes.c_int64), ("F_final", ctypes.c_double), ("kkt_rel", ctypes.c_double),
                 ("kkt0", ctypes.c_double), ("wall_s", ctypes.c_double), ("walk_s", ctypes.c_double),
-                ("bytes_model", ctypes.c_double), ("converged", ctypes.c_int32)]
+                ("bytes_model", ctypes.c_double), ("converged", ctypes.c_int32), ("walk_grid", ctypes.c_int32)]
 
 
 class pcdn_trace(ctypes.Structure):

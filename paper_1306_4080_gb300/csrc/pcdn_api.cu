@@ -81,6 +81,7 @@ struct pcdn_problem {
   int32_t* row_idx = nullptr;
   float* val = nullptr;
   int8_t* y = nullptr;
+  int8_t* ylab = nullptr;  // own copy of y, padded to a multiple of 16 bytes (the walker reads aligned words)
   // X by rows
   int64_t* row_ptr = nullptr;
   int32_t* col_idx = nullptr;
@@ -158,7 +159,7 @@ void free_all(pcdn_problem* p) {
   if (p->owns_x) {
     f(p->col_ptr); f(p->row_idx); f(p->val); f(p->y);
   }
-  f(p->row_ptr); f(p->col_idx); f(p->rval);
+  f(p->row_ptr); f(p->col_idx); f(p->rval); f(p->ylab);
   f(p->w); f(p->w_pos); f(p->mq); f(p->rec); f(p->delta); f(p->touched);
   f(p->item_len); f(p->item_off); f(p->plan);
   f(p->id_perm); f(p->id_item_ptr); f(p->id_items);
@@ -204,6 +205,12 @@ int finish_create(pcdn_problem* p) {
   const int64_t n = p->n, m = p->m, nnz = p->nnz;
   CUDA_TRY(cudaGetDevice(&p->device));
   CUDA_TRY(cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device));
+  {
+    const int64_t npad = (n + 15) / 16 * 16;
+    CUDA_TRY(palloc(p, &p->ylab, npad));
+    CUDA_TRY(cudaMemsetAsync(p->ylab, 0, npad, s));
+    CUDA_TRY(cudaMemcpyAsync(p->ylab, p->y, n, cudaMemcpyDeviceToDevice, s));
+  }
 
   // ---- row-major mirror: stable sort of the CSC entries by row
   CUDA_TRY(palloc(p, &p->row_ptr, n + 1));
@@ -356,7 +363,7 @@ int device_status(pcdn_problem* p) {
   CUDA_TRY(cudaStreamSynchronize(p->stream));
   if (h & kErrTimeout) return fail(PCDN_ETIMEOUT, "a device-side wait between thread blocks timed out");
   if (h & kErrNumeric) return fail(PCDN_ENUMERIC, "non-finite gradient, Hessian diagonal or direction");
-  if (h & kErrRange) return fail(PCDN_ENUMERIC, "maintained quantity out of range after an update (|w^T x| > 700)");
+  if (h & kErrRange) return fail(PCDN_ENUMERIC, "maintained quantity out of range after an update (|w^T x| above about 699)");
   if (h & kErrRefresh) return fail(PCDN_ENUMERIC, "|w^T x| > 700 when recomputing from z = Xw");
   return PCDN_OK;
 }
@@ -436,7 +443,7 @@ int run_walk(pcdn_problem* p, const pcdn_opts* o, const int32_t* perm, int64_t n
   w.col_ptr = p->col_ptr;
   w.row_idx = p->row_idx;
   w.val = p->val;
-  w.y = p->y;
+  w.y = p->ylab;
   w.c = p->c;
   w.w_pos = p->w_pos;
   w.mq = p->mq;
@@ -857,6 +864,7 @@ int pcdn_solve(pcdn_problem* p, int32_t P, double eps, uint64_t seed, const pcdn
     stats->bytes_model = 16.0 * (double)stats->nnz_visited + 33.0 * (double)stats->rows_touched +
                          16.0 * (double)stats->coord_updates;
     stats->converged = converged;
+    stats->walk_grid = grid;
     stats->wall_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
   }
   return converged ? PCDN_OK : PCDN_ENOTCONVERGED;

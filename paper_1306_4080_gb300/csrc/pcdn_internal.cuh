@@ -15,6 +15,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace pcdn {
 
 constexpr int kWarp = 32;
@@ -22,7 +24,7 @@ constexpr int kChunk = 1024;       // max nonzeros of one column work item
 constexpr int kMaxK = 8;           // max step sizes per line-search pass
 constexpr int kWalkThreads = 256;  // threads per walker block
 constexpr int kWalkWarps = kWalkThreads / kWarp;
-constexpr int kListCap = 1024;     // touched rows listed per warp per 32 bitmap words
+constexpr int kWarpRowCap = 256;   // touched rows whose values a warp stages at once
 constexpr int kICap = 256;         // work items staged per batch of the column pass
 constexpr int kECap = 2048;        // nonzeros staged per batch (= 8 per thread)
 constexpr int kSplitCap = 64;      // chunks of split columns a block remembers for its deferred scatter
@@ -45,6 +47,10 @@ struct Item {
   int32_t chunk;
   double w;
 };
+
+// d^T x per row: FP64 in FP64 mode; FP32 in mixed mode, whose per-row arithmetic is FP32 anyway
+// (FP64 instructions, conversions included, run at about 1/40 of the FP32 rate on this part).
+template <int PREC> using DeltaT = typename std::conditional<PREC == 0, double, float>::type;
 
 template <int PREC> struct RecT;
 template <> struct __align__(16) RecT<0> { double cg, ch; };
@@ -70,13 +76,13 @@ struct WalkParams {
   const int64_t* col_ptr;
   const int32_t* row_idx;
   const float* val;
-  const int8_t* y;
+  const int8_t* y;          // labels, padded to a multiple of 16 bytes (read as aligned words)
   double c;
   // state
   double* w_pos;            // w in position order (the partition's order) during the walk
   double* mq;
   void* rec;
-  double* delta;
+  void* delta;              // [n] d^T x of the bundle per row: DeltaT<PREC> (double or float)
   uint32_t* touched;
   int64_t nwords;
   // partition of this walk
@@ -143,6 +149,11 @@ __device__ __forceinline__ void red_release_add_u64(unsigned long long* p, unsig
 __device__ __forceinline__ void red_add_f64(double* p, double v) {
   asm volatile("red.global.add.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
 }
+__device__ __forceinline__ void red_add_f32(float* p, float v) {
+  asm volatile("red.global.add.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+}
+__device__ __forceinline__ void red_add(double* p, double v) { red_add_f64(p, v); }
+__device__ __forceinline__ void red_add(float* p, float v) { red_add_f32(p, v); }
 __device__ __forceinline__ void red_or_u32(uint32_t* p, uint32_t v) {
   asm volatile("red.global.or.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
@@ -163,6 +174,9 @@ __device__ __forceinline__ uint64_t l2_evict_first_policy() {
 }
 __device__ __forceinline__ void cp_async4_stream(void* dst, const void* src, uint64_t pol) {
   asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], 4, %2;" ::"r"(smem_u32(dst)), "l"(src), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async8(void* dst, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
@@ -244,11 +258,14 @@ template <> struct RowCoef<1, 1> {
   }
 };
 
-// Maintained quantity is usable (finite, and for the logistic loss |w^T x| <= 700).
+// Maintained quantity is usable: finite, and for the logistic loss E = e^{w^T x} in [2^-1009,
+// 2^1010), i.e. |w^T x| below about 699.  Tested on the bits (sign and exponent), which keeps the
+// test off the FP64 pipe.
 template <int LOSS>
 __device__ __forceinline__ bool mq_ok(double v) {
-  if (LOSS == 0) return v > 1e-304 && v < 1e304;
-  return isfinite(v);
+  const uint32_t se = (uint32_t)((unsigned long long)__double_as_longlong(v) >> 52);  // sign and exponent
+  if (LOSS == 0) return se >= 14u && se <= 2032u;
+  return (se & 0x7ffu) != 0x7ffu;
 }
 
 // ---------------------------------------------------------------- line-search row terms

@@ -37,6 +37,26 @@
 
 namespace pcdn {
 
+// Phases B and C: a warp's listed touched rows and their staged values.  Mixed mode also stages
+// the rows' FP32 coefficient pairs, from which its logistic line search takes p and s.
+template <int PREC>
+struct RowStage {
+  double mq[kWarpRowCap];
+  DeltaT<PREC> dl[kWarpRowCap];
+  RecT<1> rc[PREC == 1 ? kWarpRowCap : 1];
+  int32_t yw[kWarpRowCap];  // the aligned 4-byte word of y holding the row's label
+  int32_t row[kWarpRowCap];
+};
+
+// One touched row's values as phases B and C see them.
+template <int PREC>
+struct RowVals {
+  DeltaT<PREC> dl;  // d^T x_i
+  double mq;        // maintained quantity (E = e^{w^T x_i}, or b = 1 - y w^T x_i)
+  RecT<1> rc;       // mixed mode: the FP32 coefficient pair
+  int y;
+};
+
 // Phase A scratch that phases B and C reuse for their row lists.
 template <int PREC>
 struct StageA {
@@ -77,7 +97,7 @@ struct SharedWalk {
   float x[kECap];
   union {
     StageA<PREC> a;
-    int32_t list[kWalkWarps][kListCap];
+    RowStage<PREC> rs[kWalkWarps];
   } u;
 };
 
@@ -228,29 +248,13 @@ template <> struct ColAcc<1> {
   }
 };
 
+// delta_r += v and mark row r (r < 0: nothing).  v = d_j x_ij in DeltaT<PREC>: the caller converts
+// d_j once per column (dv) and forms dv * x.
 template <int PREC>
-__device__ __forceinline__ double scatter_value(double d, float x) {
-  if constexpr (PREC == 0) return d * (double)x;
-  else return (double)((float)d * x);
-}
-
-// delta_r += v and mark row r (r < 0: nothing).
-__device__ __forceinline__ void scatter_one(const WalkParams& p, int32_t r, double v) {
-  if (r >= 0 && v != 0.0) {
-    red_add_f64(p.delta + r, v);
+__device__ __forceinline__ void scatter_one(const WalkParams& p, int32_t r, DeltaT<PREC> v) {
+  if (r >= 0 && v != DeltaT<PREC>(0)) {
+    red_add(static_cast<DeltaT<PREC>*>(p.delta) + r, v);
     red_or_u32(p.touched + (r >> 5), 1u << (r & 31));
-  }
-}
-
-// Scatter d x_ij of one work item (reloaded from global memory) into delta.
-template <int PREC>
-__device__ __forceinline__ void item_scatter_global(const WalkParams& p, const Item& it, double d) {
-  const int lane = threadIdx.x & 31;
-  const int64_t end = it.start + it.len;
-  for (int64_t e0 = it.start; e0 < end; e0 += kWarp) {
-    const int64_t e = e0 + lane;
-    if (e < end) scatter_one(p, p.row_idx[e], scatter_value<PREC>(d, p.val[e]));
-    else scatter_one(p, -1, 0.0);
   }
 }
 
@@ -381,6 +385,7 @@ __device__ __forceinline__ double split_finalize(const WalkParams& p, int32_t kl
 // Scatter d x_ij of a chunk reloaded from X, the whole block (eight loads in flight per thread).
 template <int PREC>
 __device__ __forceinline__ void scatter_chunk_global(const WalkParams& p, int64_t start, int len, double d) {
+  const DeltaT<PREC> dv = (DeltaT<PREC>)d;
   int32_t rr[kChunk / kWalkThreads];
   float xx[kChunk / kWalkThreads];
 #pragma unroll
@@ -395,7 +400,7 @@ __device__ __forceinline__ void scatter_chunk_global(const WalkParams& p, int64_
   }
 #pragma unroll
   for (int u = 0; u < kChunk / kWalkThreads; ++u)
-    scatter_one(p, rr[u], rr[u] >= 0 ? scatter_value<PREC>(d, xx[u]) : 0.0);
+    scatter_one<PREC>(p, rr[u], rr[u] >= 0 ? dv * (DeltaT<PREC>)xx[u] : DeltaT<PREC>(0));
 }
 
 // Asynchronous copy of items [i, i + n) (n <= kICap) into sh.items, two 16-byte halves each.
@@ -526,12 +531,9 @@ __device__ void column_pass(const WalkParams& p, SharedWalk<PREC>& sh, int64_t l
     for (int j = wib; j < nb; j += kWalkWarps) {
       const double d = st.d[j];
       if (d == 0.0) continue;
+      const DeltaT<PREC> dv = (DeltaT<PREC>)d;
       const int b = sh.ioff[j + 1];
-      for (int v0 = sh.ioff[j]; v0 < b; v0 += kWarp) {
-        const int v = v0 + lane;
-        if (v < b) scatter_one(p, sh.row[v], scatter_value<PREC>(d, sh.x[v]));
-        else scatter_one(p, -1, 0.0);
-      }
+      for (int v = sh.ioff[j] + lane; v < b; v += kWarp) scatter_one<PREC>(p, sh.row[v], dv * (DeltaT<PREC>)sh.x[v]);
     }
     __syncthreads();  // the staging area is reused by the next batch
     last_i = i;
@@ -605,7 +607,8 @@ __device__ void column_pass(const WalkParams& p, SharedWalk<PREC>& sh, int64_t l
       if (gi >= last_i && gi < last_i + last_nb) {
         const int j = (int)(gi - last_i);
         const int b = sh.ioff[j + 1];
-        for (int v = sh.ioff[j] + tid; v < b; v += kWalkThreads) scatter_one(p, sh.row[v], scatter_value<PREC>(d, sh.x[v]));
+        const DeltaT<PREC> dv = (DeltaT<PREC>)d;
+        for (int v = sh.ioff[j] + tid; v < b; v += kWalkThreads) scatter_one<PREC>(p, sh.row[v], dv * (DeltaT<PREC>)sh.x[v]);
       } else {
         scatter_chunk_global<PREC>(p, sh.s_start[k], sh.s_len[k], d);
       }
@@ -664,8 +667,9 @@ struct LsAcc<LOSS, 0> {
 #pragma unroll
     for (int q = 0; q < kMaxK; ++q) s[q] = 0.0;
   }
-  __device__ __forceinline__ void row(double dl, double mq, int y, const double* alpha, const float*, int K,
-                                      bool halving) {
+  __device__ __forceinline__ void row(const RowVals<0>& rv, const double* alpha, const float*, int K, bool halving) {
+    const double dl = rv.dl, mq = rv.mq;
+    const int y = rv.y;
     if constexpr (LOSS == 0) {
       // form A (E <= 1): coefficient p, expm1(+u), label term -[y=+1] u
       // form B (E > 1):  coefficient s, expm1(-u), label term +[y=-1] u
@@ -721,13 +725,15 @@ struct LsAcc<LOSS, 1> {
 #pragma unroll
     for (int q = 0; q < kMaxK; ++q) { s[q] = 0.0f; cmp[q] = 0.0f; }
   }
-  __device__ __forceinline__ void row(double dl, double mq, int y, const double* alpha, const float* alpha_f, int K,
-                                      bool) {
-    const float dlf = (float)dl;
+  __device__ __forceinline__ void row(const RowVals<1>& rv, const double* alpha, const float* alpha_f, int K, bool) {
+    const float dlf = rv.dl;
     if constexpr (LOSS == 0) {
-      float e = (float)mq, pp, ss;
-      if (e <= 1.0f) { ss = 1.0f / (1.0f + e); pp = e * ss; }
-      else { const float rr = 1.0f / e; pp = 1.0f / (1.0f + rr); ss = rr * pp; }
+      // p = E/(1+E) and s = 1/(1+E) from the row's FP32 coefficient pair: |cg| is s (y = +1) or p
+      // (y = -1) as computed from E, ch = p s; the other one is 1 - |cg| when |cg| <= 1/2 (then
+      // it is the larger, so 1 - |cg| is accurate), else ch / |cg|.
+      const float known = fabsf(rv.rc.cg);
+      const float other = known <= 0.5f ? 1.0f - known : rv.rc.ch / known;
+      const float pp = rv.y > 0 ? other : known, ss = rv.y > 0 ? known : other;
       const bool use_p = pp <= ss;
       const float a = use_p ? pp : ss;
       const float vf = use_p ? dlf : -dlf;
@@ -735,8 +741,10 @@ struct LsAcc<LOSS, 1> {
       for (int q = 0; q < kMaxK; ++q)
         if (q < K) kahan_add(s[q], cmp[q], lr_remainder(a, alpha_f[q] * vf));
     } else {
-      const double yd = (double)y * dl;
-      const float ydf = (float)yd;
+      const double mq = rv.mq;
+      const int y = rv.y;
+      const float ydf = y > 0 ? dlf : -dlf;
+      const double yd = (double)ydf;
       const float bf = (float)mq;
       const bool b_pos = mq > 0.0;
 #pragma unroll
@@ -755,113 +763,148 @@ struct LsAcc<LOSS, 1> {
 
 // Update of one touched row after acceptance with step alpha (Algorithm 4).
 template <int LOSS, int PREC>
-__device__ __forceinline__ void row_update(const WalkParams& p, int32_t r, double dl, double mq, int y, double alpha) {
+__device__ __forceinline__ void row_update(const WalkParams& p, int32_t r, const RowVals<PREC>& rv, double alpha,
+                                           float alpha_f) {
+  double mq = rv.mq;
   if constexpr (LOSS == 0) {
     if constexpr (PREC == 0) {
-      mq = mq * exp(alpha * dl);
+      mq = mq * exp(alpha * rv.dl);
     } else {
       // E e^u = E + E (e^u - 1) with FP32 expm1 where that is accurate to FP32 relative to e^u
       // (u >= -1/2, so 1 + expm1(u) >= 0.6, and below FP32 overflow); FP64 exp elsewhere
-      const float uf = (float)alpha * (float)dl;
+      const float uf = alpha_f * rv.dl;
       if (uf >= -0.5f && uf < 80.0f) mq = fma(mq, (double)expm1f(uf), mq);
-      else mq = mq * exp(alpha * dl);
+      else mq = mq * exp(alpha * (double)rv.dl);
     }
   } else {
-    mq = mq - alpha * (double)y * dl;
+    if constexpr (PREC == 0) mq = mq - alpha * (double)rv.y * rv.dl;
+    else mq = mq - alpha * (double)(rv.y > 0 ? rv.dl : -rv.dl);
   }
   if (!mq_ok<LOSS>(mq)) atomicOr(p.err, kErrRange);
   p.mq[r] = mq;
-  ((RecT<PREC>*)p.rec)[r] = RowCoef<LOSS, PREC>::make(mq, y);
+  ((RecT<PREC>*)p.rec)[r] = RowCoef<LOSS, PREC>::make(mq, rv.y);
 }
 
-// The touched rows of this warp's fixed bitmap range.  When the range is at most 32 words the
-// listing made in phase B is kept (in shared memory and the lane's word) for phase C.
+// ---------------------------------------------------------------- phases B and C: the touched rows
+// Warp w of the grid owns the bitmap words [w0, w1) (equal contiguous shares).  It lists its touched
+// rows (lane l reads word l of each group of 32), copies each listed row's delta, maintained
+// quantity and label word into its own shared-memory area kWarpRowCap rows at a time (cp.async,
+// all copies of a round in flight at once) and evaluates the rows one lane per row; no block
+// barriers.  When the warp's rows fit one group and one round (the usual case) the copies stay
+// for the later line-search passes and for phase C.
 struct WarpRows {
-  int64_t w0, w1;
-  bool single;
-  uint32_t word;  // the lane's bitmap word (single range)
-  int total;      // rows listed (single range)
+  int32_t w0, w1;  // n_samples < 2^31: at most 2^26 words
+  int n;           // rows listed (cached)
+  bool cached;
+  uint32_t word;   // this lane's bitmap word (cached)
 };
 
 __device__ __forceinline__ WarpRows warp_rows_range(const WalkParams& p) {
-  const int wib = threadIdx.x >> 5;
   const int64_t W = (int64_t)gridDim.x * kWalkWarps;
-  const int64_t gw = (int64_t)blockIdx.x * kWalkWarps + wib;
+  const int64_t gw = (int64_t)blockIdx.x * kWalkWarps + (threadIdx.x >> 5);
   const int64_t per = (p.nwords + W - 1) / W;
   WarpRows wr;
-  wr.w0 = gw * per;
-  wr.w1 = min(p.nwords, wr.w0 + per);
-  wr.single = per <= kWarp;
+  wr.w0 = (int32_t)min(p.nwords, gw * per);
+  wr.w1 = (int32_t)min(p.nwords, (int64_t)wr.w0 + per);
+  wr.n = 0;
+  wr.cached = false;
   wr.word = 0u;
-  wr.total = 0;
   return wr;
 }
 
-// List the touched rows of words [base, base+32) into `list`; returns the count (all lanes).
-__device__ __forceinline__ int list_group(const WalkParams& p, int64_t base, int64_t w1, int32_t* list, uint32_t& word) {
+// Counts the touched rows of words [base, min(base + 32, w1)); returns the count (every lane);
+// `word` is this lane's word, `off` the rows of the lanes before it.
+__device__ __forceinline__ int scan_group(const WalkParams& p, int32_t base, int32_t w1, uint32_t& word, int& off) {
   const int lane = threadIdx.x & 31;
-  const int64_t wi = base + lane;
-  word = (wi < w1) ? p.touched[wi] : 0u;
-  if (__ballot_sync(0xffffffffu, word != 0u) == 0u) return 0;
+  const int32_t wi = base + lane;
+  word = wi < w1 ? p.touched[wi] : 0u;
   const int cnt = __popc(word);
-  int off = cnt;
+  int x = cnt;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const int t = __shfl_up_sync(0xffffffffu, off, o);
-    if (lane >= o) off += t;
+    const int t = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += t;
   }
-  const int total = __shfl_sync(0xffffffffu, off, 31);
-  off -= cnt;
-  uint32_t bits = word;
-  while (bits) {
-    const int b = __ffs(bits) - 1;
-    bits &= bits - 1;
-    list[off++] = (int32_t)(wi * 32 + b);
-  }
-  __syncwarp();
-  return total;
+  off = x - cnt;
+  return __shfl_sync(0xffffffffu, x, 31);
 }
 
-// fn(row, d^T x, maintained, label) for listed rows [0, total).
-template <class Fn>
-__device__ __forceinline__ void for_listed_rows(const WalkParams& p, const int32_t* list, int total, Fn&& fn) {
-  const int lane = threadIdx.x & 31;
-  for (int i = lane; i < total; i += kWarp) {
-    const int32_t r = list[i];
-    fn(r, p.delta[r], p.mq[r], (int)p.y[r]);
-  }
-}
-
-// Phase B walk over the warp's range (the listing is kept when the range is one group).
-template <class Fn>
-__device__ __forceinline__ void rows_phase_b(const WalkParams& p, WarpRows& wr, int32_t* list, Fn&& fn) {
-  for (int64_t base = wr.w0; base < wr.w1; base += kWarp) {
-    uint32_t word;
-    const int total = list_group(p, base, wr.w1, list, word);
-    for_listed_rows(p, list, total, fn);
-    __syncwarp();
-    if (wr.single) {
-      wr.word = word;
-      wr.total = total;
+// Lists the group's rows with index in [i0, i0 + kWarpRowCap) (row order) into rs.row[index - i0].
+template <int PREC>
+__device__ __forceinline__ void list_window(RowStage<PREC>& rs, int32_t base, uint32_t word, int off, int i0) {
+  if (off < i0 + kWarpRowCap && off + __popc(word) > i0) {
+    const int32_t wi = base + (threadIdx.x & 31);
+    uint32_t bits = word;
+    int k = off;
+    while (bits) {
+      const int b = __ffs(bits) - 1;
+      bits &= bits - 1;
+      if (k >= i0 && k < i0 + kWarpRowCap) rs.row[k - i0] = wi * 32 + b;
+      ++k;
     }
   }
+  __syncwarp();
 }
 
-// Phase C walk: every touched row, then the warp's bitmap words are cleared.
-template <class Fn>
-__device__ __forceinline__ void rows_phase_c(const WalkParams& p, const WarpRows& wr, int32_t* list, Fn&& fn) {
+// Copies delta, maintained quantity, label word (and in mixed mode the coefficient pair) of listed
+// rows [0, cnt) into the warp's staging arrays and waits for them.
+template <int LOSS, int PREC>
+__device__ __forceinline__ void stage_rows(const WalkParams& p, RowStage<PREC>& rs, int cnt) {
+  for (int i = threadIdx.x & 31; i < cnt; i += kWarp) {
+    const int32_t r = rs.row[i];
+    if constexpr (PREC == 0) cp_async8(&rs.dl[i], static_cast<const double*>(p.delta) + r);
+    else cp_async4(&rs.dl[i], static_cast<const float*>(p.delta) + r);
+    cp_async8(&rs.mq[i], p.mq + r);
+    if constexpr (PREC == 1 && LOSS == 0) cp_async8(&rs.rc[i], static_cast<const RecT<1>*>(p.rec) + r);
+    cp_async4(&rs.yw[i], p.y + (r & ~3));
+  }
+  cp_async_commit();
+  cp_async_wait_all();
+  __syncwarp();
+}
+
+// fn(row, values) for staged rows [0, cnt).
+template <int LOSS, int PREC, class Fn>
+__device__ __forceinline__ void for_staged_rows(const RowStage<PREC>& rs, int cnt, Fn&& fn) {
+  for (int i = threadIdx.x & 31; i < cnt; i += kWarp) {
+    const int32_t r = rs.row[i];
+    RowVals<PREC> v;
+    v.dl = rs.dl[i];
+    v.mq = rs.mq[i];
+    if constexpr (PREC == 1 && LOSS == 0) v.rc = rs.rc[i];
+    v.y = (int)(int8_t)(rs.yw[i] >> (8 * (r & 3)));
+    fn(r, v);
+  }
+}
+
+// Every touched row of the warp once (a line-search pass or phase C).  The first call of a bundle
+// decides whether the staged rows stay (wr.cached); phase C (clear = true) also clears the words.
+template <int LOSS, int PREC, class Fn>
+__device__ __forceinline__ void warp_rows(const WalkParams& p, RowStage<PREC>& rs, WarpRows& wr, bool clear, Fn&& fn) {
   const int lane = threadIdx.x & 31;
-  if (wr.single) {
-    for_listed_rows(p, list, wr.total, fn);
-    if (wr.word != 0u) p.touched[wr.w0 + lane] = 0u;
+  if (wr.cached) {
+    for_staged_rows<LOSS, PREC>(rs, wr.n, fn);
+    if (clear && wr.word != 0u) p.touched[wr.w0 + lane] = 0u;
     return;
   }
-  for (int64_t base = wr.w0; base < wr.w1; base += kWarp) {
+  const bool single = wr.w1 - wr.w0 <= kWarp;
+  for (int32_t base = wr.w0; base < wr.w1; base += kWarp) {
     uint32_t word;
-    const int total = list_group(p, base, wr.w1, list, word);
-    for_listed_rows(p, list, total, fn);
-    __syncwarp();
-    if (word != 0u) p.touched[base + lane] = 0u;
+    int off;
+    const int n = scan_group(p, base, wr.w1, word, off);
+    for (int i0 = 0; i0 < n; i0 += kWarpRowCap) {
+      const int cnt = min(kWarpRowCap, n - i0);
+      list_window(rs, base, word, off, i0);
+      stage_rows<LOSS, PREC>(p, rs, cnt);
+      for_staged_rows<LOSS, PREC>(rs, cnt, fn);
+      __syncwarp();  // the next round overwrites the list and staging arrays
+    }
+    if (clear && word != 0u) p.touched[base + lane] = 0u;
+    if (single && n <= kWarpRowCap && !clear) {
+      wr.cached = true;
+      wr.n = n;
+      wr.word = word;
+    }
   }
 }
 
@@ -933,8 +976,8 @@ __global__ void __launch_bounds__(kWalkThreads, 2) walk_kernel(WalkParams p) {
     Decision dec;
     // warps that sum the bundle-position terms (about 128 positions each)
     const int pos_warps = (int)min((int64_t)kWalkWarps, max((int64_t)1, (k1 - k0 + 127) / 128));
-    int32_t* list = sh.u.list[wib];
     WarpRows wr = warp_rows_range(p);
+    RowStage<PREC>& rs = sh.u.rs[wib];
     for (;;) {
       // step sizes of this pass: K1 on the first pass, K on later ones
       const int K = q0 == 0 ? p.K1 : p.K;
@@ -958,8 +1001,8 @@ __global__ void __launch_bounds__(kWalkThreads, 2) walk_kernel(WalkParams p) {
       LsAcc<LOSS, PREC> acc;
       acc.zero();
       int nrows = 0;
-      rows_phase_b(p, wr, list, [&](int32_t, double dl, double mq, int y) {
-        acc.row(dl, mq, y, alpha, alpha_f, K, halving);
+      warp_rows<LOSS, PREC>(p, rs, wr, false, [&](int32_t, const RowVals<PREC>& v) {
+        acc.row(v, alpha, alpha_f, K, halving);
         ++nrows;
       });
       // line-search sums of this warp
@@ -1151,9 +1194,10 @@ __global__ void __launch_bounds__(kWalkThreads, 2) walk_kernel(WalkParams p) {
         if (d != 0.0) p.w_pos[lo + kl] += a * d;
       }
     }
-    rows_phase_c(p, wr, list, [&](int32_t r, double dl, double mq, int y) {
-      if (accept) row_update<LOSS, PREC>(p, r, dl, mq, y, a);
-      p.delta[r] = 0.0;
+    const float a_f = (float)a;
+    warp_rows<LOSS, PREC>(p, rs, wr, true, [&](int32_t r, const RowVals<PREC>& v) {
+      if (accept) row_update<LOSS, PREC>(p, r, v, a, a_f);
+      static_cast<DeltaT<PREC>*>(p.delta)[r] = DeltaT<PREC>(0);
     });
     // barrier 3, with the next bundle's first batch planned and its nonzero copies issued between
     // arriving and waiting (X and the plan are read-only)
