@@ -474,6 +474,8 @@ int run_walk(pcdn_problem* p, const pcdn_opts* o, const int32_t* perm, int64_t n
   w.beta = o->beta;
   w.gamma = o->gamma;
   w.nu = o->nu;
+  w.c_f = (float)p->c;
+  w.nu_f = (float)o->nu;
   w.q_max = o->q_max;
   // step sizes per pass: almost every bundle accepts q = 0, so the first pass tests that alone;
   // a further pass (one more barrier) tests four

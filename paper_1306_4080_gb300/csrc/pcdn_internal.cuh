@@ -107,6 +107,7 @@ struct WalkParams {
   uint32_t spin_limit;
   // Armijo
   double sigma, beta, gamma, nu;
+  float c_f, nu_f;          // c and nu in FP32 (mixed mode's column directions)
   int32_t q_max, K;         // K step sizes per line-search pass after the first
   int32_t K1;               // step sizes in the first pass
   // outputs

@@ -57,11 +57,20 @@ struct RowVals {
   int y;
 };
 
+// Per-column g and h: FP64 in FP64 mode, FP32 in mixed mode (whose column sums are FP32).
+template <int PREC> using GHT = typename std::conditional<PREC == 0, double, float>::type;
+
+// A column's terms of Delta (Eq. 7): g d, h d^2, |w + d| - |w| (zero when d = 0).
+template <int PREC>
+struct ColTerms {
+  GHT<PREC> gd, hdd, l1;
+};
+
 // Phase A scratch that phases B and C reuse for their row lists.
 template <int PREC>
 struct StageA {
-  double g[kICap];
-  double h[kICap];
+  GHT<PREC> g[kICap];
+  GHT<PREC> h[kICap];
   double d[kICap];
   RecT<PREC> rec[kECap];
 };
@@ -83,6 +92,8 @@ struct SharedWalk {
   double s_w[kSplitCap];
   int64_t s_start[kSplitCap];
   double s_d[kSplitCap];
+  ColTerms<PREC> s_terms[kSplitCap];
+  double apart[3];  // the block's phase-A sums of Delta's terms (Acc slots): g d, h d^2, |w + d| - |w|
   int scan_tot[kWalkWarps];
   Decision dec;
   double tot[kPartStride];
@@ -106,6 +117,7 @@ template <int PREC> struct Acc;
 template <> struct Acc<0> {
   double v = 0.0;
   __device__ __forceinline__ void add(double x) { v += x; }
+  __device__ __forceinline__ void add_t(double x) { v += x; }
   __device__ __forceinline__ void add_acc(const Acc& o) { v += o.v; }
   __device__ __forceinline__ void warp_reduce() { v = warp_sum(v); }
   // sum over aligned groups of T lanes (T a power of two, at most 32)
@@ -119,6 +131,7 @@ template <> struct Acc<0> {
 template <> struct Acc<1> {
   dfloat v = {0.0f, 0.0f};
   __device__ __forceinline__ void add(double x) { v = df_add(v, df_make(x)); }
+  __device__ __forceinline__ void add_t(float x) { v = df_add_f(v, x); }
   __device__ __forceinline__ void add_acc(const Acc& o) { v = df_add(v, o.v); }
   __device__ __forceinline__ void warp_reduce() { v = df_warp_sum(v); }
   __device__ __forceinline__ void group_reduce(int T) {
@@ -242,9 +255,9 @@ template <> struct ColAcc<1> {
     g = fmaf(x, r.cg, g);
     h = fmaf(x * x, r.ch, h);
   }
-  __device__ __forceinline__ void reduce(double& go, double& ho) const {
-    go = (double)warp_sum_f(g);
-    ho = (double)warp_sum_f(h);
+  __device__ __forceinline__ void reduce(float& go, float& ho) const {
+    go = warp_sum_f(g);
+    ho = warp_sum_f(h);
   }
 };
 
@@ -266,13 +279,38 @@ __device__ __forceinline__ double column_direction(const WalkParams& p, double& 
   return newton_direction(g, h, wj);
 }
 
-// As column_direction, and writes gk, hk, dk of bundle position kl.
-__device__ __forceinline__ double finalize_column(const WalkParams& p, int32_t kl, double g, double h, double wj) {
-  const double d = column_direction(p, g, h, wj);
-  p.gk[kl] = g;
-  p.hk[kl] = h;
-  p.dk[kl] = d;
-  if (!isfinite(g) || !isfinite(h) || !isfinite(d)) atomicOr(p.err, kErrNumeric);
+// A column's direction (Eq. 5) from its sums g, h (without the factor c; h <= 0 replaced by nu)
+// and its terms of Delta (Eq. 7, their L1 part also the L1 change of the full step alpha = 1);
+// with `write`, gk, hk, dk of position kl too.  FP64 mode works in FP64.  Mixed mode works in FP32
+// but for |w + d| - |w| (FP64, to keep its cancellation exact) and keeps d = -w exact, so that a
+// coordinate set to zero is zero: FP64 instructions are costly on this part.
+template <int PREC>
+__device__ __forceinline__ double finalize(const WalkParams& p, int32_t kl, GHT<PREC> g, GHT<PREC> h, double wj, bool write,
+                                           ColTerms<PREC>& t) {
+  double d;
+  if constexpr (PREC == 0) {
+    d = column_direction(p, g, h, wj);
+    t.gd = g * d;
+    t.hdd = h * d * d;
+  } else {
+    g *= p.c_f;
+    h *= p.c_f;
+    if (h <= 0.0f) h = p.nu_f;
+    const float wf = (float)wj;
+    if (g + 1.0f <= h * wf) d = (double)(-(g + 1.0f) / h);
+    else if (g - 1.0f >= h * wf) d = (double)(-(g - 1.0f) / h);
+    else d = -wj;
+    const float df = (float)d;
+    t.gd = g * df;
+    t.hdd = h * df * df;
+  }
+  t.l1 = d != 0.0 ? (GHT<PREC>)(fabs(wj + d) - fabs(wj)) : GHT<PREC>(0);
+  if (write) {
+    p.gk[kl] = (double)g;
+    p.hk[kl] = (double)h;
+    p.dk[kl] = d;
+    if (!isfinite(g) || !isfinite(h) || !isfinite(d)) atomicOr(p.err, kErrNumeric);
+  }
   return d;
 }
 
@@ -377,9 +415,15 @@ __device__ __forceinline__ void split_combine_block(const double* part, int nch,
   }
 }
 
-// d of a combined split column; the holder of chunk 0 also writes gk, hk, dk.
-__device__ __forceinline__ double split_finalize(const WalkParams& p, int32_t kl, bool chunk0, double g, double h, double wj) {
-  return chunk0 ? finalize_column(p, kl, g, h, wj) : column_direction(p, g, h, wj);
+// d of a combined split column (FP64 sums) and, for the holder of chunk 0, its terms of Delta (zero
+// for the other holders, so that each column counts once); the holder of chunk 0 also writes gk,
+// hk, dk.
+template <int PREC>
+__device__ __forceinline__ double split_finalize(const WalkParams& p, int32_t kl, bool chunk0, double g, double h, double wj,
+                                                 ColTerms<PREC>& t) {
+  const double d = finalize<PREC>(p, kl, (GHT<PREC>)g, (GHT<PREC>)h, wj, chunk0, t);
+  if (!chunk0) t = ColTerms<PREC>{0, 0, 0};
+  return d;
 }
 
 // Scatter d x_ij of a chunk reloaded from X, the whole block (eight loads in flight per thread).
@@ -451,7 +495,10 @@ __device__ void column_pass(const WalkParams& p, SharedWalk<PREC>& sh, int64_t l
   const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
   StageA<PREC>& st = sh.u.a;
   const RecT<PREC>* rec = (const RecT<PREC>*)p.rec;
-  if (tid == 0) sh.n_split = 0;
+  if (tid == 0) {
+    sh.n_split = 0;
+    sh.apart[0] = sh.apart[1] = sh.apart[2] = Acc<PREC>().store();
+  }
   __syncthreads();
   int64_t last_i = i0;  // the batch still staged in shared memory
   int last_nb = 0;
@@ -497,7 +544,7 @@ __device__ void column_pass(const WalkParams& p, SharedWalk<PREC>& sh, int64_t l
       const int a = sh.ioff[j], b = sh.ioff[j + 1];
       ColAcc<PREC> acc;
       for (int v = a + lane; v < b; v += kWarp) acc.add(sh.x[v], st.rec[v]);
-      double g, h;
+      GHT<PREC> g, h;
       acc.reduce(g, h);
       if (it.nch == 1) {
         if (lane == 0) {
@@ -510,23 +557,51 @@ __device__ void column_pass(const WalkParams& p, SharedWalk<PREC>& sh, int64_t l
       // batches by every block that holds one of its chunks
       if (lane == 0) {
         const int64_t gi = i + j;  // global item index
-        p.part[2 * gi] = g;
-        p.part[2 * gi + 1] = h;
+        p.part[2 * gi] = (double)g;
+        p.part[2 * gi + 1] = (double)h;
         red_release_add_u32(col_cnt + (int32_t)(it.pos - lo), 1u);
       }
     }
     __syncthreads();
-    // one thread per item: the direction (Eq. 5)
-    if (tid < nb) {
-      const Item it = sh.items[tid];
-      double d = 0.0;
-      if (it.nch == 1) {
-        d = finalize_column(p, (int32_t)(it.pos - lo), st.g[tid], st.h[tid], sh.items[tid].w);
-        if (d != 0.0) sh.has_nz = 1;
+    // one thread per item: the direction (Eq. 5) and the column's terms of Delta, summed per warp
+    {
+      ColTerms<PREC> ct{0, 0, 0};
+      if (tid < nb) {
+        const Item it = sh.items[tid];
+        double d = 0.0;
+        if (it.nch == 1) {
+          d = finalize<PREC>(p, (int32_t)(it.pos - lo), st.g[tid], st.h[tid], it.w, true, ct);
+          if (d != 0.0) sh.has_nz = 1;
+        }
+        st.d[tid] = d;
       }
-      st.d[tid] = d;
+      if (wib * kWarp < nb) {
+        Acc<PREC> a0, a1, a2;
+        a0.add_t(ct.gd);
+        a1.add_t(ct.hdd);
+        a2.add_t(ct.l1);
+        a0.warp_reduce();
+        a1.warp_reduce();
+        a2.warp_reduce();
+        if (lane == 0) {
+          sh.red[wib][0] = a0.store();
+          sh.red[wib][1] = a1.store();
+          sh.red[wib][2] = a2.store();
+        }
+      }
     }
     __syncthreads();
+    if (tid == 0) {  // the block's sums, batches and warps in order
+      Acc<PREC> a0 = Acc<PREC>::load(sh.apart[0]), a1 = Acc<PREC>::load(sh.apart[1]), a2 = Acc<PREC>::load(sh.apart[2]);
+      for (int wv = 0; wv * kWarp < nb; ++wv) {
+        a0.add_acc(Acc<PREC>::load(sh.red[wv][0]));
+        a1.add_acc(Acc<PREC>::load(sh.red[wv][1]));
+        a2.add_acc(Acc<PREC>::load(sh.red[wv][2]));
+      }
+      sh.apart[0] = a0.store();
+      sh.apart[1] = a1.store();
+      sh.apart[2] = a2.store();
+    }
     // one warp per item: scatter from the staged copy
     for (int j = wib; j < nb; j += kWalkWarps) {
       const double d = st.d[j];
@@ -577,7 +652,7 @@ __device__ void column_pass(const WalkParams& p, SharedWalk<PREC>& sh, int64_t l
       }
       split_combine_warp(p.part + 2 * (sh.split_items[k] - sh.s_chunk[k]), sh.s_nch[k], g, h);
       if (lane == 0) {
-        const double dj = split_finalize(p, sh.s_kl[k], sh.s_chunk[k] == 0, g, h, sh.s_w[k]);
+        const double dj = split_finalize<PREC>(p, sh.s_kl[k], sh.s_chunk[k] == 0, g, h, sh.s_w[k], sh.s_terms[sh.s_col[k]]);
         if (dj != 0.0) sh.has_nz = 1;
         sh.s_d[sh.s_col[k]] = dj;
       }
@@ -592,13 +667,25 @@ __device__ void column_pass(const WalkParams& p, SharedWalk<PREC>& sh, int64_t l
       double g, h;
       split_combine_block(p.part + 2 * (sh.split_items[k] - sh.s_chunk[k]), sh.s_nch[k], sh, g, h);
       if (tid == 0) {
-        const double dj = split_finalize(p, sh.s_kl[k], sh.s_chunk[k] == 0, g, h, sh.s_w[k]);
+        const double dj = split_finalize<PREC>(p, sh.s_kl[k], sh.s_chunk[k] == 0, g, h, sh.s_w[k], sh.s_terms[sh.s_col[k]]);
         if (dj != 0.0) sh.has_nz = 1;
         sh.s_d[sh.s_col[k]] = dj;
       }
     }
     __syncthreads();
     if (!sh.split_ok) return;
+    if (tid == 0) {  // the split columns' terms of Delta, in column order (held chunk 0 only)
+      Acc<PREC> a0 = Acc<PREC>::load(sh.apart[0]), a1 = Acc<PREC>::load(sh.apart[1]), a2 = Acc<PREC>::load(sh.apart[2]);
+      const int ncol = sh.s_col[ns - 1] + 1;
+      for (int c = 0; c < ncol; ++c) {
+        a0.add_t(sh.s_terms[c].gd);
+        a1.add_t(sh.s_terms[c].hdd);
+        a2.add_t(sh.s_terms[c].l1);
+      }
+      sh.apart[0] = a0.store();
+      sh.apart[1] = a1.store();
+      sh.apart[2] = a2.store();
+    }
     // scatter every listed chunk, no barriers in between
     for (int k = 0; k < ns; ++k) {
       const double d = sh.s_d[sh.s_col[k]];
@@ -634,9 +721,19 @@ __device__ void column_pass(const WalkParams& p, SharedWalk<PREC>& sh, int64_t l
         split_combine_block(p.part + 2 * (gi - it.chunk), it.nch, sh, g, h);
       }
       if (tid == 0) {
-        const double dj = split_finalize(p, kl, it.chunk == 0, g, h, it.w);
+        ColTerms<PREC> ct;
+        const double dj = split_finalize<PREC>(p, kl, it.chunk == 0, g, h, it.w, ct);
         if (dj != 0.0) sh.has_nz = 1;
         sh.split_d = dj;
+        if (it.chunk == 0) {
+          Acc<PREC> a0 = Acc<PREC>::load(sh.apart[0]), a1 = Acc<PREC>::load(sh.apart[1]), a2 = Acc<PREC>::load(sh.apart[2]);
+          a0.add_t(ct.gd);
+          a1.add_t(ct.hdd);
+          a2.add_t(ct.l1);
+          sh.apart[0] = a0.store();
+          sh.apart[1] = a1.store();
+          sh.apart[2] = a2.store();
+        }
       }
       __syncthreads();
       d = sh.split_d;
@@ -1017,16 +1114,15 @@ __global__ void __launch_bounds__(kWalkThreads, 2) walk_kernel(WalkParams p) {
           }
         }
       }
-      // bundle-position terms (Eq. 7 parts and the L1 change of each step)
-      if (wib < pos_warps) {
-        Acc<PREC> pgd, phd, pl1, pq[kMaxK];
+      // the L1 change of each step over a slice of the bundle's positions; Delta's terms (and the
+      // L1 change of the full step, when it is the only one) come from the column pass
+      const bool full_only = q0 == 0 && K == 1;
+      if (!full_only && wib < pos_warps) {
+        Acc<PREC> pq[kMaxK];
         for (int64_t kl = k0 + wib * 32 + lane; kl < k1; kl += 32 * pos_warps) {
           const double d = p.dk[kl];
           if (d == 0.0) continue;
           const double wj = p.w_pos[lo + kl];
-          pgd.add(p.gk[kl] * d);
-          phd.add(p.hk[kl] * d * d);
-          pl1.add(fabs(wj + d) - fabs(wj));
           if constexpr (PREC == 0) {
 #pragma unroll
             for (int q = 0; q < kMaxK; ++q)
@@ -1038,14 +1134,6 @@ __global__ void __launch_bounds__(kWalkThreads, 2) walk_kernel(WalkParams p) {
             for (int q = 0; q < kMaxK; ++q)
               if (q < K) pq[q].v = df_add(pq[q].v, df_add(df_abs(df_add(wd, df_scale(dd, alpha_f[q]))), aw));
           }
-        }
-        pgd.warp_reduce();
-        phd.warp_reduce();
-        pl1.warp_reduce();
-        if (lane == 0) {
-          sh.red[wib][0] = pgd.store();
-          sh.red[wib][1] = phd.store();
-          sh.red[wib][2] = pl1.store();
         }
 #pragma unroll
         for (int q = 0; q < kMaxK; ++q) {
@@ -1074,6 +1162,10 @@ __global__ void __launch_bounds__(kWalkThreads, 2) walk_kernel(WalkParams p) {
           const int nw = posf ? pos_warps : kWalkWarps;
           if ((f >= 3 && f < 3 + kMaxK && f - 3 >= K) || (f >= 3 + kMaxK && f - 3 - kMaxK >= K)) {
             out = s.store();
+          } else if (f < 3) {
+            out = sh.apart[f];
+          } else if (f == 3 && full_only) {
+            out = sh.apart[2];
           } else {
             for (int wv = 0; wv < nw; ++wv) s.add_acc(Acc<PREC>::load(sh.red[wv][f]));
             out = s.store();
