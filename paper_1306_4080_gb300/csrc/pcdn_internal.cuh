@@ -64,6 +64,7 @@ struct Decision {
   double alpha;
   double Delta;
   double dF;
+  float alpha_f;  // alpha in FP32
 };
 
 // Per-block partial record: [0] sum g d, [1] sum h d^2, [2] sum |w+d|-|w|,

@@ -102,6 +102,9 @@ struct SharedWalk {
   // phases B and C (pf_ready), since X does not change
   int pf_ready, pf_nb, pf_eb;
   double atab[kAlphaTab];  // beta^q as the running product 1, beta, beta*beta, ... (q < kAlphaTab)
+  float atab_f[kAlphaTab];  // the same in FP32 (converted once: conversions run on the FP64 pipe)
+  int halving;              // beta == 1/2
+  int nrows[kWalkWarps];
   __align__(16) Item items[kICap];  // 16-byte halves are copied asynchronously
   int32_t ioff[kICap + 1];
   int32_t row[kECap];
@@ -1019,9 +1022,11 @@ __global__ void __launch_bounds__(kWalkThreads, 2) walk_kernel(WalkParams p) {
     sh.abort = 0;
     sh.has_nz = 0;
     sh.pf_ready = 0;
+    sh.halving = p.beta == 0.5;
     double a = 1.0;
     for (int q = 0; q < kAlphaTab; ++q) {
       sh.atab[q] = a;
+      sh.atab_f[q] = (float)a;
       a *= p.beta;
     }
   }
@@ -1082,19 +1087,21 @@ __global__ void __launch_bounds__(kWalkThreads, 2) walk_kernel(WalkParams p) {
       float alpha_f[kMaxK];
       if (q0 + kMaxK <= kAlphaTab) {
 #pragma unroll
-        for (int q = 0; q < kMaxK; ++q) alpha[q] = sh.atab[q0 + q];
+        for (int q = 0; q < kMaxK; ++q) {
+          alpha[q] = sh.atab[q0 + q];
+          alpha_f[q] = sh.atab_f[q0 + q];
+        }
       } else {
         double a = 1.0;
         for (int q = 0; q < q0; ++q) a *= p.beta;
 #pragma unroll
         for (int q = 0; q < kMaxK; ++q) {
           alpha[q] = a;
+          alpha_f[q] = (float)a;
           a *= p.beta;
         }
       }
-#pragma unroll
-      for (int q = 0; q < kMaxK; ++q) alpha_f[q] = (float)alpha[q];
-      const bool halving = (p.beta == 0.5);
+      const bool halving = sh.halving != 0;
       LsAcc<LOSS, PREC> acc;
       acc.zero();
       int nrows = 0;
@@ -1143,19 +1150,18 @@ __global__ void __launch_bounds__(kWalkThreads, 2) walk_kernel(WalkParams p) {
           }
         }
       }
-      if (lane == 0) sh.red[wib][3 + 2 * kMaxK] = (double)nrows;
+      if (lane == 0) sh.nrows[wib] = nrows;
       __syncthreads();
       // block total of each field, warps in order; the partials are stored field-major so that the
       // reduction below reads each field of all blocks contiguously
-      if (tid < kPartStride) {
+      if (tid == kWarp && q0 == 0) {  // rows touched by this bundle, a statistic (warp 1)
+        int s = 0;
+        for (int wv = 0; wv < kWalkWarps; ++wv) s += sh.nrows[wv];
+        atomicAdd(p.counters + 4, (unsigned long long)s);
+      }
+      if (tid < 3 + 2 * kMaxK) {
         const int f = tid;
-        if (f == 3 + 2 * kMaxK) {
-          if (q0 == 0) {  // rows touched by this bundle, a statistic
-            double s = 0.0;
-            for (int wv = 0; wv < kWalkWarps; ++wv) s += sh.red[wv][f];
-            atomicAdd(p.counters + 4, (unsigned long long)s);
-          }
-        } else {
+        {
           double out;
           Acc<PREC> s;
           const bool posf = f < 3 + kMaxK;
@@ -1233,6 +1239,10 @@ __global__ void __launch_bounds__(kWalkThreads, 2) walk_kernel(WalkParams p) {
           const int qa = m ? __ffs(m) - 1 : 0;
           const double dFa = __shfl_sync(0xffffffffu, dF, qa);
           const double aa = __shfl_sync(0xffffffffu, a, qa);
+          float af = alpha_f[0];
+#pragma unroll
+          for (int q = 1; q < kMaxK; ++q)
+            if (qa == q) af = alpha_f[q];
           if (lane == 0) {
             Decision dd;
             dd.Delta = Delta;
@@ -1240,16 +1250,19 @@ __global__ void __launch_bounds__(kWalkThreads, 2) walk_kernel(WalkParams p) {
               dd.state = kDecAccept;
               dd.q = qbase + qa;
               dd.alpha = aa;
+              dd.alpha_f = af;
               dd.dF = dFa;
             } else if (qbase + K < p.q_max) {
               dd.state = kDecContinue;
               dd.q = qbase + K;
               dd.alpha = 0.0;
+              dd.alpha_f = 0.0f;
               dd.dF = 0.0;
             } else {
               dd.state = kDecCap;
               dd.q = p.q_max;
               dd.alpha = 0.0;
+              dd.alpha_f = 0.0f;
               dd.dF = 0.0;
             }
             if (blockIdx.x == 0) {
@@ -1286,7 +1299,7 @@ __global__ void __launch_bounds__(kWalkThreads, 2) walk_kernel(WalkParams p) {
         if (d != 0.0) p.w_pos[lo + kl] += a * d;
       }
     }
-    const float a_f = (float)a;
+    const float a_f = dec.alpha_f;
     warp_rows<LOSS, PREC>(p, rs, wr, true, [&](int32_t r, const RowVals<PREC>& v) {
       if (accept) row_update<LOSS, PREC>(p, r, v, a, a_f);
       static_cast<DeltaT<PREC>*>(p.delta)[r] = DeltaT<PREC>(0);
