@@ -123,7 +123,7 @@ struct pcdn_problem {
   uint32_t* col_cnt = nullptr;
   double* part = nullptr;
   // reductions, barriers, flags
-  double* cta_part = nullptr;
+  double* lsacc = nullptr;
   int max_grid = 1;
   uint32_t* sync = nullptr;  // [0] bar_count [1] bar_gen [4..5] barrier-1 counter (64-bit)
   int* err = nullptr;
@@ -166,7 +166,7 @@ void free_all(pcdn_problem* p) {
   f(p->keys0); f(p->keys1); f(p->vals0); f(p->vals1); f(p->cnt); f(p->item_ptr); f(p->items);
   f(p->hist); f(p->scan_ws);
   f(p->gk); f(p->hk); f(p->dk); f(p->col_cnt); f(p->part);
-  f(p->cta_part); f(p->sync); f(p->err); f(p->counters); f(p->red_part); f(p->red_out);
+  f(p->lsacc); f(p->sync); f(p->err); f(p->counters); f(p->red_part); f(p->red_out);
   f(p->tr_q); f(p->tr_alpha); f(p->tr_Delta); f(p->tr_dF);
   if (p->ev0) cudaEventDestroy(p->ev0);
   if (p->ev1) cudaEventDestroy(p->ev1);
@@ -302,7 +302,7 @@ int finish_create(pcdn_problem* p) {
   if (bps > 2) bps = 2;
   if (bps < 1) return fail(PCDN_ECUDA, "bundle walker cannot be resident on this device");
   p->max_grid = p->sms * bps;
-  CUDA_TRY(palloc(p, &p->cta_part, 2 * (int64_t)p->max_grid * kPartStride));
+  CUDA_TRY(palloc(p, &p->lsacc, 3 * kPartStride * kAccPad));
   CUDA_TRY(palloc(p, &p->sync, 8));
   CUDA_TRY(palloc(p, &p->err, 4));
   CUDA_TRY(palloc(p, &p->counters, 8));
@@ -466,7 +466,7 @@ int run_walk(pcdn_problem* p, const pcdn_opts* o, const int32_t* perm, int64_t n
   w.col_cnt = p->col_cnt;
   w.anynz = nullptr;
   w.bar1 = reinterpret_cast<unsigned long long*>(p->sync + 4);
-  w.cta_part = p->cta_part;
+  w.lsacc = p->lsacc;
   w.bar_count = p->sync;
   w.bar_gen = p->sync + 1;
   w.spin_limit = o->spin_limit ? o->spin_limit : kDefaultSpin;
@@ -495,6 +495,7 @@ int run_walk(pcdn_problem* p, const pcdn_opts* o, const int32_t* perm, int64_t n
                       p->scan_ws, p->stream, &p->launches));
   CUDA_TRY(gather_w(p->w, perm, npos, p->w_pos, p->stream, &p->launches));
   CUDA_TRY(cudaMemsetAsync(p->sync, 0, sizeof(uint32_t) * 8, p->stream));
+  CUDA_TRY(cudaMemsetAsync(p->lsacc, 0, sizeof(double) * 3 * kPartStride * kAccPad, p->stream));
   CUDA_TRY(cudaEventRecord(p->ev0, p->stream));
   CUDA_TRY(launch_walk(p->loss, (int)o->prec, w, grid, p->stream));
   ++p->launches;

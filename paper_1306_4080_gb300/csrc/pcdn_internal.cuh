@@ -70,6 +70,7 @@ struct Decision {
 // Per-block partial record: [0] sum g d, [1] sum h d^2, [2] sum |w+d|-|w|,
 // [3, 3+K) sum |w + a_q d| - |w|, [3+K, 3+2K) line-search sums, [3+2K] touched rows
 constexpr int kPartStride = 3 + 2 * kMaxK + 1;
+constexpr int kAccPad = 16;  // doubles per line-search accumulator (128 bytes)
 
 struct WalkParams {
   // problem
@@ -102,7 +103,8 @@ struct WalkParams {
   uint32_t* col_cnt;        // [2][P] chunks of a split column that published sums, by bundle parity
   uint32_t* anynz;          // unused
   // reductions and barriers
-  double* cta_part;         // [2][gridDim.x][kPartStride], by line-search pass parity
+  double* lsacc;            // [3][kPartStride][kAccPad] sums over blocks of the line-search fields, by
+                            // pass mod 3 (FP64 atomic adds; each field on its own 128-byte line)
   uint32_t* bar_count;
   uint32_t* bar_gen;
   uint32_t spin_limit;

@@ -161,10 +161,13 @@ template <> struct Acc<1> {
 __device__ __forceinline__ bool err_set(const WalkParams& p) { return ld_volatile_int(p.err) != 0; }
 
 // Plain barrier over the grid.  Returns false when the launch must end (a wait gave up, or a
-// block recorded an error while this one waited).
+// block recorded an error while this one waited).  With one block, a GPU-scope fence stands in for
+// the release/acquire pair, so that the block's atomics (performed in L2) are seen by its later
+// loads.
 template <class SH>
 __device__ bool grid_barrier(const WalkParams& p, uint32_t& idx, SH& sh) {
   __syncthreads();
+  if (gridDim.x == 1 && threadIdx.x == 0) __threadfence();
   if (gridDim.x > 1) {
     if (threadIdx.x == 0) {
       const uint32_t target = (idx + 1) * gridDim.x;
@@ -191,6 +194,7 @@ __device__ __forceinline__ void grid_arrive(const WalkParams& p) {
 }
 template <class SH>
 __device__ bool grid_wait(const WalkParams& p, uint32_t& idx, SH& sh) {
+  if (gridDim.x == 1 && threadIdx.x == 0) __threadfence();
   if (gridDim.x > 1 && threadIdx.x == 0) {
     const uint32_t target = (idx + 1) * gridDim.x;
     uint32_t spins = 0;
@@ -229,8 +233,9 @@ __device__ bool grid_barrier_flag(const WalkParams& p, uint32_t& n1, uint32_t& s
     }
     __syncthreads();
     seen = (uint32_t)sh.scan_tot[0];
-  } else {
-    if (threadIdx.x == 0) sh.nonzero = sh.has_nz;
+  } else if (threadIdx.x == 0) {
+    __threadfence();
+    sh.nonzero = sh.has_nz;
   }
   ++n1;
   __syncthreads();
@@ -1152,8 +1157,7 @@ __global__ void __launch_bounds__(kWalkThreads, 2) walk_kernel(WalkParams p) {
       }
       if (lane == 0) sh.nrows[wib] = nrows;
       __syncthreads();
-      // block total of each field, warps in order; the partials are stored field-major so that the
-      // reduction below reads each field of all blocks contiguously
+      // block total of each field, warps in order, added (FP64) to the grid's accumulator of the field
       if (tid == kWarp && q0 == 0) {  // rows touched by this bundle, a statistic (warp 1)
         int s = 0;
         for (int wv = 0; wv < kWalkWarps; ++wv) s += sh.nrows[wv];
@@ -1176,46 +1180,24 @@ __global__ void __launch_bounds__(kWalkThreads, 2) walk_kernel(WalkParams p) {
             for (int wv = 0; wv < nw; ++wv) s.add_acc(Acc<PREC>::load(sh.red[wv][f]));
             out = s.store();
           }
-          p.cta_part[((int64_t)(npass & 1) * kPartStride + f) * G + blockIdx.x] = out;
+          red_add_f64(p.lsacc + ((npass % 3) * kPartStride + f) * kAccPad, Acc<PREC>::load(out).value());
         }
       }
       const int qbase = q0;
-      // barrier 2; then every block reduces all partials in the same fixed order and takes the same
-      // decision (no block waits for another's reduction).  The partials alternate between two
-      // buffers by pass parity: a block writes the next pass's partials only after the next
-      // barrier, which every block reaches after reading this pass's.
+      // barrier 2; then every block reads the accumulated sums and takes the same decision.  The
+      // accumulators rotate over three buffers by pass: after barrier 2 of pass k, block 0 clears the
+      // buffer of pass k + 2 (last read in pass k - 1, before this barrier; next added to after
+      // barrier 2 of pass k + 1, which block 0 reaches only after clearing it).
       if (!grid_barrier(p, bar, sh)) {
         cp_async_wait_all();  // the next bundle's item copies
         return;
       }
       {
-        const double* part = p.cta_part + (int64_t)(npass & 1) * kPartStride * G;
-        // reduction of all partials in a fixed order: the 3 + 2K used fields (gd, hdd, l1, K L1
-        // changes, K loss changes) get T threads each; thread s of a field sums blocks s, s + T, ...
-        // (coalesced over the T threads, all loads in flight at once), then a lane tree over the T.
-        {
-          const int nf = 3 + 2 * K;
-          const int T = nf <= 8 ? 32 : (nf <= 16 ? 16 : 8);
-          const int fi = tid / T, s = tid & (T - 1);
-          const int f = fi < 3 + K ? fi : fi - K + kMaxK;
-          Acc<PREC> fa;
-          if (fi < nf) {
-            const double* pf = part + (int64_t)f * G;
-            constexpr int kLd = 24;
-            for (int bb = s; bb < G; bb += kLd * T) {
-              double v[kLd];
-#pragma unroll
-              for (int u = 0; u < kLd; ++u) {
-                const int b = bb + u * T;
-                v[u] = b < G ? __ldcg(pf + b) : 0.0;
-              }
-#pragma unroll
-              for (int u = 0; u < kLd; ++u)
-                if (bb + u * T < G) fa.add_acc(Acc<PREC>::load(v[u]));
-            }
-          }
-          fa.group_reduce(T);
-          if (fi < nf && s == 0) sh.tot[f] = fa.value();
+        if (tid < 3 + 2 * kMaxK) {
+          const int f = tid;
+          const bool used = f < 3 + K || (f >= 3 + kMaxK && f < 3 + kMaxK + K);
+          if (used) sh.tot[f] = __ldcg(p.lsacc + ((npass % 3) * kPartStride + f) * kAccPad);
+          if (blockIdx.x == 0) p.lsacc[(((npass + 2) % 3) * kPartStride + f) * kAccPad] = 0.0;
         }
         __syncthreads();
         // the decision (Eq. 6): lane q of warp 0 tests step size alpha_q, the first passing one wins
