@@ -478,20 +478,19 @@ __device__ __forceinline__ void plan_batch(SH& sh, int n, int& nb, int& eb) {
   eb = sh.ioff[nb];
 }
 
-// Asynchronous copy of the batch's row indices and values into sh.row, sh.x.
+// Asynchronous copy of the batch's row indices and values into sh.row, sh.x: one warp per item,
+// coalesced over the lanes.
 template <class SH>
-__device__ __forceinline__ void stage_entries_async(const WalkParams& p, SH& sh, int nb, int eb) {
+__device__ __forceinline__ void stage_entries_async(const WalkParams& p, SH& sh, int nb) {
   const uint64_t pol = l2_evict_first_policy();
-  for (int v = threadIdx.x; v < eb; v += kWalkThreads) {
-    int a = 0, b = nb - 1;  // largest j < nb with ioff[j] <= v
-    while (a < b) {
-      const int mid = (a + b + 1) >> 1;
-      if (sh.ioff[mid] <= v) a = mid;
-      else b = mid - 1;
+  const int lane = threadIdx.x & 31;
+  for (int j = threadIdx.x >> 5; j < nb; j += kWalkWarps) {
+    const int64_t start = sh.items[j].start;
+    const int o = sh.ioff[j], len = sh.ioff[j + 1] - o;
+    for (int v = lane; v < len; v += kWarp) {
+      cp_async4_stream(&sh.row[o + v], p.row_idx + start + v, pol);
+      cp_async4_stream(&sh.x[o + v], p.val + start + v, pol);
     }
-    const int64_t e = sh.items[a].start + (v - sh.ioff[a]);
-    cp_async4_stream(&sh.row[v], p.row_idx + e, pol);
-    cp_async4_stream(&sh.x[v], p.val + e, pol);
   }
   cp_async_commit();
 }
@@ -524,7 +523,7 @@ __device__ void column_pass(const WalkParams& p, SharedWalk<PREC>& sh, int64_t l
       cp_async_wait_all();
       __syncthreads();
       plan_batch(sh, nload, nb, eb);
-      stage_entries_async(p, sh, nb, eb);
+      stage_entries_async(p, sh, nb);
       cp_async_wait_all();
       __syncthreads();
     }
@@ -1294,7 +1293,7 @@ __global__ void __launch_bounds__(kWalkThreads, 2) walk_kernel(WalkParams p) {
       __syncthreads();
       int nb, eb;
       plan_batch(sh, nx_load, nb, eb);
-      stage_entries_async(p, sh, nb, eb);
+      stage_entries_async(p, sh, nb);
       if (tid == 0) {
         sh.pf_nb = nb;
         sh.pf_eb = eb;
