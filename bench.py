@@ -50,6 +50,16 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--grid", type=int, default=0)
+    ap.add_argument("--batched", type=int, default=1, help="also run the batched workload (reported under 'batched')")
+    ap.add_argument("--batch-jobs", type=int, default=64)
+    ap.add_argument("--batch-scale", type=float, default=1.0)
+    ap.add_argument("--batch-nC", type=int, default=16)
+    ap.add_argument("--serving", type=int, default=1, help="also run the request server (reported under 'serving')")
+    ap.add_argument("--serve-rates", default="10,30,100,300,1000")
+    ap.add_argument("--serve-seconds", type=float, default=8.0, help="arrival window per rate (requests = rate x this, capped)")
+    ap.add_argument("--serve-max-requests", type=int, default=400)
+    ap.add_argument("--serve-seq", type=int, default=40, help="requests timed through the sequential plain loop")
+    ap.add_argument("--main", type=int, default=1, help="run the 2M x 3M solve (the headline metric)")
     return ap.parse_args()
 
 
@@ -218,6 +228,140 @@ def config_of(wl, prob, prec):
             "cache": "inputs larger than L2 (X alone is %.2f GB)" % (prob.nnz * 8 / 1e9)}
 
 
+def batch_pool(args):
+    """The batched workload: problems of uneven sizes, each along a 16-value C path."""
+    import datagen
+    jobs = datagen.batch_jobs(args.batch_jobs, seed=0, scale=args.batch_scale, n_C=args.batch_nC)
+    return [(j, datagen.generate(j.spec, with_csr=False)) for j in jobs]
+
+
+def run_batched(args, pk, pool):
+    """Every job's whole C path (warm-started, FP32 bulk / FP64 line search, relative KKT 1e-3):
+    all jobs at once through pcdn_solve_batch (bundle size autotuned per job, probes included in the
+    time), then the same paths one solve at a time through pcdn_solve with the bundle sizes the
+    autotuner chose.  Host wall time around each arm; inputs resident on the device."""
+    import torch
+    probs = [pk.Problem.from_csc(p.col_ptr, p.row_idx, p.val, p.y, j.C_path[0], j.loss) for j, p in pool]
+    try:
+        opts = pk.pcdn_default_opts(prec="mixed", max_epochs=args.max_epochs)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc, res, bs = pk.pcdn_solve_batch([q.handle for q in probs], [q.n_features for q in probs],
+                                          [j.C_path for j, _ in pool], 0, eps=1e-3, seed=0, opts=opts, want_w=False)
+        t_batch = time.perf_counter() - t0
+        Ps = [r["P_used"] for r in res]
+        F_batch = [[st["F_final"] for st in r["stats"]] for r in res]
+        launches = sum(st["kernel_launches"] for r in res for st in r["stats"])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        F_plain, epochs_plain, conv = [], 0, True
+        for q, (job, _), P in zip(probs, pool, Ps):
+            row = []
+            for k, C in enumerate(job.C_path):
+                pk.pcdn_set_C(q.handle, C)
+                o = pk.pcdn_default_opts(prec="mixed", max_epochs=args.max_epochs, warm_start=1 if k else 0)
+                _, _, st, _ = pk.pcdn_solve(q.handle, P, 1e-3, 0, o, q.n_features, want_w=False)
+                row.append(st["F_final"])
+                epochs_plain += st["epochs"]
+                conv = conv and bool(st["converged"])
+            F_plain.append(row)
+        t_plain = time.perf_counter() - t0
+        diff = max(abs(a - b) / abs(b) for ra, rb in zip(F_batch, F_plain) for a, b in zip(ra, rb))
+        # per job: its path's host time inside the batch (sum of its solves), size, bundle size
+        jobs_diag = []
+        for r, (job, p) in zip(res, pool):
+            sts = r["stats"]
+            bund = sum(st["bundles"] for st in sts)
+            walk = sum(st["walk_s"] for st in sts)
+            jobs_diag.append({"path_s": sum(st["wall_s"] for st in sts), "n": p.n_samples, "m": p.n_features,
+                              "nnz": p.nnz, "loss": job.loss, "P": r["P_used"], "epochs": sum(st["epochs"] for st in sts),
+                              "bundles": bund, "walk_us_per_bundle": walk / bund * 1e6 if bund else 0.0})
+        crit = sorted(jobs_diag, key=lambda d: -d["path_s"])
+        n_solves = sum(len(j.C_path) for j, _ in pool)
+        nnz = [p.nnz for _, p in pool]
+        return ({"metric": "solves/s (whole C paths, relative KKT 1e-3)", "unit": "solves/s",
+                "value": n_solves / t_batch, "plain_value": n_solves / t_plain, "speedup_vs_plain": t_plain / t_batch,
+                "batch_s": t_batch, "plain_s": t_plain, "solves": n_solves, "status": rc,
+                "probe_solves": bs["probe_solves"], "epochs_batched": bs["epochs"], "epochs_plain": epochs_plain,
+                "plain_converged": conv, "max_rel_F_diff_batched_vs_plain": diff, "gpu_launches": int(launches),
+                "P_chosen": {str(P): Ps.count(P) for P in sorted(set(Ps))},
+                "critical_jobs": crit[:4], "sum_path_s": sum(d["path_s"] for d in jobs_diag),
+                "config": {"workload": f"{len(pool)} problems, n_samples log-uniform [1k, 50k] x {args.batch_scale:g}, "
+                                       f"n_features log-uniform [5k, 200k] x {args.batch_scale:g}, density U[0.1%, 1%], "
+                                       "Zipf 1.1 columns, tf-idf rows L2-normalised, losses alternating logistic / "
+                                       f"L2-SVM, each along {args.batch_nC} C values log-spaced over [1e-2, 1e1] "
+                                       "(warm-started)", "nnz_total": int(sum(nnz)), "nnz_max": int(max(nnz)),
+                           "precision": "mixed", "bundle_size": "autotuned per problem (probes timed)"}}, Ps)
+    finally:
+        for q in probs:
+            q.close()
+
+
+def run_serving(args, pk, pool, P_of):
+    """Poisson arrivals of single solves drawn from the batched workload's problems (loss of the
+    problem, C log-uniform over [1e-2, 1e1]) into a request server with an 8 GiB device budget;
+    latency = submit to result on the host.  Baseline: the same requests one at a time
+    (pcdn_create + pcdn_solve + pcdn_destroy)."""
+    import numpy as np
+    rates = [float(r) for r in args.serve_rates.split(",") if r]
+    out = {"metric": "solves/s and p50/p99 latency to relative KKT 1e-3", "budget_bytes": 8 << 30, "rates": []}
+    opts = pk.pcdn_default_opts(prec="mixed", max_epochs=args.max_epochs)
+    rng = np.random.default_rng(12345)
+    draws = []
+    for rate in rates:
+        R = int(min(args.serve_max_requests, max(20, rate * args.serve_seconds)))
+        gaps = rng.exponential(1.0 / rate, size=R)
+        picks = rng.integers(0, len(pool), size=R)
+        Cs = 10.0 ** rng.uniform(-2.0, 1.0, size=R)
+        draws.append((rate, R, gaps, picks, Cs))
+    for rate, R, gaps, picks, Cs in draws:
+        srv = pk.Server(slots=0, hbm_budget=8 << 30, opts=opts)
+        try:
+            tickets = []
+            t0 = time.perf_counter()
+            t_next = t0
+            for k in range(R):
+                t_next += gaps[k]
+                d = t_next - time.perf_counter()
+                if d > 0:
+                    time.sleep(d)
+                job, p = pool[picks[k]]
+                tickets.append(srv.submit(p.col_ptr, p.row_idx, p.val, p.y, float(Cs[k]), job.loss, P_of[picks[k]],
+                                          1e-3, 0, borrow=True))
+            res = [srv.wait(t, 600) for t in tickets]
+            lat = np.array([r[2]["t_done"] - r[2]["t_submit"] for r in res])
+            first = min(r[2]["t_submit"] for r in res)
+            last = max(r[2]["t_done"] for r in res)
+            ok = sum(1 for r in res if r[0] in (pk.PCDN_OK, pk.PCDN_ENOTCONVERGED))
+            out["rates"].append({"rate_per_s": rate, "requests": R, "ok": ok, "solves_per_s": R / (last - first),
+                                 "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+                                 "mean_s": float(lat.mean()),
+                                 "submit_lag_s": float(time.perf_counter() - t0 - float(np.sum(gaps)))})
+        finally:
+            srv.close()
+    # sequential plain loop on the first requests of the highest rate's draw
+    rate, R, gaps, picks, Cs = draws[-1]
+    S = min(args.serve_seq, R)
+    t0 = time.perf_counter()
+    lat = []
+    for k in range(S):
+        job, p = pool[picks[k]]
+        ts = time.perf_counter()
+        h = pk.pcdn_create(p.col_ptr, p.row_idx, p.val, p.y, float(Cs[k]), job.loss)
+        pk.pcdn_solve(h, P_of[picks[k]], 1e-3, 0, opts, p.n_features, want_w=True)
+        pk.pcdn_destroy(h)
+        lat.append(time.perf_counter() - ts)
+    t_seq = time.perf_counter() - t0
+    out["sequential_plain"] = {"requests": S, "solves_per_s": S / t_seq, "mean_s": float(np.mean(lat)),
+                               "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99))}
+    best = max(r["solves_per_s"] for r in out["rates"])
+    out["speedup_vs_sequential"] = best / out["sequential_plain"]["solves_per_s"]
+    out["config"] = {"workload": f"Poisson arrivals at {args.serve_rates}/s of single solves drawn from the "
+                                 f"{len(pool)} batched problems (their loss, C log-uniform [1e-2, 1e1], their autotuned "
+                                 "bundle size), mixed precision, 8 GiB device budget, slots 2 per SM (at most 128)"}
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -235,6 +379,13 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     pk.load()
+
+    if not args.main:
+        line = {"metric": METRIC, "n_gpus": world, "config": {}}
+        if rank == 0:
+            add_extra_legs(args, pk, line)
+            print(json.dumps(line), flush=True)
+        return 0
 
     wl = workload(args)
     prob = datagen.generate(wl.spec, with_csr=False)
@@ -341,10 +492,25 @@ def run_ours(args):
                           "ls_steps": st0["ls_steps"], "ls_cap_hits": st0["ls_cap_hits"],
                           "rows_touched": st0["rows_touched"]}}
         line.update(extra)
+        if world == 1:
+            add_extra_legs(args, pk, line)
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def add_extra_legs(args, pk, line):
+    """The batched and serving workloads (one GPU), added to the JSON line."""
+    if not (args.batched or args.serving):
+        return
+    pool = batch_pool(args)
+    # serving requests use the bundle size the batch's autotuner chose for their problem
+    P_of = [min(64, p.n_features) for _, p in pool]
+    if args.batched:
+        line["batched"], P_of = run_batched(args, pk, pool)
+    if args.serving:
+        line["serving"] = run_serving(args, pk, pool, P_of)
 
 
 def main():

@@ -213,3 +213,42 @@ def scaled(name: str, factor: float, seed: int | None = None) -> Workload:
     if seed is not None:
         s.seed = seed
     return Workload(f"{name}@{factor:g}", s, w.loss, w.C, max(1, int(round(w.P * factor))), w.eps, w.solver_seed)
+
+
+# ---- batched workload: many independent problems, each along a regularisation path ---------------
+
+@dataclass
+class PathJob:
+    """One problem of the batched workload and the C values it is solved at (in order, each
+    warm-started from the previous solution)."""
+    name: str
+    spec: Spec
+    loss: str
+    C_path: list
+    eps: float = 1e-3
+    solver_seed: int = 0
+
+
+def batch_jobs(count: int = 64, seed: int = 0, scale: float = 1.0, n_C: int = 16,
+               C_range: tuple = (1e-2, 1e1)) -> list:
+    """``count`` problems of uneven sizes in the shape of the paper's sparse text workloads:
+    n_samples log-uniform in [1k, 50k], n_features log-uniform in [5k, 200k] (both times ``scale``),
+    density uniform in [0.1 %, 1 %] (row length = density * n_features), Zipf 1.1 columns, tf-idf
+    values, rows L2-normalised, planted w* with max(10, n_features/500) nonzeros; losses alternate
+    logistic (5 % label flips) / L2-SVM (3 %); each solved along ``n_C`` values of C log-spaced over
+    ``C_range``.  Problem k's generator seed is k + 1000 * seed."""
+    rng = np.random.default_rng(np.random.SeedSequence([0x5CD, int(seed)]))
+    out = []
+    C_path = list(np.logspace(np.log10(C_range[0]), np.log10(C_range[1]), n_C))
+    for k in range(count):
+        n = int(round(np.exp(rng.uniform(np.log(1e3), np.log(5e4))) * scale))
+        m = int(round(np.exp(rng.uniform(np.log(5e3), np.log(2e5))) * scale))
+        dens = float(rng.uniform(1e-3, 1e-2))
+        n, m = max(16, n), max(32, m)
+        row_mean = max(2.0, dens * m)
+        loss = "logistic" if k % 2 == 0 else "l2svm"
+        spec = Spec(n, m, "zipf", row_mean=row_mean, zipf_s=1.1, values="tfidf",
+                    wstar_nnz=max(10, min(m, m // 500)), flip_frac=0.05 if loss == "logistic" else 0.03,
+                    seed=k + 1000 * int(seed))
+        out.append(PathJob(f"batch{k}", spec, loss, C_path))
+    return out

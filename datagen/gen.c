@@ -58,6 +58,14 @@ static double std_normal(uint64_t* s) {
 }
 
 static int64_t poisson_inv(uint64_t* s, double lam) {
+  if (lam > 500.0) {
+    /* exp(-lam) underflows beyond ~745: draw the sum of independent Poisson pieces of mean <= 500,
+       which is Poisson(lam) exactly */
+    const int pieces = (int)ceil(lam / 500.0);
+    int64_t k = 0;
+    for (int i = 0; i < pieces; ++i) k += poisson_inv(s, lam / pieces);
+    return k;
+  }
   /* inversion by sequential search */
   double u = u01(s);
   double p = exp(-lam), F = p;

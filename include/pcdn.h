@@ -150,6 +150,10 @@ int pcdn_bundle_step(pcdn_problem* prob, const double* w_in, const int32_t* bund
 
 /* Set w (host, n_features entries) and recompute the maintained quantities. */
 int pcdn_set_w(pcdn_problem* prob, const double* w);
+/* Change the loss weight c of Eq. 1 (C > 0, finite).  w and the maintained quantities are kept
+ * (neither depends on c), so a following pcdn_solve with opts.warm_start = 1 continues from the
+ * current w: one step of a warm-started regularisation path.  Errors: PCDN_EINVAL. */
+int pcdn_set_C(pcdn_problem* prob, double C);
 /* Copy the current w to the host (n_features entries). */
 int pcdn_get_w(pcdn_problem* prob, double* w);
 /* Objective F(w) (Eq. 1) at the current w, from z = Xw. */
@@ -161,6 +165,123 @@ int pcdn_kkt(pcdn_problem* prob, double* kkt_l1);
 int pcdn_permutation(pcdn_problem* prob, uint64_t seed, int64_t epoch, int32_t* perm);
 /* Device-resident sizes (bytes) held by the problem. */
 int pcdn_memory(pcdn_problem* prob, int64_t* bytes);
+
+/* ---- many solves on one GPU ----------------------------------------------------------------
+ *
+ * The paper solves one problem at a time (Algorithm 3).  These calls run many independent solves
+ * concurrently on one GPU; each solve runs exactly pcdn_solve's stages, kernels and stop rule,
+ * with its bundle walker as one thread block on its problem's own stream, so solves of different
+ * problems overlap on the device while each advances at its own pace. */
+
+/* One job of a batch: a problem solved along a regularisation path. */
+typedef struct {
+  pcdn_problem* prob;   /* from pcdn_create / pcdn_create_device; distinct for every job */
+  int32_t P;            /* bundle size in [1, n_features], or 0: chosen by the autotuner (below) */
+  double eps;           /* relative KKT tolerance of every solve of the job */
+  uint64_t seed;        /* partition seed (Eq. 8) of every solve */
+  int32_t n_C;          /* >= 1 */
+  const double* C_path; /* host [n_C]: C_path[0] is solved from opts->warm_start's start point,
+                           each later C from the previous solution (warm start) */
+  double* w_out;        /* host [n_C * n_features] (row k = w at C_path[k]), may be NULL */
+  pcdn_stats* stats;    /* host [n_C], may be NULL */
+  int32_t status;       /* out: PCDN_OK, PCDN_ENOTCONVERGED (some solve hit max_epochs) or the error
+                           that ended the job */
+  int32_t P_used;       /* out: the bundle size the job's path ran with */
+} pcdn_batch_job;
+
+typedef struct {
+  int32_t max_inflight;   /* jobs in flight at once (0 = 2 per SM, at most 128) */
+  int32_t threads;        /* host threads driving them (0 = 4) */
+  double probe_eps;       /* autotuner: relative KKT a probe solve aims at (0 = 0.1) */
+  int32_t probe_epochs;   /* autotuner: outer-iteration cap of a probe solve (0 = no cap beyond opts) */
+  int32_t n_candidates;   /* autotuner: bundle sizes to try (0 = powers of 4 from 16 to min(4096, n_features)) */
+  const int32_t* candidates;
+} pcdn_batch_opts;
+
+typedef struct {
+  double wall_s;          /* host wall time of the whole batch */
+  int64_t solves;         /* path solves completed */
+  int64_t probe_solves;   /* autotuner probe solves */
+  int64_t epochs;         /* outer iterations of the path solves */
+  int64_t coord_updates;  /* features visited by the path solves */
+  double bytes_model;     /* algorithmic bytes of the path solves' bundle steps */
+} pcdn_batch_stats;
+
+/* Defaults: max_inflight 0, threads 0, probe_eps 0.1, probe_epochs 3, default candidates. */
+void pcdn_default_batch_opts(pcdn_batch_opts* bopts);
+
+/* Solve every job's path (opts, may be NULL = defaults, apply to every solve; grid_ctas is
+ * ignored: each walker is one thread block).  A job with P = 0 first runs a short probe solve from
+ * w = 0 at C_path[0] for each candidate bundle size (to probe_eps, at most probe_epochs outer
+ * iterations) and keeps the one with the least host time per decade of KKT reduction; it then
+ * needs opts->warm_start = 0.  Jobs run concurrently, up to max_inflight at a time.  Returns the
+ * first error of any job (with its message), else PCDN_ENOTCONVERGED if some solve reached
+ * max_epochs, else PCDN_OK; every job's status is written.  Errors: PCDN_EINVAL (bad job, two jobs
+ * on one problem), PCDN_ECUDA, and the solve errors of pcdn_solve. */
+int pcdn_solve_batch(pcdn_batch_job* jobs, int32_t n_jobs, const pcdn_opts* opts, const pcdn_batch_opts* bopts,
+                     pcdn_batch_stats* out);
+
+/* The bundle-size autotuner on one problem: for each candidate P (NULL/0 = the defaults above), a
+ * probe solve from w = 0 to probe_eps (at most probe_epochs outer iterations; 0 = opts' cap) with a
+ * one-block walker; *P_best = the candidate with the least host time per decade of relative-KKT
+ * reduction; probe_s (may be NULL, [n_candidates or the default count]) receives each score.  The
+ * problem is left at the last probe's w. */
+int pcdn_autotune(pcdn_problem* prob, const int32_t* candidates, int32_t n_candidates, double probe_eps,
+                    int32_t probe_epochs, uint64_t seed, const pcdn_opts* opts, int32_t* P_best, double* probe_s);
+
+/* ---- request server: continuous batching ------------------------------------------------------
+ *
+ * A server owns its host threads.  The admission thread takes submitted requests in arrival
+ * order, waits until a slot is free and the request's device footprint fits the memory budget
+ * (a request larger than the whole budget is admitted alone) and reserves both; creator threads
+ * then copy admitted requests to the device (pcdn_create), several at once.  The driver thread starts each admitted request's solve in a free slot and
+ * advances all of them concurrently, one stream each.  A finished request's w and statistics are
+ * kept on the host until pcdn_server_wait collects them, and its device memory is released at
+ * once, so waiting requests are admitted while others are still on the GPU. */
+typedef struct pcdn_server pcdn_server;
+
+typedef struct {
+  int32_t slots;        /* solves in flight at once (0 = 2 per SM, at most 128) */
+  int64_t hbm_budget;   /* device bytes the admitted requests may hold together (0 = 8 GiB) */
+  pcdn_opts solve;      /* options of every solve (warm_start and grid_ctas are ignored) */
+} pcdn_server_opts;
+
+/* What pcdn_server_wait reports about a request; times are seconds since the server was created. */
+typedef struct {
+  int32_t status;       /* the solve's status (as pcdn_solve's return value) */
+  double t_submit;      /* pcdn_server_submit returned */
+  double t_admit;       /* admitted (slot and memory reserved; requests are admitted in arrival order) */
+  double t_done;        /* solved, w on the host */
+  int64_t bytes;        /* device footprint used for admission */
+  pcdn_stats stats;
+} pcdn_request_info;
+
+void pcdn_default_server_opts(pcdn_server_opts* opts);
+/* Start a server on the current device.  Errors: PCDN_EINVAL, PCDN_ENOMEM, PCDN_ECUDA. */
+int pcdn_server_create(const pcdn_server_opts* opts, pcdn_server** out);
+/* Queue one solve (as pcdn_create + pcdn_solve from w = 0).  X and y are host arrays, copied
+ * before the call returns.  *ticket identifies the request.  Full validation of X and y happens at
+ * admission; a malformed request then finishes with PCDN_EINVAL.  Errors: PCDN_EINVAL (sizes, C,
+ * loss, P, eps), PCDN_ENOMEM. */
+int pcdn_server_submit(pcdn_server* srv, const pcdn_csc* X, const int8_t* y, double C, pcdn_loss loss, int32_t P,
+                       double eps, uint64_t seed, int64_t* ticket);
+/* As pcdn_server_submit, but X's arrays and y are not copied: the caller keeps them valid and
+ * unchanged until pcdn_server_wait has returned the request's result (a caller that already holds
+ * its problems in host memory saves a copy per request). */
+int pcdn_server_submit_borrowed(pcdn_server* srv, const pcdn_csc* X, const int8_t* y, double C, pcdn_loss loss,
+                                int32_t P, double eps, uint64_t seed, int64_t* ticket);
+/* Wait up to timeout_s seconds (<= 0: no limit) for a request; then w_out (host, n_features
+ * entries, may be NULL) and info (may be NULL) receive its result and the request is forgotten
+ * (each ticket can be collected once).  Returns the request's status, PCDN_ETIMEOUT if it did not
+ * finish in time (it can be waited for again), or PCDN_EINVAL for an unknown ticket. */
+int pcdn_server_wait(pcdn_server* srv, int64_t ticket, double timeout_s, double* w_out, pcdn_request_info* info);
+/* Counters: requests submitted and finished so far, requests holding device memory, and the
+ * device bytes they were admitted with.  Any pointer may be NULL. */
+int pcdn_server_stats(pcdn_server* srv, int64_t* submitted, int64_t* finished, int32_t* in_flight,
+                      int64_t* bytes_in_use);
+/* Stop the server: solves in flight end after their current stage, uncollected results and queued
+ * requests are dropped, all device memory is released. */
+void pcdn_server_destroy(pcdn_server* srv);
 
 /* Objective without allocation.
  *

@@ -31,7 +31,10 @@ PRECISIONS = {"fp64": 0, "mixed": 1}
 
 SYMBOLS = ["pcdn_default_opts", "pcdn_create", "pcdn_create_device", "pcdn_solve", "pcdn_bundle_step",
            "pcdn_set_w", "pcdn_get_w", "pcdn_objective", "pcdn_kkt", "pcdn_permutation", "pcdn_memory",
-           "pcdn_destroy", "pcdn_last_error", "pcdn_objective_noalloc"]
+           "pcdn_destroy", "pcdn_last_error", "pcdn_objective_noalloc", "pcdn_set_C",
+           "pcdn_default_batch_opts", "pcdn_solve_batch", "pcdn_autotune", "pcdn_default_server_opts",
+           "pcdn_server_create", "pcdn_server_submit", "pcdn_server_submit_borrowed", "pcdn_server_wait", "pcdn_server_stats",
+           "pcdn_server_destroy"]
 PCDN_NOALLOC_MAX_SAMPLES = 262144
 
 
@@ -66,6 +69,31 @@ class pcdn_trace(ctypes.Structure):
     _fields_ = [("bundle_cap", ctypes.c_int64), ("q", ctypes.c_void_p), ("alpha", ctypes.c_void_p),
                 ("Delta", ctypes.c_void_p), ("dF", ctypes.c_void_p), ("epoch_cap", ctypes.c_int64),
                 ("epoch_kkt", ctypes.c_void_p)]
+
+
+class pcdn_batch_job(ctypes.Structure):
+    _fields_ = [("prob", ctypes.c_void_p), ("P", ctypes.c_int32), ("eps", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("n_C", ctypes.c_int32), ("C_path", ctypes.c_void_p), ("w_out", ctypes.c_void_p),
+                ("stats", ctypes.c_void_p), ("status", ctypes.c_int32), ("P_used", ctypes.c_int32)]
+
+
+class pcdn_batch_opts(ctypes.Structure):
+    _fields_ = [("max_inflight", ctypes.c_int32), ("threads", ctypes.c_int32), ("probe_eps", ctypes.c_double),
+                ("probe_epochs", ctypes.c_int32), ("n_candidates", ctypes.c_int32), ("candidates", ctypes.c_void_p)]
+
+
+class pcdn_batch_stats(ctypes.Structure):
+    _fields_ = [("wall_s", ctypes.c_double), ("solves", ctypes.c_int64), ("probe_solves", ctypes.c_int64),
+                ("epochs", ctypes.c_int64), ("coord_updates", ctypes.c_int64), ("bytes_model", ctypes.c_double)]
+
+
+class pcdn_server_opts(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int32), ("hbm_budget", ctypes.c_int64), ("solve", pcdn_opts)]
+
+
+class pcdn_request_info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double),
+                ("t_done", ctypes.c_double), ("bytes", ctypes.c_int64), ("stats", pcdn_stats)]
 
 
 _lib = None
@@ -110,6 +138,28 @@ def load() -> ctypes.CDLL:
     lib.pcdn_last_error.restype = ctypes.c_char_p
     lib.pcdn_objective_noalloc.argtypes = [P(pcdn_csc), vp, d, ctypes.c_int, vp, vp, vp]
     lib.pcdn_objective_noalloc.restype = ctypes.c_int
+    lib.pcdn_set_C.argtypes = [vp, d]
+    lib.pcdn_set_C.restype = ctypes.c_int
+    lib.pcdn_default_batch_opts.argtypes = [P(pcdn_batch_opts)]
+    lib.pcdn_default_batch_opts.restype = None
+    lib.pcdn_solve_batch.argtypes = [vp, i32, P(pcdn_opts), P(pcdn_batch_opts), P(pcdn_batch_stats)]
+    lib.pcdn_solve_batch.restype = ctypes.c_int
+    lib.pcdn_autotune.argtypes = [vp, vp, i32, d, i32, ctypes.c_uint64, P(pcdn_opts), P(i32), vp]
+    lib.pcdn_autotune.restype = ctypes.c_int
+    lib.pcdn_default_server_opts.argtypes = [P(pcdn_server_opts)]
+    lib.pcdn_default_server_opts.restype = None
+    lib.pcdn_server_create.argtypes = [P(pcdn_server_opts), P(vp)]
+    lib.pcdn_server_create.restype = ctypes.c_int
+    lib.pcdn_server_submit.argtypes = [vp, P(pcdn_csc), vp, d, ctypes.c_int, i32, d, ctypes.c_uint64, P(i64)]
+    lib.pcdn_server_submit.restype = ctypes.c_int
+    lib.pcdn_server_submit_borrowed.argtypes = lib.pcdn_server_submit.argtypes
+    lib.pcdn_server_submit_borrowed.restype = ctypes.c_int
+    lib.pcdn_server_wait.argtypes = [vp, i64, d, vp, P(pcdn_request_info)]
+    lib.pcdn_server_wait.restype = ctypes.c_int
+    lib.pcdn_server_stats.argtypes = [vp, P(i64), P(i64), P(i32), P(i64)]
+    lib.pcdn_server_stats.restype = ctypes.c_int
+    lib.pcdn_server_destroy.argtypes = [vp]
+    lib.pcdn_server_destroy.restype = None
     _lib = lib
     return lib
 
@@ -255,6 +305,134 @@ def pcdn_objective_noalloc(col_ptr, row_idx, val, y, C: float, loss: str, w, F, 
     s = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
     _check(lib.pcdn_objective_noalloc(ctypes.byref(X), y.data_ptr(), float(C), LOSSES[loss], w.data_ptr(),
                                       F.data_ptr(), s))
+
+
+def pcdn_set_C(h: int, C: float) -> None:
+    _check(load().pcdn_set_C(h, float(C)))
+
+
+def pcdn_default_batch_opts(**overrides) -> pcdn_batch_opts:
+    o = pcdn_batch_opts()
+    load().pcdn_default_batch_opts(ctypes.byref(o))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+def _stats_dict(st: pcdn_stats) -> dict:
+    return {f: getattr(st, f) for f, _ in pcdn_stats._fields_}
+
+
+def pcdn_solve_batch(handles, n_features, C_paths, P, eps=1e-3, seed=0, opts: pcdn_opts | None = None,
+                     bopts: pcdn_batch_opts | None = None, want_w: bool = True):
+    """Solve many problems concurrently, each along its C path (warm-started).  ``P`` is one bundle
+    size for all jobs or a list (0 = autotuned).  Returns (status, per-job list of dicts with
+    status, P_used, w [n_C, n_features] or None, stats list) and the batch statistics."""
+    lib = load()
+    J = len(handles)
+    Ps = list(P) if hasattr(P, "__len__") else [int(P)] * J
+    seeds = list(seed) if hasattr(seed, "__len__") else [int(seed)] * J
+    jobs = (pcdn_batch_job * max(J, 1))()
+    keep = []
+    outs = []
+    for k in range(J):
+        cp = _host(C_paths[k], np.float64)
+        nC = int(cp.shape[0])
+        w = np.empty((nC, int(n_features[k])), dtype=np.float64) if want_w else None
+        st = (pcdn_stats * nC)()
+        keep += [cp, w, st]
+        jobs[k] = pcdn_batch_job(handles[k], int(Ps[k]), float(eps), int(seeds[k]) & (2**64 - 1), nC, cp.ctypes.data,
+                                 w.ctypes.data if w is not None else None, ctypes.cast(st, ctypes.c_void_p), 0, 0)
+        outs.append((w, st, nC))
+    o = opts if opts is not None else pcdn_default_opts()
+    bo = bopts if bopts is not None else pcdn_default_batch_opts()
+    bs = pcdn_batch_stats()
+    rc = lib.pcdn_solve_batch(jobs, J, ctypes.byref(o), ctypes.byref(bo), ctypes.byref(bs))
+    _check(rc, ok=(PCDN_OK, PCDN_ENOTCONVERGED))
+    res = []
+    for k in range(J):
+        w, st, nC = outs[k]
+        res.append(dict(status=jobs[k].status, P_used=jobs[k].P_used, w=w, stats=[_stats_dict(st[i]) for i in range(nC)]))
+    return rc, res, {f: getattr(bs, f) for f, _ in pcdn_batch_stats._fields_}
+
+
+def pcdn_autotune(h: int, candidates=None, probe_eps: float = 0.1, probe_epochs: int = 3, seed: int = 0,
+                    opts: pcdn_opts | None = None):
+    """The bundle-size autotuner on one problem; returns (P_best, list of (P, score))."""
+    lib = load()
+    cand = None if candidates is None else _host(candidates, np.int32)
+    n = 0 if cand is None else int(cand.shape[0])
+    scores = np.zeros(max(n, 16))
+    Pb = ctypes.c_int32()
+    o = opts if opts is not None else pcdn_default_opts()
+    _check(lib.pcdn_autotune(h, cand.ctypes.data if cand is not None else None, n, float(probe_eps), int(probe_epochs),
+                               int(seed) & (2**64 - 1), ctypes.byref(o), ctypes.byref(Pb), scores.ctypes.data))
+    return Pb.value, scores
+
+
+class Server:
+    """Request server (continuous batching on one GPU); see include/pcdn.h."""
+
+    def __init__(self, slots: int = 0, hbm_budget: int = 0, opts: pcdn_opts | None = None):
+        lib = load()
+        so = pcdn_server_opts()
+        lib.pcdn_default_server_opts(ctypes.byref(so))
+        so.slots = int(slots)
+        if hbm_budget:
+            so.hbm_budget = int(hbm_budget)
+        if opts is not None:
+            so.solve = opts
+        h = ctypes.c_void_p()
+        _check(lib.pcdn_server_create(ctypes.byref(so), ctypes.byref(h)))
+        self.handle = h.value
+        self._nf = {}
+        self._keep = {}
+
+    def submit(self, col_ptr, row_idx, val, y, C: float, loss: str, P: int, eps: float = 1e-3, seed: int = 0,
+               borrow: bool = False) -> int:
+        """Queue a solve; with ``borrow`` the arrays are not copied and are kept referenced here
+        until the result is collected."""
+        cp, ri, vv, yy = _host(col_ptr, np.int64), _host(row_idx, np.int32), _host(val, np.float32), _host(y, np.int8)
+        X = pcdn_csc(int(yy.shape[0]), int(cp.shape[0] - 1), int(ri.shape[0]), cp.ctypes.data, ri.ctypes.data,
+                     vv.ctypes.data)
+        t = ctypes.c_int64()
+        fn = load().pcdn_server_submit_borrowed if borrow else load().pcdn_server_submit
+        _check(fn(self.handle, ctypes.byref(X), yy.ctypes.data, float(C), LOSSES[loss], int(P), float(eps),
+                  int(seed) & (2**64 - 1), ctypes.byref(t)))
+        self._nf[t.value] = int(cp.shape[0] - 1)
+        if borrow:
+            self._keep[t.value] = (cp, ri, vv, yy)
+        return t.value
+
+    def wait(self, ticket: int, timeout_s: float = 0.0):
+        """Returns (status, w, info dict)."""
+        nf = self._nf[ticket]
+        w = np.empty(nf, dtype=np.float64)
+        info = pcdn_request_info()
+        rc = load().pcdn_server_wait(self.handle, int(ticket), float(timeout_s), w.ctypes.data, ctypes.byref(info))
+        if rc == PCDN_ETIMEOUT:
+            raise PcdnError(rc, pcdn_last_error())
+        del self._nf[ticket]
+        self._keep.pop(ticket, None)
+        d = dict(status=info.status, t_submit=info.t_submit, t_admit=info.t_admit, t_done=info.t_done,
+                 bytes=info.bytes, stats=_stats_dict(info.stats))
+        return rc, w, d
+
+    def stats(self):
+        a, b, c, e = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int64()
+        _check(load().pcdn_server_stats(self.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(e)))
+        return dict(submitted=a.value, finished=b.value, in_flight=c.value, bytes_in_use=e.value)
+
+    def close(self):
+        if self.handle:
+            load().pcdn_server_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def pcdn_memory(h: int) -> int:

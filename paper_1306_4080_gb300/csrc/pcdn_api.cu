@@ -11,6 +11,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -18,6 +19,7 @@
 #include "pcdn.h"
 #include "pcdn_internal.cuh"
 #include "pcdn_prep.h"
+#include "pcdn_task.h"
 
 namespace pcdn {
 cudaError_t launch_walk(int loss, int prec, const WalkParams& p, int grid, cudaStream_t s);
@@ -60,11 +62,48 @@ int fail(int code, const char* fmt, ...) {
 
 constexpr uint32_t kDefaultSpin = 1u << 22;  // ~seconds of polling before a wait gives up
 
+// Device memory comes from one stream-ordered pool per device, owned by the library for the life of
+// the process: allocations and frees are ordered on the problem's stream and never synchronise the
+// device, so problems can be created and destroyed while other problems' solves run (the request
+// server does exactly that).  Up to kPoolKeep bytes of freed memory stay reserved for reuse.
+constexpr uint64_t kPoolKeep = uint64_t(8) << 30;
+
+cudaError_t library_pool(cudaMemPool_t* out) {
+  static std::mutex mu;
+  static cudaMemPool_t pools[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!pools[dev]) {
+    cudaMemPoolProps props;
+    std::memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if ((e = cudaMemPoolCreate(&pool, &props)) != cudaSuccess) return e;
+    uint64_t keep = kPoolKeep;
+    if ((e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep)) != cudaSuccess) return e;
+    pools[dev] = pool;
+  }
+  *out = pools[dev];
+  return cudaSuccess;
+}
+
 template <typename T>
-cudaError_t dalloc(T** p, int64_t count) {
+cudaError_t dalloc(T** p, int64_t count, cudaStream_t s) {
   *p = nullptr;
   if (count <= 0) count = 1;
-  return cudaMalloc((void**)p, sizeof(T) * (size_t)count);
+  cudaMemPool_t pool = nullptr;
+  cudaError_t e = library_pool(&pool);
+  if (e != cudaSuccess) return e;
+  return cudaMallocFromPoolAsync((void**)p, sizeof(T) * (size_t)count, pool, s);
+}
+
+void dfree(void* q, cudaStream_t s) {
+  if (q) cudaFreeAsync(q, s);
 }
 
 }  // namespace
@@ -149,13 +188,13 @@ namespace {
 
 template <typename T>
 cudaError_t palloc(pcdn_problem* p, T** ptr, int64_t count) {
-  cudaError_t e = dalloc(ptr, count);
+  cudaError_t e = dalloc(ptr, count, p->stream);
   if (e == cudaSuccess) p->device_bytes += (int64_t)sizeof(T) * (count > 0 ? count : 1);
   return e;
 }
 
 void free_all(pcdn_problem* p) {
-  auto f = [](void* q) { if (q) cudaFree(q); };
+  auto f = [p](void* q) { dfree(q, p->stream); };
   if (p->owns_x) {
     f(p->col_ptr); f(p->row_idx); f(p->val); f(p->y);
   }
@@ -224,12 +263,12 @@ int finish_create(pcdn_problem* p) {
     const int64_t hn = radix_hist_elems(nnz);
     cudaError_t e = cudaSuccess;
     auto cleanup = [&]() {
-      cudaFree(entry_col); cudaFree(k0); cudaFree(k1); cudaFree(v0); cudaFree(v1);
-      cudaFree(hist); cudaFree(ws); cudaFree(counts);
+      dfree(entry_col, s); dfree(k0, s); dfree(k1, s); dfree(v0, s); dfree(v1, s);
+      dfree(hist, s); dfree(ws, s); dfree(counts, s);
     };
-    if ((e = dalloc(&entry_col, nnz)) || (e = dalloc(&k0, nnz)) || (e = dalloc(&k1, nnz)) || (e = dalloc(&v0, nnz)) ||
-        (e = dalloc(&v1, nnz)) || (e = dalloc(&hist, hn)) ||
-        (e = dalloc(&ws, scan_workspace_elems(hn > n + 1 ? hn : n + 1))) || (e = dalloc(&counts, n + 1))) {
+    if ((e = dalloc(&entry_col, nnz, s)) || (e = dalloc(&k0, nnz, s)) || (e = dalloc(&k1, nnz, s)) ||
+        (e = dalloc(&v0, nnz, s)) || (e = dalloc(&v1, nnz, s)) || (e = dalloc(&hist, hn, s)) ||
+        (e = dalloc(&ws, scan_workspace_elems(hn > n + 1 ? hn : n + 1), s)) || (e = dalloc(&counts, n + 1, s))) {
       cleanup();
       return fail(e == cudaErrorMemoryAllocation ? PCDN_ENOMEM : PCDN_ECUDA, "mirror workspace: %s", cudaGetErrorString(e));
     }
@@ -318,7 +357,7 @@ int finish_create(pcdn_problem* p) {
 
 int ensure_bundle_scratch(pcdn_problem* p, int32_t P) {
   if (P <= p->P_cap) return PCDN_OK;
-  auto f = [](void* q) { if (q) cudaFree(q); };
+  auto f = [p](void* q) { dfree(q, p->stream); };
   f(p->gk); f(p->hk); f(p->dk); f(p->col_cnt);
   p->gk = p->hk = p->dk = nullptr;
   p->col_cnt = nullptr;
@@ -334,7 +373,7 @@ int ensure_bundle_scratch(pcdn_problem* p, int32_t P) {
 
 int ensure_plan(pcdn_problem* p, int64_t entries) {
   if (entries <= p->plan_cap) return PCDN_OK;
-  if (p->plan) cudaFree(p->plan);
+  dfree(p->plan, p->stream);
   p->plan = nullptr;
   p->plan_cap = 0;
   CUDA_TRY(palloc(p, &p->plan, entries));
@@ -344,7 +383,7 @@ int ensure_plan(pcdn_problem* p, int64_t entries) {
 
 int ensure_trace(pcdn_problem* p, int64_t nb) {
   if (nb <= p->tr_cap) return PCDN_OK;
-  auto f = [](void* q) { if (q) cudaFree(q); };
+  auto f = [p](void* q) { dfree(q, p->stream); };
   f(p->tr_q); f(p->tr_alpha); f(p->tr_Delta); f(p->tr_dF);
   p->tr_q = nullptr;
   p->tr_alpha = p->tr_Delta = p->tr_dF = nullptr;
@@ -357,10 +396,17 @@ int ensure_trace(pcdn_problem* p, int64_t nb) {
   return PCDN_OK;
 }
 
+int status_from_flags(int h);
+
 int device_status(pcdn_problem* p) {
   int h = 0;
   CUDA_TRY(cudaMemcpyAsync(&h, p->err, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
   CUDA_TRY(cudaStreamSynchronize(p->stream));
+  return status_from_flags(h);
+}
+
+// The device error flags as a status code (and message).
+int status_from_flags(int h) {
   if (h & kErrTimeout) return fail(PCDN_ETIMEOUT, "a device-side wait between thread blocks timed out");
   if (h & kErrNumeric) return fail(PCDN_ENUMERIC, "non-finite gradient, Hessian diagonal or direction");
   if (h & kErrRange) return fail(PCDN_ENUMERIC, "maintained quantity out of range after an update (|w^T x| above about 699)");
@@ -379,8 +425,10 @@ int reset_scratch(pcdn_problem* p) {
 }
 
 int do_refresh(pcdn_problem* p, int prec, bool write_state, bool with_loss) {
-  CUDA_TRY(refresh(p->loss, prec, p->row_ptr, p->col_idx, p->rval, p->y, p->w, p->n, p->mq, p->rec, write_state,
-                   with_loss ? p->red_part : nullptr, p->red_grid, p->err, p->stream, &p->launches));
+  // w_pos (position-order w, used only inside a walk) holds the mixed mode's split copy of w
+  CUDA_TRY(refresh(p->loss, prec, p->row_ptr, p->col_idx, p->rval, p->y, p->w, p->n, p->m, p->nnz, p->w_pos, p->mq,
+                   p->rec, write_state, with_loss ? p->red_part : nullptr, p->red_grid, p->err, p->stream,
+                   &p->launches));
   if (write_state) p->rec_prec = prec;
   return PCDN_OK;
 }
@@ -521,6 +569,274 @@ int make_partition(pcdn_problem* p, uint64_t seed, int64_t epoch, int32_t** perm
 
 }  // namespace
 
+// ---------------------------------------------------------------- non-blocking solve (pcdn_task.h)
+namespace pcdn {
+
+namespace {
+// Scalars a stage leaves for the host (pinned, written by the stage's device-to-host copies).
+struct Mail {
+  double kkt;
+  double F;
+  int32_t err;
+  int32_t pad;
+  unsigned long long cnt[8];
+};
+enum { kStageNone = 0, kStageStart = 1, kStageEpoch = 2, kStageFinal = 3, kStageEnded = 4 };
+}  // namespace
+
+struct SolveTask {
+  Mail* mail = nullptr;
+  cudaEvent_t ev = nullptr;
+  pcdn_problem* p = nullptr;
+  pcdn_opts o{};
+  int32_t P = 0;
+  double eps = 0.0;
+  uint64_t seed = 0;
+  int grid = 1;
+  int64_t nb = 0;
+  int stage = kStageNone;
+  int rc = PCDN_OK;
+  double kkt0 = 0.0, kkt_rel = 0.0, F = 0.0;
+  int64_t epochs = 0;
+  int converged = 0;
+  double walk_ms = 0.0;
+  int64_t launches0 = 0;
+  unsigned long long cnt[8] = {0};
+  std::chrono::steady_clock::time_point t0;
+  double wall_s = 0.0;
+};
+
+int task_create(SolveTask** out) {
+  if (!out) return fail(PCDN_EINVAL, "out must be given");
+  *out = nullptr;
+  SolveTask* t = new (std::nothrow) SolveTask();
+  if (!t) return fail(PCDN_ENOMEM, "host allocation");
+  cudaError_t e = cudaHostAlloc((void**)&t->mail, sizeof(Mail), cudaHostAllocDefault);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&t->ev, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    task_destroy(t);
+    return fail(e == cudaErrorMemoryAllocation ? PCDN_ENOMEM : PCDN_ECUDA, "task set-up: %s", cudaGetErrorString(e));
+  }
+  std::memset(t->mail, 0, sizeof(Mail));
+  *out = t;
+  return PCDN_OK;
+}
+
+void task_destroy(SolveTask* t) {
+  if (!t) return;
+  if (t->ev) {
+    cudaEventSynchronize(t->ev);
+    cudaEventDestroy(t->ev);
+  }
+  if (t->mail) cudaFreeHost(t->mail);
+  delete t;
+}
+
+namespace {
+
+// The stage's scalars into the mailbox, then the stage's completion event.
+int post(SolveTask* t, int kkt_slot, bool final_stage) {
+  pcdn_problem* p = t->p;
+  if (kkt_slot >= 0)
+    CUDA_TRY(cudaMemcpyAsync(&t->mail->kkt, p->red_out + kkt_slot, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+  if (final_stage) {
+    CUDA_TRY(cudaMemcpyAsync(&t->mail->F, p->red_out, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+    CUDA_TRY(cudaMemcpyAsync(t->mail->cnt, p->counters, sizeof(t->mail->cnt), cudaMemcpyDeviceToHost, p->stream));
+  }
+  CUDA_TRY(cudaMemcpyAsync(&t->mail->err, p->err, sizeof(int32_t), cudaMemcpyDeviceToHost, p->stream));
+  CUDA_TRY(cudaEventRecord(t->ev, p->stream));
+  return PCDN_OK;
+}
+
+// One outer iteration: partition (Eq. 8), work items, the bundle walk, refresh, KKT.
+int issue_epoch(SolveTask* t, int64_t k) {
+  pcdn_problem* p = t->p;
+  int32_t* perm = nullptr;
+  int rc = make_partition(p, t->seed, k, &perm);
+  if (rc) return rc;
+  CUDA_TRY(build_items(perm, p->m, p->col_ptr, p->w, p->cnt, p->item_ptr, p->items, p->scan_ws, p->stream,
+                       &p->launches));
+  rc = run_walk(p, &t->o, perm, p->m, t->P, 0, t->nb, t->grid, nullptr);
+  if (rc) return rc;
+  if (t->o.refresh) {
+    rc = do_refresh(p, (int)t->o.prec, true, false);
+    if (rc) return rc;
+  }
+  rc = do_kkt(p, 1);
+  if (rc) return rc;
+  t->stage = kStageEpoch;
+  return post(t, 1, false);
+}
+
+int issue_final(SolveTask* t) {
+  int rc = do_objective(t->p, 0);
+  if (rc) return rc;
+  t->stage = kStageFinal;
+  return post(t, -1, true);
+}
+
+int end_task(SolveTask* t, int rc) {
+  t->stage = kStageEnded;
+  t->rc = rc;
+  t->wall_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t->t0).count();
+  return rc;
+}
+
+}  // namespace
+
+int task_start(SolveTask* t, pcdn_problem* p, int32_t P, double eps, uint64_t seed, const pcdn_opts* opts, int grid) {
+  g_err.clear();
+  if (!t || !p) return fail(PCDN_EINVAL, "task and problem must be given");
+  if (t->stage != kStageNone && t->stage != kStageEnded) return fail(PCDN_EINVAL, "task has a solve in flight");
+  if (P < 1 || P > p->m) return fail(PCDN_EINVAL, "P must be in [1, n_features]");
+  if (!(eps > 0)) return fail(PCDN_EINVAL, "eps must be positive");
+  pcdn_opts o;
+  if (opts) o = *opts;
+  else pcdn_default_opts(&o);
+  int rc = check_opts(&o);
+  if (rc) return rc;
+  if (grid > 0) o.grid_ctas = grid;
+  t->p = p;
+  t->o = o;
+  t->P = P;
+  t->eps = eps;
+  t->seed = seed;
+  t->nb = (p->m + P - 1) / P;
+  t->grid = pick_grid(p, &o, P);
+  t->kkt0 = t->kkt_rel = t->F = t->walk_ms = 0.0;
+  t->epochs = 0;
+  t->converged = 0;
+  t->rc = PCDN_OK;
+  t->launches0 = p->launches;
+  t->t0 = std::chrono::steady_clock::now();
+  std::memset(t->cnt, 0, sizeof(t->cnt));
+  if ((rc = ensure_bundle_scratch(p, P)) || (rc = ensure_trace(p, t->nb)) ||
+      (rc = ensure_plan(p, t->nb * (t->grid + 1))) || (rc = reset_scratch(p)))
+    return end_task(t, rc);
+  if (!o.warm_start) CUDA_TRY(cudaMemsetAsync(p->w, 0, sizeof(double) * p->m, p->stream));
+  CUDA_TRY(cudaMemsetAsync(p->err, 0, sizeof(int), p->stream));
+  CUDA_TRY(cudaMemsetAsync(p->counters, 0, sizeof(unsigned long long) * 8, p->stream));
+  if ((rc = do_refresh(p, (int)o.prec, true, false)) || (rc = do_kkt(p, 2))) return end_task(t, rc);
+  t->stage = kStageStart;
+  rc = post(t, 2, false);
+  if (rc) return end_task(t, rc);
+  return PCDN_OK;
+}
+
+int task_poll(SolveTask* t, int* done) {
+  *done = 0;
+  if (!t || t->stage == kStageNone) return fail(PCDN_EINVAL, "no solve started");
+  if (t->stage == kStageEnded) {
+    *done = 1;
+    return t->rc;
+  }
+  const cudaError_t q = cudaEventQuery(t->ev);
+  if (q == cudaErrorNotReady) return PCDN_OK;
+  int rc = PCDN_OK;
+  if (q != cudaSuccess) {
+    rc = fail(PCDN_ECUDA, "solve stage: %s", cudaGetErrorString(q));
+  } else {
+    rc = status_from_flags(t->mail->err);
+  }
+  if (rc) {
+    *done = 1;
+    return end_task(t, rc);
+  }
+  switch (t->stage) {
+    case kStageStart:
+      t->kkt0 = t->mail->kkt;
+      t->kkt_rel = t->kkt0 > 0 ? 1.0 : 0.0;
+      t->converged = t->kkt0 == 0.0;
+      rc = (!t->converged && t->o.max_epochs > 0) ? issue_epoch(t, 0) : issue_final(t);
+      break;
+    case kStageEpoch: {
+      float ms = 0.0f;
+      if (cudaEventElapsedTime(&ms, t->p->ev0, t->p->ev1) == cudaSuccess) t->walk_ms += ms;
+      cudaGetLastError();
+      t->epochs += 1;
+      t->kkt_rel = t->kkt0 > 0 ? t->mail->kkt / t->kkt0 : 0.0;
+      if (t->kkt_rel <= t->eps) t->converged = 1;
+      rc = (t->converged || t->epochs >= t->o.max_epochs) ? issue_final(t) : issue_epoch(t, t->epochs);
+      break;
+    }
+    case kStageFinal:
+      t->F = t->mail->F;
+      std::memcpy(t->cnt, t->mail->cnt, sizeof(t->cnt));
+      *done = 1;
+      return end_task(t, t->converged ? PCDN_OK : PCDN_ENOTCONVERGED);
+    default:
+      break;
+  }
+  if (rc) {
+    *done = 1;
+    return end_task(t, rc);
+  }
+  return PCDN_OK;
+}
+
+int task_wait(SolveTask* t) {
+  if (!t || t->stage == kStageNone || t->stage == kStageEnded) return PCDN_OK;
+  CUDA_TRY(cudaEventSynchronize(t->ev));
+  return PCDN_OK;
+}
+
+int task_result(SolveTask* t, double* w_out, pcdn_stats* stats) {
+  if (!t || t->stage != kStageEnded) return fail(PCDN_EINVAL, "the solve has not ended");
+  pcdn_problem* p = t->p;
+  if (w_out) {
+    CUDA_TRY(cudaMemcpyAsync(w_out, p->w, sizeof(double) * p->m, cudaMemcpyDeviceToHost, p->stream));
+    CUDA_TRY(cudaStreamSynchronize(p->stream));
+  }
+  if (stats) {
+    std::memset(stats, 0, sizeof(*stats));
+    stats->epochs = t->epochs;
+    stats->bundles = (int64_t)t->cnt[5];
+    stats->coord_updates = (int64_t)t->cnt[6];
+    stats->ls_steps = (int64_t)t->cnt[0];
+    stats->ls_cap_hits = (int64_t)t->cnt[1];
+    stats->ls_passes = (int64_t)t->cnt[2];
+    stats->nnz_visited = t->epochs * p->nnz;
+    stats->rows_touched = (int64_t)t->cnt[4];
+    stats->kernel_launches = p->launches - t->launches0;
+    stats->F_final = t->F;
+    stats->kkt_rel = t->kkt_rel;
+    stats->kkt0 = t->kkt0;
+    stats->walk_s = t->walk_ms * 1e-3;
+    stats->bytes_model = 16.0 * (double)stats->nnz_visited + 33.0 * (double)stats->rows_touched +
+                         16.0 * (double)stats->coord_updates;
+    stats->converged = t->converged;
+    stats->walk_grid = t->grid;
+    stats->wall_s = t->wall_s;
+  }
+  return t->rc;
+}
+
+int64_t problem_n_features(pcdn_problem* p) { return p ? p->m : 0; }
+
+int64_t problem_bytes_estimate(int64_t n, int64_t m, int64_t nnz, int32_t P) {
+  if (P < 1) P = 1;
+  const int64_t max_items = m + nnz / kChunk + 2;
+  const int64_t hm = radix_hist_elems(m);
+  int64_t scan_n = std::max<int64_t>(std::max<int64_t>(hm, m + 1), max_items + 1);
+  const int64_t nb = (m + P - 1) / P;
+  int64_t b = 0;
+  b += 8 * (m + 1) + 8 * nnz + n;                       // X by columns, labels
+  b += (n + 15) / 16 * 16;                              // padded labels
+  b += 8 * (n + 1) + 8 * nnz;                           // X by rows
+  b += 16 * m + 8 * n + (int64_t)sizeof(RecT<0>) * n + 8 * n + 4 * ((n + 31) / 32);  // w, w_pos, mq, rec, delta, bitmap
+  b += 16 * m + 8 * m + 16 * (m + 1) + (int64_t)sizeof(Item) * max_items;           // keys, values, cnt, item_ptr, items
+  b += 8 * hm + 8 * scan_workspace_elems(scan_n) + 16 * max_items + 16 * (max_items + 1);
+  b += 4 * m + 8 * (m + 1) + (int64_t)sizeof(Item) * max_items;                     // identity-order items
+  b += 8 * 3 * kPartStride * kAccPad + 4096;                                         // accumulators, flags, partials
+  b += 32 * (int64_t)P + 28 * nb + 16 * nb;                                          // bundle scratch, trace, plan (1 block)
+  // the row mirror's build workspace, held while the problem is created
+  const int64_t hn = radix_hist_elems(nnz);
+  const int64_t transient = 20 * nnz + 8 * hn + 8 * scan_workspace_elems(std::max<int64_t>(hn, n + 1)) + 8 * (n + 1);
+  return b + transient;
+}
+
+}  // namespace pcdn
+
 extern "C" {
 
 void pcdn_default_opts(pcdn_opts* o) {
@@ -627,7 +943,7 @@ int pcdn_create_device(const pcdn_csc* X, const int8_t* y, double C, pcdn_loss l
       (e = cudaStreamSynchronize(p->stream)))
     return bail(fail(PCDN_ECUDA, "validation: %s", cudaGetErrorString(e)));
   if (flag) return bail(fail(PCDN_EINVAL, "device CSC/labels invalid (flags 0x%x)", flag));
-  cudaFree(p->err);
+  dfree(p->err, p->stream);
   p->err = nullptr;
   int rc = finish_create(p);
   if (rc) return bail(rc);
@@ -657,6 +973,15 @@ int pcdn_set_w(pcdn_problem* p, const double* w) {
   rc = do_refresh(p, p->rec_prec, true, false);
   if (rc) return rc;
   return device_status(p);
+}
+
+int pcdn_set_C(pcdn_problem* p, double C) {
+  g_err.clear();
+  if (!p) return fail(PCDN_EINVAL, "problem must be given");
+  if (!(C > 0) || !std::isfinite(C)) return fail(PCDN_EINVAL, "C must be positive and finite");
+  // the maintained quantities and the per-sample coefficients do not involve c
+  p->c = C;
+  return PCDN_OK;
 }
 
 int pcdn_get_w(pcdn_problem* p, double* w) {

@@ -394,6 +394,106 @@ __global__ void __launch_bounds__(kRedThreads) refresh_kernel(const int64_t* row
   }
 }
 
+// Mixed precision: w as a pair of FP32 numbers hi + lo (w - hi rounded), about 48 significant bits.
+__global__ void split_w_kernel(const double* w, int64_t m, float2* w2) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
+    const double v = w[j];
+    const float hi = (float)v;
+    w2[j] = make_float2(hi, (float)(v - (double)hi));
+  }
+}
+
+// Mixed precision: z = Xw with T lanes per row in double-float arithmetic on the FP32 pipe (the
+// FP64 pipe of this part runs at a small fraction of the FP32 rate).  Each product x_ij w_j is
+// formed as x_ij hi_j exactly (error-free product by FMA) plus x_ij lo_j, summed as a double-float
+// pair; the T partial sums combine in a fixed tree.  Relative error of z about 2^-44 of sum |x_ij w_j|.
+// Every lane of a warp runs the same number of row rounds, so the shuffles are full-warp.
+template <int LOSS, int T>
+__global__ void __launch_bounds__(kRedThreads) refresh_df_kernel(const int64_t* row_ptr, const int32_t* col_idx,
+                                                                 const float* rval, const int8_t* y, const float2* w2,
+                                                                 int64_t n, double* mq, void* rec, int write_state,
+                                                                 double* loss_part, int* err) {
+  __shared__ double wsum[kRedThreads];
+  constexpr int G = 32 / T;  // rows per warp round
+  const int gl = threadIdx.x & (T - 1);
+  const int grp = (threadIdx.x & 31) / T;
+  const int64_t warp = ((int64_t)blockIdx.x * kRedThreads + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * kRedThreads) >> 5;
+  double lsum = 0.0;
+  for (int64_t r0 = warp * G; r0 < n; r0 += nwarps * G) {
+    const int64_t i = r0 + grp;
+    const bool valid = i < n;
+    const int64_t a = valid ? row_ptr[i] : 0, b = valid ? row_ptr[i + 1] : 0;
+    dfloat acc = {0.0f, 0.0f};
+    int64_t e = a + gl;
+    for (; e + 3 * T < b; e += 4 * T) {
+      int32_t c[4];
+      float v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        c[u] = col_idx[e + u * T];
+        v[u] = rval[e + u * T];
+      }
+      float2 wv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) wv[u] = w2[c[u]];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float ph = v[u] * wv[u].x;
+        const float pl = fmaf(v[u], wv[u].y, fmaf(v[u], wv[u].x, -ph));
+        acc = df_add(acc, dfloat{ph, pl});
+      }
+    }
+    for (; e < b; e += T) {
+      const float v = rval[e];
+      const float2 wv = w2[col_idx[e]];
+      const float ph = v * wv.x;
+      const float pl = fmaf(v, wv.y, fmaf(v, wv.x, -ph));
+      acc = df_add(acc, dfloat{ph, pl});
+    }
+#pragma unroll
+    for (int o = T / 2; o > 0; o >>= 1) acc = df_add(acc, df_shfl_xor(acc, o));
+    if (valid && gl == 0) {
+      const double z = df_value(acc);
+      const int yi = y[i];
+      if (loss_part) lsum += row_loss(LOSS, z, yi);
+      if (write_state) {
+        double mv;
+        if (LOSS == 0) {
+          if (fabs(z) > 700.0) atomicOr(err, kErrRefresh);
+          mv = exp(z);
+        } else {
+          mv = 1.0 - (double)yi * z;
+        }
+        mq[i] = mv;
+        ((RecT<1>*)rec)[i] = RowCoef<LOSS, 1>::make(mv, yi);
+      }
+    }
+  }
+  if (loss_part) {
+    wsum[threadIdx.x] = lsum;
+    __syncthreads();
+    for (int o = kRedThreads / 2; o > 0; o >>= 1) {
+      if (threadIdx.x < o) wsum[threadIdx.x] += wsum[threadIdx.x + o];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) loss_part[blockIdx.x] = wsum[0];
+  }
+}
+
+template <int LOSS>
+cudaError_t launch_refresh_df(int T, int grid, cudaStream_t s, const int64_t* row_ptr, const int32_t* col_idx,
+                              const float* rval, const int8_t* y, const float2* w2, int64_t n, double* mq, void* rec,
+                              int ws, double* loss_part, int* err) {
+  if (T <= 8)
+    refresh_df_kernel<LOSS, 8><<<grid, kRedThreads, 0, s>>>(row_ptr, col_idx, rval, y, w2, n, mq, rec, ws, loss_part, err);
+  else if (T <= 16)
+    refresh_df_kernel<LOSS, 16><<<grid, kRedThreads, 0, s>>>(row_ptr, col_idx, rval, y, w2, n, mq, rec, ws, loss_part, err);
+  else
+    refresh_df_kernel<LOSS, 32><<<grid, kRedThreads, 0, s>>>(row_ptr, col_idx, rval, y, w2, n, mq, rec, ws, loss_part, err);
+  return cudaGetLastError();
+}
+
 template <int LOSS, int PREC>
 __global__ void rec_from_mq_kernel(const double* mq, const int8_t* y, int64_t n, void* rec) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -608,9 +708,23 @@ cudaError_t validate_device(const int64_t* col_ptr, const int32_t* row_idx, cons
 }
 
 cudaError_t refresh(int loss, int prec, const int64_t* row_ptr, const int32_t* col_idx, const float* rval,
-                    const int8_t* y, const double* w, int64_t n, double* mq, void* rec, bool write_state,
-                    double* loss_part, int grid, int* err, cudaStream_t s, int64_t* launches) {
+                    const int8_t* y, const double* w, int64_t n, int64_t m, int64_t nnz, void* w2_scratch,
+                    double* mq, void* rec, bool write_state, double* loss_part, int grid, int* err, cudaStream_t s,
+                    int64_t* launches) {
   const int ws = write_state ? 1 : 0;
+  if (prec == 1 && w2_scratch) {
+    float2* w2 = static_cast<float2*>(w2_scratch);
+    split_w_kernel<<<grid_for(m, 256), 256, 0, s>>>(w, m, w2);
+    cudaError_t e = post(launches);
+    if (e != cudaSuccess) return e;
+    // lanes per row from the mean row length: about 4-8 nonzeros per lane
+    const double mean = n > 0 ? (double)nnz / (double)n : 0.0;
+    const int T = mean < 64.0 ? 8 : (mean < 256.0 ? 16 : 32);
+    if (loss == 0) e = launch_refresh_df<0>(T, grid, s, row_ptr, col_idx, rval, y, w2, n, mq, rec, ws, loss_part, err);
+    else e = launch_refresh_df<1>(T, grid, s, row_ptr, col_idx, rval, y, w2, n, mq, rec, ws, loss_part, err);
+    if (launches) ++*launches;
+    return e;
+  }
   if (loss == 0 && prec == 0)
     refresh_kernel<0, 0><<<grid, kRedThreads, 0, s>>>(row_ptr, col_idx, rval, y, w, n, mq, rec, ws, loss_part, err);
   else if (loss == 0)

@@ -60,9 +60,12 @@ cudaError_t validate_device(const int64_t* col_ptr, const int32_t* row_idx, cons
 
 // ---- maintained quantities --------------------------------------------------------------------
 // z = Xw by rows; mq and rec from z (write_state), optional per-block loss partial sums.
+// FP64 (prec 0, or no scratch): one lane per row, separate multiply and add in column order.
+// Mixed (prec 1 with w2_scratch, 8 bytes per feature): double-float sums on the FP32 pipe.
 cudaError_t refresh(int loss, int prec, const int64_t* row_ptr, const int32_t* col_idx, const float* rval,
-                    const int8_t* y, const double* w, int64_t n, double* mq, void* rec, bool write_state,
-                    double* loss_part, int grid, int* err, cudaStream_t s, int64_t* launches);
+                    const int8_t* y, const double* w, int64_t n, int64_t m, int64_t nnz, void* w2_scratch,
+                    double* mq, void* rec, bool write_state, double* loss_part, int grid, int* err, cudaStream_t s,
+                    int64_t* launches);
 // rec from the current mq (precision switch without recomputing z).
 cudaError_t rec_from_mq(int loss, int prec, const double* mq, const int8_t* y, int64_t n, void* rec, cudaStream_t s,
                         int64_t* launches);

@@ -23,7 +23,7 @@ def pk():
 def declared_functions():
     src = open(os.path.join(ROOT, "include", "pcdn.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(pcdn_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(pcdn_[A-Za-z0-9_]+)\s*\(", src)))
 
 
 def test_every_declared_symbol_is_exported(pk):
@@ -107,6 +107,36 @@ def test_product_path_does_not_import_the_oracle():
     pkg = os.path.join(ROOT, "paper_1306_4080_gb300")
     for dirpath, _, files in os.walk(pkg):
         for f in files:
-            if f.endswith((".py", ".cu", ".cuh", ".h")):
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt and "pcdn_oracle" not in txt, f
+
+
+def test_batch_and_server_validate_on_host(pk, has_cuda):
+    lib = pk.load()
+    bs = pk.pcdn_batch_stats()
+    # an empty batch is a no-op; a job without a problem or C path is rejected before any device work
+    assert lib.pcdn_solve_batch(None, 0, None, None, ctypes.byref(bs)) == pk.PCDN_OK
+    assert bs.solves == 0
+    jobs = (pk.pcdn_batch_job * 1)()
+    assert lib.pcdn_solve_batch(jobs, 1, None, None, None) == pk.PCDN_EINVAL
+    assert "problem" in pk.pcdn_last_error()
+    assert lib.pcdn_solve_batch(None, -1, None, None, None) == pk.PCDN_EINVAL
+    bo = pk.pcdn_default_batch_opts()
+    assert bo.probe_eps == 0.1 and bo.probe_epochs == 3 and bo.max_inflight == 0
+    Pb = ctypes.c_int32()
+    assert lib.pcdn_autotune(None, None, 0, 0.1, 3, 0, None, ctypes.byref(Pb), None) == pk.PCDN_EINVAL
+    assert lib.pcdn_set_C(None, 1.0) == pk.PCDN_EINVAL
+    so = pk.pcdn_server_opts()
+    lib.pcdn_default_server_opts(ctypes.byref(so))
+    assert so.hbm_budget == 8 << 30 and so.slots == 0 and so.solve.q_max == 30
+    so.slots = -1
+    h = ctypes.c_void_p()
+    assert lib.pcdn_server_create(ctypes.byref(so), ctypes.byref(h)) == pk.PCDN_EINVAL
+    assert lib.pcdn_server_submit(None, None, None, 1.0, 0, 1, 1e-3, 0, None) == pk.PCDN_EINVAL
+    assert lib.pcdn_server_wait(None, 1, 0.0, None, None) == pk.PCDN_EINVAL
+    assert lib.pcdn_server_stats(None, None, None, None, None) == pk.PCDN_EINVAL
+    lib.pcdn_server_destroy(None)
+    if not has_cuda:
+        lib.pcdn_default_server_opts(ctypes.byref(so))
+        assert lib.pcdn_server_create(ctypes.byref(so), ctypes.byref(h)) == pk.PCDN_ECUDA

@@ -174,6 +174,26 @@ def test_objective_and_kkt(pk, name):
         P.close()
 
 
+@pytest.mark.parametrize("name", ["lr_2k_10k", "svm_20k_100k", "ragged_svm"])
+def test_mixed_mode_refresh(pk, name):
+    """After a mixed-precision solve the problem refreshes z = Xw in double-float arithmetic on the
+    FP32 pipe: the objective from it stays within 1e-12 of the oracle's FP64 one, also at large
+    margins; the KKT norm (FP32 column sums in this mode) within 1e-5."""
+    wl, p = problem(name)
+    orc = oracle.Oracle.from_problem(p, wl.C, wl.loss)
+    P = pk.Problem.from_csc(p.col_ptr, p.row_idx, p.val, p.y, wl.C, wl.loss)
+    try:
+        P.solve(min(wl.P, p.n_features), 1e-1, 0, pk.pcdn_default_opts(prec="mixed", max_epochs=1), want_w=False)
+        rng = np.random.default_rng(5)
+        for scale in (0.5, 20.0):
+            w = rng.normal(0, scale, p.n_features) * (rng.random(p.n_features) < 0.05)
+            P.set_w(w)
+            assert P.objective() == pytest.approx(orc.objective(w), rel=1e-12)
+            assert P.kkt() == pytest.approx(orc.kkt_l1(w), rel=1e-5)
+    finally:
+        P.close()
+
+
 def test_device_pointer_create_matches_host_create(pk):
     import torch
     wl, p = problem("svm_20k_100k")
