@@ -56,8 +56,10 @@ def parse():
     ap.add_argument("--batch-nC", type=int, default=16)
     ap.add_argument("--serving", type=int, default=1, help="also run the request server (reported under 'serving')")
     ap.add_argument("--serve-rates", default="10,30,100,300,1000")
-    ap.add_argument("--serve-seconds", type=float, default=8.0, help="arrival window per rate (requests = rate x this, capped)")
-    ap.add_argument("--serve-max-requests", type=int, default=400)
+    ap.add_argument("--serve-seconds", type=float, default=4.0, help="arrival window per rate (requests = rate x this, capped)")
+    ap.add_argument("--serve-max-requests", type=int, default=200)
+    ap.add_argument("--batch-plain-every", type=int, default=4,
+                    help="one-at-a-time comparison on every k-th job (batched again on the same jobs); 1 = all")
     ap.add_argument("--serve-seq", type=int, default=40, help="requests timed through the sequential plain loop")
     ap.add_argument("--main", type=int, default=1, help="run the 2M x 3M solve (the headline metric)")
     return ap.parse_args()
@@ -236,31 +238,45 @@ def batch_pool(args):
 
 
 def run_batched(args, pk, pool):
-    """Every job's whole C path (warm-started, FP32 bulk / FP64 line search, relative KKT 1e-3):
-    all jobs at once through pcdn_solve_batch (bundle size autotuned per job, probes included in the
-    time), then the same paths one solve at a time through pcdn_solve with the bundle sizes the
-    autotuner chose.  Host wall time around each arm; inputs resident on the device."""
+    """Every job's whole C path (warm-started, FP32 bulk / FP64 line search, relative KKT 1e-3)
+    through pcdn_solve_batch, bundle size autotuned per job (probes included in the time).  The
+    one-at-a-time comparison runs on every k-th job: the same paths solve by solve through
+    pcdn_solve with the bundle sizes the autotuner chose, and the batch again on just those jobs.
+    Host wall time around each arm; inputs resident on the device."""
     import torch
     probs = [pk.Problem.from_csc(p.col_ptr, p.row_idx, p.val, p.y, j.C_path[0], j.loss) for j, p in pool]
-    try:
-        opts = pk.pcdn_default_opts(prec="mixed", max_epochs=args.max_epochs)
+
+    def batch(idx, P):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        rc, res, bs = pk.pcdn_solve_batch([q.handle for q in probs], [q.n_features for q in probs],
-                                          [j.C_path for j, _ in pool], 0, eps=1e-3, seed=0, opts=opts, want_w=False)
-        t_batch = time.perf_counter() - t0
+        rc, res, bs = pk.pcdn_solve_batch([probs[k].handle for k in idx], [probs[k].n_features for k in idx],
+                                          [pool[k][0].C_path for k in idx], P, eps=1e-3, seed=0,
+                                          opts=pk.pcdn_default_opts(prec="mixed", max_epochs=args.max_epochs),
+                                          want_w=False)
+        return time.perf_counter() - t0, rc, res, bs
+
+    try:
+        every = max(1, args.batch_plain_every)
+        all_idx = list(range(len(pool)))
+        t_batch, rc, res, bs = batch(all_idx, 0)
         Ps = [r["P_used"] for r in res]
-        F_batch = [[st["F_final"] for st in r["stats"]] for r in res]
         launches = sum(st["kernel_launches"] for r in res for st in r["stats"])
+        sub = all_idx[::every]
+        if every == 1:
+            t_sub, res_sub = t_batch, res
+        else:
+            t_sub, _, res_sub, _ = batch(sub, [Ps[k] for k in sub])
+        F_batch = [[st["F_final"] for st in r["stats"]] for r in res_sub]
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         F_plain, epochs_plain, conv = [], 0, True
-        for q, (job, _), P in zip(probs, pool, Ps):
+        for k in sub:
+            q, job = probs[k], pool[k][0]
             row = []
-            for k, C in enumerate(job.C_path):
+            for ci, C in enumerate(job.C_path):
                 pk.pcdn_set_C(q.handle, C)
-                o = pk.pcdn_default_opts(prec="mixed", max_epochs=args.max_epochs, warm_start=1 if k else 0)
-                _, _, st, _ = pk.pcdn_solve(q.handle, P, 1e-3, 0, o, q.n_features, want_w=False)
+                o = pk.pcdn_default_opts(prec="mixed", max_epochs=args.max_epochs, warm_start=1 if ci else 0)
+                _, _, st, _ = pk.pcdn_solve(q.handle, Ps[k], 1e-3, 0, o, q.n_features, want_w=False)
                 row.append(st["F_final"])
                 epochs_plain += st["epochs"]
                 conv = conv and bool(st["converged"])
@@ -275,23 +291,30 @@ def run_batched(args, pk, pool):
             walk = sum(st["walk_s"] for st in sts)
             jobs_diag.append({"path_s": sum(st["wall_s"] for st in sts), "n": p.n_samples, "m": p.n_features,
                               "nnz": p.nnz, "loss": job.loss, "P": r["P_used"], "epochs": sum(st["epochs"] for st in sts),
-                              "bundles": bund, "walk_us_per_bundle": walk / bund * 1e6 if bund else 0.0})
+                              "bundles": bund, "walk_blocks_max": max(st["walk_grid"] for st in sts),
+                              "walk_us_per_bundle": walk / bund * 1e6 if bund else 0.0})
         crit = sorted(jobs_diag, key=lambda d: -d["path_s"])
         n_solves = sum(len(j.C_path) for j, _ in pool)
+        n_sub = sum(len(pool[k][0].C_path) for k in sub)
         nnz = [p.nnz for _, p in pool]
         return ({"metric": "solves/s (whole C paths, relative KKT 1e-3)", "unit": "solves/s",
-                "value": n_solves / t_batch, "plain_value": n_solves / t_plain, "speedup_vs_plain": t_plain / t_batch,
-                "batch_s": t_batch, "plain_s": t_plain, "solves": n_solves, "status": rc,
-                "probe_solves": bs["probe_solves"], "epochs_batched": bs["epochs"], "epochs_plain": epochs_plain,
-                "plain_converged": conv, "max_rel_F_diff_batched_vs_plain": diff, "gpu_launches": int(launches),
-                "P_chosen": {str(P): Ps.count(P) for P in sorted(set(Ps))},
-                "critical_jobs": crit[:4], "sum_path_s": sum(d["path_s"] for d in jobs_diag),
-                "config": {"workload": f"{len(pool)} problems, n_samples log-uniform [1k, 50k] x {args.batch_scale:g}, "
-                                       f"n_features log-uniform [5k, 200k] x {args.batch_scale:g}, density U[0.1%, 1%], "
-                                       "Zipf 1.1 columns, tf-idf rows L2-normalised, losses alternating logistic / "
-                                       f"L2-SVM, each along {args.batch_nC} C values log-spaced over [1e-2, 1e1] "
-                                       "(warm-started)", "nnz_total": int(sum(nnz)), "nnz_max": int(max(nnz)),
-                           "precision": "mixed", "bundle_size": "autotuned per problem (probes timed)"}}, Ps)
+                 "value": n_solves / t_batch, "batch_s": t_batch, "solves": n_solves, "status": rc,
+                 "probe_solves": bs["probe_solves"], "epochs_batched": bs["epochs"], "gpu_launches": int(launches),
+                 "graph_solves": bs["graph_solves"],
+                 "vs_plain": {"jobs": len(sub), "solves": n_sub, "batched_s": t_sub, "plain_s": t_plain,
+                              "batched_solves_per_s": n_sub / t_sub, "plain_solves_per_s": n_sub / t_plain,
+                              "speedup": t_plain / t_sub, "plain_converged": conv, "epochs_plain": epochs_plain,
+                              "max_rel_F_diff": diff,
+                              "how": f"every {every}-th job; plain = pcdn_solve one solve at a time, same bundle sizes, "
+                                     "its own choice of walker blocks"},
+                 "P_chosen": {str(P): Ps.count(P) for P in sorted(set(Ps))},
+                 "critical_jobs": crit[:4], "sum_path_s": sum(d["path_s"] for d in jobs_diag),
+                 "config": {"workload": f"{len(pool)} problems, n_samples log-uniform [1k, 50k] x {args.batch_scale:g}, "
+                                        f"n_features log-uniform [5k, 200k] x {args.batch_scale:g}, density U[0.1%, 1%], "
+                                        "Zipf 1.1 columns, tf-idf rows L2-normalised, losses alternating logistic / "
+                                        f"L2-SVM, each along {args.batch_nC} C values log-spaced over [1e-2, 1e1] "
+                                        "(warm-started)", "nnz_total": int(sum(nnz)), "nnz_max": int(max(nnz)),
+                            "precision": "mixed", "bundle_size": "autotuned per problem (probes timed)"}}, Ps)
     finally:
         for q in probs:
             q.close()
@@ -328,6 +351,7 @@ def run_serving(args, pk, pool, P_of):
                 job, p = pool[picks[k]]
                 tickets.append(srv.submit(p.col_ptr, p.row_idx, p.val, p.y, float(Cs[k]), job.loss, P_of[picks[k]],
                                           1e-3, 0, borrow=True))
+            submit_lag = time.perf_counter() - t0 - float(np.sum(gaps))
             res = [srv.wait(t, 600) for t in tickets]
             lat = np.array([r[2]["t_done"] - r[2]["t_submit"] for r in res])
             first = min(r[2]["t_submit"] for r in res)
@@ -336,7 +360,7 @@ def run_serving(args, pk, pool, P_of):
             out["rates"].append({"rate_per_s": rate, "requests": R, "ok": ok, "solves_per_s": R / (last - first),
                                  "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
                                  "mean_s": float(lat.mean()),
-                                 "submit_lag_s": float(time.perf_counter() - t0 - float(np.sum(gaps)))})
+                                 "submit_lag_s": float(submit_lag)})
         finally:
             srv.close()
     # sequential plain loop on the first requests of the highest rate's draw

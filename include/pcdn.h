@@ -169,9 +169,12 @@ int pcdn_memory(pcdn_problem* prob, int64_t* bytes);
 /* ---- many solves on one GPU ----------------------------------------------------------------
  *
  * The paper solves one problem at a time (Algorithm 3).  These calls run many independent solves
- * concurrently on one GPU; each solve runs exactly pcdn_solve's stages, kernels and stop rule,
- * with its bundle walker as one thread block on its problem's own stream, so solves of different
- * problems overlap on the device while each advances at its own pace. */
+ * concurrently on one GPU; each solve runs exactly pcdn_solve's stages, kernels and stop rule on
+ * its problem's own stream, so solves of different problems overlap on the device while each
+ * advances at its own pace.  A solve's bundle walker is one thread block, or several (a
+ * cooperative launch) when its bundles are large and the GPU has blocks to spare: the walker
+ * blocks of all concurrent multi-block walkers are kept within what the GPU holds resident.  Each
+ * solve's outer iterations are replayed from a CUDA graph captured at its first one. */
 
 /* One job of a batch: a problem solved along a regularisation path. */
 typedef struct {
@@ -205,6 +208,7 @@ typedef struct {
   int64_t epochs;         /* outer iterations of the path solves */
   int64_t coord_updates;  /* features visited by the path solves */
   double bytes_model;     /* algorithmic bytes of the path solves' bundle steps */
+  int64_t graph_solves;   /* path solves whose outer iterations replayed a captured CUDA graph */
 } pcdn_batch_stats;
 
 /* Defaults: max_inflight 0, threads 0, probe_eps 0.1, probe_epochs 3, default candidates. */

@@ -84,7 +84,8 @@ class pcdn_batch_opts(ctypes.Structure):
 
 class pcdn_batch_stats(ctypes.Structure):
     _fields_ = [("wall_s", ctypes.c_double), ("solves", ctypes.c_int64), ("probe_solves", ctypes.c_int64),
-                ("epochs", ctypes.c_int64), ("coord_updates", ctypes.c_int64), ("bytes_model", ctypes.c_double)]
+                ("epochs", ctypes.c_int64), ("coord_updates", ctypes.c_int64), ("bytes_model", ctypes.c_double),
+                ("graph_solves", ctypes.c_int64)]
 
 
 class pcdn_server_opts(ctypes.Structure):

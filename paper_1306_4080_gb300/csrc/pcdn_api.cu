@@ -14,6 +14,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "pcdn.h"
@@ -22,7 +23,7 @@
 #include "pcdn_task.h"
 
 namespace pcdn {
-cudaError_t launch_walk(int loss, int prec, const WalkParams& p, int grid, cudaStream_t s);
+cudaError_t launch_walk(int loss, int prec, const WalkParams& p, int grid, cudaStream_t s, bool capturing);
 cudaError_t walk_max_blocks_per_sm(int loss, int prec, int* out);
 cudaError_t walk_configure(int loss, int prec);
 }  // namespace pcdn
@@ -176,6 +177,9 @@ struct pcdn_problem {
   double* tr_alpha = nullptr;
   double* tr_Delta = nullptr;
   double* tr_dF = nullptr;
+  // outer-iteration index on the device (read by a captured outer iteration's partition)
+  int64_t* epoch_dev = nullptr;
+  bool capturing = false;  // the stream is being captured into a graph
   // stream, events
   cudaStream_t stream = nullptr;
   bool own_stream = false;
@@ -206,10 +210,43 @@ void free_all(pcdn_problem* p) {
   f(p->hist); f(p->scan_ws);
   f(p->gk); f(p->hk); f(p->dk); f(p->col_cnt); f(p->part);
   f(p->lsacc); f(p->sync); f(p->err); f(p->counters); f(p->red_part); f(p->red_out);
-  f(p->tr_q); f(p->tr_alpha); f(p->tr_Delta); f(p->tr_dF);
+  f(p->tr_q); f(p->tr_alpha); f(p->tr_Delta); f(p->tr_dF); f(p->epoch_dev);
   if (p->ev0) cudaEventDestroy(p->ev0);
   if (p->ev1) cudaEventDestroy(p->ev1);
   if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
+}
+
+// Columns [j0, j1) of a host CSC: rows in range and strictly ascending, values finite.  Returns the
+// first failing column (or j1) and its message.
+int64_t check_columns(const pcdn_csc* X, int64_t j0, int64_t j1, std::string* msg) {
+  char buf[256];
+  for (int64_t j = j0; j < j1; ++j) {
+    const int64_t a = X->col_ptr[j], b = X->col_ptr[j + 1];
+    if (b < a || a < 0 || b > X->nnz) {
+      snprintf(buf, sizeof buf, "col_ptr decreases or leaves [0, nnz] at column %lld", (long long)j);
+      *msg = buf;
+      return j;
+    }
+    for (int64_t e = a; e < b; ++e) {
+      const int32_t r = X->row_idx[e];
+      if (r < 0 || r >= X->n_samples) {
+        snprintf(buf, sizeof buf, "row index %d out of range in column %lld", r, (long long)j);
+        *msg = buf;
+        return j;
+      }
+      if (e > a && r <= X->row_idx[e - 1]) {
+        snprintf(buf, sizeof buf, "rows not strictly ascending in column %lld", (long long)j);
+        *msg = buf;
+        return j;
+      }
+      if (!std::isfinite(X->val[e])) {
+        snprintf(buf, sizeof buf, "non-finite value in column %lld", (long long)j);
+        *msg = buf;
+        return j;
+      }
+    }
+  }
+  return j1;
 }
 
 int check_host_csc(const pcdn_csc* X, const int8_t* y) {
@@ -222,17 +259,34 @@ int check_host_csc(const pcdn_csc* X, const int8_t* y) {
   if (!X->col_ptr || (X->nnz > 0 && (!X->row_idx || !X->val))) return fail(PCDN_EINVAL, "CSC arrays missing");
   if (X->col_ptr[0] != 0 || X->col_ptr[X->n_features] != X->nnz)
     return fail(PCDN_EINVAL, "col_ptr must start at 0 and end at nnz");
-  for (int64_t j = 0; j < X->n_features; ++j) {
-    const int64_t a = X->col_ptr[j], b = X->col_ptr[j + 1];
-    if (b < a) return fail(PCDN_EINVAL, "col_ptr decreases at column %lld", (long long)j);
-    for (int64_t e = a; e < b; ++e) {
-      const int32_t r = X->row_idx[e];
-      if (r < 0 || r >= X->n_samples) return fail(PCDN_EINVAL, "row index %d out of range in column %lld", r, (long long)j);
-      if (e > a && r <= X->row_idx[e - 1])
-        return fail(PCDN_EINVAL, "rows not strictly ascending in column %lld", (long long)j);
-      if (!std::isfinite(X->val[e])) return fail(PCDN_EINVAL, "non-finite value in column %lld", (long long)j);
+  // the columns in contiguous ranges of about equal nonzero count, one host thread each; the first
+  // failing column over all ranges decides the message
+  const int64_t m = X->n_features;
+  int threads = (int)std::min<int64_t>(std::max(1u, std::thread::hardware_concurrency()), 16);
+  if (X->nnz < (int64_t(1) << 20)) threads = 1;
+  std::vector<int64_t> cut(threads + 1, m);
+  cut[0] = 0;
+  for (int t = 1; t < threads; ++t) {
+    // first column whose start passes t/threads of the nonzeros (col_ptr may be malformed: clamp)
+    const int64_t target = X->nnz / threads * t;
+    int64_t lo = cut[t - 1], hi = m;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) / 2;
+      if (X->col_ptr[mid] < target) lo = mid + 1;
+      else hi = mid;
     }
+    cut[t] = std::max(lo, cut[t - 1]);
   }
+  std::vector<int64_t> bad(threads, m);
+  std::vector<std::string> msgs(threads);
+  std::vector<std::thread> pool;
+  for (int t = 1; t < threads; ++t)
+    pool.emplace_back([&, t]() { bad[t] = check_columns(X, cut[t], cut[t + 1], &msgs[t]); if (bad[t] == cut[t + 1]) bad[t] = m; });
+  bad[0] = check_columns(X, cut[0], cut[1], &msgs[0]);
+  if (bad[0] == cut[1]) bad[0] = m;
+  for (auto& th : pool) th.join();
+  for (int t = 0; t < threads; ++t)
+    if (bad[t] < m) return fail(PCDN_EINVAL, "%s", msgs[t].c_str());
   for (int64_t i = 0; i < X->n_samples; ++i)
     if (y[i] != 1 && y[i] != -1) return fail(PCDN_EINVAL, "label %d of sample %lld is not +1 or -1", (int)y[i], (long long)i);
   return PCDN_OK;
@@ -277,7 +331,7 @@ int finish_create(pcdn_problem* p) {
     uint32_t* ko = nullptr;
     int32_t* vo = nullptr;
     if (nnz > 0) {
-      if ((e = entry_columns(p->col_ptr, m, entry_col, s, &p->launches)) ||
+      if ((e = entry_columns(p->col_ptr, m, nnz, entry_col, s, &p->launches)) ||
           (e = copy_keys_u32(p->row_idx, k0, nnz, s, &p->launches)) || (e = iota_i32(v0, nnz, s, &p->launches)) ||
           (e = radix_sort_u32(k0, v0, k1, v1, nnz, key_bits, hist, ws, &ko, &vo, s, &p->launches)) ||
           (e = gather_csr(vo, entry_col, p->val, nnz, p->col_idx, p->rval, s, &p->launches))) {
@@ -345,6 +399,7 @@ int finish_create(pcdn_problem* p) {
   CUDA_TRY(palloc(p, &p->sync, 8));
   CUDA_TRY(palloc(p, &p->err, 4));
   CUDA_TRY(palloc(p, &p->counters, 8));
+  CUDA_TRY(palloc(p, &p->epoch_dev, 1));
   p->red_grid = p->sms * 4;
   CUDA_TRY(palloc(p, &p->red_part, 2 * (int64_t)p->red_grid));
   CUDA_TRY(palloc(p, &p->red_out, 4));
@@ -482,6 +537,11 @@ int pick_grid(const pcdn_problem* p, const pcdn_opts* o, int32_t P) {
   return g;
 }
 
+// An event record on the problem's stream; inside a capture it becomes a record node of the graph.
+cudaError_t record(cudaEvent_t ev, pcdn_problem* p) {
+  return cudaEventRecordWithFlags(ev, p->stream, p->capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
+}
+
 // Launch the walker over bundles [t0, t1) of the partition held in perm/items.
 int run_walk(pcdn_problem* p, const pcdn_opts* o, const int32_t* perm, int64_t npos, int32_t P, int64_t t0, int64_t t1,
              int grid, float* ms) {
@@ -544,10 +604,10 @@ int run_walk(pcdn_problem* p, const pcdn_opts* o, const int32_t* perm, int64_t n
   CUDA_TRY(gather_w(p->w, perm, npos, p->w_pos, p->stream, &p->launches));
   CUDA_TRY(cudaMemsetAsync(p->sync, 0, sizeof(uint32_t) * 8, p->stream));
   CUDA_TRY(cudaMemsetAsync(p->lsacc, 0, sizeof(double) * 3 * kPartStride * kAccPad, p->stream));
-  CUDA_TRY(cudaEventRecord(p->ev0, p->stream));
-  CUDA_TRY(launch_walk(p->loss, (int)o->prec, w, grid, p->stream));
+  CUDA_TRY(record(p->ev0, p));
+  CUDA_TRY(launch_walk(p->loss, (int)o->prec, w, grid, p->stream, p->capturing));
   ++p->launches;
-  CUDA_TRY(cudaEventRecord(p->ev1, p->stream));
+  CUDA_TRY(record(p->ev1, p));
   CUDA_TRY(scatter_w(p->w_pos, perm, npos, p->w, p->stream, &p->launches));
   if (ms) {
     CUDA_TRY(cudaEventSynchronize(p->ev1));
@@ -557,8 +617,8 @@ int run_walk(pcdn_problem* p, const pcdn_opts* o, const int32_t* perm, int64_t n
 }
 
 // The partition of outer iteration `epoch` into p->vals? -> returns the device pointer of perm.
-int make_partition(pcdn_problem* p, uint64_t seed, int64_t epoch, int32_t** perm_out) {
-  CUDA_TRY(perm_keys(seed, epoch, p->m, p->keys0, p->vals0, p->stream, &p->launches));
+int make_partition(pcdn_problem* p, uint64_t seed, int64_t epoch, int32_t** perm_out, const int64_t* epoch_dev = nullptr) {
+  CUDA_TRY(perm_keys(seed, epoch, epoch_dev, p->m, p->keys0, p->vals0, p->stream, &p->launches));
   uint64_t* ko = nullptr;
   int32_t* vo = nullptr;
   CUDA_TRY(radix_sort_u64(p->keys0, p->vals0, p->keys1, p->vals1, p->m, 64, p->hist, p->scan_ws, &ko, &vo, p->stream,
@@ -604,7 +664,55 @@ struct SolveTask {
   unsigned long long cnt[8] = {0};
   std::chrono::steady_clock::time_point t0;
   double wall_s = 0.0;
+  // walker blocks: a shared budget for multi-block walkers, the blocks wanted, the blocks this
+  // solve holds (taken at its start, returned at its end)
+  BlockBudget* budget = nullptr;
+  int want = 1;
+  int held = 0;
+  // an outer iteration captured as a CUDA graph at the solve's first outer iteration and replayed
+  // for the others (one launch instead of ~45); the partition reads the iteration index from the
+  // device, which the graph advances
+  bool graphs = true;
+  bool graph_tried = false;
+  cudaGraphExec_t exec = nullptr;
+  int64_t graph_kernels = 0;
+  bool used_graph = false;
 };
+
+void task_set_blocks(SolveTask* t, BlockBudget* budget, int want) {
+  if (!t) return;
+  t->budget = budget;
+  t->want = want < 1 ? 1 : want;
+}
+
+void task_set_graphs(SolveTask* t, bool on) {
+  if (t) t->graphs = on;
+}
+
+bool task_used_graph(SolveTask* t) { return t && t->graph_kernels > 0 && t->graph_tried && t->used_graph; }
+
+int walker_blocks_wanted(pcdn_problem* p, int32_t P) {
+  if (!p || P < 1 || p->m < 1) return 1;
+  const double nnz_b = (double)p->nnz * (double)P / (double)p->m;
+  const double b = std::ceil(nnz_b / (double)kBlockNnz);
+  return (int)std::max(1.0, std::min((double)std::min(kMaxBlocks, p->max_grid), b));
+}
+
+int device_walker_capacity(int* out) {
+  int dev = 0, sms = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  int bps = 2;
+  for (int loss = 0; loss < 2; ++loss)
+    for (int prec = 0; prec < 2; ++prec) {
+      int b = 1;
+      CUDA_TRY(walk_max_blocks_per_sm(loss, prec, &b));
+      bps = std::min(bps, b);
+    }
+  if (bps < 1) return fail(PCDN_ECUDA, "bundle walker cannot be resident on this device");
+  *out = sms * bps;
+  return PCDN_OK;
+}
 
 int task_create(SolveTask** out) {
   if (!out) return fail(PCDN_EINVAL, "out must be given");
@@ -644,15 +752,41 @@ int post(SolveTask* t, int kkt_slot, bool final_stage) {
     CUDA_TRY(cudaMemcpyAsync(t->mail->cnt, p->counters, sizeof(t->mail->cnt), cudaMemcpyDeviceToHost, p->stream));
   }
   CUDA_TRY(cudaMemcpyAsync(&t->mail->err, p->err, sizeof(int32_t), cudaMemcpyDeviceToHost, p->stream));
-  CUDA_TRY(cudaEventRecord(t->ev, p->stream));
+  CUDA_TRY(record(t->ev, p));
   return PCDN_OK;
 }
 
-// One outer iteration: partition (Eq. 8), work items, the bundle walk, refresh, KKT.
-int issue_epoch(SolveTask* t, int64_t k) {
+void release_blocks(SolveTask* t) {
+  if (t->held > 0 && t->budget) t->budget->free.fetch_add(t->held);
+  t->held = 0;
+}
+
+// Walker blocks for the solve: up to t->want from the budget when at least two are free (a
+// cooperative launch), else one (an ordinary launch).
+void take_blocks(SolveTask* t) {
+  int g = 1;
+  if (t->budget && t->want > 1) {
+    int f = t->budget->free.load();
+    while (f >= 2) {
+      const int take = std::min(f, t->want);
+      if (t->budget->free.compare_exchange_weak(f, f - take)) {
+        g = take;
+        break;
+      }
+    }
+  }
+  t->held = g > 1 ? g : 0;
+  pcdn_opts o = t->o;
+  o.grid_ctas = g;
+  t->grid = pick_grid(t->p, &o, t->P);
+}
+
+// One outer iteration: partition (Eq. 8) of iteration k (or of the index in epoch_dev, advanced at
+// the end), work items, the bundle walk, refresh, KKT, the mailbox.
+int epoch_body(SolveTask* t, int64_t k, int64_t* epoch_dev) {
   pcdn_problem* p = t->p;
   int32_t* perm = nullptr;
-  int rc = make_partition(p, t->seed, k, &perm);
+  int rc = make_partition(p, t->seed, k, &perm, epoch_dev);
   if (rc) return rc;
   CUDA_TRY(build_items(perm, p->m, p->col_ptr, p->w, p->cnt, p->item_ptr, p->items, p->scan_ws, p->stream,
                        &p->launches));
@@ -664,8 +798,54 @@ int issue_epoch(SolveTask* t, int64_t k) {
   }
   rc = do_kkt(p, 1);
   if (rc) return rc;
-  t->stage = kStageEpoch;
+  if (epoch_dev) CUDA_TRY(advance_epoch(epoch_dev, p->stream, &p->launches));
   return post(t, 1, false);
+}
+
+// Capture one outer iteration into t->exec; on any failure the task keeps issuing directly.
+void capture_epoch(SolveTask* t) {
+  pcdn_problem* p = t->p;
+  t->graph_tried = true;
+  if (cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  p->capturing = true;
+  const int64_t l0 = p->launches;
+  const int rc = epoch_body(t, 0, p->epoch_dev);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(p->stream, &g);
+  p->capturing = false;
+  const int64_t kernels = p->launches - l0;
+  p->launches = l0;
+  cudaGetLastError();
+  if (rc != PCDN_OK || e != cudaSuccess || !g) {
+    if (g) cudaGraphDestroy(g);
+    g_err.clear();
+    return;
+  }
+  cudaGraphExec_t ex = nullptr;
+  const cudaError_t e2 = cudaGraphInstantiate(&ex, g, 0);
+  cudaGraphDestroy(g);
+  if (e2 != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  t->exec = ex;
+  t->graph_kernels = kernels;
+}
+
+int issue_epoch(SolveTask* t, int64_t k) {
+  pcdn_problem* p = t->p;
+  if (t->graphs && !t->graph_tried) capture_epoch(t);
+  t->stage = kStageEpoch;
+  if (t->exec) {
+    CUDA_TRY(cudaGraphLaunch(t->exec, p->stream));
+    p->launches += t->graph_kernels;
+    t->used_graph = true;
+    return PCDN_OK;
+  }
+  return epoch_body(t, k, nullptr);
 }
 
 int issue_final(SolveTask* t) {
@@ -676,6 +856,11 @@ int issue_final(SolveTask* t) {
 }
 
 int end_task(SolveTask* t, int rc) {
+  release_blocks(t);
+  if (t->exec) {
+    cudaGraphExecDestroy(t->exec);  // freed once a launch still in flight completes
+    t->exec = nullptr;
+  }
   t->stage = kStageEnded;
   t->rc = rc;
   t->wall_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t->t0).count();
@@ -702,7 +887,13 @@ int task_start(SolveTask* t, pcdn_problem* p, int32_t P, double eps, uint64_t se
   t->eps = eps;
   t->seed = seed;
   t->nb = (p->m + P - 1) / P;
-  t->grid = pick_grid(p, &o, P);
+  t->held = 0;
+  t->graph_tried = false;
+  t->exec = nullptr;
+  t->used_graph = false;
+  t->graph_kernels = 0;
+  if (t->budget) take_blocks(t);
+  else t->grid = pick_grid(p, &o, P);
   t->kkt0 = t->kkt_rel = t->F = t->walk_ms = 0.0;
   t->epochs = 0;
   t->converged = 0;
@@ -716,6 +907,7 @@ int task_start(SolveTask* t, pcdn_problem* p, int32_t P, double eps, uint64_t se
   if (!o.warm_start) CUDA_TRY(cudaMemsetAsync(p->w, 0, sizeof(double) * p->m, p->stream));
   CUDA_TRY(cudaMemsetAsync(p->err, 0, sizeof(int), p->stream));
   CUDA_TRY(cudaMemsetAsync(p->counters, 0, sizeof(unsigned long long) * 8, p->stream));
+  CUDA_TRY(cudaMemsetAsync(p->epoch_dev, 0, sizeof(int64_t), p->stream));
   if ((rc = do_refresh(p, (int)o.prec, true, false)) || (rc = do_kkt(p, 2))) return end_task(t, rc);
   t->stage = kStageStart;
   rc = post(t, 2, false);

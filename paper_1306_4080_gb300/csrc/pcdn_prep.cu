@@ -184,7 +184,11 @@ __device__ __forceinline__ uint64_t sm64_mix(uint64_t z) {
   return z ^ (z >> 31);
 }
 
-__global__ void perm_keys_kernel(uint64_t seed, uint64_t epoch, int64_t m, uint64_t* keys, int32_t* vals) {
+// epoch_dev (may be NULL): the outer-iteration index is read from device memory instead, so that a
+// captured graph of an outer iteration draws a new partition at every replay
+__global__ void perm_keys_kernel(uint64_t seed, uint64_t epoch, const int64_t* epoch_dev, int64_t m, uint64_t* keys,
+                                 int32_t* vals) {
+  if (epoch_dev) epoch = (uint64_t)*epoch_dev;
   const uint64_t gamma = 0x9E3779B97F4A7C15ULL;
   // state of the epoch's stream: first output of the stream started at seed ^ epoch * C
   const uint64_t s_epoch = sm64_mix((seed ^ (epoch * 0xD1B54A32D192ED03ULL)) + gamma);
@@ -273,11 +277,30 @@ __global__ void scatter_w_kernel(const double* w_pos, const int32_t* perm, int64
 }
 
 // ------------------------------------------------------------------------------------ mirror
-__global__ void entry_col_kernel(const int64_t* col_ptr, int64_t m, int32_t* entry_col) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
-  for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; j < m; j += warps) {
-    for (int64_t e = col_ptr[j] + lane; e < col_ptr[j + 1]; e += 32) entry_col[e] = (int32_t)j;
+// Column of entry e: the last j with col_ptr[j] <= e (col_ptr ascending, col_ptr[m] = nnz > e).
+__device__ __forceinline__ int64_t column_of(const int64_t* col_ptr, int64_t m, int64_t e) {
+  int64_t lo = 0, hi = m;  // col_ptr[lo] <= e < col_ptr[hi]
+  while (hi - lo > 1) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (col_ptr[mid] <= e) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+constexpr int kSpan = 16;  // consecutive nonzeros per thread in the entry-parallel passes
+
+// entry_col[e] = column of entry e; a thread takes kSpan consecutive entries (one search, then a
+// walk), so a long column is spread over many threads.
+__global__ void entry_col_kernel(const int64_t* col_ptr, int64_t m, int64_t nnz, int32_t* entry_col) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t * kSpan < nnz; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e0 = t * kSpan, e1 = min(nnz, e0 + kSpan);
+    int64_t j = column_of(col_ptr, m, e0);
+    int64_t next = col_ptr[j + 1];
+    for (int64_t e = e0; e < e1; ++e) {
+      while (e >= next && j + 1 < m) next = col_ptr[++j + 1];  // j stays below m
+      entry_col[e] = (int32_t)j;
+    }
   }
 }
 
@@ -323,13 +346,25 @@ __global__ void validate_kernel(const int64_t* col_ptr, const int32_t* row_idx, 
     if (y[i] != 1 && y[i] != -1) atomicOr(flag, 4);
 }
 
-// rows strictly ascending within every column (run after the column pointers passed)
-__global__ void validate_order_kernel(const int64_t* col_ptr, const int32_t* row_idx, int64_t m, int* flag) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
-  for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; j < m; j += warps) {
-    for (int64_t e = col_ptr[j] + 1 + lane; e < col_ptr[j + 1]; e += 32)
-      if (row_idx[e] <= row_idx[e - 1]) atomicOr(flag, 8);
+// rows strictly ascending within every column (run after the column pointers passed): entry e
+// (not the first of its column) must exceed entry e - 1; kSpan consecutive entries per thread
+__global__ void validate_order_kernel(const int64_t* col_ptr, const int32_t* row_idx, int64_t m, int64_t nnz,
+                                      int* flag) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t * kSpan < nnz; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e0 = t * kSpan, e1 = min(nnz, e0 + kSpan);
+    // every index stays in range even when col_ptr itself is malformed (this check runs in the same
+    // launch sequence as the one that tests col_ptr): j in [0, m), e in [0, nnz)
+    int64_t j = column_of(col_ptr, m, e0);
+    int64_t start = col_ptr[j], next = col_ptr[j + 1];
+    bool bad = false;
+    for (int64_t e = e0; e < e1; ++e) {
+      while (e >= next && j + 1 < m) {
+        start = next;
+        next = col_ptr[++j + 1];
+      }
+      if (e > start && row_idx[e] <= row_idx[e - 1]) bad = true;
+    }
+    if (bad) atomicOr(flag, 8);
   }
 }
 
@@ -407,54 +442,66 @@ __global__ void split_w_kernel(const double* w, int64_t m, float2* w2) {
 // FP64 pipe of this part runs at a small fraction of the FP32 rate).  Each product x_ij w_j is
 // formed as x_ij hi_j exactly (error-free product by FMA) plus x_ij lo_j, summed as a double-float
 // pair; the T partial sums combine in a fixed tree.  Relative error of z about 2^-44 of sum |x_ij w_j|.
-// Every lane of a warp runs the same number of row rounds, so the shuffles are full-warp.
+// A warp sums 32 consecutive rows, 32/T at a time, keeps their sums in shared memory, then finishes
+// them one lane per row (the FP64 part: e^z, the coefficients, the loss) with every lane busy.
+// Every lane of a warp runs the same number of rounds, so the shuffles are full-warp.
 template <int LOSS, int T>
 __global__ void __launch_bounds__(kRedThreads) refresh_df_kernel(const int64_t* row_ptr, const int32_t* col_idx,
                                                                  const float* rval, const int8_t* y, const float2* w2,
                                                                  int64_t n, double* mq, void* rec, int write_state,
                                                                  double* loss_part, int* err) {
   __shared__ double wsum[kRedThreads];
-  constexpr int G = 32 / T;  // rows per warp round
-  const int gl = threadIdx.x & (T - 1);
-  const int grp = (threadIdx.x & 31) / T;
+  __shared__ float2 zs[kRedThreads / 32][32];
+  constexpr int G = 32 / T;  // rows per round
+  const int lane = threadIdx.x & 31;
+  const int gl = lane & (T - 1);
+  const int grp = lane / T;
+  float2* zw = zs[threadIdx.x >> 5];
   const int64_t warp = ((int64_t)blockIdx.x * kRedThreads + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * kRedThreads) >> 5;
   double lsum = 0.0;
-  for (int64_t r0 = warp * G; r0 < n; r0 += nwarps * G) {
-    const int64_t i = r0 + grp;
-    const bool valid = i < n;
-    const int64_t a = valid ? row_ptr[i] : 0, b = valid ? row_ptr[i + 1] : 0;
-    dfloat acc = {0.0f, 0.0f};
-    int64_t e = a + gl;
-    for (; e + 3 * T < b; e += 4 * T) {
-      int32_t c[4];
-      float v[4];
+  for (int64_t r0 = warp * 32; r0 < n; r0 += nwarps * 32) {
+#pragma unroll 1
+    for (int sub = 0; sub < T; ++sub) {
+      const int64_t i = r0 + sub * G + grp;
+      const bool valid = i < n;
+      const int64_t a = valid ? row_ptr[i] : 0, b = valid ? row_ptr[i + 1] : 0;
+      dfloat acc = {0.0f, 0.0f};
+      int64_t e = a + gl;
+      for (; e + 3 * T < b; e += 4 * T) {
+        int32_t c[4];
+        float v[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        c[u] = col_idx[e + u * T];
-        v[u] = rval[e + u * T];
+        for (int u = 0; u < 4; ++u) {
+          c[u] = col_idx[e + u * T];
+          v[u] = rval[e + u * T];
+        }
+        float2 wv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) wv[u] = w2[c[u]];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float ph = v[u] * wv[u].x;
+          const float pl = fmaf(v[u], wv[u].y, fmaf(v[u], wv[u].x, -ph));
+          acc = df_add(acc, dfloat{ph, pl});
+        }
       }
-      float2 wv[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) wv[u] = w2[c[u]];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const float ph = v[u] * wv[u].x;
-        const float pl = fmaf(v[u], wv[u].y, fmaf(v[u], wv[u].x, -ph));
+      for (; e < b; e += T) {
+        const float v = rval[e];
+        const float2 wv = w2[col_idx[e]];
+        const float ph = v * wv.x;
+        const float pl = fmaf(v, wv.y, fmaf(v, wv.x, -ph));
         acc = df_add(acc, dfloat{ph, pl});
       }
-    }
-    for (; e < b; e += T) {
-      const float v = rval[e];
-      const float2 wv = w2[col_idx[e]];
-      const float ph = v * wv.x;
-      const float pl = fmaf(v, wv.y, fmaf(v, wv.x, -ph));
-      acc = df_add(acc, dfloat{ph, pl});
-    }
 #pragma unroll
-    for (int o = T / 2; o > 0; o >>= 1) acc = df_add(acc, df_shfl_xor(acc, o));
-    if (valid && gl == 0) {
-      const double z = df_value(acc);
+      for (int o = T / 2; o > 0; o >>= 1) acc = df_add(acc, df_shfl_xor(acc, o));
+      if (gl == 0) zw[sub * G + grp] = make_float2(acc.hi, acc.lo);
+    }
+    __syncwarp();
+    const int64_t i = r0 + lane;
+    if (i < n) {
+      const float2 zz = zw[lane];
+      const double z = (double)zz.x + (double)zz.y;
       const int yi = y[i];
       if (loss_part) lsum += row_loss(LOSS, z, yi);
       if (write_state) {
@@ -469,6 +516,7 @@ __global__ void __launch_bounds__(kRedThreads) refresh_df_kernel(const int64_t* 
         ((RecT<1>*)rec)[i] = RowCoef<LOSS, 1>::make(mv, yi);
       }
     }
+    __syncwarp();
   }
   if (loss_part) {
     wsum[threadIdx.x] = lsum;
@@ -509,20 +557,22 @@ __global__ void __launch_bounds__(kRedThreads) kkt_item_kernel(const Item* items
   const RecT<PREC>* rec = (const RecT<PREC>*)recp;
   for (int64_t i = (int64_t)blockIdx.x * (kRedThreads / 32) + wid; i < n_items; i += warps) {
     const Item it = items[i];
-    double g;
     if constexpr (PREC == 0) {
       double acc = 0.0;
       for (int64_t e = it.start + lane; e < it.start + it.len; e += 32) acc = fma((double)val[e], rec[row_idx[e]].cg, acc);
-      g = warp_sum(acc);
+      const double g = warp_sum(acc);
+      if (lane == 0) gpart[i] = g;
     } else {
+      // FP32 sums (this mode's column sums), stored as float; the column kernel widens them
       float acc = 0.0f;
       for (int64_t e = it.start + lane; e < it.start + it.len; e += 32) acc = fmaf(val[e], rec[row_idx[e]].cg, acc);
-      g = warp_sum((double)acc);
+      acc = warp_sum_f(acc);
+      if (lane == 0) reinterpret_cast<float*>(gpart)[i] = acc;
     }
-    if (lane == 0) gpart[i] = g;
   }
 }
 
+template <int PREC>
 __global__ void __launch_bounds__(kRedThreads) kkt_col_kernel(const int64_t* item_ptr, const int32_t* perm, int64_t npos,
                                                               const double* gpart, const double* w, double c,
                                                               double* block_part) {
@@ -530,7 +580,8 @@ __global__ void __launch_bounds__(kRedThreads) kkt_col_kernel(const int64_t* ite
   double acc = 0.0;
   for (int64_t k = (int64_t)blockIdx.x * kRedThreads + threadIdx.x; k < npos; k += (int64_t)gridDim.x * kRedThreads) {
     double g = 0.0;
-    for (int64_t i = item_ptr[k]; i < item_ptr[k + 1]; ++i) g += gpart[i];
+    for (int64_t i = item_ptr[k]; i < item_ptr[k + 1]; ++i)
+      g += PREC == 0 ? gpart[i] : (double)reinterpret_cast<const float*>(gpart)[i];
     g *= c;
     const double wj = w[perm[k]];
     double v;
@@ -633,9 +684,17 @@ cudaError_t radix_sort_u32(uint32_t* k0, int32_t* v0, uint32_t* k1, int32_t* v1,
   return radix_sort_impl<uint32_t>(k0, v0, k1, v1, n, key_bits, hist, ws, k_out, v_out, s, launches);
 }
 
-cudaError_t perm_keys(uint64_t seed, int64_t epoch, int64_t m, uint64_t* keys, int32_t* vals, cudaStream_t s,
+__global__ void advance_epoch_kernel(int64_t* epoch_dev) { *epoch_dev += 1; }
+
+cudaError_t advance_epoch(int64_t* epoch_dev, cudaStream_t s, int64_t* launches) {
+  advance_epoch_kernel<<<1, 1, 0, s>>>(epoch_dev);
+  return post(launches);
+}
+
+cudaError_t perm_keys(uint64_t seed, int64_t epoch, const int64_t* epoch_dev, int64_t m, uint64_t* keys, int32_t* vals,
+                      cudaStream_t s,
                       int64_t* launches) {
-  perm_keys_kernel<<<grid_for(m, 256), 256, 0, s>>>(seed, (uint64_t)epoch, m, keys, vals);
+  perm_keys_kernel<<<grid_for(m, 256), 256, 0, s>>>(seed, (uint64_t)epoch, epoch_dev, m, keys, vals);
   return post(launches);
 }
 
@@ -672,8 +731,10 @@ cudaError_t scatter_w(const double* w_pos, const int32_t* perm, int64_t npos, do
   return post(launches);
 }
 
-cudaError_t entry_columns(const int64_t* col_ptr, int64_t m, int32_t* entry_col, cudaStream_t s, int64_t* launches) {
-  entry_col_kernel<<<grid_for(m * 32, 256), 256, 0, s>>>(col_ptr, m, entry_col);
+cudaError_t entry_columns(const int64_t* col_ptr, int64_t m, int64_t nnz, int32_t* entry_col, cudaStream_t s,
+                          int64_t* launches) {
+  if (nnz <= 0) return cudaSuccess;
+  entry_col_kernel<<<grid_for(cdiv(nnz, kSpan), 256), 256, 0, s>>>(col_ptr, m, nnz, entry_col);
   return post(launches);
 }
 
@@ -703,7 +764,8 @@ cudaError_t validate_device(const int64_t* col_ptr, const int32_t* row_idx, cons
   validate_kernel<<<grid_for(nnz > n ? nnz : n, 256), 256, 0, s>>>(col_ptr, row_idx, val, y, n, m, nnz, flag);
   cudaError_t e = post(launches);
   if (e != cudaSuccess) return e;
-  validate_order_kernel<<<grid_for(m * 32, 256), 256, 0, s>>>(col_ptr, row_idx, m, flag);
+  if (nnz <= 0) return cudaSuccess;
+  validate_order_kernel<<<grid_for(cdiv(nnz, kSpan), 256), 256, 0, s>>>(col_ptr, row_idx, m, nnz, flag);
   return post(launches);
 }
 
@@ -753,7 +815,8 @@ cudaError_t kkt_l1(int prec, const Item* items, int64_t n_items, const int64_t* 
   else kkt_item_kernel<1><<<grid, kRedThreads, 0, s>>>(items, n_items, row_idx, val, rec, gpart);
   cudaError_t e = post(launches);
   if (e != cudaSuccess) return e;
-  kkt_col_kernel<<<grid, kRedThreads, 0, s>>>(item_ptr, perm, npos, gpart, w, c, block_part);
+  if (prec == 0) kkt_col_kernel<0><<<grid, kRedThreads, 0, s>>>(item_ptr, perm, npos, gpart, w, c, block_part);
+  else kkt_col_kernel<1><<<grid, kRedThreads, 0, s>>>(item_ptr, perm, npos, gpart, w, c, block_part);
   e = post(launches);
   if (e != cudaSuccess) return e;
   finish_sum_kernel<<<1, kRedThreads, 0, s>>>(block_part, grid, 1.0, nullptr, 0, out);

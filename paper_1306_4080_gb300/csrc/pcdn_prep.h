@@ -25,9 +25,12 @@ cudaError_t radix_sort_u32(uint32_t* k0, int32_t* v0, uint32_t* k1, int32_t* v1,
                            int64_t* launches);
 
 // ---- partition of one outer iteration (Eq. 8) ------------------------------------------------
-// perm_keys: key_j = splitmix64 output j+1 of the stream of (seed, epoch); values j.
-cudaError_t perm_keys(uint64_t seed, int64_t epoch, int64_t m, uint64_t* keys, int32_t* vals, cudaStream_t s,
-                      int64_t* launches);
+// perm_keys: key_j = splitmix64 output j+1 of the stream of (seed, epoch); values j.  With
+// epoch_dev (device, may be NULL) the epoch is read from there when the kernel runs.
+cudaError_t perm_keys(uint64_t seed, int64_t epoch, const int64_t* epoch_dev, int64_t m, uint64_t* keys, int32_t* vals,
+                      cudaStream_t s, int64_t* launches);
+// *epoch_dev += 1 (one thread)
+cudaError_t advance_epoch(int64_t* epoch_dev, cudaStream_t s, int64_t* launches);
 
 // ---- column work items ------------------------------------------------------------------------
 // For positions [0, npos) of `perm`: item_ptr[npos+1] and items[] (chunks of <= kChunk nonzeros),
@@ -47,7 +50,8 @@ cudaError_t gather_w(const double* w, const int32_t* perm, int64_t npos, double*
 cudaError_t scatter_w(const double* w_pos, const int32_t* perm, int64_t npos, double* w, cudaStream_t s, int64_t* launches);
 
 // ---- row-major mirror -------------------------------------------------------------------------
-cudaError_t entry_columns(const int64_t* col_ptr, int64_t m, int32_t* entry_col, cudaStream_t s, int64_t* launches);
+cudaError_t entry_columns(const int64_t* col_ptr, int64_t m, int64_t nnz, int32_t* entry_col, cudaStream_t s,
+                          int64_t* launches);
 cudaError_t row_counts(const int32_t* row_idx, int64_t nnz, int64_t* counts, cudaStream_t s, int64_t* launches);
 cudaError_t iota_i32(int32_t* v, int64_t n, cudaStream_t s, int64_t* launches);
 cudaError_t copy_keys_u32(const int32_t* src, uint32_t* dst, int64_t n, cudaStream_t s, int64_t* launches);

@@ -119,10 +119,11 @@ struct BatchShared {
   int32_t probe_epochs;
   std::vector<int32_t> cand;
   std::atomic<int32_t> next{0};
-  std::atomic<int64_t> solves{0}, probes{0}, epochs{0}, coord{0};
+  std::atomic<int64_t> solves{0}, probes{0}, epochs{0}, coord{0}, graphs{0};
   std::mutex acc_mu;
   double bytes_model = 0.0;
   FirstError err;
+  BlockBudget budget;  // walker blocks for multi-block walkers
 };
 
 // Start the job's next solve on task t; returns a status (< 0: the job failed).
@@ -134,11 +135,13 @@ int start_next(BatchShared& B, JobRun& r, SolveTask* t) {
     if (B.probe_epochs > 0 && o.max_epochs > B.probe_epochs) o.max_epochs = B.probe_epochs;
     int rc = pcdn_set_C(j.prob, j.C_path[0]);
     if (rc) return rc;
+    task_set_blocks(t, &B.budget, walker_blocks_wanted(j.prob, r.cand[r.probe]));
     return task_start(t, j.prob, r.cand[r.probe], B.probe_eps, j.seed, &o, 1);
   }
   if (r.ci > 0) o.warm_start = 1;
   int rc = pcdn_set_C(j.prob, j.C_path[r.ci]);
   if (rc) return rc;
+  task_set_blocks(t, &B.budget, walker_blocks_wanted(j.prob, r.P));
   return task_start(t, j.prob, r.P, j.eps, j.seed, &o, 1);
 }
 
@@ -174,6 +177,7 @@ bool on_done(BatchShared& B, JobRun& r, SolveTask* t, int rc) {
     if (j.stats) j.stats[r.ci] = st;
     if (rr == PCDN_ENOTCONVERGED) r.status = PCDN_ENOTCONVERGED;
     B.solves.fetch_add(1);
+    if (task_used_graph(t)) B.graphs.fetch_add(1);
     B.epochs.fetch_add(st.epochs);
     B.coord.fetch_add(st.coord_updates);
     {
@@ -329,6 +333,7 @@ struct pcdn_server {
   int32_t in_flight = 0;             // admitted and not yet retired
   int64_t bytes_in_use = 0;
   bool stop = false;
+  BlockBudget blocks;                // walker blocks for multi-block walkers
   std::thread admit_thread, drive_thread;
   std::vector<std::thread> creators;
   int64_t submitted = 0, finished = 0;
@@ -461,6 +466,7 @@ void drive_loop(pcdn_server* s) {
       } else {
         pcdn_opts o = s->opts;
         o.warm_start = 0;
+        task_set_blocks(tasks[k], &s->blocks, walker_blocks_wanted(r->prob, r->P));
         rc = task_start(tasks[k], r->prob, r->P, r->eps, r->seed, &o, 1);
         r->started = true;
         progressed = true;
@@ -568,6 +574,10 @@ int pcdn_solve_batch(pcdn_batch_job* jobs, int32_t n_jobs, const pcdn_opts* opts
   for (int32_t k = 0; k < bo.n_candidates; ++k) B.cand.push_back(bo.candidates[k]);
   int inflight = bo.max_inflight > 0 ? bo.max_inflight : default_slots();
   inflight = std::min<int>(inflight, n_jobs);
+  // multi-block walkers share what the one-block walkers of the in-flight jobs leave of the GPU
+  int cap = 0;
+  if (device_walker_capacity(&cap) != PCDN_OK) return PCDN_ECUDA;
+  B.budget.free = std::max(0, cap - inflight);
   int threads = bo.threads > 0 ? bo.threads : 4;
   threads = std::max(1, std::min(threads, inflight));
   std::vector<std::thread> pool;
@@ -583,6 +593,7 @@ int pcdn_solve_batch(pcdn_batch_job* jobs, int32_t n_jobs, const pcdn_opts* opts
     out->epochs = B.epochs.load();
     out->coord_updates = B.coord.load();
     out->bytes_model = B.bytes_model;
+    out->graph_solves = B.graphs.load();
   }
   if (B.err.code < 0) {
     set_last_error(B.err.msg.c_str());
@@ -668,6 +679,12 @@ int pcdn_server_create(const pcdn_server_opts* opts, pcdn_server** out) {
   s->budget = so.hbm_budget > 0 ? so.hbm_budget : (int64_t(8) << 30);
   s->opts = so.solve;
   s->t0 = Clock::now();
+  int cap = 0;
+  if (device_walker_capacity(&cap) != PCDN_OK) {
+    delete s;
+    return PCDN_ECUDA;
+  }
+  s->blocks.free = std::max(0, cap - s->slots);
   s->admit_thread = std::thread(admission_loop, s);
   s->drive_thread = std::thread(drive_loop, s);
   for (int k = 0; k < kCreators; ++k) s->creators.emplace_back(creator_loop, s);

@@ -12,11 +12,43 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "pcdn.h"
 
 namespace pcdn {
 
 struct SolveTask;
+
+// Thread blocks that the multi-block (cooperative) walkers of concurrent solves may hold together.
+// A solve takes its blocks when it issues an outer iteration and returns them when that iteration
+// ends.  Keeping the cooperative walkers' total within what the GPU holds resident next to the
+// one-block walkers guarantees that each of them can become fully resident: what it may wait for
+// (one-block walkers, the other kernels) finishes on its own, and no two cooperative walkers can
+// each hold part of the GPU while waiting for the rest.
+struct BlockBudget {
+  std::atomic<int> free{0};
+};
+
+// Walker blocks a solve of this problem wants at bundle size P: about kBlockNnz nonzeros of a
+// bundle per block, at most kMaxBlocks; 1 for bundles that one block handles quickly.
+constexpr int64_t kBlockNnz = 4096;
+constexpr int kMaxBlocks = 64;
+int walker_blocks_wanted(pcdn_problem* p, int32_t P);
+
+// Let the task's solves take up to `want` walker blocks from `budget` (a multi-block walker when at
+// least 2 are free, else one block), held from the solve's start to its end.  budget NULL: the
+// grid passed to task_start.
+void task_set_blocks(SolveTask* t, BlockBudget* budget, int want);
+
+// Replay each solve's outer iterations from a CUDA graph captured at its first one (default on;
+// a solve whose capture fails issues its kernels directly).
+void task_set_graphs(SolveTask* t, bool on);
+// Whether the task's last solve replayed its outer iterations from a graph.
+bool task_used_graph(SolveTask* t);
+
+// Walker blocks the current device holds resident at once (the whole-GPU walker's grid).
+int device_walker_capacity(int* out);
 
 // A task with its pinned mailbox and completion event (created once, reused across solves).
 int task_create(SolveTask** out);

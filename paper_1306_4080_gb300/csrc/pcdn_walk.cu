@@ -1326,11 +1326,26 @@ cudaError_t walk_configure(int loss, int prec) {
   return cudaFuncSetAttribute(walk_fn(loss, prec), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)walk_smem(prec));
 }
 
-// Host launcher (cooperative launch: all blocks are co-resident, which the barriers need).
-cudaError_t launch_walk(int loss, int prec, const WalkParams& p, int grid, cudaStream_t s) {
+// Host launcher (cooperative launch: all blocks are co-resident, which the barriers need).  While
+// the stream is captured into a graph, the cooperative launch goes through cudaLaunchKernelEx with
+// the cooperative attribute, which graph kernel nodes carry.
+cudaError_t launch_walk(int loss, int prec, const WalkParams& p, int grid, cudaStream_t s, bool capturing) {
   void* args[] = {(void*)&p};
   const void* fn = walk_fn(loss, prec);
   const size_t smem = walk_smem(prec);
+  if (grid > 1 && capturing) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kWalkThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, fn, args);
+  }
   if (grid > 1) return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kWalkThreads), args, smem, s);
   return cudaLaunchKernel(fn, dim3(1), dim3(kWalkThreads), args, smem, s);
 }

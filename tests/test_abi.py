@@ -140,3 +140,34 @@ def test_batch_and_server_validate_on_host(pk, has_cuda):
     if not has_cuda:
         lib.pcdn_default_server_opts(ctypes.byref(so))
         assert lib.pcdn_server_create(ctypes.byref(so), ctypes.byref(h)) == pk.PCDN_ECUDA
+
+
+def test_host_validation_of_a_large_csc_reports_the_first_bad_column(pk):
+    # above 2^20 nonzeros the host check runs on several threads over column ranges; the message
+    # must still name the lowest failing column
+    rng = np.random.default_rng(0)
+    n, m, per = 4096, 20000, 64
+    cols = [np.unique(r) for r in rng.integers(0, n, size=(m, per))]  # ascending rows per column
+    col_ptr = np.zeros(m + 1, dtype=np.int64)
+    col_ptr[1:] = np.cumsum([len(c) for c in cols])
+    ri = np.concatenate(cols).astype(np.int32)
+    assert ri.shape[0] >= (1 << 20)
+    val = np.ones(ri.shape[0], dtype=np.float32)
+    y = np.ones(n, dtype=np.int8)
+    bad_late, bad_early = 17000, 9001
+    v2 = val.copy()
+    v2[col_ptr[bad_late] + 1] = np.inf
+    r2 = ri.copy()
+    a = col_ptr[bad_early]
+    r2[a], r2[a + 1] = r2[a + 1], r2[a]
+    with pytest.raises(pk.PcdnError) as ei:
+        pk.pcdn_create(col_ptr, r2, v2, y, 1.0, "logistic")
+    assert ei.value.code == pk.PCDN_EINVAL and f"column {bad_early}" in str(ei.value)
+    with pytest.raises(pk.PcdnError) as ei:
+        pk.pcdn_create(col_ptr, ri, v2, y, 1.0, "logistic")
+    assert ei.value.code == pk.PCDN_EINVAL and f"column {bad_late}" in str(ei.value)
+    cp = col_ptr.copy()
+    cp[5000] = 10**12  # a column pointer beyond nnz is caught before any entry is read
+    with pytest.raises(pk.PcdnError) as ei:
+        pk.pcdn_create(cp, ri, val, y, 1.0, "logistic")
+    assert ei.value.code == pk.PCDN_EINVAL and "column 4999" in str(ei.value)

@@ -80,6 +80,8 @@ def test_batch_path_matches_solo_and_oracle(pk, prec):
                                           [j.C_path for j, _ in items], Ps, eps=1e-3, seed=seeds, opts=opts, bopts=bo)
         assert rc == pk.PCDN_OK
         assert bs["solves"] == sum(len(j.C_path) for j, _ in items) and bs["probe_solves"] == 0
+        # every solve replayed its outer iterations from a captured CUDA graph
+        assert bs["graph_solves"] == bs["solves"]
         tol_solo = 1e-9 if prec == "fp64" else 1e-6
         for k, ((job, p), q) in enumerate(zip(items, probs)):
             r = res[k]
@@ -125,6 +127,40 @@ def test_autotune_picks_a_candidate_and_the_path_still_matches(pk):
         Pb, scores = pk.pcdn_autotune(probs[0].handle, cand, probe_eps=0.1, probe_epochs=3, seed=5, opts=opts)
         assert Pb in cand and np.all(scores[:3] > 0)
         assert scores[cand.index(Pb)] == scores[:3].min()
+    finally:
+        for q in probs:
+            q.close()
+
+
+def test_batch_multiblock_walkers(pk):
+    """A job with large bundles (svm_20k_100k at P = 1024, about 20k nonzeros per bundle) gets a
+    multi-block (cooperative) walker from the block budget, captured in its graph, next to
+    one-block jobs; its path matches the oracle's and pcdn_solve's."""
+    wl = datagen.workload("svm_20k_100k")
+    p_big = datagen.generate(wl.spec, with_csr=False)
+    small = batch(3, seed=6, scale=0.03, n_C=2, C_range=(0.5, 1.0))
+    path = [0.5, 1.0]
+    probs = [pk.Problem.from_csc(p_big.col_ptr, p_big.row_idx, p_big.val, p_big.y, path[0], wl.loss)]
+    probs += [pk.Problem.from_csc(p.col_ptr, p.row_idx, p.val, p.y, j.C_path[0], j.loss) for j, p in small]
+    try:
+        Ps = [1024] + [min(32, p.n_features) for _, p in small]
+        opts = pk.pcdn_default_opts(prec="fp64", max_epochs=400)
+        rc, res, bs = pk.pcdn_solve_batch([q.handle for q in probs], [q.n_features for q in probs],
+                                          [path] + [j.C_path for j, _ in small], Ps, eps=1e-3, seed=1, opts=opts)
+        assert rc == pk.PCDN_OK and bs["graph_solves"] == bs["solves"] == 2 * len(probs)
+        big = res[0]
+        assert all(st["walk_grid"] > 1 for st in big["stats"]), [st["walk_grid"] for st in big["stats"]]
+        w = None
+        for ci, C in enumerate(path):
+            orc = oracle.Oracle.from_problem(p_big, C, wl.loss)
+            w, so = orc.solve(1024, eps=1e-3, seed=1, w0=w, max_epochs=400)
+            Fb = big["stats"][ci]["F_final"]
+            assert abs(Fb - so["F_final"]) <= 1e-6 * abs(so["F_final"]), (ci, Fb, so["F_final"])
+        solo = solo_path(pk, probs[0].handle, probs[0].n_features, datagen.PathJob("big", wl.spec, wl.loss, path),
+                         1024, 1e-3, 1, "fp64")
+        for ci in range(len(path)):
+            Fb, Fs = big["stats"][ci]["F_final"], solo[ci][1]["F_final"]
+            assert abs(Fb - Fs) <= 1e-9 * abs(Fs), (ci, Fb, Fs)
     finally:
         for q in probs:
             q.close()

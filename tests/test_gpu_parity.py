@@ -213,6 +213,40 @@ def test_device_pointer_create_matches_host_create(pk):
         Ph.close()
 
 
+@pytest.mark.parametrize("case", ["rows_not_ascending", "row_out_of_range", "nan_value", "bad_label",
+                                  "col_ptr_decreasing"])
+def test_device_create_rejects_bad_input(pk, case):
+    """Validation on the device (pcdn_create_device), with the fault placed inside the longest
+    (Zipf head) column, which the entry-parallel order check spreads over many threads."""
+    import torch
+    wl, p = problem("svm_20k_100k")
+    cp, ri, vv, yy = p.col_ptr.copy(), p.row_idx.copy(), p.val.copy(), p.y.copy()
+    j = int(np.argmax(np.diff(cp)))
+    a = int(cp[j] + (cp[j + 1] - cp[j]) // 2)
+    if case == "rows_not_ascending":
+        ri[a], ri[a + 1] = ri[a + 1], ri[a]
+    elif case == "row_out_of_range":
+        ri[a] = p.n_samples
+    elif case == "nan_value":
+        vv[a] = np.nan
+    elif case == "bad_label":
+        yy[3] = 0
+    elif case == "col_ptr_decreasing":
+        cp[j + 1] = cp[j] - 1
+    dev = torch.device("cuda:0")
+    t = [torch.from_numpy(x).to(dev) for x in (cp, ri, vv, yy)]
+    with pytest.raises(pk.PcdnError) as ei:
+        pk.Problem.from_device(*t, wl.C, wl.loss)
+    assert ei.value.code == pk.PCDN_EINVAL
+    # the context is intact: the unmodified problem creates and solves
+    t = [torch.from_numpy(x).to(dev) for x in (p.col_ptr, p.row_idx, p.val, p.y)]
+    q = pk.Problem.from_device(*t, wl.C, wl.loss)
+    try:
+        assert q.solve(wl.P, 1e-1, 0)[2]["converged"]
+    finally:
+        q.close()
+
+
 @pytest.mark.parametrize("loss", ["logistic", "l2svm"])
 def test_p1_and_pm(pk, loss):
     # P = 1 (CDN, Algorithm 1) and P = m (one bundle per outer iteration)
