@@ -354,12 +354,16 @@ def run_serving(args, pk, pool, P_of):
             submit_lag = time.perf_counter() - t0 - float(np.sum(gaps))
             res = [srv.wait(t, 600) for t in tickets]
             lat = np.array([r[2]["t_done"] - r[2]["t_submit"] for r in res])
+            queue = np.array([r[2]["t_admit"] - r[2]["t_submit"] for r in res])
+            create = np.array([r[2]["t_start"] - r[2]["t_admit"] for r in res])
+            solve = np.array([r[2]["t_done"] - r[2]["t_start"] for r in res])
             first = min(r[2]["t_submit"] for r in res)
             last = max(r[2]["t_done"] for r in res)
             ok = sum(1 for r in res if r[0] in (pk.PCDN_OK, pk.PCDN_ENOTCONVERGED))
             out["rates"].append({"rate_per_s": rate, "requests": R, "ok": ok, "solves_per_s": R / (last - first),
                                  "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
-                                 "mean_s": float(lat.mean()),
+                                 "mean_s": float(lat.mean()), "mean_queue_s": float(queue.mean()),
+                                 "mean_create_s": float(create.mean()), "mean_solve_s": float(solve.mean()),
                                  "submit_lag_s": float(submit_lag)})
         finally:
             srv.close()

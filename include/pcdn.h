@@ -199,6 +199,7 @@ typedef struct {
   int32_t probe_epochs;   /* autotuner: outer-iteration cap of a probe solve (0 = no cap beyond opts) */
   int32_t n_candidates;   /* autotuner: bundle sizes to try (0 = powers of 4 from 16 to min(4096, n_features)) */
   const int32_t* candidates;
+  int32_t no_graphs;      /* 1: issue every outer iteration's kernels directly instead of replaying a graph */
 } pcdn_batch_opts;
 
 typedef struct {
@@ -255,6 +256,7 @@ typedef struct {
   int32_t status;       /* the solve's status (as pcdn_solve's return value) */
   double t_submit;      /* pcdn_server_submit returned */
   double t_admit;       /* admitted (slot and memory reserved; requests are admitted in arrival order) */
+  double t_start;       /* copied to the device, solve started */
   double t_done;        /* solved, w on the host */
   int64_t bytes;        /* device footprint used for admission */
   pcdn_stats stats;

@@ -79,7 +79,8 @@ class pcdn_batch_job(ctypes.Structure):
 
 class pcdn_batch_opts(ctypes.Structure):
     _fields_ = [("max_inflight", ctypes.c_int32), ("threads", ctypes.c_int32), ("probe_eps", ctypes.c_double),
-                ("probe_epochs", ctypes.c_int32), ("n_candidates", ctypes.c_int32), ("candidates", ctypes.c_void_p)]
+                ("probe_epochs", ctypes.c_int32), ("n_candidates", ctypes.c_int32), ("candidates", ctypes.c_void_p),
+                ("no_graphs", ctypes.c_int32)]
 
 
 class pcdn_batch_stats(ctypes.Structure):
@@ -94,7 +95,8 @@ class pcdn_server_opts(ctypes.Structure):
 
 class pcdn_request_info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double),
-                ("t_done", ctypes.c_double), ("bytes", ctypes.c_int64), ("stats", pcdn_stats)]
+                ("t_start", ctypes.c_double), ("t_done", ctypes.c_double), ("bytes", ctypes.c_int64),
+                ("stats", pcdn_stats)]
 
 
 _lib = None
@@ -415,7 +417,8 @@ class Server:
             raise PcdnError(rc, pcdn_last_error())
         del self._nf[ticket]
         self._keep.pop(ticket, None)
-        d = dict(status=info.status, t_submit=info.t_submit, t_admit=info.t_admit, t_done=info.t_done,
+        d = dict(status=info.status, t_submit=info.t_submit, t_admit=info.t_admit, t_start=info.t_start,
+                 t_done=info.t_done,
                  bytes=info.bytes, stats=_stats_dict(info.stats))
         return rc, w, d
 

@@ -400,7 +400,13 @@ int finish_create(pcdn_problem* p) {
   CUDA_TRY(palloc(p, &p->err, 4));
   CUDA_TRY(palloc(p, &p->counters, 8));
   CUDA_TRY(palloc(p, &p->epoch_dev, 1));
-  p->red_grid = p->sms * 4;
+  // blocks of the refresh, KKT and objective reductions: 4 per SM, fewer for a small problem (about
+  // 256 rows or work items per block), so that many small problems on one GPU do not flood it with
+  // empty blocks
+  {
+    const int64_t work = std::max<int64_t>(n, m + nnz / kChunk);
+    p->red_grid = (int)std::max<int64_t>(1, std::min<int64_t>(p->sms * 4, (work + 255) / 256));
+  }
   CUDA_TRY(palloc(p, &p->red_part, 2 * (int64_t)p->red_grid));
   CUDA_TRY(palloc(p, &p->red_out, 4));
   CUDA_TRY(cudaMemsetAsync(p->err, 0, sizeof(int) * 4, s));
@@ -1004,6 +1010,7 @@ int task_result(SolveTask* t, double* w_out, pcdn_stats* stats) {
 }
 
 int64_t problem_n_features(pcdn_problem* p) { return p ? p->m : 0; }
+int64_t problem_nnz(pcdn_problem* p) { return p ? p->nnz : 0; }
 
 int64_t problem_bytes_estimate(int64_t n, int64_t m, int64_t nnz, int32_t P) {
   if (P < 1) P = 1;

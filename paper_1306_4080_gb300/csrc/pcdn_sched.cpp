@@ -114,9 +114,11 @@ struct JobRun {
 struct BatchShared {
   pcdn_batch_job* jobs;
   int32_t n_jobs;
+  std::vector<int32_t> order;  // jobs in the order they are started: most work first
   pcdn_opts opts;
   double probe_eps;
   int32_t probe_epochs;
+  bool use_graphs = true;
   std::vector<int32_t> cand;
   std::atomic<int32_t> next{0};
   std::atomic<int64_t> solves{0}, probes{0}, epochs{0}, coord{0}, graphs{0};
@@ -201,6 +203,7 @@ void batch_worker(BatchShared& B, int cap, int device) {
   std::vector<bool> busy(cap, false);
   for (int k = 0; k < cap; ++k) {
     int rc = task_create(&tasks[k]);
+    if (!rc) task_set_graphs(tasks[k], B.use_graphs);
     if (rc) {
       B.err.note(rc);
       for (int i = 0; i < k; ++i) task_destroy(tasks[i]);
@@ -208,7 +211,7 @@ void batch_worker(BatchShared& B, int cap, int device) {
       for (;;) {
         int32_t idx = B.next.fetch_add(1);
         if (idx >= B.n_jobs) return;
-        B.jobs[idx].status = rc;
+        B.jobs[B.order[idx]].status = rc;
       }
     }
   }
@@ -231,7 +234,7 @@ void batch_worker(BatchShared& B, int cap, int device) {
       }
       JobRun& r = runs[k];
       r = JobRun();
-      r.job = &B.jobs[idx];
+      r.job = &B.jobs[B.order[idx]];
       r.job->status = PCDN_OK;
       r.m = problem_n_features(r.job->prob);
       r.P = r.job->P;
@@ -300,7 +303,7 @@ struct Request {
   double eps = 1e-3;
   uint64_t seed = 0;
   int64_t bytes = 0;
-  double t_submit = 0.0, t_admit = 0.0, t_done = 0.0;
+  double t_submit = 0.0, t_admit = 0.0, t_start = 0.0, t_done = 0.0;
   pcdn_problem* prob = nullptr;
   bool started = false;   // its solve has been started by the driver
   bool done = false;      // result (or error) available to pcdn_server_wait
@@ -469,6 +472,7 @@ void drive_loop(pcdn_server* s) {
         task_set_blocks(tasks[k], &s->blocks, walker_blocks_wanted(r->prob, r->P));
         rc = task_start(tasks[k], r->prob, r->P, r->eps, r->seed, &o, 1);
         r->started = true;
+        r->t_start = s->now();
         progressed = true;
         if (rc < 0) done = 1;
       }
@@ -571,6 +575,14 @@ int pcdn_solve_batch(pcdn_batch_job* jobs, int32_t n_jobs, const pcdn_opts* opts
   B.opts = o;
   B.probe_eps = bo.probe_eps;
   B.probe_epochs = bo.probe_epochs;
+  B.use_graphs = bo.no_graphs == 0;
+  // longest jobs first (nonzeros times path length), so that the batch's critical paths start at
+  // once and take the walker blocks they want before the short jobs fill the GPU
+  B.order.resize(n_jobs);
+  for (int32_t i = 0; i < n_jobs; ++i) B.order[i] = i;
+  std::stable_sort(B.order.begin(), B.order.end(), [&](int32_t a, int32_t b) {
+    return (double)problem_nnz(jobs[a].prob) * jobs[a].n_C > (double)problem_nnz(jobs[b].prob) * jobs[b].n_C;
+  });
   for (int32_t k = 0; k < bo.n_candidates; ++k) B.cand.push_back(bo.candidates[k]);
   int inflight = bo.max_inflight > 0 ? bo.max_inflight : default_slots();
   inflight = std::min<int>(inflight, n_jobs);
@@ -777,6 +789,7 @@ int pcdn_server_wait(pcdn_server* s, int64_t ticket, double timeout_s, double* w
     info->status = r->status;
     info->t_submit = r->t_submit;
     info->t_admit = r->t_admit;
+    info->t_start = r->t_start;
     info->t_done = r->t_done;
     info->bytes = r->bytes;
     info->stats = r->stats;

@@ -32,7 +32,7 @@ struct BlockBudget {
 
 // Walker blocks a solve of this problem wants at bundle size P: about kBlockNnz nonzeros of a
 // bundle per block, at most kMaxBlocks; 1 for bundles that one block handles quickly.
-constexpr int64_t kBlockNnz = 4096;
+constexpr int64_t kBlockNnz = 2048;
 constexpr int kMaxBlocks = 64;
 int walker_blocks_wanted(pcdn_problem* p, int32_t P);
 
@@ -72,8 +72,9 @@ int task_wait(SolveTask* t);
 // host synchronously on the problem's stream.
 int task_result(SolveTask* t, double* w_out, pcdn_stats* stats);
 
-// Number of features of a problem.
+// Number of features and of nonzeros of a problem.
 int64_t problem_n_features(pcdn_problem* p);
+int64_t problem_nnz(pcdn_problem* p);
 
 // Device bytes a problem of this shape holds once created (and at most transiently while it is
 // created), for admission under a memory budget.

@@ -80,8 +80,9 @@ def test_batch_path_matches_solo_and_oracle(pk, prec):
                                           [j.C_path for j, _ in items], Ps, eps=1e-3, seed=seeds, opts=opts, bopts=bo)
         assert rc == pk.PCDN_OK
         assert bs["solves"] == sum(len(j.C_path) for j, _ in items) and bs["probe_solves"] == 0
-        # every solve replayed its outer iterations from a captured CUDA graph
-        assert bs["graph_solves"] == bs["solves"]
+        # every solve with an outer iteration replayed them from a captured CUDA graph (a solve that
+        # starts at the optimum, e.g. w = 0 at a small C, has none)
+        assert bs["graph_solves"] == sum(st["epochs"] > 0 for r in res for st in r["stats"])
         tol_solo = 1e-9 if prec == "fp64" else 1e-6
         for k, ((job, p), q) in enumerate(zip(items, probs)):
             r = res[k]
@@ -147,7 +148,8 @@ def test_batch_multiblock_walkers(pk):
         opts = pk.pcdn_default_opts(prec="fp64", max_epochs=400)
         rc, res, bs = pk.pcdn_solve_batch([q.handle for q in probs], [q.n_features for q in probs],
                                           [path] + [j.C_path for j, _ in small], Ps, eps=1e-3, seed=1, opts=opts)
-        assert rc == pk.PCDN_OK and bs["graph_solves"] == bs["solves"] == 2 * len(probs)
+        assert rc == pk.PCDN_OK and bs["solves"] == 2 * len(probs)
+        assert bs["graph_solves"] == sum(st["epochs"] > 0 for r in res for st in r["stats"])
         big = res[0]
         assert all(st["walk_grid"] > 1 for st in big["stats"]), [st["walk_grid"] for st in big["stats"]]
         w = None
@@ -223,7 +225,8 @@ def test_server_result_is_the_same_alone_and_in_the_mix(pk, prec):
         Pt = min(P, p.n_features)
         t = srv.submit(p.col_ptr, p.row_idx, p.val, p.y, 0.5, job.loss, Pt, eps, seed)
         rc, w_alone, info_alone = srv.wait(t, timeout_s=120)
-        assert rc == pk.PCDN_OK and info_alone["t_submit"] <= info_alone["t_admit"] <= info_alone["t_done"]
+        assert rc == pk.PCDN_OK
+        assert info_alone["t_submit"] <= info_alone["t_admit"] <= info_alone["t_start"] <= info_alone["t_done"]
         tickets = []
         with StatsPoller(srv) as poll:
             for job_k, p_k in items:
