@@ -28,6 +28,9 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# one hardware work queue per concurrent solve of the batched and served legs (read when the CUDA
+# context is created, so before torch touches the GPU)
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 METRIC = "time-to-eps (KKT 1e-3) & bundle-step HBM GB/s vs peak; batched/served vs plain"
 UNIT = "s"

@@ -193,7 +193,8 @@ typedef struct {
 } pcdn_batch_job;
 
 typedef struct {
-  int32_t max_inflight;   /* jobs in flight at once (0 = 2 per SM, at most 128) */
+  int32_t max_inflight;   /* jobs in flight at once (0 = one per hardware work queue: CUDA_DEVICE_MAX_CONNECTIONS,
+                             CUDA's default 8, at most 32; set it before the process creates its CUDA context) */
   int32_t threads;        /* host threads driving them (0 = 4) */
   double probe_eps;       /* autotuner: relative KKT a probe solve aims at (0 = 0.1) */
   int32_t probe_epochs;   /* autotuner: outer-iteration cap of a probe solve (0 = no cap beyond opts) */
@@ -246,7 +247,7 @@ int pcdn_autotune(pcdn_problem* prob, const int32_t* candidates, int32_t n_candi
 typedef struct pcdn_server pcdn_server;
 
 typedef struct {
-  int32_t slots;        /* solves in flight at once (0 = 2 per SM, at most 128) */
+  int32_t slots;        /* solves in flight at once (0 = one per hardware work queue, as for batches) */
   int64_t hbm_budget;   /* device bytes the admitted requests may hold together (0 = 8 GiB) */
   pcdn_opts solve;      /* options of every solve (warm_start and grid_ctas are ignored) */
 } pcdn_server_opts;

@@ -87,6 +87,9 @@ cudaError_t library_pool(cudaMemPool_t* out) {
     if ((e = cudaMemPoolCreate(&pool, &props)) != cudaSuccess) return e;
     uint64_t keep = kPoolKeep;
     if ((e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep)) != cudaSuccess) return e;
+    // never make one problem's stream wait for another's to reuse memory freed there
+    int no = 0;
+    if ((e = cudaMemPoolSetAttribute(pool, cudaMemPoolReuseAllowInternalDependencies, &no)) != cudaSuccess) return e;
     pools[dev] = pool;
   }
   *out = pools[dev];

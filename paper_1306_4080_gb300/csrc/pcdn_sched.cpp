@@ -21,6 +21,7 @@
 #include <condition_variable>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <mutex>
@@ -70,13 +71,22 @@ struct FirstError {
   }
 };
 
+// Solves in flight by default: one per hardware work queue.  Streams beyond the queues share them,
+// and a stream waiting for its own previous kernel then holds up the others in its queue.  The
+// queue count is CUDA_DEVICE_MAX_CONNECTIONS (CUDA's default 8, at most 32), read when the CUDA
+// context is created: set it before the process touches the GPU.
 int default_slots() {
+  int conn = 8;
+  if (const char* v = std::getenv("CUDA_DEVICE_MAX_CONNECTIONS")) {
+    const int c = std::atoi(v);
+    if (c > 0) conn = std::min(c, 32);
+  }
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
     cudaGetLastError();
     sms = 64;
   }
-  return std::min(128, 2 * sms);
+  return std::min(conn, 2 * sms);
 }
 
 // Bundle sizes the autotuner tries: powers of four from 16, those not above n_features (at

@@ -4,6 +4,10 @@ import sys
 
 import pytest
 
+# concurrent solves (batch and server tests) get their own hardware work queues; read when the CUDA
+# context is created
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
