@@ -286,3 +286,44 @@ def test_server_admission_respects_the_memory_budget(pk):
         assert admits == sorted(admits)
     finally:
         srv.close()
+
+
+def test_server_error_paths(pk):
+    """A malformed request finishes with PCDN_EINVAL while the others complete; a wait that times
+    out can be repeated; an unknown ticket is an error; destroying a server with requests queued
+    and in flight leaves the GPU usable."""
+    items = batch(4, seed=7, scale=0.03, n_C=1, C_range=(1.0, 1.0))
+    wl = datagen.workload("svm_20k_100k")
+    p_big = datagen.generate(wl.spec, with_csr=False)
+    srv = pk.Server(slots=2, opts=pk.pcdn_default_opts(max_epochs=300))
+    try:
+        job, p = items[0]
+        bad_rows = p.row_idx.copy()
+        bad_rows[len(bad_rows) // 2] = p.n_samples  # row index out of range: caught at admission
+        t_bad = srv.submit(p.col_ptr, bad_rows, p.val, p.y, 1.0, job.loss, 8, 1e-3, 0)
+        t_ok = [srv.submit(q.col_ptr, q.row_idx, q.val, q.y, 1.0, j.loss, 8, 1e-3, 0) for j, q in items[1:]]
+        # a long solve (tight tolerance on a 2M-nonzero problem): its first wait times out
+        t_long = srv.submit(p_big.col_ptr, p_big.row_idx, p_big.val, p_big.y, wl.C, wl.loss, 64, 1e-9, 0)
+        rc, _, info = srv.wait(t_bad, 120)
+        assert rc == pk.PCDN_EINVAL and info["status"] == pk.PCDN_EINVAL
+        for t in t_ok:
+            assert srv.wait(t, 120)[0] == pk.PCDN_OK
+        with pytest.raises(pk.PcdnError) as ei:
+            srv.wait(t_long, 0.001)
+        assert ei.value.code == pk.PCDN_ETIMEOUT
+        rc, w, info = srv.wait(t_long, 600)
+        assert rc in (pk.PCDN_OK, pk.PCDN_ENOTCONVERGED) and np.all(np.isfinite(w))
+        lib = pk.load()
+        assert lib.pcdn_server_wait(srv.handle, 987654, 0.0, None, None) == pk.PCDN_EINVAL
+        # requests left queued and in flight when the server is destroyed
+        for _ in range(3):
+            srv.submit(p_big.col_ptr, p_big.row_idx, p_big.val, p_big.y, wl.C, wl.loss, 64, 1e-9, 0)
+        time.sleep(0.2)
+    finally:
+        srv.close()
+    # the device is intact
+    q = pk.Problem.from_csc(items[1][1].col_ptr, items[1][1].row_idx, items[1][1].val, items[1][1].y, 1.0, items[1][0].loss)
+    try:
+        assert q.solve(8, 1e-3, 0)[2]["converged"]
+    finally:
+        q.close()

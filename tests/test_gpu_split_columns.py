@@ -1,9 +1,9 @@
-"""Columns longer than one chunk (1024 nonzeros): the GPU path cuts them into chunks whose sums
+"""Columns longer than one chunk (512 nonzeros): the GPU path cuts them into chunks whose sums
 are combined across thread blocks.  Checked against the FP64 oracle through the C ABI on a matrix
-built for the purpose (seeded): one column of 300,000 nonzeros (293 chunks, combined by a whole
-block), many columns of 1,025 to 6,000 nonzeros (2 to 6 chunks, several per block), and short
-columns; with one block (more split chunks than a block lists: the one-at-a-time path) and with
-every block of the GPU (listed chunks, one warp per column).
+built for the purpose (seeded): one column of 300,000 nonzeros (586 chunks, combined by a whole
+block), many columns of 1,025 to 6,000 nonzeros (3 to 12 chunks, several per block), and short
+columns of 1 to 900 nonzeros (one or two chunks); with one block (more split chunks than a block
+lists: the one-at-a-time path) and with every block of the GPU (listed chunks, one warp per column).
 """
 import numpy as np
 import pytest
