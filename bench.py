@@ -84,14 +84,21 @@ def measured_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+def walker_source_hash():
+    """Hash of the walker's sources (the kernel and the header with its constants)."""
+    h = hashlib.sha256()
+    for f in ("pcdn_walk.cu", "pcdn_internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1306_4080_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def walker_traffic():
     """DRAM bytes per walker launch from the committed ncu summary, if it was taken on the
-    current walker source; else None."""
+    current walker sources; else None."""
     path = os.path.join(ROOT, "profiles", "walk_traffic.json")
-    src = os.path.join(ROOT, "paper_1306_4080_gb300", "csrc", "pcdn_walk.cu")
     try:
         d = json.load(open(path))
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        h = walker_source_hash()
         if d.get("walk_source_sha256_16") != h:
             return None
         return d

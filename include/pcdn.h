@@ -217,33 +217,35 @@ typedef struct {
 void pcdn_default_batch_opts(pcdn_batch_opts* bopts);
 
 /* Solve every job's path (opts, may be NULL = defaults, apply to every solve; grid_ctas is
- * ignored: each walker is one thread block).  A job with P = 0 first runs a short probe solve from
- * w = 0 at C_path[0] for each candidate bundle size (to probe_eps, at most probe_epochs outer
- * iterations) and keeps the one with the least host time per decade of KKT reduction; it then
- * needs opts->warm_start = 0.  Jobs run concurrently, up to max_inflight at a time.  Returns the
+ * ignored: each solve's walker is one thread block, or several from the shared block budget when
+ * its bundles hold more than about 2048 nonzeros).  A job with P = 0 first runs a short probe solve
+ * from w = 0 at the geometric middle of its C path for each candidate bundle size (to probe_eps, at
+ * most probe_epochs outer iterations) and keeps the one with the least walker device time per
+ * decade of KKT reduction; it then needs opts->warm_start = 0.  Jobs run concurrently, up to max_inflight at a time.  Returns the
  * first error of any job (with its message), else PCDN_ENOTCONVERGED if some solve reached
  * max_epochs, else PCDN_OK; every job's status is written.  Errors: PCDN_EINVAL (bad job, two jobs
  * on one problem), PCDN_ECUDA, and the solve errors of pcdn_solve. */
 int pcdn_solve_batch(pcdn_batch_job* jobs, int32_t n_jobs, const pcdn_opts* opts, const pcdn_batch_opts* bopts,
                      pcdn_batch_stats* out);
 
-/* The bundle-size autotuner on one problem: for each candidate P (NULL/0 = the defaults above), a
- * probe solve from w = 0 to probe_eps (at most probe_epochs outer iterations; 0 = opts' cap) with a
- * one-block walker; *P_best = the candidate with the least host time per decade of relative-KKT
- * reduction; probe_s (may be NULL, [n_candidates or the default count]) receives each score.  The
+/* The bundle-size autotuner on one problem (at its current C): for each candidate P (NULL/0 = the
+ * defaults above), a probe solve from w = 0 to probe_eps (at most probe_epochs outer iterations;
+ * 0 = opts' cap) with a one-block walker; *P_best = the candidate with the least walker device
+ * time per decade of relative-KKT reduction; probe_s (may be NULL, [n_candidates or the default count]) receives each score.  The
  * problem is left at the last probe's w. */
 int pcdn_autotune(pcdn_problem* prob, const int32_t* candidates, int32_t n_candidates, double probe_eps,
-                    int32_t probe_epochs, uint64_t seed, const pcdn_opts* opts, int32_t* P_best, double* probe_s);
+                  int32_t probe_epochs, uint64_t seed, const pcdn_opts* opts, int32_t* P_best, double* probe_s);
 
 /* ---- request server: continuous batching ------------------------------------------------------
  *
  * A server owns its host threads.  The admission thread takes submitted requests in arrival
  * order, waits until a slot is free and the request's device footprint fits the memory budget
  * (a request larger than the whole budget is admitted alone) and reserves both; creator threads
- * then copy admitted requests to the device (pcdn_create), several at once.  The driver thread starts each admitted request's solve in a free slot and
- * advances all of them concurrently, one stream each.  A finished request's w and statistics are
- * kept on the host until pcdn_server_wait collects them, and its device memory is released at
- * once, so waiting requests are admitted while others are still on the GPU. */
+ * then copy admitted requests to the device (pcdn_create), several at once.  The driver thread
+ * starts each created request's solve in a free slot and advances all of them concurrently, one
+ * stream each, with the walker blocks and CUDA graphs of the batch solver.  A finished request's w
+ * and statistics are kept on the host until pcdn_server_wait collects them, and its device memory
+ * is released at once, so waiting requests are admitted while others are still on the GPU. */
 typedef struct pcdn_server pcdn_server;
 
 typedef struct {

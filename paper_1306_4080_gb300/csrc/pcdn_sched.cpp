@@ -98,12 +98,18 @@ std::vector<int32_t> default_candidates(int64_t m) {
   return c;
 }
 
-// Autotuner score of a probe solve: host seconds per decade of relative-KKT reduction (a probe
-// that stops at its epoch cap before the probe tolerance is scored by the progress it made).
+// Autotuner score of a probe solve: device seconds of its bundle walks (CUDA events on its stream,
+// which unlike host time do not include the host's polling of many concurrent solves) per decade
+// of relative-KKT reduction; a probe that stops at its epoch cap before the probe tolerance is
+// scored by the progress it made.
 double probe_score(const pcdn_stats& st) {
   const double decades = st.kkt_rel > 0 ? -std::log10(st.kkt_rel) : 16.0;
-  return st.wall_s / std::max(decades, 1e-3);
+  return st.walk_s / std::max(decades, 1e-3);
 }
+
+// The C a job's probes run at: the geometric middle of its path (the larger C values of a path
+// cost the most outer iterations, the smallest the fewest).
+double probe_C(const pcdn_batch_job& j) { return std::sqrt(j.C_path[0] * j.C_path[j.n_C - 1]); }
 
 // ------------------------------------------------------------------------------------------ batch
 struct JobRun {
@@ -145,7 +151,7 @@ int start_next(BatchShared& B, JobRun& r, SolveTask* t) {
   if (r.probing) {
     o.warm_start = 0;
     if (B.probe_epochs > 0 && o.max_epochs > B.probe_epochs) o.max_epochs = B.probe_epochs;
-    int rc = pcdn_set_C(j.prob, j.C_path[0]);
+    int rc = pcdn_set_C(j.prob, probe_C(j));
     if (rc) return rc;
     task_set_blocks(t, &B.budget, walker_blocks_wanted(j.prob, r.cand[r.probe]));
     return task_start(t, j.prob, r.cand[r.probe], B.probe_eps, j.seed, &o, 1);
@@ -627,7 +633,7 @@ int pcdn_solve_batch(pcdn_batch_job* jobs, int32_t n_jobs, const pcdn_opts* opts
 }
 
 int pcdn_autotune(pcdn_problem* prob, const int32_t* candidates, int32_t n_candidates, double probe_eps,
-                    int32_t probe_epochs, uint64_t seed, const pcdn_opts* opts, int32_t* P_best, double* probe_s) {
+                  int32_t probe_epochs, uint64_t seed, const pcdn_opts* opts, int32_t* P_best, double* probe_s) {
   set_last_error("");
   if (!prob || !P_best) return sfail(PCDN_EINVAL, "problem and P_best must be given");
   if (n_candidates < 0 || (n_candidates > 0 && !candidates)) return sfail(PCDN_EINVAL, "bad candidates");

@@ -126,7 +126,7 @@ def test_autotune_picks_a_candidate_and_the_path_still_matches(pk):
                 assert abs(Fb - Fo) <= 1e-6 * abs(Fo), (k, ci, Fb, Fo)
         # the single-problem autotuner
         Pb, scores = pk.pcdn_autotune(probs[0].handle, cand, probe_eps=0.1, probe_epochs=3, seed=5, opts=opts)
-        assert Pb in cand and np.all(scores[:3] > 0)
+        assert Pb in cand and np.all(scores[:3] >= 0)
         assert scores[cand.index(Pb)] == scores[:3].min()
     finally:
         for q in probs:
