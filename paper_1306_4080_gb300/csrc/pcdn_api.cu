@@ -913,10 +913,13 @@ int task_start(SolveTask* t, pcdn_problem* p, int32_t P, double eps, uint64_t se
   if ((rc = ensure_bundle_scratch(p, P)) || (rc = ensure_trace(p, t->nb)) ||
       (rc = ensure_plan(p, t->nb * (t->grid + 1))) || (rc = reset_scratch(p)))
     return end_task(t, rc);
-  if (!o.warm_start) CUDA_TRY(cudaMemsetAsync(p->w, 0, sizeof(double) * p->m, p->stream));
-  CUDA_TRY(cudaMemsetAsync(p->err, 0, sizeof(int), p->stream));
-  CUDA_TRY(cudaMemsetAsync(p->counters, 0, sizeof(unsigned long long) * 8, p->stream));
-  CUDA_TRY(cudaMemsetAsync(p->epoch_dev, 0, sizeof(int64_t), p->stream));
+  // from here every failure ends the task (which returns its walker blocks)
+  cudaError_t e = cudaSuccess;
+  if ((!o.warm_start && (e = cudaMemsetAsync(p->w, 0, sizeof(double) * p->m, p->stream)) != cudaSuccess) ||
+      (e = cudaMemsetAsync(p->err, 0, sizeof(int), p->stream)) != cudaSuccess ||
+      (e = cudaMemsetAsync(p->counters, 0, sizeof(unsigned long long) * 8, p->stream)) != cudaSuccess ||
+      (e = cudaMemsetAsync(p->epoch_dev, 0, sizeof(int64_t), p->stream)) != cudaSuccess)
+    return end_task(t, fail(PCDN_ECUDA, "solve set-up: %s", cudaGetErrorString(e)));
   if ((rc = do_refresh(p, (int)o.prec, true, false)) || (rc = do_kkt(p, 2))) return end_task(t, rc);
   t->stage = kStageStart;
   rc = post(t, 2, false);
