@@ -372,6 +372,7 @@ def run_serving(args, pk, pool, P_of):
             ok = sum(1 for r in res if r[0] in (pk.PCDN_OK, pk.PCDN_ENOTCONVERGED))
             out["rates"].append({"rate_per_s": rate, "requests": R, "ok": ok, "solves_per_s": R / (last - first),
                                  "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+                                 "max_s": float(lat.max()),
                                  "mean_s": float(lat.mean()), "mean_queue_s": float(queue.mean()),
                                  "mean_create_s": float(create.mean()), "mean_solve_s": float(solve.mean()),
                                  "submit_lag_s": float(submit_lag)})

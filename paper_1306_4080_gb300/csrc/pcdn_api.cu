@@ -252,7 +252,8 @@ int64_t check_columns(const pcdn_csc* X, int64_t j0, int64_t j1, std::string* ms
   return j1;
 }
 
-int check_host_csc(const pcdn_csc* X, const int8_t* y) {
+// Sizes and pointers of a host CSC (before any entry is read).
+int check_host_shape(const pcdn_csc* X, const int8_t* y) {
   if (!X || !y) return fail(PCDN_EINVAL, "X and y must be given");
   if (X->n_samples <= 0 || X->n_features <= 0 || X->nnz < 0)
     return fail(PCDN_EINVAL, "n_samples and n_features must be positive, nnz >= 0");
@@ -262,6 +263,11 @@ int check_host_csc(const pcdn_csc* X, const int8_t* y) {
   if (!X->col_ptr || (X->nnz > 0 && (!X->row_idx || !X->val))) return fail(PCDN_EINVAL, "CSC arrays missing");
   if (X->col_ptr[0] != 0 || X->col_ptr[X->n_features] != X->nnz)
     return fail(PCDN_EINVAL, "col_ptr must start at 0 and end at nnz");
+  return PCDN_OK;
+}
+
+// Every entry of a host CSC (shape checked) and every label.
+int check_host_entries(const pcdn_csc* X, const int8_t* y) {
   // the columns in contiguous ranges of about equal nonzero count, one host thread each; the first
   // failing column over all ranges decides the message
   const int64_t m = X->n_features;
@@ -1069,11 +1075,13 @@ int pcdn_create(const pcdn_csc* X, const int8_t* y, double C, pcdn_loss loss, pc
   *out = nullptr;
   if (!(C > 0) || !std::isfinite(C)) return fail(PCDN_EINVAL, "C must be positive and finite");
   if (loss != PCDN_LOSS_LOGISTIC && loss != PCDN_LOSS_L2SVM) return fail(PCDN_EINVAL, "unknown loss");
-  int rc = check_host_csc(X, y);
+  int rc = check_host_shape(X, y);
   if (rc) return rc;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
     cudaGetLastError();
+    rc = check_host_entries(X, y);  // bad input is PCDN_EINVAL with or without a device
+    if (rc) return rc;
     return fail(PCDN_ECUDA, "no CUDA device");
   }
   pcdn_problem* p = new (std::nothrow) pcdn_problem();
@@ -1097,6 +1105,13 @@ int pcdn_create(const pcdn_csc* X, const int8_t* y, double C, pcdn_loss loss, pc
       (p->nnz > 0 && (e = cudaMemcpyAsync(p->val, X->val, sizeof(float) * p->nnz, cudaMemcpyHostToDevice, p->stream))) ||
       (e = cudaMemcpyAsync(p->y, y, p->n, cudaMemcpyHostToDevice, p->stream)))
     return bail(fail(PCDN_ECUDA, "input copy: %s", cudaGetErrorString(e)));
+  // every entry is checked on the host while the copies run (asynchronous from pinned memory);
+  // nothing reads the device copy before the check has passed
+  rc = check_host_entries(X, y);
+  if (rc) {
+    cudaStreamSynchronize(p->stream);  // the copies still read the caller's arrays
+    return bail(rc);
+  }
   rc = finish_create(p);
   if (rc) return bail(rc);
   rc = do_refresh(p, 0, true, false);

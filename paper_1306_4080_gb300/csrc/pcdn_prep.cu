@@ -774,6 +774,8 @@ cudaError_t refresh(int loss, int prec, const int64_t* row_ptr, const int32_t* c
                     double* mq, void* rec, bool write_state, double* loss_part, int grid, int* err, cudaStream_t s,
                     int64_t* launches) {
   const int ws = write_state ? 1 : 0;
+  // without per-block loss partials any block count works: twice the blocks for more loads in flight
+  if (!loss_part) grid *= 2;
   if (prec == 1 && w2_scratch) {
     float2* w2 = static_cast<float2*>(w2_scratch);
     split_w_kernel<<<grid_for(m, 256), 256, 0, s>>>(w, m, w2);
@@ -811,8 +813,9 @@ cudaError_t rec_from_mq(int loss, int prec, const double* mq, const int8_t* y, i
 cudaError_t kkt_l1(int prec, const Item* items, int64_t n_items, const int64_t* item_ptr, const int32_t* perm,
                    int64_t npos, const int32_t* row_idx, const float* val, const void* rec, const double* w, double c,
                    double* gpart, double* block_part, int grid, double* out, cudaStream_t s, int64_t* launches) {
-  if (prec == 0) kkt_item_kernel<0><<<grid, kRedThreads, 0, s>>>(items, n_items, row_idx, val, rec, gpart);
-  else kkt_item_kernel<1><<<grid, kRedThreads, 0, s>>>(items, n_items, row_idx, val, rec, gpart);
+  // the item pass writes one sum per item, no block partials: twice the blocks for more loads in flight
+  if (prec == 0) kkt_item_kernel<0><<<2 * grid, kRedThreads, 0, s>>>(items, n_items, row_idx, val, rec, gpart);
+  else kkt_item_kernel<1><<<2 * grid, kRedThreads, 0, s>>>(items, n_items, row_idx, val, rec, gpart);
   cudaError_t e = post(launches);
   if (e != cudaSuccess) return e;
   if (prec == 0) kkt_col_kernel<0><<<grid, kRedThreads, 0, s>>>(item_ptr, perm, npos, gpart, w, c, block_part);
