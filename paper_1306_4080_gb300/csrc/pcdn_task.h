@@ -1,12 +1,12 @@
 // Non-blocking solve: the outer loop of Algorithm 3 (the same stages and stop rule as pcdn_solve)
 // as a state machine that issues one stage at a time on the problem's own stream and never waits
-// on the host.  The batch solver and the request server (pcdn_sched.cu) drive many of these at
+// on the host.  The batch solver and the request server (pcdn_sched.cpp) drive many of these at
 // once, one stream each, so independent solves overlap on the device.
 //
 // Stages: [refresh + KKT at the start point] -> ([partition, items, walk, refresh, KKT] per outer
-// iteration) -> [objective, counters].  Each stage ends by copying its scalars (KKT norm,
-// objective, error flags, counters) into a pinned host mailbox and recording an event;
-// task_poll() consumes a finished stage and issues the next.
+// iteration, replayed from a CUDA graph captured at the first one) -> [objective, counters].  Each
+// stage ends by copying its scalars (KKT norm, objective, error flags, counters) into a pinned host
+// mailbox and recording an event; task_poll() consumes a finished stage and issues the next.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -21,8 +21,7 @@ namespace pcdn {
 struct SolveTask;
 
 // Thread blocks that the multi-block (cooperative) walkers of concurrent solves may hold together.
-// A solve takes its blocks when it issues an outer iteration and returns them when that iteration
-// ends.  Keeping the cooperative walkers' total within what the GPU holds resident next to the
+// A solve takes its blocks when it starts and returns them when it ends.  Keeping the cooperative walkers' total within what the GPU holds resident next to the
 // one-block walkers guarantees that each of them can become fully resident: what it may wait for
 // (one-block walkers, the other kernels) finishes on its own, and no two cooperative walkers can
 // each hold part of the GPU while waiting for the rest.
