@@ -401,6 +401,30 @@ def run_serving(args, pk, pool, P_of):
     return out
 
 
+def init_replicas():
+    """One process per GPU under torchrun: each rank solves its own replica of the workload (no
+    collective on the data path).  Returns the process group module, or None for one process.
+    NCCL with a GPU, gloo without (the host-side logic is tested that way)."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world <= 1:
+        return None
+    import torch
+    import torch.distributed as dist
+    if not dist.is_initialized():
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return dist
+
+
+def slowest_rank_ms(ms, dist, device=None):
+    """The largest per-rank time (the job's time: every rank's replica must finish)."""
+    if dist is None:
+        return float(ms)
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -411,10 +435,7 @@ def run_ours(args):
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
+    dist = init_replicas()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     pk.load()
@@ -456,9 +477,7 @@ def run_ours(args):
             torch.cuda.synchronize()
         ms = ev0.elapsed_time(ev1) / steps
         if dist:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+            ms = slowest_rank_ms(ms, dist, dev)
             dist.barrier()
         return ms, sts, clk.summary()
 

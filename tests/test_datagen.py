@@ -41,3 +41,25 @@ def test_deterministic():
     a, b = datagen.generate(s), datagen.generate(s)
     for f in ("col_ptr", "row_idx", "val", "y"):
         np.testing.assert_array_equal(getattr(a, f), getattr(b, f))
+
+
+def test_batch_jobs_follow_their_recipe():
+    jobs = datagen.batch_jobs(64)
+    again = datagen.batch_jobs(64)
+    assert [j.spec for j in jobs] == [j.spec for j in again]  # seeded
+    assert len(jobs) == 64 and len({j.spec.seed for j in jobs}) == 64
+    for k, j in enumerate(jobs):
+        assert 1000 <= j.spec.n_samples <= 50000 and 5000 <= j.spec.n_features <= 200000
+        dens = j.spec.row_mean / j.spec.n_features
+        assert 1e-3 - 1e-9 <= dens <= 1e-2 + 1e-9
+        assert j.loss == ("logistic" if k % 2 == 0 else "l2svm")
+        assert len(j.C_path) == 16 and j.C_path[0] == pytest.approx(1e-2) and j.C_path[-1] == pytest.approx(10.0)
+        assert all(a < b for a, b in zip(j.C_path, j.C_path[1:]))
+    # a generated problem has about its expected number of nonzeros (Poisson row lengths, also for
+    # means above 500, drawn as sums of pieces)
+    big = max(jobs, key=lambda j: j.spec.row_mean)
+    assert big.spec.row_mean > 500
+    small = datagen.Spec(400, big.spec.n_features, "zipf", row_mean=big.spec.row_mean, zipf_s=1.1, values="tfidf",
+                         wstar_nnz=10, flip_frac=0.03, seed=3)
+    p = datagen.generate(small, with_csr=False)
+    assert p.nnz == pytest.approx(400 * big.spec.row_mean, rel=0.02)

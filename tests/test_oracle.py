@@ -425,3 +425,27 @@ def test_objective_is_the_definition():
         for _ in range(5):
             w = rand_w(p.n_features, rng, scale=2)
             assert o.objective(w) == pytest.approx(D.F(X, y, w, 0.3, loss), rel=1e-12)
+
+
+@pytest.mark.parametrize("loss,P", [("logistic", 4), ("l2svm", 3)])
+def test_warm_started_path_reaches_each_optimum(loss, P):
+    """A regularisation path (reading 14): each C solved from the previous C's solution, with the
+    relative KKT measured against the start point.  Every step ends at that C's optimum (FISTA,
+    Beck and Teboulle), and a warm start at the optimum itself needs no outer iteration."""
+    p, X, y = tiny(loss, n=30, m=12, seed=23, density=0.45)
+    w = None
+    for c in (0.05, 0.3, 1.5, 6.0):
+        o = oracle.Oracle.from_problem(p, c, loss)
+        w, st = o.solve(P, eps=1e-9, seed=4, max_epochs=20000, w0=w)
+        assert st["converged"]
+        Ff = D.F(X, y, D.fista(X, y, c, loss), c, loss)
+        assert st["F_final"] == pytest.approx(Ff, rel=1e-8)
+        g = np.array([D.fd_grad(X, y, w, c, loss, j) for j in range(p.n_features)])
+        assert np.abs(D.min_norm_subgradient(g, w)).sum() <= 1e-5
+    # w = 0 is optimal when every |g_j(0)| <= 1: the start point's KKT is 0 and the solve ends at once
+    c0 = 1e-3
+    o = oracle.Oracle.from_problem(p, c0, loss)
+    g0 = np.array([D.fd_grad(X, y, np.zeros(p.n_features), c0, loss, j) for j in range(p.n_features)])
+    assert np.abs(g0).max() <= 1.0
+    w0, st = o.solve(P, eps=1e-3, seed=4, w0=np.zeros(p.n_features))
+    assert st["converged"] and st["epochs"] == 0 and st["kkt0"] == 0.0 and not np.any(w0)
