@@ -301,6 +301,45 @@ int check_host_entries(const pcdn_csc* X, const int8_t* y) {
   return PCDN_OK;
 }
 
+// The row mirror by a stable LSD radix sort of all entries by row (any row lengths); row_ptr is
+// already set.
+int mirror_by_sort(pcdn_problem* p) {
+  cudaStream_t s = p->stream;
+  const int64_t n = p->n, m = p->m, nnz = p->nnz;
+  int32_t* entry_col = nullptr;
+  uint32_t *k0 = nullptr, *k1 = nullptr;
+  int32_t *v0 = nullptr, *v1 = nullptr;
+  int64_t *hist = nullptr, *ws = nullptr;
+  const int64_t hn = radix_hist_elems(nnz);
+  cudaError_t e = cudaSuccess;
+  auto cleanup = [&]() {
+    dfree(entry_col, s); dfree(k0, s); dfree(k1, s); dfree(v0, s); dfree(v1, s);
+    dfree(hist, s); dfree(ws, s);
+  };
+  if ((e = dalloc(&entry_col, nnz, s)) || (e = dalloc(&k0, nnz, s)) || (e = dalloc(&k1, nnz, s)) ||
+      (e = dalloc(&v0, nnz, s)) || (e = dalloc(&v1, nnz, s)) || (e = dalloc(&hist, hn, s)) ||
+      (e = dalloc(&ws, scan_workspace_elems(hn > n + 1 ? hn : n + 1), s))) {
+    cleanup();
+    return fail(e == cudaErrorMemoryAllocation ? PCDN_ENOMEM : PCDN_ECUDA, "mirror workspace: %s", cudaGetErrorString(e));
+  }
+  int key_bits = 1;
+  while ((int64_t(1) << key_bits) < n) ++key_bits;
+  uint32_t* ko = nullptr;
+  int32_t* vo = nullptr;
+  if (nnz > 0) {
+    if ((e = entry_columns(p->col_ptr, m, nnz, entry_col, s, &p->launches)) ||
+        (e = copy_keys_u32(p->row_idx, k0, nnz, s, &p->launches)) || (e = iota_i32(v0, nnz, s, &p->launches)) ||
+        (e = radix_sort_u32(k0, v0, k1, v1, nnz, key_bits, hist, ws, &ko, &vo, s, &p->launches)) ||
+        (e = gather_csr(vo, entry_col, p->val, nnz, p->col_idx, p->rval, s, &p->launches)) ||
+        (e = cudaStreamSynchronize(s))) {
+      cleanup();
+      return fail(PCDN_ECUDA, "mirror build: %s", cudaGetErrorString(e));
+    }
+  }
+  cleanup();
+  return PCDN_OK;
+}
+
 // Everything after X and y are on the device: mirror, state, workspaces.
 int finish_create(pcdn_problem* p) {
   cudaStream_t s = p->stream;
@@ -314,47 +353,44 @@ int finish_create(pcdn_problem* p) {
     CUDA_TRY(cudaMemcpyAsync(p->ylab, p->y, n, cudaMemcpyDeviceToDevice, s));
   }
 
-  // ---- row-major mirror: stable sort of the CSC entries by row
+  // ---- row-major mirror: the CSC entries in row order, columns ascending within each row (the order
+  // of the FP64 refresh's sums).  Rows of at most kRowSortCap entries: scatter by row through atomic
+  // cursors, then sort each row by column.  Longer rows: a stable radix sort of all entries by row.
   CUDA_TRY(palloc(p, &p->row_ptr, n + 1));
   CUDA_TRY(palloc(p, &p->col_idx, nnz));
   CUDA_TRY(palloc(p, &p->rval, nnz));
   {
-    int32_t* entry_col = nullptr;
-    uint32_t *k0 = nullptr, *k1 = nullptr;
-    int32_t *v0 = nullptr, *v1 = nullptr;
-    int64_t *hist = nullptr, *ws = nullptr, *counts = nullptr;
-    const int64_t hn = radix_hist_elems(nnz);
+    int64_t *counts = nullptr, *ws = nullptr;
+    unsigned long long* mx = nullptr;
     cudaError_t e = cudaSuccess;
-    auto cleanup = [&]() {
-      dfree(entry_col, s); dfree(k0, s); dfree(k1, s); dfree(v0, s); dfree(v1, s);
-      dfree(hist, s); dfree(ws, s); dfree(counts, s);
-    };
-    if ((e = dalloc(&entry_col, nnz, s)) || (e = dalloc(&k0, nnz, s)) || (e = dalloc(&k1, nnz, s)) ||
-        (e = dalloc(&v0, nnz, s)) || (e = dalloc(&v1, nnz, s)) || (e = dalloc(&hist, hn, s)) ||
-        (e = dalloc(&ws, scan_workspace_elems(hn > n + 1 ? hn : n + 1), s)) || (e = dalloc(&counts, n + 1, s))) {
+    auto cleanup = [&]() { dfree(counts, s); dfree(ws, s); dfree(mx, s); };
+    if ((e = dalloc(&counts, n + 1, s)) || (e = dalloc(&ws, scan_workspace_elems(n + 1), s)) || (e = dalloc(&mx, 1, s))) {
       cleanup();
       return fail(e == cudaErrorMemoryAllocation ? PCDN_ENOMEM : PCDN_ECUDA, "mirror workspace: %s", cudaGetErrorString(e));
     }
-    int key_bits = 1;
-    while ((int64_t(1) << key_bits) < n) ++key_bits;
-    uint32_t* ko = nullptr;
-    int32_t* vo = nullptr;
-    if (nnz > 0) {
-      if ((e = entry_columns(p->col_ptr, m, nnz, entry_col, s, &p->launches)) ||
-          (e = copy_keys_u32(p->row_idx, k0, nnz, s, &p->launches)) || (e = iota_i32(v0, nnz, s, &p->launches)) ||
-          (e = radix_sort_u32(k0, v0, k1, v1, nnz, key_bits, hist, ws, &ko, &vo, s, &p->launches)) ||
-          (e = gather_csr(vo, entry_col, p->val, nnz, p->col_idx, p->rval, s, &p->launches))) {
-        cleanup();
-        return fail(PCDN_ECUDA, "mirror build: %s", cudaGetErrorString(e));
-      }
-    }
+    unsigned long long longest = 0;
     if ((e = cudaMemsetAsync(counts, 0, sizeof(int64_t) * (n + 1), s)) ||
         (nnz > 0 && (e = row_counts(p->row_idx, nnz, counts, s, &p->launches))) ||
-        (e = scan_exclusive(counts, p->row_ptr, n + 1, ws, s, &p->launches)) || (e = cudaStreamSynchronize(s))) {
+        (e = scan_exclusive(counts, p->row_ptr, n + 1, ws, s, &p->launches)) ||
+        (e = max_count(counts, n, mx, s, &p->launches)) ||
+        (e = cudaMemcpyAsync(&longest, mx, sizeof(longest), cudaMemcpyDeviceToHost, s)) || (e = cudaStreamSynchronize(s))) {
       cleanup();
       return fail(PCDN_ECUDA, "mirror row pointers: %s", cudaGetErrorString(e));
     }
-    cleanup();
+    if (longest <= (unsigned long long)kRowSortCap) {
+      // the counts are no longer needed: they become the per-row cursors
+      if ((e = mirror_by_rows(p->col_ptr, m, p->row_idx, p->val, nnz, p->row_ptr, n,
+                              reinterpret_cast<unsigned long long*>(counts), p->col_idx, p->rval, s, &p->launches)) ||
+          (e = cudaStreamSynchronize(s))) {
+        cleanup();
+        return fail(PCDN_ECUDA, "mirror build: %s", cudaGetErrorString(e));
+      }
+      cleanup();
+    } else {
+      cleanup();
+      int rc = mirror_by_sort(p);
+      if (rc) return rc;
+    }
   }
 
   // ---- state

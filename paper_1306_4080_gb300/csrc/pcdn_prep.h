@@ -53,6 +53,15 @@ cudaError_t scatter_w(const double* w_pos, const int32_t* perm, int64_t npos, do
 cudaError_t entry_columns(const int64_t* col_ptr, int64_t m, int64_t nnz, int32_t* entry_col, cudaStream_t s,
                           int64_t* launches);
 cudaError_t row_counts(const int32_t* row_idx, int64_t nnz, int64_t* counts, cudaStream_t s, int64_t* launches);
+// *out = max of counts[0..n) (device).
+cudaError_t max_count(const int64_t* counts, int64_t n, unsigned long long* out, cudaStream_t s, int64_t* launches);
+// Row mirror without a sort of all entries: each entry scattered to its row through an atomic
+// cursor (cursor: n words of scratch), then every row sorted by column; rows of at most
+// kRowSortCap entries.  The same arrays as the stable sort by row.  Inputs must be valid.
+constexpr int kRowSortCap = 1024;
+cudaError_t mirror_by_rows(const int64_t* col_ptr, int64_t m, const int32_t* row_idx, const float* val, int64_t nnz,
+                           const int64_t* row_ptr, int64_t n, unsigned long long* cursor, int32_t* col_idx, float* rval,
+                           cudaStream_t s, int64_t* launches);
 cudaError_t iota_i32(int32_t* v, int64_t n, cudaStream_t s, int64_t* launches);
 cudaError_t copy_keys_u32(const int32_t* src, uint32_t* dst, int64_t n, cudaStream_t s, int64_t* launches);
 cudaError_t gather_csr(const int32_t* order, const int32_t* entry_col, const float* val, int64_t nnz,

@@ -194,6 +194,39 @@ def test_mixed_mode_refresh(pk, name):
         P.close()
 
 
+@pytest.mark.parametrize("long_row", [False, True])
+def test_row_mirror_paths(pk, long_row):
+    """z = Xw runs on a row-major copy of X built at creation: by a scatter into rows and a sort of
+    each row when every row has at most 1024 entries, else by a stable sort of all entries by row.
+    Both give each row's entries in column order, the oracle's summation order: the FP64 objective
+    (refresh) matches the oracle to 1e-13 and an FP64 solve follows the oracle's trajectory."""
+    rng = np.random.default_rng(9)
+    n, m = 3000, 4000
+    cols = [np.sort(rng.choice(n, size=int(k), replace=False)) for k in rng.integers(1, 12, m)]
+    if long_row:  # row 7 present in 1,500 columns
+        for j in rng.choice(m, size=1500, replace=False):
+            cols[j] = np.unique(np.append(cols[j], 7))
+    col_ptr = np.zeros(m + 1, dtype=np.int64)
+    col_ptr[1:] = np.cumsum([len(c) for c in cols])
+    row_idx = np.concatenate(cols).astype(np.int32)
+    val = (np.abs(rng.standard_normal(len(row_idx))) / 3).astype(np.float32)
+    y = np.where(rng.random(n) < 0.5, 1, -1).astype(np.int8)
+    assert (np.bincount(row_idx, minlength=n).max() > 1024) == long_row
+    orc = oracle.Oracle(col_ptr, row_idx, val, y, 1.0, "logistic")
+    P = pk.Problem.from_csc(col_ptr, row_idx, val, y, 1.0, "logistic")
+    try:
+        for _ in range(3):
+            w = rng.normal(0, 1.0, m) * (rng.random(m) < 0.2)
+            P.set_w(w)
+            assert P.objective() == pytest.approx(orc.objective(w), rel=1e-13)
+        _, w1, st, _ = P.solve(64, 1e-3, 0, pk.pcdn_default_opts(max_epochs=300))
+        _, so = orc.solve(64, eps=1e-3, seed=0, max_epochs=300)
+        assert st["epochs"] == so["epochs"]
+        assert st["F_final"] == pytest.approx(so["F_final"], rel=1e-9)
+    finally:
+        P.close()
+
+
 def test_device_pointer_create_matches_host_create(pk):
     import torch
     wl, p = problem("svm_20k_100k")
