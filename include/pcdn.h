@@ -71,6 +71,10 @@ typedef struct {
   int32_t grid_ctas;  /* thread blocks of the bundle walker; 0 = one group covering the whole GPU */
   int32_t refresh;    /* 1 (default): recompute the maintained quantities from z = Xw after each outer iteration */
   uint32_t spin_limit;/* iterations a device-side wait may spin before PCDN_ETIMEOUT (0 = default) */
+  int64_t epoch0;     /* index of the first outer iteration (its partition, Eq. 8, is drawn with this index; default 0) */
+  double kkt_ref;     /* > 0: relative KKT measured against this ||v||_1 instead of the start point's (default 0).
+                         A solve stopped after k outer iterations resumes exactly with warm_start = 1 from its w,
+                         epoch0 = k and kkt_ref = its stats.kkt0 */
 } pcdn_opts;
 
 /* Per-solve statistics (written by pcdn_solve). */

@@ -53,7 +53,8 @@ class pcdn_opts(ctypes.Structure):
     _fields_ = [("sigma", ctypes.c_double), ("beta", ctypes.c_double), ("gamma", ctypes.c_double),
                 ("nu", ctypes.c_double), ("q_max", ctypes.c_int32), ("ls_batch", ctypes.c_int32),
                 ("max_epochs", ctypes.c_int64), ("prec", ctypes.c_int), ("warm_start", ctypes.c_int32),
-                ("grid_ctas", ctypes.c_int32), ("refresh", ctypes.c_int32), ("spin_limit", ctypes.c_uint32)]
+                ("grid_ctas", ctypes.c_int32), ("refresh", ctypes.c_int32), ("spin_limit", ctypes.c_uint32),
+                ("epoch0", ctypes.c_int64), ("kkt_ref", ctypes.c_double)]
 
 
 class pcdn_stats(ctypes.Structure):

@@ -17,6 +17,8 @@
 #include <thread>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "pcdn.h"
 #include "pcdn_internal.cuh"
 #include "pcdn_prep.h"
@@ -33,6 +35,15 @@ using namespace pcdn;
 namespace {
 
 thread_local std::string g_err;
+
+// An NVTX range for the lifetime of a scope (host-side phases in profiler timelines; free without a
+// profiler attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 }  // namespace
 
@@ -569,6 +580,8 @@ int check_opts(const pcdn_opts* o) {
   if (o->ls_batch < 0 || o->ls_batch > kMaxK) return fail(PCDN_EINVAL, "ls_batch must be in [0, %d]", kMaxK);
   if (o->max_epochs < 0) return fail(PCDN_EINVAL, "max_epochs must be >= 0");
   if (o->prec != PCDN_PREC_FP64 && o->prec != PCDN_PREC_MIXED) return fail(PCDN_EINVAL, "unknown precision");
+  if (o->epoch0 < 0) return fail(PCDN_EINVAL, "epoch0 must be >= 0");
+  if (!(o->kkt_ref >= 0) || !std::isfinite(o->kkt_ref)) return fail(PCDN_EINVAL, "kkt_ref must be >= 0 and finite");
   return PCDN_OK;
 }
 
@@ -707,7 +720,7 @@ struct SolveTask {
   int64_t nb = 0;
   int stage = kStageNone;
   int rc = PCDN_OK;
-  double kkt0 = 0.0, kkt_rel = 0.0, F = 0.0;
+  double kkt0 = 0.0, kref = 0.0, kkt_rel = 0.0, F = 0.0;
   int64_t epochs = 0;
   int converged = 0;
   double walk_ms = 0.0;
@@ -863,7 +876,7 @@ void capture_epoch(SolveTask* t) {
   }
   p->capturing = true;
   const int64_t l0 = p->launches;
-  const int rc = epoch_body(t, 0, p->epoch_dev);
+  const int rc = epoch_body(t, t->o.epoch0, p->epoch_dev);
   cudaGraph_t g = nullptr;
   const cudaError_t e = cudaStreamEndCapture(p->stream, &g);
   p->capturing = false;
@@ -887,6 +900,7 @@ void capture_epoch(SolveTask* t) {
 }
 
 int issue_epoch(SolveTask* t, int64_t k) {
+  NvtxRange range("issue outer iteration");
   pcdn_problem* p = t->p;
   if (t->graphs && !t->graph_tried) capture_epoch(t);
   t->stage = kStageEpoch;
@@ -896,7 +910,7 @@ int issue_epoch(SolveTask* t, int64_t k) {
     t->used_graph = true;
     return PCDN_OK;
   }
-  return epoch_body(t, k, nullptr);
+  return epoch_body(t, t->o.epoch0 + k, nullptr);
 }
 
 int issue_final(SolveTask* t) {
@@ -991,8 +1005,9 @@ int task_poll(SolveTask* t, int* done) {
   switch (t->stage) {
     case kStageStart:
       t->kkt0 = t->mail->kkt;
-      t->kkt_rel = t->kkt0 > 0 ? 1.0 : 0.0;
-      t->converged = t->kkt0 == 0.0;
+      t->kref = t->o.kkt_ref > 0 ? t->o.kkt_ref : t->kkt0;
+      t->kkt_rel = t->kkt0 > 0 ? t->kkt0 / t->kref : 0.0;
+      t->converged = t->kkt0 == 0.0 || (t->o.kkt_ref > 0 && t->kkt_rel <= t->eps);
       rc = (!t->converged && t->o.max_epochs > 0) ? issue_epoch(t, 0) : issue_final(t);
       break;
     case kStageEpoch: {
@@ -1000,7 +1015,7 @@ int task_poll(SolveTask* t, int* done) {
       if (cudaEventElapsedTime(&ms, t->p->ev0, t->p->ev1) == cudaSuccess) t->walk_ms += ms;
       cudaGetLastError();
       t->epochs += 1;
-      t->kkt_rel = t->kkt0 > 0 ? t->mail->kkt / t->kkt0 : 0.0;
+      t->kkt_rel = t->kref > 0 ? t->mail->kkt / t->kref : 0.0;
       if (t->kkt_rel <= t->eps) t->converged = 1;
       rc = (t->converged || t->epochs >= t->o.max_epochs) ? issue_final(t) : issue_epoch(t, t->epochs);
       break;
@@ -1107,6 +1122,7 @@ const char* pcdn_last_error(void) { return g_err.c_str(); }
 
 int pcdn_create(const pcdn_csc* X, const int8_t* y, double C, pcdn_loss loss, pcdn_problem** out) {
   g_err.clear();
+  NvtxRange range("pcdn_create");
   if (!out) return fail(PCDN_EINVAL, "out must be given");
   *out = nullptr;
   if (!(C > 0) || !std::isfinite(C)) return fail(PCDN_EINVAL, "C must be positive and finite");
@@ -1159,6 +1175,7 @@ int pcdn_create(const pcdn_csc* X, const int8_t* y, double C, pcdn_loss loss, pc
 
 int pcdn_create_device(const pcdn_csc* X, const int8_t* y, double C, pcdn_loss loss, void* stream, pcdn_problem** out) {
   g_err.clear();
+  NvtxRange range("pcdn_create_device");
   if (!out) return fail(PCDN_EINVAL, "out must be given");
   *out = nullptr;
   if (!X || !y) return fail(PCDN_EINVAL, "X and y must be given");
@@ -1284,6 +1301,7 @@ int pcdn_memory(pcdn_problem* p, int64_t* bytes) {
 int pcdn_bundle_step(pcdn_problem* p, const double* w_in, const int32_t* bundle, int32_t P, const pcdn_opts* opts,
                      double* g, double* h, double* d, double* Delta, int32_t* q, double* alpha, double* dF) {
   g_err.clear();
+  NvtxRange range("pcdn_bundle_step");
   if (!p || !bundle) return fail(PCDN_EINVAL, "problem and bundle must be given");
   if (P < 1 || P > p->m) return fail(PCDN_EINVAL, "P must be in [1, n_features]");
   pcdn_opts o;
@@ -1347,6 +1365,7 @@ int pcdn_bundle_step(pcdn_problem* p, const double* w_in, const int32_t* bundle,
 int pcdn_solve(pcdn_problem* p, int32_t P, double eps, uint64_t seed, const pcdn_opts* opts, double* w_out,
                pcdn_stats* stats, pcdn_trace* trace) {
   g_err.clear();
+  NvtxRange range("pcdn_solve");
   const auto t_start = std::chrono::steady_clock::now();
   if (!p) return fail(PCDN_EINVAL, "problem must be given");
   if (P < 1 || P > p->m) return fail(PCDN_EINVAL, "P must be in [1, n_features]");
@@ -1378,15 +1397,18 @@ int pcdn_solve(pcdn_problem* p, int32_t P, double eps, uint64_t seed, const pcdn
   rc = device_status(p);
   if (rc) return rc;
   const int grid = pick_grid(p, &o, P);
-  double kkt_rel = kkt0 > 0 ? 1.0 : 0.0;
-  int converged = kkt0 == 0.0;
+  // the relative KKT's reference: the start point's, or the caller's (a resumed solve)
+  const double kref = o.kkt_ref > 0 ? o.kkt_ref : kkt0;
+  double kkt_rel = kkt0 > 0 ? kkt0 / kref : 0.0;
+  int converged = kkt0 == 0.0 || (o.kkt_ref > 0 && kkt_rel <= eps);
   int64_t epochs = 0;
   double walk_ms = 0.0;
   std::vector<int32_t> hq;
   std::vector<double> ha, hD, hF;
   for (int64_t k = 0; k < o.max_epochs && !converged; ++k) {
+    NvtxRange iteration("outer iteration");
     int32_t* perm = nullptr;
-    rc = make_partition(p, seed, k, &perm);
+    rc = make_partition(p, seed, o.epoch0 + k, &perm);
     if (rc) return rc;
     CUDA_TRY(build_items(perm, p->m, p->col_ptr, p->w, p->cnt, p->item_ptr, p->items, p->scan_ws, p->stream,
                          &p->launches));
@@ -1415,7 +1437,7 @@ int pcdn_solve(pcdn_problem* p, int32_t P, double eps, uint64_t seed, const pcdn
     rc = device_status(p);
     if (rc) return rc;
     epochs = k + 1;
-    kkt_rel = kkt0 > 0 ? kk / kkt0 : 0.0;
+    kkt_rel = kref > 0 ? kk / kref : 0.0;
     if (trace && trace->epoch_kkt && k < trace->epoch_cap) trace->epoch_kkt[k] = kkt_rel;
     if (kkt_rel <= eps) converged = 1;
   }

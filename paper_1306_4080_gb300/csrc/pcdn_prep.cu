@@ -184,11 +184,11 @@ __device__ __forceinline__ uint64_t sm64_mix(uint64_t z) {
   return z ^ (z >> 31);
 }
 
-// epoch_dev (may be NULL): the outer-iteration index is read from device memory instead, so that a
-// captured graph of an outer iteration draws a new partition at every replay
+// epoch_dev (may be NULL): the outer-iteration index is epoch + the value read from device memory,
+// so that a captured graph of an outer iteration draws a new partition at every replay
 __global__ void perm_keys_kernel(uint64_t seed, uint64_t epoch, const int64_t* epoch_dev, int64_t m, uint64_t* keys,
                                  int32_t* vals) {
-  if (epoch_dev) epoch = (uint64_t)*epoch_dev;
+  if (epoch_dev) epoch += (uint64_t)*epoch_dev;
   const uint64_t gamma = 0x9E3779B97F4A7C15ULL;
   // state of the epoch's stream: first output of the stream started at seed ^ epoch * C
   const uint64_t s_epoch = sm64_mix((seed ^ (epoch * 0xD1B54A32D192ED03ULL)) + gamma);

@@ -26,7 +26,7 @@ cudaError_t radix_sort_u32(uint32_t* k0, int32_t* v0, uint32_t* k1, int32_t* v1,
 
 // ---- partition of one outer iteration (Eq. 8) ------------------------------------------------
 // perm_keys: key_j = splitmix64 output j+1 of the stream of (seed, epoch); values j.  With
-// epoch_dev (device, may be NULL) the epoch is read from there when the kernel runs.
+// epoch_dev (device, may be NULL) the epoch is epoch + the value read there when the kernel runs.
 cudaError_t perm_keys(uint64_t seed, int64_t epoch, const int64_t* epoch_dev, int64_t m, uint64_t* keys, int32_t* vals,
                       cudaStream_t s, int64_t* launches);
 // *epoch_dev += 1 (one thread)

@@ -227,6 +227,46 @@ def test_row_mirror_paths(pk, long_row):
         P.close()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_checkpoint_and_resume(pk, prec):
+    """A solve stopped after k outer iterations (its checkpoint: w and k) and resumed on a fresh
+    problem with warm_start = 1, epoch0 = k and kkt_ref = the first part's start-point KKT draws the
+    same partitions (Eq. 8) and stops at the same outer iteration as the uninterrupted solve."""
+    wl, p = problem("lr_2k_10k")
+    Pb, eps = 64, 1e-4
+    A = pk.Problem.from_csc(p.col_ptr, p.row_idx, p.val, p.y, wl.C, wl.loss)
+    B = pk.Problem.from_csc(p.col_ptr, p.row_idx, p.val, p.y, wl.C, wl.loss)
+    try:
+        opts = pk.pcdn_default_opts(prec=prec, max_epochs=500)
+        _, w_full, st_full, _ = A.solve(Pb, eps, 3, opts)
+        assert st_full["converged"] and st_full["epochs"] >= 4
+        k = st_full["epochs"] // 2
+        _, w_k, st1, _ = A.solve(Pb, eps, 3, pk.pcdn_default_opts(prec=prec, max_epochs=k))
+        assert st1["epochs"] == k and not st1["converged"]
+        B.set_w(w_k)
+        _, w_end, st2, _ = B.solve(Pb, eps, 3, pk.pcdn_default_opts(prec=prec, max_epochs=500, warm_start=1, epoch0=k,
+                                                                   kkt_ref=st1["kkt0"]))
+        assert st2["converged"]
+        if prec == "fp64":  # the same trajectory (up to the order of the atomic adds of d^T x_i)
+            assert st1["epochs"] + st2["epochs"] == st_full["epochs"]
+            assert st2["kkt_rel"] == pytest.approx(st_full["kkt_rel"], rel=1e-6)
+            assert st2["F_final"] == pytest.approx(st_full["F_final"], rel=1e-12)
+            np.testing.assert_allclose(w_end, w_full, rtol=0, atol=1e-8 * max(1.0, np.abs(w_full).max()))
+        else:  # FP32 atomic sums: trajectories equal to rounding
+            assert abs(st1["epochs"] + st2["epochs"] - st_full["epochs"]) <= 1
+            assert st2["F_final"] == pytest.approx(st_full["F_final"], rel=1e-6)
+        # a resumed solve that is already converged ends at once
+        _, _, st3, _ = B.solve(Pb, eps, 3, pk.pcdn_default_opts(prec=prec, warm_start=1, epoch0=st_full["epochs"],
+                                                                kkt_ref=st1["kkt0"]))
+        assert st3["converged"] and st3["epochs"] == 0
+        with pytest.raises(pk.PcdnError) as ei:
+            B.solve(Pb, eps, 3, pk.pcdn_default_opts(epoch0=-1))
+        assert ei.value.code == pk.PCDN_EINVAL
+    finally:
+        A.close()
+        B.close()
+
+
 def test_device_pointer_create_matches_host_create(pk):
     import torch
     wl, p = problem("svm_20k_100k")
