@@ -1403,8 +1403,6 @@ int pcdn_solve(pcdn_problem* p, int32_t P, double eps, uint64_t seed, const pcdn
   int converged = kkt0 == 0.0 || (o.kkt_ref > 0 && kkt_rel <= eps);
   int64_t epochs = 0;
   double walk_ms = 0.0;
-  std::vector<int32_t> hq;
-  std::vector<double> ha, hD, hF;
   for (int64_t k = 0; k < o.max_epochs && !converged; ++k) {
     NvtxRange iteration("outer iteration");
     int32_t* perm = nullptr;
