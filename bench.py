@@ -166,20 +166,30 @@ def gpu_uuid(dev):
         return None
 
 
-def cpu_sample(prob, wl, bundles_total, epochs_total, n_bundles):
-    """The FP64 oracle as it stands, single-threaded: the set-up of a solve (refresh + KKT at w = 0,
-    which is also the per-outer-iteration cost) and the first n_bundles bundle steps, projected to a
-    whole solve of bundles_total bundles over epochs_total outer iterations."""
+def cpu_sample(prob, wl, bundles_total, epochs_total, n_bundles, openmp=False):
+    """The FP64 oracle as it stands, single-threaded (or its OpenMP variant, the paper's shared-memory
+    scheme on all host cores): the set-up of a solve (refresh + KKT at w = 0, which is also the
+    per-outer-iteration cost) and the first n_bundles bundle steps, projected to a whole solve of
+    bundles_total bundles over epochs_total outer iterations."""
     import oracle
     o = oracle.Oracle.from_problem(prob, wl.C, wl.loss)
+    solve = o.solve_omp if openmp else o.solve
     t0 = time.perf_counter()
-    o.solve(wl.P, eps=wl.eps, seed=wl.solver_seed, bundle_limit=0)
+    solve(wl.P, eps=wl.eps, seed=wl.solver_seed, bundle_limit=0)
     t_setup = time.perf_counter() - t0
     t0 = time.perf_counter()
-    o.solve(wl.P, eps=wl.eps, seed=wl.solver_seed, bundle_limit=n_bundles)
+    solve(wl.P, eps=wl.eps, seed=wl.solver_seed, bundle_limit=n_bundles)
     t_run = time.perf_counter() - t0
     per_bundle = max(0.0, t_run - t_setup) / n_bundles
     projected = t_setup * (epochs_total + 1) + per_bundle * bundles_total
+    if openmp:
+        cores = oracle.omp_threads()
+        return dict(value=projected, unit=UNIT, cores=cores, kind="oracle-openmp",
+                    sample=f"the oracle's algorithm with the paper's shared-memory parallel scheme (OpenMP, {cores} "
+                           f"threads, FP64) on {n_bundles} bundles of outer iteration 0 plus one solve set-up, "
+                           f"projected to {bundles_total} bundles and {epochs_total} outer iterations: per bundle "
+                           f"{per_bundle * 1e3:.3f} ms, per outer-iteration refresh+KKT {t_setup:.3f} s",
+                    per_bundle_s=per_bundle, setup_s=t_setup)
     return dict(value=projected, unit=UNIT, cores=1, kind="oracle",
                 sample=f"oracle (1 thread, FP64) on {n_bundles} bundles of outer iteration 0 plus one solve set-up "
                        f"(refresh + KKT) of this workload, projected to {bundles_total} bundles and "
@@ -530,12 +540,15 @@ def run_ours(args):
                "d2h_bytes_per_step": int(8 * prob.n_features + 8), "steps": len(times),
                "includes": "pcdn_create from pinned host CSC + row-mirror build + solve + w to host + destroy"}
 
-    cpu = None
+    cpu = cpu_omp = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         nbun = args.cpu_bundles or max(8, min(200, (prob.n_features + wl.P - 1) // wl.P))
         cpu = cpu_sample(prob, wl, int(st0["bundles"]), int(st0["epochs"]), nbun)
         cpu.pop("per_bundle_s", None)
         cpu.pop("setup_s", None)
+        cpu_omp = cpu_sample(prob, wl, int(st0["bundles"]), int(st0["epochs"]), nbun, openmp=True)
+        cpu_omp.pop("per_bundle_s", None)
+        cpu_omp.pop("setup_s", None)
 
     P.close()
     if rank == 0:
@@ -543,7 +556,8 @@ def run_ours(args):
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32/f64 mixed" if args.prec == "mixed" else "f64",
                 "data": "synthetic (seeded generator, shapes of the paper's sparse text workloads)",
-                "config": config_of(wl, prob, args.prec), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "config": config_of(wl, prob, args.prec), "roofline": roof, "cpu_baseline": cpu,
+                "cpu_baseline_openmp": cpu_omp, "e2e": e2e,
                 "gpu_launches": int(launches), "clocks": clocks,
                 "solve": {"epochs": st0["epochs"], "bundles": st0["bundles"], "F_final": st0["F_final"],
                           "kkt_rel": st0["kkt_rel"], "coord_updates_per_s": st0["coord_updates"] / (ms * 1e-3),

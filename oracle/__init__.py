@@ -24,21 +24,51 @@ _libs: dict = {}
 LOSSES = {"logistic": 0, "l2svm": 1}
 
 
-def compile_source(src: str, out: str) -> str:
+_OMP_SRC = os.path.join(_HERE, "pcdn_omp.c")
+_OMP_LIB = os.path.join(_HERE, "_liboracle_omp.so")
+
+
+def compile_source(src: str, out: str, openmp: bool = False) -> str:
     """gcc, FP64, no floating-point contraction, no fast-math."""
     tmp = out + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-shared", "-fPIC",
-           "-o", tmp, src, "-lm"]
+           *(["-fopenmp"] if openmp else []), "-o", tmp, src, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, out)
     return out
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle next to its source."""
+    """Compile the oracle (and its OpenMP CPU-baseline variant) next to the sources."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         compile_source(_SRC, _LIB)
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_OMP_SRC))
+    if force or not os.path.exists(_OMP_LIB) or os.path.getmtime(_OMP_LIB) < newest:
+        compile_source(_OMP_SRC, _OMP_LIB, openmp=True)
     return _LIB
+
+
+_omp_lib = None
+
+
+def _load_omp():
+    """The OpenMP variant (the paper's shared-memory parallel scheme, all host cores): CPU baseline."""
+    global _omp_lib
+    with _lock:
+        if _omp_lib is None:
+            build()
+            lib = ctypes.CDLL(_OMP_LIB)
+            P = ctypes.POINTER
+            lib.or_solve_omp.argtypes = [P(_Problem), P(_Armijo), ctypes.c_int64, ctypes.c_double, ctypes.c_uint64,
+                                         ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, P(_Stats)]
+            lib.or_solve_omp.restype = ctypes.c_int
+            lib.or_omp_threads.restype = ctypes.c_int
+            _omp_lib = lib
+    return _omp_lib
+
+
+def omp_threads() -> int:
+    return int(_load_omp().or_omp_threads())
 
 
 class _Problem(ctypes.Structure):
@@ -211,6 +241,21 @@ class Oracle:
             out.update(q=tq[:nbt], alpha=ta[:nbt], Delta=tD[:nbt], dF=tF[:nbt],
                        epoch_kkt=ek[:st.epochs], epoch_F=eF[:st.epochs])
         return w, out
+
+    def solve_omp(self, P: int, eps: float = 1e-3, seed: int = 0, max_epochs: int = 1000, armijo: Armijo = Armijo(),
+                  bundle_limit: int = -1, w0=None):
+        """Algorithm 3 with the paper's shared-memory parallel scheme on all host cores (OpenMP);
+        the CPU baseline.  Same partitions and stop rule as solve(); sums in another order."""
+        lib = _load_omp()
+        w = np.zeros(self.m) if w0 is None else np.array(w0, dtype=np.float64, copy=True)
+        st = _Stats()
+        rc = lib.or_solve_omp(ctypes.byref(self._p), ctypes.byref(armijo._c()), int(P), float(eps),
+                              int(seed) & (2**64 - 1), int(max_epochs), int(bundle_limit), _ptr(w), ctypes.byref(st))
+        if rc < 0:
+            raise RuntimeError(f"or_solve_omp failed: {rc}")
+        return w, dict(epochs=st.epochs, bundles=st.bundles, coord_updates=st.coord_updates, ls_steps=st.ls_steps,
+                       ls_cap_hits=st.ls_cap_hits, F_final=st.F_final, kkt_rel=st.kkt_rel, kkt0=st.kkt0,
+                       converged=bool(st.converged), status=rc)
 
     def cdn_epoch(self, w, mq, seed: int, epoch: int, armijo: Armijo = Armijo()):
         w = np.array(w, dtype=np.float64, copy=True)

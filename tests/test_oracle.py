@@ -449,3 +449,21 @@ def test_warm_started_path_reaches_each_optimum(loss, P):
     assert np.abs(g0).max() <= 1.0
     w0, st = o.solve(P, eps=1e-3, seed=4, w0=np.zeros(p.n_features))
     assert st["converged"] and st["epochs"] == 0 and st["kkt0"] == 0.0 and not np.any(w0)
+
+
+@pytest.mark.parametrize("loss,P", [("logistic", 16), ("l2svm", 64)])
+def test_openmp_baseline_solves_the_same_problem(loss, P):
+    """The OpenMP CPU baseline (the paper's shared-memory parallel scheme) runs Algorithm 3 with the
+    oracle's partitions and stop rule: same number of outer iterations and bundles, objective equal
+    to rounding (its sums are atomic and parallel)."""
+    spec = datagen.Spec(1500, 4000, "zipf", row_mean=40.0, zipf_s=1.1, values="tfidf", wstar_nnz=30, flip_frac=0.05,
+                        seed=11)
+    p = datagen.generate(spec, with_csr=False)
+    o = oracle.Oracle.from_problem(p, 0.7, loss)
+    w1, s1 = o.solve(P, eps=1e-3, seed=6, max_epochs=300)
+    w2, s2 = o.solve_omp(P, eps=1e-3, seed=6, max_epochs=300)
+    assert s1["converged"] and s2["converged"]
+    assert abs(s1["epochs"] - s2["epochs"]) <= 1
+    assert s2["F_final"] == pytest.approx(s1["F_final"], rel=1e-7)
+    assert s2["F_final"] == pytest.approx(o.objective(w2), rel=1e-12)
+    assert oracle.omp_threads() >= 1
