@@ -116,7 +116,9 @@ def _load(path: str | None = None):
                                            vp, vp, vp, P(d), P(ctypes.c_int32), P(d), P(d)]
             lib.or_bundle_step.restype = i32
             lib.or_solve.argtypes = [P(_Problem), P(_Armijo), i64, d, ctypes.c_uint64, i64, i32, i64, vp,
-                                     P(_Stats), i64, vp, vp, vp, vp, i64, vp, vp]
+                                     P(_Stats), i64, vp, vp, vp, vp, i64, vp, vp, i32, vp]
+            lib.or_active_set.argtypes = [P(_Problem), vp, vp, d, vp, P(d)]
+            lib.or_active_set.restype = i64
             lib.or_solve.restype = i32
             lib.or_loss_change.argtypes = [P(_Problem), d, i32, d]
             lib.or_loss_change.restype = d
@@ -212,14 +214,17 @@ class Oracle:
         return w, mq, dict(g=g, h=h, d=d, Delta=Delta.value, q=q.value, alpha=alpha.value, dF=dF.value, status=rc)
 
     def solve(self, P: int, eps: float = 1e-3, seed: int = 0, max_epochs: int = 1000, armijo: Armijo = Armijo(),
-              direct: bool = False, bundle_limit: int = -1, w0=None, trace: bool = False):
-        """Algorithm 3 to the relative KKT tolerance eps; returns (w, stats dict)."""
+              direct: bool = False, bundle_limit: int = -1, w0=None, trace: bool = False, shrink: bool = False):
+        """Algorithm 3 to the relative KKT tolerance eps; returns (w, stats dict).  With shrink, outer
+        iterations after the first visit only the active features (stats 'epoch_active': features
+        visited per outer iteration)."""
         w = np.zeros(self.m) if w0 is None else np.array(w0, dtype=np.float64, copy=True)
         st = _Stats()
         cap = 0
         tq = ta = tD = tF = None
-        ecap = max_epochs if trace else 0
+        ecap = max_epochs if (trace or shrink) else 0
         ek = eF = None
+        ea = np.zeros(max(ecap, 1), dtype=np.int64)
         if trace:
             nb = (self.m + P - 1) // P
             cap = nb * max_epochs if bundle_limit < 0 else bundle_limit
@@ -230,12 +235,15 @@ class Oracle:
                                int(max_epochs), int(direct), int(bundle_limit), _ptr(w), ctypes.byref(st),
                                cap, _ptr(tq) if trace else nul, _ptr(ta) if trace else nul,
                                _ptr(tD) if trace else nul, _ptr(tF) if trace else nul,
-                               ecap, _ptr(ek) if trace else nul, _ptr(eF) if trace else nul)
+                               ecap, _ptr(ek) if trace else nul, _ptr(eF) if trace else nul, int(bool(shrink)),
+                               _ptr(ea))
         if rc < 0:
             raise RuntimeError(f"or_solve failed: {rc}")
         out = dict(epochs=st.epochs, bundles=st.bundles, coord_updates=st.coord_updates, ls_steps=st.ls_steps,
                    ls_cap_hits=st.ls_cap_hits, F_final=st.F_final, kkt_rel=st.kkt_rel, kkt0=st.kkt0,
                    converged=bool(st.converged), status=rc)
+        if trace or shrink:
+            out["epoch_active"] = ea[:st.epochs].copy()
         if trace:
             nbt = int(st.bundles)
             out.update(q=tq[:nbt], alpha=ta[:nbt], Delta=tD[:nbt], dF=tF[:nbt],
@@ -256,6 +264,17 @@ class Oracle:
         return w, dict(epochs=st.epochs, bundles=st.bundles, coord_updates=st.coord_updates, ls_steps=st.ls_steps,
                        ls_cap_hits=st.ls_cap_hits, F_final=st.F_final, kkt_rel=st.kkt_rel, kkt0=st.kkt0,
                        converged=bool(st.converged), status=rc)
+
+    def active_set(self, w, nu: float = 1e-12):
+        """Shrinking's active set at w (maintained quantities recomputed from w): (mask, M)."""
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        mq = self.maintained(w)
+        act = np.zeros(self.m, dtype=np.uint8)
+        M = ctypes.c_double()
+        cnt = self.lib.or_active_set(ctypes.byref(self._p), _ptr(w), _ptr(mq), float(nu), _ptr(act), ctypes.byref(M))
+        if cnt < 0:
+            raise RuntimeError("or_active_set failed")
+        return act.astype(bool), M.value
 
     def cdn_epoch(self, w, mq, seed: int, epoch: int, armijo: Armijo = Armijo()):
         w = np.array(w, dtype=np.float64, copy=True)

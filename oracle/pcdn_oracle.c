@@ -37,6 +37,17 @@
  *     after each outer iteration the maintained quantities are recomputed
  *     from z = Xw, and the solve stops once the l1 norm of the minimum-norm
  *     subgradient is at most eps times its value at w = 0.
+ *   - Shrinking (Section 5.1 says only that the comparison's shrinking runs
+ *     outside the parallel loop): optional, between outer iterations.  The
+ *     first outer iteration of a solve visits every feature; outer iteration
+ *     k >= 1 visits the active set of w^k (the iterate after k outer
+ *     iterations, with its maintained quantities just recomputed): feature j
+ *     is active unless w_j = 0 and |g_j(w^k)| < 1 - M_k / s, where M_k is the
+ *     largest |v_j(w^k)| of the minimum-norm subgradient and s the number of
+ *     samples (the margin of LIBLINEAR's CDN shrinking, taken from a fresh
+ *     gradient).  The iteration's partition is the full random order of Eq. 8
+ *     restricted to the active features, in bundles of P.  The stopping rule
+ *     is unchanged (all features).
  *
  * Build: gcc -O2 -std=c11 -ffp-contract=off -shared -fPIC (no fast-math).
  */
@@ -360,6 +371,34 @@ int or_bundle_step(const or_problem* p, const or_armijo* ar, double* w, double* 
   return capped;
 }
 
+/* Active set for shrinking (reading above): active[j] = 1 unless w_j = 0 and
+ * |g_j| < 1 - M / s, M = max_j |v_j| with v the minimum-norm subgradient.
+ * Returns the number of active features; *M_out gets M. */
+int64_t or_active_set(const or_problem* p, const double* w, const double* mq, double nu, uint8_t* active,
+                      double* M_out) {
+  double* g = (double*)malloc(sizeof(double) * (size_t)p->m);
+  if (!g) return -1;
+  double M = 0.0;
+  for (int64_t j = 0; j < p->m; ++j) {
+    double h;
+    or_grad_hess(p, mq, j, nu, &g[j], &h);
+    double v;
+    if (w[j] > 0) v = g[j] + 1.0;
+    else if (w[j] < 0) v = g[j] - 1.0;
+    else v = fabs(g[j]) > 1.0 ? (g[j] > 0 ? g[j] - 1.0 : g[j] + 1.0) : 0.0;
+    if (fabs(v) > M) M = fabs(v);
+  }
+  const double bound = 1.0 - M / (double)p->n;
+  int64_t count = 0;
+  for (int64_t j = 0; j < p->m; ++j) {
+    active[j] = (w[j] != 0.0 || fabs(g[j]) >= bound) ? 1 : 0;
+    count += active[j];
+  }
+  free(g);
+  if (M_out) *M_out = M;
+  return count;
+}
+
 /*
  * Algorithm 3: outer iterations k = 0, 1, ...; in each, a fresh random
  * partition and a sequential walk over its bundles.  After every outer
@@ -373,14 +412,15 @@ int or_bundle_step(const or_problem* p, const or_armijo* ar, double* w, double* 
 int or_solve(const or_problem* p, const or_armijo* ar, int64_t P, double eps, uint64_t seed, int64_t max_epochs,
              int direct, int64_t bundle_limit, double* w, or_stats* st,
              int64_t trace_cap, int32_t* tr_q, double* tr_alpha, double* tr_Delta, double* tr_dF,
-             int64_t epoch_cap, double* ep_kkt, double* ep_F) {
+             int64_t epoch_cap, double* ep_kkt, double* ep_F, int shrink, int64_t* ep_active) {
   if (!p || !ar || !w || !st || P < 1 || P > p->m || !(eps > 0)) return OR_EINVAL;
   memset(st, 0, sizeof(*st));
   double* mq = (double*)malloc(sizeof(double) * (size_t)(p->n > 0 ? p->n : 1));
   int32_t* perm = (int32_t*)malloc(sizeof(int32_t) * (size_t)p->m);
-  if (!mq || !perm) { free(mq); free(perm); return OR_ENOMEM; }
+  uint8_t* active = shrink ? (uint8_t*)malloc((size_t)p->m) : NULL;
+  if (!mq || !perm || (shrink && !active)) { free(mq); free(perm); free(active); return OR_ENOMEM; }
   int rc = or_refresh(p, w, mq);
-  if (rc) { free(mq); free(perm); return rc; }
+  if (rc) { free(mq); free(perm); free(active); return rc; }
   double kkt0 = or_kkt_l1(p, w, mq, ar->nu);
   st->kkt0 = kkt0;
   st->kkt_rel = kkt0 > 0 ? 1.0 : 0.0;
@@ -391,9 +431,19 @@ int or_solve(const or_problem* p, const or_armijo* ar, int64_t P, double eps, ui
   for (int64_t k = 0; k < max_epochs && !st->converged && !stop_early; ++k) {
     rc = or_permutation(seed, k, p->m, perm);
     if (rc) break;
+    int64_t npos = p->m;
+    if (shrink && k > 0) {  /* the random order restricted to the active set of the current w */
+      const int64_t na = or_active_set(p, w, mq, ar->nu, active, NULL);
+      if (na < 0) { rc = OR_ENOMEM; break; }
+      npos = 0;
+      for (int64_t t = 0; t < p->m; ++t)
+        if (active[perm[t]]) perm[npos++] = perm[t];
+    }
+    if (k < epoch_cap && ep_active) ep_active[k] = npos;
+    nb = (npos + P - 1) / P;
     for (int64_t t = 0; t < nb; ++t) {
       if (bundle_limit >= 0 && tcount >= bundle_limit) { stop_early = 1; break; }
-      int64_t lo = t * P, hi = lo + P < p->m ? lo + P : p->m;
+      int64_t lo = t * P, hi = lo + P < npos ? lo + P : npos;
       int32_t q;
       double alpha, Delta, dF;
       int r = or_bundle_step(p, ar, w, mq, perm + lo, hi - lo, direct, NULL, NULL, NULL, &Delta, &q, &alpha, &dF);
@@ -424,6 +474,7 @@ int or_solve(const or_problem* p, const or_armijo* ar, int64_t P, double eps, ui
   st->F_final = or_objective(p, w);
   free(mq);
   free(perm);
+  free(active);
   if (rc < 0) return rc;
   return st->converged ? OR_OK : OR_ENOTCONVERGED;
 }

@@ -68,6 +68,18 @@ def ternary_min(f, lo, hi, iters=300) -> float:
     return 0.5 * (lo + hi)
 
 
+def grad(X, y, w, c, loss) -> np.ndarray:
+    """Gradient of c sum_i phi(w; x_i, y_i) (Eq. 2 / Eq. 3 differentiated in matrix form); X dense
+    or scipy-sparse."""
+    yf = np.asarray(y, dtype=np.float64)
+    z = X @ w
+    if loss == "logistic":
+        s = -yf / (1.0 + np.exp(yf * z))
+    else:
+        s = -2.0 * yf * np.maximum(0.0, 1.0 - yf * z)
+    return c * np.asarray(X.T @ s).ravel()
+
+
 def fista(X, y, c, loss, iters=200000, tol=1e-13):
     """FISTA with constant step 1/Lip for min L(w) + ||w||_1 (Beck and Teboulle 2009), with the
     gradient-based adaptive restart of O'Donoghue and Candes (2015)."""
@@ -75,21 +87,15 @@ def fista(X, y, c, loss, iters=200000, tol=1e-13):
     theta = 0.25 if loss == "logistic" else 2.0
     lip = theta * c * np.linalg.norm(X, 2) ** 2
     step = 1.0 / lip
-    yf = y.astype(np.float64)
 
-    def grad(w):
-        z = X @ w
-        if loss == "logistic":
-            s = -yf / (1.0 + np.exp(yf * z))
-        else:
-            s = -2.0 * yf * np.maximum(0.0, 1.0 - yf * z)
-        return c * (X.T @ s)
+    def grad_w(w):
+        return grad(X, y, w, c, loss)
 
     w = np.zeros(m)
     v = w.copy()
     t = 1.0
     for it in range(iters):
-        u = v - step * grad(v)
+        u = v - step * grad_w(v)
         w_new = np.sign(u) * np.maximum(np.abs(u) - step, 0.0)
         if float(np.dot(v - w_new, w_new - w)) > 0:
             t = 1.0

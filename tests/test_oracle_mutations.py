@@ -12,6 +12,7 @@ import pytest
 
 import oracle
 from tests import test_oracle as T
+from tests import test_oracle_shrink as S
 
 MUTANTS = [
     # Eq. 5 exactly as printed (conditions without the +/-1 terms)
@@ -37,6 +38,11 @@ MUTANTS = [
     ("nu_ignored", "if (h <= 0.0) h = nu;", "if (h < 0.0) h = nu;"),
     # Eq. 10's log-ratio taken literally for every sample (cancels at large margins)
     ("eq10_literal", "      if (E <= 1.0) return log1p(E / (1.0 + E) * expm1(u)) - (y_i > 0 ? u : 0.0);\n", ""),
+    # shrinking: the margin's sign, the w_j != 0 condition, the partition order of the active set
+    ("shrink_margin_sign", "const double bound = 1.0 - M / (double)p->n;", "const double bound = 1.0 + M / (double)p->n;"),
+    ("shrink_drops_nonzero_w", "active[j] = (w[j] != 0.0 || fabs(g[j]) >= bound) ? 1 : 0;",
+     "active[j] = (fabs(g[j]) >= bound) ? 1 : 0;"),
+    ("shrink_filter_index", "if (active[perm[t]]) perm[npos++] = perm[t];", "if (active[t]) perm[npos++] = perm[t];"),
 ]
 
 
@@ -68,6 +74,10 @@ def _pins():
         ("bound_svm", lambda: T.test_delta_bound_descent_and_step_lower_bound("l2svm", 2.0)),
         ("fista_lr", lambda: T.test_converged_objective_matches_fista("logistic", 1.0, 3)),
         ("fista_svm", lambda: T.test_converged_objective_matches_fista("l2svm", 0.5, 4)),
+        ("shrink_first", lambda: S.test_first_outer_iteration_visits_every_feature(*S.CASES[0])),
+        ("shrink_active", lambda: S.test_active_set_from_an_independent_gradient(*S.CASES[0])),
+        ("shrink_random", lambda: S.test_active_set_at_random_points(*S.CASES[0])),
+        ("shrink_order", lambda: S.test_shrunk_outer_iteration_is_the_restricted_partition(*S.CASES[0])),
     ]
     return out
 
