@@ -71,6 +71,12 @@ typedef struct {
   int32_t grid_ctas;  /* thread blocks of the bundle walker; 0 = one group covering the whole GPU */
   int32_t refresh;    /* 1 (default): recompute the maintained quantities from z = Xw after each outer iteration */
   uint32_t spin_limit;/* iterations a device-side wait may spin before PCDN_ETIMEOUT (0 = default) */
+  int32_t shrink;     /* 1: shrinking between outer iterations (default 0: every outer iteration visits every
+                         feature, Algorithm 3).  The first outer iteration visits every feature; outer
+                         iteration k >= 1 visits, in its random order (Eq. 8), only the features with
+                         w_j != 0 or |g_j| >= 1 - M/n_samples at the stopping test of iteration k-1
+                         (M = max_j |v_j|, v the minimum-norm subgradient).  The stopping test still
+                         covers every feature.  Solves that shrink are not captured as CUDA graphs. */
   int64_t epoch0;     /* index of the first outer iteration (its partition, Eq. 8, is drawn with this index; default 0) */
   double kkt_ref;     /* > 0: relative KKT measured against this ||v||_1 instead of the start point's (default 0).
                          A solve stopped after k outer iterations resumes exactly with warm_start = 1 from its w,
@@ -108,6 +114,7 @@ typedef struct {
   double* dF;        /* [bundle_cap] F(w + alpha d) - F(w) as evaluated by the line search */
   int64_t epoch_cap;
   double* epoch_kkt; /* [epoch_cap] relative KKT after each outer iteration */
+  int64_t* epoch_features; /* [epoch_cap] features visited by each outer iteration (n_features unless shrinking) */
 } pcdn_trace;
 
 typedef struct pcdn_problem pcdn_problem;

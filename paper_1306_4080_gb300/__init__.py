@@ -54,7 +54,7 @@ class pcdn_opts(ctypes.Structure):
                 ("nu", ctypes.c_double), ("q_max", ctypes.c_int32), ("ls_batch", ctypes.c_int32),
                 ("max_epochs", ctypes.c_int64), ("prec", ctypes.c_int), ("warm_start", ctypes.c_int32),
                 ("grid_ctas", ctypes.c_int32), ("refresh", ctypes.c_int32), ("spin_limit", ctypes.c_uint32),
-                ("epoch0", ctypes.c_int64), ("kkt_ref", ctypes.c_double)]
+                ("shrink", ctypes.c_int32), ("epoch0", ctypes.c_int64), ("kkt_ref", ctypes.c_double)]
 
 
 class pcdn_stats(ctypes.Structure):
@@ -69,7 +69,7 @@ class pcdn_stats(ctypes.Structure):
 class pcdn_trace(ctypes.Structure):
     _fields_ = [("bundle_cap", ctypes.c_int64), ("q", ctypes.c_void_p), ("alpha", ctypes.c_void_p),
                 ("Delta", ctypes.c_void_p), ("dF", ctypes.c_void_p), ("epoch_cap", ctypes.c_int64),
-                ("epoch_kkt", ctypes.c_void_p)]
+                ("epoch_kkt", ctypes.c_void_p), ("epoch_features", ctypes.c_void_p)]
 
 
 class pcdn_batch_job(ctypes.Structure):
@@ -238,9 +238,11 @@ def pcdn_solve(h: int, P: int, eps: float = 1e-3, seed: int = 0, opts: pcdn_opts
     arrs = {}
     if trace_bundles or trace_epochs:
         arrs = dict(q=np.zeros(trace_bundles, np.int32), alpha=np.zeros(trace_bundles), Delta=np.zeros(trace_bundles),
-                    dF=np.zeros(trace_bundles), epoch_kkt=np.zeros(trace_epochs))
+                    dF=np.zeros(trace_bundles), epoch_kkt=np.zeros(trace_epochs),
+                    epoch_features=np.zeros(trace_epochs, np.int64))
         tr = pcdn_trace(trace_bundles, arrs["q"].ctypes.data, arrs["alpha"].ctypes.data, arrs["Delta"].ctypes.data,
-                        arrs["dF"].ctypes.data, trace_epochs, arrs["epoch_kkt"].ctypes.data)
+                        arrs["dF"].ctypes.data, trace_epochs, arrs["epoch_kkt"].ctypes.data,
+                        arrs["epoch_features"].ctypes.data)
     rc = lib.pcdn_solve(h, int(P), float(eps), int(seed) & (2**64 - 1), ctypes.byref(o),
                         w.ctypes.data if w is not None else None, ctypes.byref(st),
                         ctypes.byref(tr) if tr is not None else None)
@@ -249,7 +251,8 @@ def pcdn_solve(h: int, P: int, eps: float = 1e-3, seed: int = 0, opts: pcdn_opts
     stats["status"] = rc
     if arrs:
         nb = min(int(stats["bundles"]), trace_bundles)
-        arrs = {k: (v[:nb] if k != "epoch_kkt" else v[:min(int(stats["epochs"]), trace_epochs)]) for k, v in arrs.items()}
+        ne = min(int(stats["epochs"]), trace_epochs)
+        arrs = {k: (v[:ne] if k.startswith("epoch_") else v[:nb]) for k, v in arrs.items()}
     return rc, w, stats, arrs
 
 

@@ -193,6 +193,10 @@ struct pcdn_problem {
   double* tr_dF = nullptr;
   // outer-iteration index on the device (read by a captured outer iteration's partition)
   int64_t* epoch_dev = nullptr;
+  // shrinking: g_j of every feature at the last stopping test, and [0] max |v_j| (bits of the
+  // double), [1] active features, [2] their nonzeros (allocated by the first solve that shrinks)
+  double* gfull = nullptr;
+  unsigned long long* shr = nullptr;
   bool capturing = false;  // the stream is being captured into a graph
   // stream, events
   cudaStream_t stream = nullptr;
@@ -225,6 +229,7 @@ void free_all(pcdn_problem* p) {
   f(p->gk); f(p->hk); f(p->dk); f(p->col_cnt); f(p->part);
   f(p->lsacc); f(p->sync); f(p->err); f(p->counters); f(p->red_part); f(p->red_out);
   f(p->tr_q); f(p->tr_alpha); f(p->tr_Delta); f(p->tr_dF); f(p->epoch_dev);
+  f(p->gfull); f(p->shr);
   if (p->ev0) cudaEventDestroy(p->ev0);
   if (p->ev1) cudaEventDestroy(p->ev1);
   if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
@@ -513,6 +518,13 @@ int ensure_trace(pcdn_problem* p, int64_t nb) {
   return PCDN_OK;
 }
 
+int ensure_shrink(pcdn_problem* p) {
+  if (p->gfull) return PCDN_OK;
+  CUDA_TRY(palloc(p, &p->shr, 4));
+  CUDA_TRY(palloc(p, &p->gfull, p->m));
+  return PCDN_OK;
+}
+
 int status_from_flags(int h);
 
 int device_status(pcdn_problem* p) {
@@ -551,9 +563,25 @@ int do_refresh(pcdn_problem* p, int prec, bool write_state, bool with_loss) {
 }
 
 // ||v||_1 into red_out[slot] (device); the caller copies.
-int do_kkt(pcdn_problem* p, int slot) {
+// ||v||_1 into red_out[slot]; with shrink also g_j of every feature, max |v_j| and the count and
+// nonzeros of the features active in the next outer iteration (p->shr).
+int do_kkt(pcdn_problem* p, int slot, bool shrink = false) {
+  if (shrink) CUDA_TRY(cudaMemsetAsync(p->shr, 0, sizeof(unsigned long long) * 3, p->stream));
   CUDA_TRY(kkt_l1(p->rec_prec, p->id_items, p->n_id_items, p->id_item_ptr, p->id_perm, p->m, p->row_idx, p->val, p->rec,
-                  p->w, p->c, p->part, p->red_part, p->red_grid, p->red_out + slot, p->stream, &p->launches));
+                  p->w, p->c, p->part, p->red_part, p->red_grid, p->red_out + slot, p->stream, &p->launches,
+                  shrink ? p->gfull : nullptr, shrink ? p->shr : nullptr));
+  if (shrink)
+    CUDA_TRY(active_count(p->gfull, p->w, p->m, p->col_ptr, p->shr, p->n, p->shr + 1, p->stream, &p->launches));
+  return PCDN_OK;
+}
+
+// The partition perm of all features restricted to the active set of the last stopping test (in
+// partition order), into the other radix-sort value buffer.
+int shrink_partition(pcdn_problem* p, int32_t* perm, int32_t** out) {
+  int32_t* dst = perm == p->vals0 ? p->vals1 : p->vals0;
+  CUDA_TRY(compact_active(perm, p->m, p->gfull, p->w, p->shr, p->n, p->cnt, p->item_off, p->scan_ws, dst, p->stream,
+                          &p->launches));
+  *out = dst;
   return PCDN_OK;
 }
 
@@ -582,6 +610,7 @@ int check_opts(const pcdn_opts* o) {
   if (o->prec != PCDN_PREC_FP64 && o->prec != PCDN_PREC_MIXED) return fail(PCDN_EINVAL, "unknown precision");
   if (o->epoch0 < 0) return fail(PCDN_EINVAL, "epoch0 must be >= 0");
   if (!(o->kkt_ref >= 0) || !std::isfinite(o->kkt_ref)) return fail(PCDN_EINVAL, "kkt_ref must be >= 0 and finite");
+  if (o->shrink != 0 && o->shrink != 1) return fail(PCDN_EINVAL, "shrink must be 0 or 1");
   return PCDN_OK;
 }
 
@@ -704,6 +733,7 @@ struct Mail {
   int32_t err;
   int32_t pad;
   unsigned long long cnt[8];
+  unsigned long long act[2];  // shrinking: features and nonzeros active in the next outer iteration
 };
 enum { kStageNone = 0, kStageStart = 1, kStageEpoch = 2, kStageFinal = 3, kStageEnded = 4 };
 }  // namespace
@@ -725,6 +755,9 @@ struct SolveTask {
   int converged = 0;
   double walk_ms = 0.0;
   int64_t launches0 = 0;
+  // shrinking: features and nonzeros of the next outer iteration, nonzeros visited so far
+  int64_t npos = 0, nnz_next = 0, nnz_visited = 0;
+  bool shrunk = false;
   unsigned long long cnt[8] = {0};
   std::chrono::steady_clock::time_point t0;
   double wall_s = 0.0;
@@ -811,6 +844,8 @@ int post(SolveTask* t, int kkt_slot, bool final_stage) {
   pcdn_problem* p = t->p;
   if (kkt_slot >= 0)
     CUDA_TRY(cudaMemcpyAsync(&t->mail->kkt, p->red_out + kkt_slot, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+  if (kkt_slot == 1 && t->o.shrink)
+    CUDA_TRY(cudaMemcpyAsync(t->mail->act, p->shr + 1, sizeof(t->mail->act), cudaMemcpyDeviceToHost, p->stream));
   if (final_stage) {
     CUDA_TRY(cudaMemcpyAsync(&t->mail->F, p->red_out, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
     CUDA_TRY(cudaMemcpyAsync(t->mail->cnt, p->counters, sizeof(t->mail->cnt), cudaMemcpyDeviceToHost, p->stream));
@@ -852,15 +887,17 @@ int epoch_body(SolveTask* t, int64_t k, int64_t* epoch_dev) {
   int32_t* perm = nullptr;
   int rc = make_partition(p, t->seed, k, &perm, epoch_dev);
   if (rc) return rc;
-  CUDA_TRY(build_items(perm, p->m, p->col_ptr, p->w, p->cnt, p->item_ptr, p->items, p->scan_ws, p->stream,
+  if (t->shrunk && (rc = shrink_partition(p, perm, &perm))) return rc;
+  const int64_t npos = t->shrunk ? t->npos : p->m;
+  CUDA_TRY(build_items(perm, npos, p->col_ptr, p->w, p->cnt, p->item_ptr, p->items, p->scan_ws, p->stream,
                        &p->launches));
-  rc = run_walk(p, &t->o, perm, p->m, t->P, 0, t->nb, t->grid, nullptr);
+  rc = run_walk(p, &t->o, perm, npos, t->P, 0, (npos + t->P - 1) / t->P, t->grid, nullptr);
   if (rc) return rc;
   if (t->o.refresh) {
     rc = do_refresh(p, (int)t->o.prec, true, false);
     if (rc) return rc;
   }
-  rc = do_kkt(p, 1);
+  rc = do_kkt(p, 1, t->o.shrink != 0);
   if (rc) return rc;
   if (epoch_dev) CUDA_TRY(advance_epoch(epoch_dev, p->stream, &p->launches));
   return post(t, 1, false);
@@ -902,7 +939,8 @@ void capture_epoch(SolveTask* t) {
 int issue_epoch(SolveTask* t, int64_t k) {
   NvtxRange range("issue outer iteration");
   pcdn_problem* p = t->p;
-  if (t->graphs && !t->graph_tried) capture_epoch(t);
+  // a shrinking solve's outer iterations differ in size: issued directly
+  if (t->graphs && !t->graph_tried && !t->o.shrink) capture_epoch(t);
   t->stage = kStageEpoch;
   if (t->exec) {
     CUDA_TRY(cudaGraphLaunch(t->exec, p->stream));
@@ -961,13 +999,17 @@ int task_start(SolveTask* t, pcdn_problem* p, int32_t P, double eps, uint64_t se
   else t->grid = pick_grid(p, &o, P);
   t->kkt0 = t->kkt_rel = t->F = t->walk_ms = 0.0;
   t->epochs = 0;
+  t->npos = p->m;
+  t->nnz_next = p->nnz;
+  t->nnz_visited = 0;
+  t->shrunk = false;
   t->converged = 0;
   t->rc = PCDN_OK;
   t->launches0 = p->launches;
   t->t0 = std::chrono::steady_clock::now();
   std::memset(t->cnt, 0, sizeof(t->cnt));
   if ((rc = ensure_bundle_scratch(p, P)) || (rc = ensure_trace(p, t->nb)) ||
-      (rc = ensure_plan(p, t->nb * (t->grid + 1))) || (rc = reset_scratch(p)))
+      (rc = ensure_plan(p, t->nb * (t->grid + 1))) || (rc = reset_scratch(p)) || (o.shrink && (rc = ensure_shrink(p))))
     return end_task(t, rc);
   // from here every failure ends the task (which returns its walker blocks)
   cudaError_t e = cudaSuccess;
@@ -1015,8 +1057,13 @@ int task_poll(SolveTask* t, int* done) {
       if (cudaEventElapsedTime(&ms, t->p->ev0, t->p->ev1) == cudaSuccess) t->walk_ms += ms;
       cudaGetLastError();
       t->epochs += 1;
+      t->nnz_visited += t->nnz_next;
       t->kkt_rel = t->kref > 0 ? t->mail->kkt / t->kref : 0.0;
       if (t->kkt_rel <= t->eps) t->converged = 1;
+      // the next outer iteration's active set (all features when shrinking is off or the set is empty)
+      t->shrunk = t->o.shrink && t->mail->act[0] > 0;
+      t->npos = t->shrunk ? (int64_t)t->mail->act[0] : t->p->m;
+      t->nnz_next = t->shrunk ? (int64_t)t->mail->act[1] : t->p->nnz;
       rc = (t->converged || t->epochs >= t->o.max_epochs) ? issue_final(t) : issue_epoch(t, t->epochs);
       break;
     }
@@ -1056,7 +1103,7 @@ int task_result(SolveTask* t, double* w_out, pcdn_stats* stats) {
     stats->ls_steps = (int64_t)t->cnt[0];
     stats->ls_cap_hits = (int64_t)t->cnt[1];
     stats->ls_passes = (int64_t)t->cnt[2];
-    stats->nnz_visited = t->epochs * p->nnz;
+    stats->nnz_visited = t->nnz_visited;
     stats->rows_touched = (int64_t)t->cnt[4];
     stats->kernel_launches = p->launches - t->launches0;
     stats->F_final = t->F;
@@ -1384,6 +1431,7 @@ int pcdn_solve(pcdn_problem* p, int32_t P, double eps, uint64_t seed, const pcdn
   if (rc) return rc;
   rc = reset_scratch(p);
   if (rc) return rc;
+  if (o.shrink && (rc = ensure_shrink(p))) return rc;
   if (!o.warm_start) CUDA_TRY(cudaMemsetAsync(p->w, 0, sizeof(double) * p->m, p->stream));
   CUDA_TRY(cudaMemsetAsync(p->err, 0, sizeof(int), p->stream));
   CUDA_TRY(cudaMemsetAsync(p->counters, 0, sizeof(unsigned long long) * 8, p->stream));
@@ -1403,32 +1451,43 @@ int pcdn_solve(pcdn_problem* p, int32_t P, double eps, uint64_t seed, const pcdn
   int converged = kkt0 == 0.0 || (o.kkt_ref > 0 && kkt_rel <= eps);
   int64_t epochs = 0;
   double walk_ms = 0.0;
+  // shrinking: features and nonzeros of the next outer iteration (all of them until a stopping test
+  // has chosen an active set)
+  int64_t npos = p->m, nnz_next = p->nnz, nnz_visited = 0, tr_off = 0;
+  bool shrunk = false;
   for (int64_t k = 0; k < o.max_epochs && !converged; ++k) {
     NvtxRange iteration("outer iteration");
     int32_t* perm = nullptr;
     rc = make_partition(p, seed, o.epoch0 + k, &perm);
     if (rc) return rc;
-    CUDA_TRY(build_items(perm, p->m, p->col_ptr, p->w, p->cnt, p->item_ptr, p->items, p->scan_ws, p->stream,
+    if (shrunk && (rc = shrink_partition(p, perm, &perm))) return rc;
+    const int64_t nbk = (npos + P - 1) / P;
+    CUDA_TRY(build_items(perm, npos, p->col_ptr, p->w, p->cnt, p->item_ptr, p->items, p->scan_ws, p->stream,
                          &p->launches));
     float ms = 0.0f;
-    rc = run_walk(p, &o, perm, p->m, P, 0, nb, grid, &ms);
+    rc = run_walk(p, &o, perm, npos, P, 0, nbk, grid, &ms);
     if (rc) return rc;
     walk_ms += ms;
+    nnz_visited += nnz_next;
     rc = device_status(p);
     if (rc) return rc;
-    if (trace && (trace->q || trace->alpha || trace->Delta || trace->dF) && k * nb < trace->bundle_cap) {
-      const int64_t cnt = std::min<int64_t>(nb, trace->bundle_cap - k * nb);
-      if (trace->q) CUDA_TRY(cudaMemcpyAsync(trace->q + k * nb, p->tr_q, sizeof(int32_t) * cnt, cudaMemcpyDeviceToHost, p->stream));
-      if (trace->alpha) CUDA_TRY(cudaMemcpyAsync(trace->alpha + k * nb, p->tr_alpha, sizeof(double) * cnt, cudaMemcpyDeviceToHost, p->stream));
-      if (trace->Delta) CUDA_TRY(cudaMemcpyAsync(trace->Delta + k * nb, p->tr_Delta, sizeof(double) * cnt, cudaMemcpyDeviceToHost, p->stream));
-      if (trace->dF) CUDA_TRY(cudaMemcpyAsync(trace->dF + k * nb, p->tr_dF, sizeof(double) * cnt, cudaMemcpyDeviceToHost, p->stream));
+    if (trace && (trace->q || trace->alpha || trace->Delta || trace->dF) && tr_off < trace->bundle_cap) {
+      const int64_t cnt = std::min<int64_t>(nbk, trace->bundle_cap - tr_off);
+      if (trace->q) CUDA_TRY(cudaMemcpyAsync(trace->q + tr_off, p->tr_q, sizeof(int32_t) * cnt, cudaMemcpyDeviceToHost, p->stream));
+      if (trace->alpha) CUDA_TRY(cudaMemcpyAsync(trace->alpha + tr_off, p->tr_alpha, sizeof(double) * cnt, cudaMemcpyDeviceToHost, p->stream));
+      if (trace->Delta) CUDA_TRY(cudaMemcpyAsync(trace->Delta + tr_off, p->tr_Delta, sizeof(double) * cnt, cudaMemcpyDeviceToHost, p->stream));
+      if (trace->dF) CUDA_TRY(cudaMemcpyAsync(trace->dF + tr_off, p->tr_dF, sizeof(double) * cnt, cudaMemcpyDeviceToHost, p->stream));
     }
+    tr_off += nbk;
+    if (trace && trace->epoch_features && k < trace->epoch_cap) trace->epoch_features[k] = npos;
     if (o.refresh) {
       rc = do_refresh(p, prec, true, false);
       if (rc) return rc;
     }
-    rc = do_kkt(p, 1);
+    rc = do_kkt(p, 1, o.shrink != 0);
     if (rc) return rc;
+    unsigned long long act[2] = {0, 0};
+    if (o.shrink) CUDA_TRY(cudaMemcpyAsync(act, p->shr + 1, sizeof(act), cudaMemcpyDeviceToHost, p->stream));
     double kk = 0.0;
     rc = read_double(p, 1, &kk);
     if (rc) return rc;
@@ -1438,6 +1497,17 @@ int pcdn_solve(pcdn_problem* p, int32_t P, double eps, uint64_t seed, const pcdn
     kkt_rel = kref > 0 ? kk / kref : 0.0;
     if (trace && trace->epoch_kkt && k < trace->epoch_cap) trace->epoch_kkt[k] = kkt_rel;
     if (kkt_rel <= eps) converged = 1;
+    // an empty active set means v = 0 (every violating feature is active): the next outer
+    // iteration, if any, visits every feature
+    if (o.shrink && act[0] > 0) {
+      shrunk = true;
+      npos = (int64_t)act[0];
+      nnz_next = (int64_t)act[1];
+    } else {
+      shrunk = false;
+      npos = p->m;
+      nnz_next = p->nnz;
+    }
   }
   double F = 0.0;
   rc = do_objective(p, 0);
@@ -1458,7 +1528,7 @@ int pcdn_solve(pcdn_problem* p, int32_t P, double eps, uint64_t seed, const pcdn
     stats->ls_steps = (int64_t)cnt[0];
     stats->ls_cap_hits = (int64_t)cnt[1];
     stats->ls_passes = (int64_t)cnt[2];
-    stats->nnz_visited = epochs * p->nnz;
+    stats->nnz_visited = nnz_visited;
     stats->rows_touched = (int64_t)cnt[4];
     stats->kernel_launches = p->launches - launches0;
     stats->F_final = F;

@@ -648,23 +648,30 @@ __global__ void __launch_bounds__(kRedThreads) kkt_item_kernel(const Item* items
   }
 }
 
+// Per feature: g_j from its items' partial sums, v_j the minimum-norm subgradient; block sums of
+// |v_j|.  For shrinking, also g_j (g_out, by feature) and max_j |v_j| (vmax: the bits of a
+// non-negative double, whose order as unsigned integers is the order of the values).
 template <int PREC>
 __global__ void __launch_bounds__(kRedThreads) kkt_col_kernel(const int64_t* item_ptr, const int32_t* perm, int64_t npos,
                                                               const double* gpart, const double* w, double c,
-                                                              double* block_part) {
+                                                              double* block_part, double* g_out,
+                                                              unsigned long long* vmax) {
   __shared__ double red[kRedThreads];
-  double acc = 0.0;
+  double acc = 0.0, vm = 0.0;
   for (int64_t k = (int64_t)blockIdx.x * kRedThreads + threadIdx.x; k < npos; k += (int64_t)gridDim.x * kRedThreads) {
     double g = 0.0;
     for (int64_t i = item_ptr[k]; i < item_ptr[k + 1]; ++i)
       g += PREC == 0 ? gpart[i] : (double)reinterpret_cast<const float*>(gpart)[i];
     g *= c;
-    const double wj = w[perm[k]];
+    const int32_t j = perm[k];
+    const double wj = w[j];
     double v;
     if (wj > 0) v = g + 1.0;
     else if (wj < 0) v = g - 1.0;
     else v = fabs(g) > 1.0 ? (g > 0 ? g - 1.0 : g + 1.0) : 0.0;
     acc += fabs(v);
+    vm = fmax(vm, fabs(v));
+    if (g_out) g_out[j] = g;
   }
   red[threadIdx.x] = acc;
   __syncthreads();
@@ -673,6 +680,78 @@ __global__ void __launch_bounds__(kRedThreads) kkt_col_kernel(const int64_t* ite
     __syncthreads();
   }
   if (threadIdx.x == 0) block_part[blockIdx.x] = red[0];
+  if (vmax) {
+    __syncthreads();
+    red[threadIdx.x] = vm;
+    __syncthreads();
+    for (int o = kRedThreads / 2; o > 0; o >>= 1) {
+      if (threadIdx.x < o) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + o]);
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicMax(vmax, (unsigned long long)__double_as_longlong(red[0]));
+  }
+}
+
+// ------------------------------------------------------------------------------------ shrinking
+// Feature j takes part in the next outer iteration unless w_j = 0 and |g_j| < 1 - M / s (M the
+// largest |v_j|, s the number of samples): outer-iteration shrinking with LIBLINEAR's margin, from
+// the fresh gradient of the stopping test.
+__device__ __forceinline__ bool feature_active(double g, double wj, double bound) {
+  return wj != 0.0 || fabs(g) >= bound;
+}
+__device__ __forceinline__ double shrink_bound(const unsigned long long* vmax, int64_t n_samples) {
+  return 1.0 - __longlong_as_double((long long)*vmax) / (double)n_samples;
+}
+
+// out[0] += active features, out[1] += their nonzeros.
+__global__ void __launch_bounds__(kRedThreads) active_count_kernel(const double* g, const double* w, int64_t m,
+                                                                   const int64_t* col_ptr,
+                                                                   const unsigned long long* vmax, int64_t n_samples,
+                                                                   unsigned long long* out) {
+  __shared__ unsigned long long red[2][kRedThreads / 32];
+  const double bound = shrink_bound(vmax, n_samples);
+  unsigned long long cnt = 0, nz = 0;
+  for (int64_t j = (int64_t)blockIdx.x * kRedThreads + threadIdx.x; j < m; j += (int64_t)gridDim.x * kRedThreads) {
+    if (feature_active(g[j], w[j], bound)) {
+      ++cnt;
+      nz += (unsigned long long)(col_ptr[j + 1] - col_ptr[j]);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    nz += __shfl_xor_sync(0xffffffffu, nz, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = cnt;
+    red[1][threadIdx.x >> 5] = nz;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long a = 0, b = 0;
+    for (int i = 0; i < kRedThreads / 32; ++i) {
+      a += red[0][i];
+      b += red[1][i];
+    }
+    if (a) atomicAdd(out, a);
+    if (b) atomicAdd(out + 1, b);
+  }
+}
+
+// flags[k] = 1 when feature perm[k] is active (k < m), flags[m] = 0.
+__global__ void active_flags_kernel(const int32_t* perm, int64_t m, const double* g, const double* w,
+                                    const unsigned long long* vmax, int64_t n_samples, int64_t* flags) {
+  const double bound = shrink_bound(vmax, n_samples);
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k <= m; k += (int64_t)gridDim.x * blockDim.x) {
+    if (k == m) { flags[k] = 0; continue; }
+    const int32_t j = perm[k];
+    flags[k] = feature_active(g[j], w[j], bound) ? 1 : 0;
+  }
+}
+
+// The active features in partition order: out[pos[k]] = perm[k] for flagged k (a stable filter).
+__global__ void compact_kernel(const int32_t* perm, int64_t m, const int64_t* flags, const int64_t* pos, int32_t* out) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m; k += (int64_t)gridDim.x * blockDim.x)
+    if (flags[k]) out[pos[k]] = perm[k];
 }
 
 __global__ void abs_sum_kernel(const double* w, int64_t m, double* block_part) {
@@ -908,17 +987,37 @@ cudaError_t rec_from_mq(int loss, int prec, const double* mq, const int8_t* y, i
 
 cudaError_t kkt_l1(int prec, const Item* items, int64_t n_items, const int64_t* item_ptr, const int32_t* perm,
                    int64_t npos, const int32_t* row_idx, const float* val, const void* rec, const double* w, double c,
-                   double* gpart, double* block_part, int grid, double* out, cudaStream_t s, int64_t* launches) {
+                   double* gpart, double* block_part, int grid, double* out, cudaStream_t s, int64_t* launches,
+                   double* g_out, unsigned long long* vmax) {
   // the item pass writes one sum per item, no block partials: twice the blocks for more loads in flight
   if (prec == 0) kkt_item_kernel<0><<<2 * grid, kRedThreads, 0, s>>>(items, n_items, row_idx, val, rec, gpart);
   else kkt_item_kernel<1><<<2 * grid, kRedThreads, 0, s>>>(items, n_items, row_idx, val, rec, gpart);
   cudaError_t e = post(launches);
   if (e != cudaSuccess) return e;
-  if (prec == 0) kkt_col_kernel<0><<<grid, kRedThreads, 0, s>>>(item_ptr, perm, npos, gpart, w, c, block_part);
-  else kkt_col_kernel<1><<<grid, kRedThreads, 0, s>>>(item_ptr, perm, npos, gpart, w, c, block_part);
+  if (prec == 0) kkt_col_kernel<0><<<grid, kRedThreads, 0, s>>>(item_ptr, perm, npos, gpart, w, c, block_part, g_out, vmax);
+  else kkt_col_kernel<1><<<grid, kRedThreads, 0, s>>>(item_ptr, perm, npos, gpart, w, c, block_part, g_out, vmax);
   e = post(launches);
   if (e != cudaSuccess) return e;
   finish_sum_kernel<<<1, kRedThreads, 0, s>>>(block_part, grid, 1.0, nullptr, 0, out);
+  return post(launches);
+}
+
+cudaError_t active_count(const double* g, const double* w, int64_t m, const int64_t* col_ptr,
+                         const unsigned long long* vmax, int64_t n_samples, unsigned long long* out, cudaStream_t s,
+                         int64_t* launches) {
+  active_count_kernel<<<grid_for(m, kRedThreads, 1024), kRedThreads, 0, s>>>(g, w, m, col_ptr, vmax, n_samples, out);
+  return post(launches);
+}
+
+cudaError_t compact_active(const int32_t* perm, int64_t m, const double* g, const double* w,
+                           const unsigned long long* vmax, int64_t n_samples, int64_t* flags_ws, int64_t* pos_ws,
+                           int64_t* scan_ws, int32_t* out, cudaStream_t s, int64_t* launches) {
+  active_flags_kernel<<<grid_for(m + 1, 256), 256, 0, s>>>(perm, m, g, w, vmax, n_samples, flags_ws);
+  cudaError_t e = post(launches);
+  if (e != cudaSuccess) return e;
+  e = scan_exclusive(flags_ws, pos_ws, m + 1, scan_ws, s, launches);
+  if (e != cudaSuccess) return e;
+  compact_kernel<<<grid_for(m, 256), 256, 0, s>>>(perm, m, flags_ws, pos_ws, out);
   return post(launches);
 }
 

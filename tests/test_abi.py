@@ -171,3 +171,30 @@ def test_host_validation_of_a_large_csc_reports_the_first_bad_column(pk):
     with pytest.raises(pk.PcdnError) as ei:
         pk.pcdn_create(cp, ri, val, y, 1.0, "logistic")
     assert ei.value.code == pk.PCDN_EINVAL and "column 4999" in str(ei.value)
+
+
+STRUCTS = ["pcdn_csc", "pcdn_opts", "pcdn_stats", "pcdn_trace", "pcdn_batch_job", "pcdn_batch_opts",
+           "pcdn_batch_stats", "pcdn_server_opts", "pcdn_request_info"]
+
+
+def test_binding_structs_match_the_header_layout(pk, tmp_path):
+    """Every struct the binding mirrors has the header's size and field offsets (a C program built
+    against include/pcdn.h prints them)."""
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "pcdn.h"', "int main(void) {"]
+    for name in STRUCTS:
+        cls = getattr(pk, name)
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'  printf("{name} {fname} %zu\\n", offsetof({name}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    c_layout = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for name in STRUCTS:
+        cls = getattr(pk, name)
+        assert c_layout[(name, "size")] == ctypes.sizeof(cls), name
+        for fname, _ in cls._fields_:
+            assert c_layout[(name, fname)] == getattr(cls, fname).offset, (name, fname)
