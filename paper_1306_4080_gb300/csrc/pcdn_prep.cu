@@ -10,6 +10,8 @@
 //   objective: Eq. 1 from z.
 // Every reduction sums in a fixed order (lanes in a tree, warps and blocks in index order).
 
+#include <type_traits>
+
 #include "pcdn_prep.h"
 
 namespace pcdn {
@@ -631,17 +633,37 @@ __global__ void __launch_bounds__(kRedThreads) kkt_item_kernel(const Item* items
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t warps = (int64_t)gridDim.x * (kRedThreads / 32);
   const RecT<PREC>* rec = (const RecT<PREC>*)recp;
+  constexpr int U = 4;  // entries per lane in flight: U index/value loads, then U gathers
   for (int64_t i = (int64_t)blockIdx.x * (kRedThreads / 32) + wid; i < n_items; i += warps) {
     const Item it = items[i];
+    const int64_t end = it.start + it.len;
+    // each lane sums its entries e = start + lane, + 32, ... in that order
+    using Acc = typename std::conditional<PREC == 0, double, float>::type;
+    Acc acc = Acc(0);
+    for (int64_t e0 = it.start + lane; e0 < end; e0 += 32 * U) {
+      int32_t r[U];
+      float v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t e = e0 + 32 * u;
+        r[u] = e < end ? row_idx[e] : -1;
+        v[u] = e < end ? val[e] : 0.0f;
+      }
+      Acc cg[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) cg[u] = r[u] >= 0 ? (Acc)rec[r[u]].cg : Acc(0);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (r[u] < 0) break;
+        if constexpr (PREC == 0) acc = fma((double)v[u], cg[u], acc);
+        else acc = fmaf(v[u], cg[u], acc);
+      }
+    }
     if constexpr (PREC == 0) {
-      double acc = 0.0;
-      for (int64_t e = it.start + lane; e < it.start + it.len; e += 32) acc = fma((double)val[e], rec[row_idx[e]].cg, acc);
       const double g = warp_sum(acc);
       if (lane == 0) gpart[i] = g;
     } else {
       // FP32 sums (this mode's column sums), stored as float; the column kernel widens them
-      float acc = 0.0f;
-      for (int64_t e = it.start + lane; e < it.start + it.len; e += 32) acc = fmaf(val[e], rec[row_idx[e]].cg, acc);
       acc = warp_sum_f(acc);
       if (lane == 0) reinterpret_cast<float*>(gpart)[i] = acc;
     }
@@ -658,10 +680,31 @@ __global__ void __launch_bounds__(kRedThreads) kkt_col_kernel(const int64_t* ite
                                                               unsigned long long* vmax) {
   __shared__ double red[kRedThreads];
   double acc = 0.0, vm = 0.0;
-  for (int64_t k = (int64_t)blockIdx.x * kRedThreads + threadIdx.x; k < npos; k += (int64_t)gridDim.x * kRedThreads) {
+  const int lane = threadIdx.x & 31;
+  auto part = [&](int64_t i) { return PREC == 0 ? gpart[i] : (double)reinterpret_cast<const float*>(gpart)[i]; };
+  // a thread per feature; a feature of more than kLongItems items (a Zipf head column cut into
+  // thousands of chunks) is summed by its whole warp, lane-strided and then a fixed butterfly
+  constexpr int64_t kLongItems = 64;
+  const int64_t stride = (int64_t)gridDim.x * kRedThreads;
+  for (int64_t base = (int64_t)blockIdx.x * kRedThreads + (threadIdx.x & ~31); base < npos; base += stride) {
+    const int64_t k = base + lane;
+    const bool valid = k < npos;
+    const int64_t i0 = valid ? item_ptr[k] : 0, i1 = valid ? item_ptr[k + 1] : 0;
+    const bool long_col = i1 - i0 > kLongItems;
     double g = 0.0;
-    for (int64_t i = item_ptr[k]; i < item_ptr[k + 1]; ++i)
-      g += PREC == 0 ? gpart[i] : (double)reinterpret_cast<const float*>(gpart)[i];
+    if (!long_col)
+      for (int64_t i = i0; i < i1; ++i) g += part(i);
+    uint32_t lm = __ballot_sync(0xffffffffu, long_col);
+    while (lm) {
+      const int src = __ffs(lm) - 1;
+      lm &= lm - 1;
+      const int64_t a = __shfl_sync(0xffffffffu, i0, src), b = __shfl_sync(0xffffffffu, i1, src);
+      double sl = 0.0;
+      for (int64_t i = a + lane; i < b; i += 32) sl += part(i);
+      sl = warp_sum(sl);
+      if (lane == src) g = sl;
+    }
+    if (!valid) continue;
     g *= c;
     const int32_t j = perm[k];
     const double wj = w[j];
