@@ -563,6 +563,15 @@ int do_refresh(pcdn_problem* p, int prec, bool write_state, bool with_loss) {
 }
 
 // ||v||_1 into red_out[slot] (device); the caller copies.
+// The maintained quantities at a solve's start point: a cold start (w = 0) has z = 0, so they are
+// set directly (the values a refresh from z = Xw gives there, bit for bit) without the pass over X.
+int start_state(pcdn_problem* p, int prec, bool cold) {
+  if (!cold) return do_refresh(p, prec, true, false);
+  CUDA_TRY(state_at_zero(p->loss, prec, p->y, p->n, p->mq, p->rec, p->stream, &p->launches));
+  p->rec_prec = prec;
+  return PCDN_OK;
+}
+
 // ||v||_1 into red_out[slot]; with shrink also g_j of every feature, max |v_j| and the count and
 // nonzeros of the features active in the next outer iteration (p->shr).
 int do_kkt(pcdn_problem* p, int slot, bool shrink = false) {
@@ -1018,7 +1027,7 @@ int task_start(SolveTask* t, pcdn_problem* p, int32_t P, double eps, uint64_t se
       (e = cudaMemsetAsync(p->counters, 0, sizeof(unsigned long long) * 8, p->stream)) != cudaSuccess ||
       (e = cudaMemsetAsync(p->epoch_dev, 0, sizeof(int64_t), p->stream)) != cudaSuccess)
     return end_task(t, fail(PCDN_ECUDA, "solve set-up: %s", cudaGetErrorString(e)));
-  if ((rc = do_refresh(p, (int)o.prec, true, false)) || (rc = do_kkt(p, 2))) return end_task(t, rc);
+  if ((rc = start_state(p, (int)o.prec, !o.warm_start)) || (rc = do_kkt(p, 2))) return end_task(t, rc);
   t->stage = kStageStart;
   rc = post(t, 2, false);
   if (rc) return end_task(t, rc);
@@ -1435,7 +1444,7 @@ int pcdn_solve(pcdn_problem* p, int32_t P, double eps, uint64_t seed, const pcdn
   if (!o.warm_start) CUDA_TRY(cudaMemsetAsync(p->w, 0, sizeof(double) * p->m, p->stream));
   CUDA_TRY(cudaMemsetAsync(p->err, 0, sizeof(int), p->stream));
   CUDA_TRY(cudaMemsetAsync(p->counters, 0, sizeof(unsigned long long) * 8, p->stream));
-  rc = do_refresh(p, prec, true, false);
+  rc = start_state(p, prec, !o.warm_start);
   if (rc) return rc;
   rc = do_kkt(p, 2);
   if (rc) return rc;

@@ -626,6 +626,16 @@ __global__ void rec_from_mq_kernel(const double* mq, const int8_t* y, int64_t n,
     ((RecT<PREC>*)rec)[i] = RowCoef<LOSS, PREC>::make(mq[i], y[i]);
 }
 
+// At w = 0: z = 0, so E = e^0 = 1 (logistic) and b = 1 - y 0 = 1 (L2-SVM), exactly what a refresh
+// from z = Xw gives there.
+template <int LOSS, int PREC>
+__global__ void state_at_zero_kernel(const int8_t* y, int64_t n, double* mq, void* rec) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    mq[i] = 1.0;
+    ((RecT<PREC>*)rec)[i] = RowCoef<LOSS, PREC>::make(1.0, y[i]);
+  }
+}
+
 // ------------------------------------------------------------------------------------ KKT
 template <int PREC>
 __global__ void __launch_bounds__(kRedThreads) kkt_item_kernel(const Item* items, int64_t n_items, const int32_t* row_idx,
@@ -1025,6 +1035,16 @@ cudaError_t rec_from_mq(int loss, int prec, const double* mq, const int8_t* y, i
   else if (loss == 0) rec_from_mq_kernel<0, 1><<<g, 256, 0, s>>>(mq, y, n, rec);
   else if (prec == 0) rec_from_mq_kernel<1, 0><<<g, 256, 0, s>>>(mq, y, n, rec);
   else rec_from_mq_kernel<1, 1><<<g, 256, 0, s>>>(mq, y, n, rec);
+  return post(launches);
+}
+
+cudaError_t state_at_zero(int loss, int prec, const int8_t* y, int64_t n, double* mq, void* rec, cudaStream_t s,
+                          int64_t* launches) {
+  const unsigned g = grid_for(n, 256);
+  if (loss == 0 && prec == 0) state_at_zero_kernel<0, 0><<<g, 256, 0, s>>>(y, n, mq, rec);
+  else if (loss == 0) state_at_zero_kernel<0, 1><<<g, 256, 0, s>>>(y, n, mq, rec);
+  else if (prec == 0) state_at_zero_kernel<1, 0><<<g, 256, 0, s>>>(y, n, mq, rec);
+  else state_at_zero_kernel<1, 1><<<g, 256, 0, s>>>(y, n, mq, rec);
   return post(launches);
 }
 

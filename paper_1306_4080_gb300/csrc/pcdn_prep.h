@@ -79,6 +79,9 @@ cudaError_t refresh(int loss, int prec, const int64_t* row_ptr, const int32_t* c
                     const int8_t* y, const double* w, int64_t n, int64_t m, int64_t nnz, void* w2_scratch,
                     double* mq, void* rec, bool write_state, double* loss_part, int grid, int* err, cudaStream_t s,
                     int64_t* launches);
+// The maintained quantities and coefficients at w = 0 (mq = 1 for both losses), without reading X.
+cudaError_t state_at_zero(int loss, int prec, const int8_t* y, int64_t n, double* mq, void* rec, cudaStream_t s,
+                          int64_t* launches);
 // rec from the current mq (precision switch without recomputing z).
 cudaError_t rec_from_mq(int loss, int prec, const double* mq, const int8_t* y, int64_t n, void* rec, cudaStream_t s,
                         int64_t* launches);
