@@ -74,7 +74,8 @@ def omp_threads() -> int:
 class _Problem(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("m", ctypes.c_int64),
                 ("col_ptr", ctypes.c_void_p), ("row_idx", ctypes.c_void_p), ("val", ctypes.c_void_p),
-                ("y", ctypes.c_void_p), ("c", ctypes.c_double), ("loss", ctypes.c_int)]
+                ("y", ctypes.c_void_p), ("c", ctypes.c_double), ("loss", ctypes.c_int),
+                ("l1", ctypes.c_double), ("l2", ctypes.c_double)]
 
 
 class _Armijo(ctypes.Structure):
@@ -110,6 +111,8 @@ def _load(path: str | None = None):
             lib.or_grad_hess.restype = None
             lib.or_direction.argtypes = [d, d, d]
             lib.or_direction.restype = d
+            lib.or_direction_l1.argtypes = [d, d, d, d]
+            lib.or_direction_l1.restype = d
             lib.or_kkt_l1.argtypes = [P(_Problem), vp, vp, d]
             lib.or_kkt_l1.restype = d
             lib.or_bundle_step.argtypes = [P(_Problem), P(_Armijo), vp, vp, vp, i64, i32,
@@ -147,9 +150,11 @@ class Armijo:
 
 
 class Oracle:
-    """FP64 oracle bound to one problem (X in CSC, labels y, weight c, loss)."""
+    """FP64 oracle bound to one problem (X in CSC, labels y, weight c, loss; penalty
+    l1 ||w||_1 + (l2/2) ||w||^2, the paper's l1 = 1, l2 = 0 by default)."""
 
-    def __init__(self, col_ptr, row_idx, val, y, c: float, loss: str, lib_path: str | None = None):
+    def __init__(self, col_ptr, row_idx, val, y, c: float, loss: str, lib_path: str | None = None,
+                 l1: float = 1.0, l2: float = 0.0):
         self.lib = _load(lib_path)
         self.col_ptr = np.ascontiguousarray(col_ptr, dtype=np.int64)
         self.row_idx = np.ascontiguousarray(row_idx, dtype=np.int32)
@@ -159,12 +164,14 @@ class Oracle:
         self.m = int(self.col_ptr.shape[0] - 1)
         self.c = float(c)
         self.loss = loss
+        self.l1, self.l2 = float(l1), float(l2)
         self._p = _Problem(self.n, self.m, _ptr(self.col_ptr), _ptr(self.row_idx), _ptr(self.val), _ptr(self.y),
-                           self.c, LOSSES[loss])
+                           self.c, LOSSES[loss], self.l1, self.l2)
 
     @classmethod
-    def from_problem(cls, prob, c: float, loss: str, lib_path: str | None = None) -> "Oracle":
-        return cls(prob.col_ptr, prob.row_idx, prob.val, prob.y, c, loss, lib_path)
+    def from_problem(cls, prob, c: float, loss: str, lib_path: str | None = None, l1: float = 1.0,
+                     l2: float = 0.0) -> "Oracle":
+        return cls(prob.col_ptr, prob.row_idx, prob.val, prob.y, c, loss, lib_path, l1=l1, l2=l2)
 
     # -- pieces -------------------------------------------------------------------------
     def objective(self, w) -> float:
@@ -303,5 +310,8 @@ def splitmix64_output(s0: int, k: int) -> int:
     return int(_load().or_splitmix64_output(int(s0) & (2**64 - 1), int(k)))
 
 
-def direction(g: float, h: float, w: float, lib_path: str | None = None) -> float:
-    return float(_load(lib_path).or_direction(float(g), float(h), float(w)))
+def direction(g: float, h: float, w: float, lib_path: str | None = None, l1: float | None = None) -> float:
+    """argmin_d g d + h d^2/2 + l1 |w + d| (Eq. 5; l1 = 1 unless given)."""
+    if l1 is None:
+        return float(_load(lib_path).or_direction(float(g), float(h), float(w)))
+    return float(_load(lib_path).or_direction_l1(float(g), float(h), float(w), float(l1)))

@@ -169,6 +169,7 @@ int or_omp_threads(void) { return omp_get_max_threads(); }
 int or_solve_omp(const or_problem* p, const or_armijo* ar, int64_t P, double eps, uint64_t seed, int64_t max_epochs,
                  int64_t bundle_limit, double* w, or_stats* st) {
   if (!p || !ar || !w || !st || P < 1 || P > p->m || !(eps > 0)) return OR_EINVAL;
+  if (p->l1 != 1.0 || p->l2 != 0.0) return OR_EINVAL; /* the paper's penalty only */
   memset(st, 0, sizeof(*st));
   const size_t n1 = (size_t)(p->n > 0 ? p->n : 1);
   double* mq = (double*)malloc(sizeof(double) * n1);

@@ -37,6 +37,14 @@
  *     after each outer iteration the maintained quantities are recomputed
  *     from z = Xw, and the solve stops once the l1 norm of the minimum-norm
  *     subgradient is at most eps times its value at w = 0.
+ *   - Separable regularisers (the concluding remarks: a convex twice-
+ *     differentiable loss plus a separable penalty, covering L1, L2 and
+ *     their mixture): F(w) = c sum_i phi + l1 ||w||_1 + (l2/2) ||w||_2^2
+ *     with l1, l2 >= 0 (the paper's problem: l1 = 1, l2 = 0).  The smooth
+ *     part's gradient and Hessian diagonal are g + l2 w and h + l2 (h after
+ *     the nu rule); the direction minimises the model of Eq. 4 with l1 |.|;
+ *     Delta (Eq. 7) takes the smooth part's g and h and l1 times the L1
+ *     change; the line search adds (l2/2)(||w + a d||^2 - ||w||^2).
  *   - Shrinking (Section 5.1 says only that the comparison's shrinking runs
  *     outside the parallel loop): optional, between outer iterations.  The
  *     first outer iteration of a solve visits every feature; outer iteration
@@ -73,6 +81,7 @@ typedef struct {
   const int8_t* y;        /* [n], +1 / -1 */
   double c;               /* loss weight c > 0 of Eq. 1 */
   int loss;               /* OR_LOSS_* */
+  double l1, l2;          /* penalty l1 ||w||_1 + (l2/2) ||w||^2 (Eq. 1: l1 = 1, l2 = 0) */
 } or_problem;
 
 typedef struct {
@@ -154,9 +163,11 @@ double or_objective(const or_problem* p, const double* w) {
     }
   }
   free(z);
-  double r = 0.0;
+  double r = 0.0, q = 0.0;
   for (int64_t j = 0; j < p->m; ++j) r += fabs(w[j]);
-  return p->c * L + r;
+  if (p->l2 != 0.0)
+    for (int64_t j = 0; j < p->m; ++j) q += w[j] * w[j];
+  return p->c * L + p->l1 * r + 0.5 * p->l2 * q;
 }
 
 /* Maintained per-sample quantity from w (Section 3.1): e^{w^T x_i} for the
@@ -205,10 +216,37 @@ void or_grad_hess(const or_problem* p, const double* mq, int64_t j, double nu, d
 
 /* argmin_d  g d + h d^2 / 2 + |w + d|   (Eq. 4, closed form Eq. 5 with the
  * +/-1 terms in the branch conditions) */
-double or_direction(double g, double h, double w) {
-  if (g + 1.0 <= h * w) return -(g + 1.0) / h;
-  if (g - 1.0 >= h * w) return -(g - 1.0) / h;
+double or_direction_l1(double g, double h, double w, double l1) {
+  if (g + l1 <= h * w) return -(g + l1) / h;
+  if (g - l1 >= h * w) return -(g - l1) / h;
   return -w;
+}
+
+double or_direction(double g, double h, double w) { return or_direction_l1(g, h, w, 1.0); }
+
+/* Gradient and Hessian diagonal of the smooth part c L(w) + (l2/2)||w||^2 at
+ * feature j (the loss's after the nu rule, plus l2 w_j and l2). */
+static void smooth_grad_hess(const or_problem* p, const double* mq, int64_t j, double nu, double wj, double* g,
+                             double* h) {
+  or_grad_hess(p, mq, j, nu, g, h);
+  if (p->l2 != 0.0) {
+    *g += p->l2 * wj;
+    *h += p->l2;
+  }
+}
+
+/* Minimum-norm subgradient of the penalised objective at one feature. */
+static double min_norm_v(double g, double wj, double l1) {
+  if (wj > 0) return g + l1;
+  if (wj < 0) return g - l1;
+  return fabs(g) > l1 ? (g > 0 ? g - l1 : g + l1) : 0.0;
+}
+
+/* Change of the penalty of one feature when w_j moves by t. */
+static double penalty_change(const or_problem* p, double wj, double t) {
+  double r = p->l1 * (fabs(wj + t) - fabs(wj));
+  if (p->l2 != 0.0) r += 0.5 * p->l2 * ((wj + t) * (wj + t) - wj * wj);
+  return r;
 }
 
 /* Minimum-norm subgradient of F at w, l1 norm, with the gradient recomputed
@@ -217,12 +255,8 @@ double or_kkt_l1(const or_problem* p, const double* w, const double* mq, double 
   double s = 0.0;
   for (int64_t j = 0; j < p->m; ++j) {
     double g, h;
-    or_grad_hess(p, mq, j, nu, &g, &h);
-    double v;
-    if (w[j] > 0) v = g + 1.0;
-    else if (w[j] < 0) v = g - 1.0;
-    else v = fabs(g) > 1.0 ? (g > 0 ? g - 1.0 : g + 1.0) : 0.0;
-    s += fabs(v);
+    smooth_grad_hess(p, mq, j, nu, w[j], &g, &h);
+    s += fabs(min_norm_v(g, w[j], p->l1));
   }
   return s;
 }
@@ -285,8 +319,8 @@ int or_bundle_step(const or_problem* p, const or_armijo* ar, double* w, double* 
   int any = 0;
   for (int64_t k = 0; k < P; ++k) {
     int64_t j = bundle[k];
-    or_grad_hess(p, mq, j, ar->nu, &g[k], &h[k]);
-    d[k] = or_direction(g[k], h[k], w[j]);
+    smooth_grad_hess(p, mq, j, ar->nu, w[j], &g[k], &h[k]);
+    d[k] = or_direction_l1(g[k], h[k], w[j], p->l1);
     if (d[k] != 0.0) any = 1;
   }
   /* Delta = grad^T d + gamma d^T H d + ||w + d||_1 - ||w||_1   (Eq. 7) */
@@ -297,7 +331,7 @@ int or_bundle_step(const or_problem* p, const or_armijo* ar, double* w, double* 
       int64_t j = bundle[k];
       lin += g[k] * d[k];
       quad += h[k] * d[k] * d[k];
-      l1 += fabs(w[j] + d[k]) - fabs(w[j]);
+      l1 += p->l1 * (fabs(w[j] + d[k]) - fabs(w[j]));
     }
     Delta = lin + ar->gamma * quad + l1;
   }
@@ -332,10 +366,7 @@ int or_bundle_step(const or_problem* p, const or_armijo* ar, double* w, double* 
         for (int64_t i = 0; i < p->n; ++i)
           if (dx[i] != 0.0) Ls += row_loss_change(p, mq[i], p->y[i], a * dx[i]);
         double r = 0.0;
-        for (int64_t k = 0; k < P; ++k) {
-          int64_t j = bundle[k];
-          r += fabs(w[j] + a * d[k]) - fabs(w[j]);
-        }
+        for (int64_t k = 0; k < P; ++k) r += penalty_change(p, w[bundle[k]], a * d[k]);
         dF = p->c * Ls + r;
       }
       if (dF <= ar->sigma * a * Delta) { accepted = 1; break; }
@@ -372,7 +403,8 @@ int or_bundle_step(const or_problem* p, const or_armijo* ar, double* w, double* 
 }
 
 /* Active set for shrinking (reading above): active[j] = 1 unless w_j = 0 and
- * |g_j| < 1 - M / s, M = max_j |v_j| with v the minimum-norm subgradient.
+ * |g_j| < l1 - M / s (the reading's bound 1 - M / s for the paper's penalty),
+ * g the smooth part's gradient, M = max_j |v_j| with v the minimum-norm subgradient.
  * Returns the number of active features; *M_out gets M. */
 int64_t or_active_set(const or_problem* p, const double* w, const double* mq, double nu, uint8_t* active,
                       double* M_out) {
@@ -381,14 +413,11 @@ int64_t or_active_set(const or_problem* p, const double* w, const double* mq, do
   double M = 0.0;
   for (int64_t j = 0; j < p->m; ++j) {
     double h;
-    or_grad_hess(p, mq, j, nu, &g[j], &h);
-    double v;
-    if (w[j] > 0) v = g[j] + 1.0;
-    else if (w[j] < 0) v = g[j] - 1.0;
-    else v = fabs(g[j]) > 1.0 ? (g[j] > 0 ? g[j] - 1.0 : g[j] + 1.0) : 0.0;
+    smooth_grad_hess(p, mq, j, nu, w[j], &g[j], &h);
+    const double v = min_norm_v(g[j], w[j], p->l1);
     if (fabs(v) > M) M = fabs(v);
   }
-  const double bound = 1.0 - M / (double)p->n;
+  const double bound = p->l1 - M / (double)p->n;
   int64_t count = 0;
   for (int64_t j = 0; j < p->m; ++j) {
     active[j] = (w[j] != 0.0 || fabs(g[j]) >= bound) ? 1 : 0;
@@ -489,11 +518,11 @@ int or_cdn_epoch(const or_problem* p, const or_armijo* ar, uint64_t seed, int64_
   for (int64_t t = 0; t < p->m; ++t) {
     int64_t j = perm[t];
     double g, h;
-    or_grad_hess(p, mq, j, ar->nu, &g, &h);
-    double d = or_direction(g, h, w[j]);
+    smooth_grad_hess(p, mq, j, ar->nu, w[j], &g, &h);
+    double d = or_direction_l1(g, h, w[j], p->l1);
     if (d == 0.0) continue;
     /* same operation order as the bundle step with P = 1 */
-    double Delta = (g * d + ar->gamma * (h * d * d)) + (fabs(w[j] + d) - fabs(w[j]));
+    double Delta = (g * d + ar->gamma * (h * d * d)) + p->l1 * (fabs(w[j] + d) - fabs(w[j]));
     double a = 1.0;
     int ok = 0;
     for (int q = 0; q < ar->q_max; ++q) {
@@ -503,7 +532,7 @@ int or_cdn_epoch(const or_problem* p, const or_armijo* ar, uint64_t seed, int64_
         double dx = d * (double)p->val[e];
         if (dx != 0.0) Ls += row_loss_change(p, mq[i], p->y[i], a * dx);
       }
-      double dF = p->c * Ls + (fabs(w[j] + a * d) - fabs(w[j]));
+      double dF = p->c * Ls + penalty_change(p, w[j], a * d);
       if (dF <= ar->sigma * a * Delta) { ok = 1; break; }
       a *= ar->beta;
     }

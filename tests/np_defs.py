@@ -44,6 +44,22 @@ def F(X, y, w, c, loss) -> float:
     return L(X, y, w, c, loss) + float(np.abs(w).sum())
 
 
+def F_pen(X, y, w, c, loss, l1=1.0, l2=0.0) -> float:
+    """c * sum_i phi + l1 ||w||_1 + (l2/2) ||w||_2^2 (a separable penalty: L1, L2 or both)."""
+    return L(X, y, w, c, loss) + l1 * float(np.abs(w).sum()) + 0.5 * l2 * float(w @ w)
+
+
+def fd_grad_smooth(X, y, w, c, loss, j, l2, eps=1e-5) -> float:
+    """Central difference of the smooth part c L(w) + (l2/2) ||w||^2 along e_j."""
+    e = np.zeros_like(w)
+    e[j] = eps
+
+    def S(v):
+        return L(X, y, v, c, loss) + 0.5 * l2 * float(v @ v)
+
+    return (S(w + e) - S(w - e)) / (2 * eps)
+
+
 def fd_grad(X, y, w, c, loss, j, eps=1e-5) -> float:
     e = np.zeros_like(w)
     e[j] = eps
@@ -80,23 +96,24 @@ def grad(X, y, w, c, loss) -> np.ndarray:
     return c * np.asarray(X.T @ s).ravel()
 
 
-def fista(X, y, c, loss, iters=200000, tol=1e-13):
-    """FISTA with constant step 1/Lip for min L(w) + ||w||_1 (Beck and Teboulle 2009), with the
-    gradient-based adaptive restart of O'Donoghue and Candes (2015)."""
+def fista(X, y, c, loss, iters=200000, tol=1e-13, l1=1.0, l2=0.0):
+    """FISTA with constant step 1/Lip for min L(w) + l1 ||w||_1 + (l2/2) ||w||^2 (Beck and Teboulle
+    2009; the L2 term in the smooth part), with the gradient-based adaptive restart of O'Donoghue
+    and Candes (2015)."""
     n, m = X.shape
     theta = 0.25 if loss == "logistic" else 2.0
-    lip = theta * c * np.linalg.norm(X, 2) ** 2
+    lip = theta * c * np.linalg.norm(X, 2) ** 2 + l2
     step = 1.0 / lip
 
     def grad_w(w):
-        return grad(X, y, w, c, loss)
+        return grad(X, y, w, c, loss) + l2 * w
 
     w = np.zeros(m)
     v = w.copy()
     t = 1.0
     for it in range(iters):
         u = v - step * grad_w(v)
-        w_new = np.sign(u) * np.maximum(np.abs(u) - step, 0.0)
+        w_new = np.sign(u) * np.maximum(np.abs(u) - step * l1, 0.0)
         if float(np.dot(v - w_new, w_new - w)) > 0:
             t = 1.0
         t_new = 0.5 * (1 + math.sqrt(1 + 4 * t * t))
@@ -108,17 +125,17 @@ def fista(X, y, c, loss, iters=200000, tol=1e-13):
     return w
 
 
-def min_norm_subgradient(g: np.ndarray, w: np.ndarray) -> np.ndarray:
-    """g_j + s with s minimising |g_j + s| over the subdifferential of |w_j| ({sign w_j}, or [-1, 1]
-    at w_j = 0), the latter by ternary search."""
+def min_norm_subgradient(g: np.ndarray, w: np.ndarray, l1: float = 1.0) -> np.ndarray:
+    """g_j + s with s minimising |g_j + s| over the subdifferential of l1 |w_j| ({l1 sign w_j}, or
+    [-l1, l1] at w_j = 0), the latter by ternary search."""
     out = np.empty_like(g)
     for j in range(g.shape[0]):
         if w[j] > 0:
-            out[j] = g[j] + 1.0
+            out[j] = g[j] + l1
         elif w[j] < 0:
-            out[j] = g[j] - 1.0
+            out[j] = g[j] - l1
         else:
-            s = ternary_min(lambda t, gj=g[j]: abs(gj + t), -1.0, 1.0, iters=200)
+            s = ternary_min(lambda t, gj=g[j]: abs(gj + t), -l1, l1, iters=200) if l1 > 0 else 0.0
             out[j] = g[j] + s
     return out
 

@@ -12,11 +12,12 @@ import pytest
 
 import oracle
 from tests import test_oracle as T
+from tests import test_oracle_penalty as Q
 from tests import test_oracle_shrink as S
 
 MUTANTS = [
     # Eq. 5 exactly as printed (conditions without the +/-1 terms)
-    ("eq5_as_printed", "if (g + 1.0 <= h * w) return -(g + 1.0) / h;", "if (g <= h * w) return -(g + 1.0) / h;"),
+    ("eq5_as_printed", "if (g + l1 <= h * w) return -(g + l1) / h;", "if (g <= h * w) return -(g + l1) / h;"),
     ("grad_sign", "g += (tau - 1.0) * y * x;", "g += (1.0 - tau) * y * x;"),
     ("hess_power", "h += tau * (1.0 - tau) * x * x;", "h += tau * (1.0 - tau) * x;"),
     ("svm_hess_factor", "h += 2.0 * x * x;", "h += x * x;"),
@@ -29,8 +30,8 @@ MUTANTS = [
     ("lr_label_term", "return log1p(expm1(-u) / (1.0 + E)) + (y_i < 0 ? u : 0.0);",
      "return log1p(expm1(-u) / (1.0 + E)) + (y_i > 0 ? u : 0.0);"),
     ("dx_overwrites", "dx[p->row_idx[e]] += d[k] * (double)p->val[e];", "dx[p->row_idx[e]] = d[k] * (double)p->val[e];"),
-    ("kkt_branch_swap", "else v = fabs(g) > 1.0 ? (g > 0 ? g - 1.0 : g + 1.0) : 0.0;",
-     "else v = fabs(g) > 1.0 ? (g > 0 ? g + 1.0 : g - 1.0) : 0.0;"),
+    ("kkt_branch_swap", "return fabs(g) > l1 ? (g > 0 ? g - l1 : g + l1) : 0.0;",
+     "return fabs(g) > l1 ? (g > 0 ? g + l1 : g - l1) : 0.0;"),
     ("refresh_sign", "mq[i] = (p->loss == OR_LOSS_LOGISTIC) ? exp(z[i]) : 1.0 - (double)p->y[i] * z[i];",
      "mq[i] = (p->loss == OR_LOSS_LOGISTIC) ? exp(-z[i]) : 1.0 - (double)p->y[i] * z[i];"),
     ("perm_key_index", "return or_splitmix64_output(s_epoch, (uint64_t)j + 1);",
@@ -39,10 +40,15 @@ MUTANTS = [
     # Eq. 10's log-ratio taken literally for every sample (cancels at large margins)
     ("eq10_literal", "      if (E <= 1.0) return log1p(E / (1.0 + E) * expm1(u)) - (y_i > 0 ? u : 0.0);\n", ""),
     # shrinking: the margin's sign, the w_j != 0 condition, the partition order of the active set
-    ("shrink_margin_sign", "const double bound = 1.0 - M / (double)p->n;", "const double bound = 1.0 + M / (double)p->n;"),
+    ("shrink_margin_sign", "const double bound = p->l1 - M / (double)p->n;", "const double bound = p->l1 + M / (double)p->n;"),
     ("shrink_drops_nonzero_w", "active[j] = (w[j] != 0.0 || fabs(g[j]) >= bound) ? 1 : 0;",
      "active[j] = (fabs(g[j]) >= bound) ? 1 : 0;"),
     ("shrink_filter_index", "if (active[perm[t]]) perm[npos++] = perm[t];", "if (active[t]) perm[npos++] = perm[t];"),
+    # the separable penalty: its L2 part left out of the line search, of the Hessian diagonal, its L1
+    # weight left out of Delta
+    ("pen_ls_drops_l2", "if (p->l2 != 0.0) r += 0.5 * p->l2 * ((wj + t) * (wj + t) - wj * wj);", ""),
+    ("pen_hess_drops_l2", "    *h += p->l2;\n", ""),
+    ("pen_delta_l1_weight", "l1 += p->l1 * (fabs(w[j] + d[k]) - fabs(w[j]));", "l1 += fabs(w[j] + d[k]) - fabs(w[j]);"),
 ]
 
 
@@ -78,6 +84,9 @@ def _pins():
         ("shrink_active", lambda: S.test_active_set_from_an_independent_gradient(*S.CASES[0])),
         ("shrink_random", lambda: S.test_active_set_at_random_points(*S.CASES[0])),
         ("shrink_order", lambda: S.test_shrunk_outer_iteration_is_the_restricted_partition(*S.CASES[0])),
+        ("pen_step", lambda: Q.test_full_bundle_step_is_the_penalised_proximal_newton_step("logistic", 0.3, 2.0)),
+        ("pen_ls", lambda: Q.test_penalised_line_search_equals_direct("logistic", 1.0, 0.5)),
+        ("pen_kkt", lambda: Q.test_kkt_is_the_penalised_min_norm_subgradient("l2svm", 0.3, 2.0)),
     ]
     return out
 
