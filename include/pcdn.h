@@ -165,9 +165,19 @@ int pcdn_set_w(pcdn_problem* prob, const double* w);
  * (neither depends on c), so a following pcdn_solve with opts.warm_start = 1 continues from the
  * current w: one step of a warm-started regularisation path.  Errors: PCDN_EINVAL. */
 int pcdn_set_C(pcdn_problem* prob, double C);
+/* Separable penalty (the concluding remarks' generalisation to a convex twice-differentiable loss
+ * plus a separable regulariser): the problem becomes
+ *   min_w  c sum_i phi(w; x_i, y_i) + l1 ||w||_1 + (l2/2) ||w||_2^2,
+ * L1 (the paper's problem, l1 = 1, l2 = 0: the default), ridge (l1 = 0) or elastic net.  Every
+ * step uses the smooth part's gradient g + l2 w and Hessian diagonal h + l2; the direction is Eq. 5
+ * with l1 in place of 1; Delta (Eq. 7) takes l1 times the L1 change; the line search adds the
+ * penalty's change; pcdn_objective, pcdn_kkt and the stopping test use the penalised objective
+ * (shrinking's bound becomes l1 - M/n_samples).  w and the maintained quantities are kept.
+ * Errors: PCDN_EINVAL (l1 or l2 negative or not finite, both zero). */
+int pcdn_set_penalty(pcdn_problem* prob, double l1, double l2);
 /* Copy the current w to the host (n_features entries). */
 int pcdn_get_w(pcdn_problem* prob, double* w);
-/* Objective F(w) (Eq. 1) at the current w, from z = Xw. */
+/* Objective F(w) (Eq. 1, with the problem's penalty) at the current w, from z = Xw. */
 int pcdn_objective(pcdn_problem* prob, double* F);
 /* ||v(w)||_1 of the minimum-norm subgradient at the current w (fresh gradient). */
 int pcdn_kkt(pcdn_problem* prob, double* kkt_l1);

@@ -31,7 +31,7 @@ PRECISIONS = {"fp64": 0, "mixed": 1}
 
 SYMBOLS = ["pcdn_default_opts", "pcdn_create", "pcdn_create_device", "pcdn_solve", "pcdn_bundle_step",
            "pcdn_set_w", "pcdn_get_w", "pcdn_objective", "pcdn_kkt", "pcdn_permutation", "pcdn_memory",
-           "pcdn_destroy", "pcdn_last_error", "pcdn_objective_noalloc", "pcdn_set_C",
+           "pcdn_destroy", "pcdn_last_error", "pcdn_objective_noalloc", "pcdn_set_C", "pcdn_set_penalty",
            "pcdn_default_batch_opts", "pcdn_solve_batch", "pcdn_autotune", "pcdn_default_server_opts",
            "pcdn_server_create", "pcdn_server_submit", "pcdn_server_submit_borrowed", "pcdn_server_wait", "pcdn_server_stats",
            "pcdn_server_destroy"]
@@ -144,6 +144,8 @@ def load() -> ctypes.CDLL:
     lib.pcdn_objective_noalloc.restype = ctypes.c_int
     lib.pcdn_set_C.argtypes = [vp, d]
     lib.pcdn_set_C.restype = ctypes.c_int
+    lib.pcdn_set_penalty.argtypes = [vp, d, d]
+    lib.pcdn_set_penalty.restype = ctypes.c_int
     lib.pcdn_default_batch_opts.argtypes = [P(pcdn_batch_opts)]
     lib.pcdn_default_batch_opts.restype = None
     lib.pcdn_solve_batch.argtypes = [vp, i32, P(pcdn_opts), P(pcdn_batch_opts), P(pcdn_batch_stats)]
@@ -318,6 +320,11 @@ def pcdn_set_C(h: int, C: float) -> None:
     _check(load().pcdn_set_C(h, float(C)))
 
 
+def pcdn_set_penalty(h: int, l1: float = 1.0, l2: float = 0.0) -> None:
+    """Penalty l1 ||w||_1 + (l2/2) ||w||^2 (the paper's problem: l1 = 1, l2 = 0)."""
+    _check(load().pcdn_set_penalty(h, float(l1), float(l2)))
+
+
 def pcdn_default_batch_opts(**overrides) -> pcdn_batch_opts:
     o = pcdn_batch_opts()
     load().pcdn_default_batch_opts(ctypes.byref(o))
@@ -470,6 +477,9 @@ class Problem:
 
     def bundle_step(self, w_in, bundle, opts=None):
         return pcdn_bundle_step(self.handle, w_in, bundle, opts)
+
+    def set_penalty(self, l1=1.0, l2=0.0):
+        pcdn_set_penalty(self.handle, l1, l2)
 
     def set_w(self, w):
         pcdn_set_w(self.handle, w)

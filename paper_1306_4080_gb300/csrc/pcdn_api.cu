@@ -197,6 +197,8 @@ struct pcdn_problem {
   // double), [1] active features, [2] their nonzeros (allocated by the first solve that shrinks)
   double* gfull = nullptr;
   unsigned long long* shr = nullptr;
+  // penalty l1 ||w||_1 + (l2/2) ||w||^2 (Eq. 1: l1 = 1, l2 = 0; pcdn_set_penalty)
+  double l1 = 1.0, l2 = 0.0;
   bool capturing = false;  // the stream is being captured into a graph
   // stream, events
   cudaStream_t stream = nullptr;
@@ -577,10 +579,11 @@ int start_state(pcdn_problem* p, int prec, bool cold) {
 int do_kkt(pcdn_problem* p, int slot, bool shrink = false) {
   if (shrink) CUDA_TRY(cudaMemsetAsync(p->shr, 0, sizeof(unsigned long long) * 3, p->stream));
   CUDA_TRY(kkt_l1(p->rec_prec, p->id_items, p->n_id_items, p->id_item_ptr, p->id_perm, p->m, p->row_idx, p->val, p->rec,
-                  p->w, p->c, p->part, p->red_part, p->red_grid, p->red_out + slot, p->stream, &p->launches,
-                  shrink ? p->gfull : nullptr, shrink ? p->shr : nullptr));
+                  p->w, p->c, p->l1, p->l2, p->part, p->red_part, p->red_grid, p->red_out + slot, p->stream,
+                  &p->launches, shrink ? p->gfull : nullptr, shrink ? p->shr : nullptr));
   if (shrink)
-    CUDA_TRY(active_count(p->gfull, p->w, p->m, p->col_ptr, p->shr, p->n, p->shr + 1, p->stream, &p->launches));
+    CUDA_TRY(active_count(p->gfull, p->w, p->m, p->col_ptr, p->shr, p->n, p->l1, p->shr + 1, p->stream,
+                          &p->launches));
   return PCDN_OK;
 }
 
@@ -588,8 +591,8 @@ int do_kkt(pcdn_problem* p, int slot, bool shrink = false) {
 // partition order), into the other radix-sort value buffer.
 int shrink_partition(pcdn_problem* p, int32_t* perm, int32_t** out) {
   int32_t* dst = perm == p->vals0 ? p->vals1 : p->vals0;
-  CUDA_TRY(compact_active(perm, p->m, p->gfull, p->w, p->shr, p->n, p->cnt, p->item_off, p->scan_ws, dst, p->stream,
-                          &p->launches));
+  CUDA_TRY(compact_active(perm, p->m, p->gfull, p->w, p->shr, p->n, p->l1, p->cnt, p->item_off, p->scan_ws, dst,
+                          p->stream, &p->launches));
   *out = dst;
   return PCDN_OK;
 }
@@ -597,8 +600,8 @@ int shrink_partition(pcdn_problem* p, int32_t* perm, int32_t** out) {
 int do_objective(pcdn_problem* p, int slot) {
   int rc = do_refresh(p, p->rec_prec, false, true);
   if (rc) return rc;
-  CUDA_TRY(objective_finish(p->red_part, p->red_grid, p->w, p->m, p->c, p->red_part + p->red_grid, p->red_grid,
-                            p->red_out + slot, p->stream, &p->launches));
+  CUDA_TRY(objective_finish(p->red_part, p->red_grid, p->w, p->m, p->c, p->l1, p->l2, p->red_part + p->red_grid,
+                            p->red_grid, p->red_out + slot, p->stream, &p->launches));
   return PCDN_OK;
 }
 
@@ -686,6 +689,10 @@ int run_walk(pcdn_problem* p, const pcdn_opts* o, const int32_t* perm, int64_t n
   w.nu = o->nu;
   w.c_f = (float)p->c;
   w.nu_f = (float)o->nu;
+  w.l1 = p->l1;
+  w.l2 = p->l2;
+  w.l1_f = (float)p->l1;
+  w.l2_f = (float)p->l2;
   w.q_max = o->q_max;
   // step sizes per pass: almost every bundle accepts q = 0, so the first pass tests that alone;
   // a further pass (one more barrier) tests four
@@ -1310,6 +1317,19 @@ int pcdn_set_C(pcdn_problem* p, double C) {
   if (!(C > 0) || !std::isfinite(C)) return fail(PCDN_EINVAL, "C must be positive and finite");
   // the maintained quantities and the per-sample coefficients do not involve c
   p->c = C;
+  return PCDN_OK;
+}
+
+int pcdn_set_penalty(pcdn_problem* p, double l1, double l2) {
+  g_err.clear();
+  if (!p) return fail(PCDN_EINVAL, "problem must be given");
+  if (!(l1 >= 0) || !(l2 >= 0) || !std::isfinite(l1) || !std::isfinite(l2))
+    return fail(PCDN_EINVAL, "l1 and l2 must be finite and >= 0");
+  if (l1 == 0.0 && l2 == 0.0) return fail(PCDN_EINVAL, "l1 and l2 must not both be 0");
+  // like c, the penalty enters only the directions, Delta, the line search's penalty change and the
+  // stopping test; w and the maintained quantities are kept
+  p->l1 = l1;
+  p->l2 = l2;
   return PCDN_OK;
 }
 

@@ -111,6 +111,9 @@ struct WalkParams {
   // Armijo
   double sigma, beta, gamma, nu;
   float c_f, nu_f;          // c and nu in FP32 (mixed mode's column directions)
+  // penalty l1 ||w||_1 + (l2/2) ||w||^2 (the paper's problem: l1 = 1, l2 = 0)
+  double l1, l2;
+  float l1_f, l2_f;
   int32_t q_max, K;         // K step sizes per line-search pass after the first
   int32_t K1;               // step sizes in the first pass
   // outputs
@@ -204,10 +207,11 @@ __device__ __forceinline__ int warp_sum_int(int v) {
 }
 
 // ---------------------------------------------------------------- direction (Eq. 4 / Eq. 5)
-// argmin_d g d + h d^2/2 + |w + d|; Eq. 5's branch conditions read with the +/-1 terms.
-__device__ __forceinline__ double newton_direction(double g, double h, double w) {
-  if (g + 1.0 <= h * w) return -(g + 1.0) / h;
-  if (g - 1.0 >= h * w) return -(g - 1.0) / h;
+// argmin_d g d + h d^2/2 + l1 |w + d|; Eq. 5's branch conditions read with the +/-l1 terms (l1 = 1
+// in the paper).
+__device__ __forceinline__ double newton_direction(double g, double h, double w, double l1) {
+  if (g + l1 <= h * w) return -(g + l1) / h;
+  if (g - l1 >= h * w) return -(g - l1) / h;
   return -w;
 }
 

@@ -686,8 +686,8 @@ __global__ void __launch_bounds__(kRedThreads) kkt_item_kernel(const Item* items
 template <int PREC>
 __global__ void __launch_bounds__(kRedThreads) kkt_col_kernel(const int64_t* item_ptr, const int32_t* perm, int64_t npos,
                                                               const double* gpart, const double* w, double c,
-                                                              double* block_part, double* g_out,
-                                                              unsigned long long* vmax) {
+                                                              double l1, double l2, double* block_part,
+                                                              double* g_out, unsigned long long* vmax) {
   __shared__ double red[kRedThreads];
   double acc = 0.0, vm = 0.0;
   const int lane = threadIdx.x & 31;
@@ -718,10 +718,11 @@ __global__ void __launch_bounds__(kRedThreads) kkt_col_kernel(const int64_t* ite
     g *= c;
     const int32_t j = perm[k];
     const double wj = w[j];
+    if (l2 != 0.0) g += l2 * wj;  // the smooth part's gradient
     double v;
-    if (wj > 0) v = g + 1.0;
-    else if (wj < 0) v = g - 1.0;
-    else v = fabs(g) > 1.0 ? (g > 0 ? g - 1.0 : g + 1.0) : 0.0;
+    if (wj > 0) v = g + l1;
+    else if (wj < 0) v = g - l1;
+    else v = fabs(g) > l1 ? (g > 0 ? g - l1 : g + l1) : 0.0;
     acc += fabs(v);
     vm = fmax(vm, fabs(v));
     if (g_out) g_out[j] = g;
@@ -746,23 +747,23 @@ __global__ void __launch_bounds__(kRedThreads) kkt_col_kernel(const int64_t* ite
 }
 
 // ------------------------------------------------------------------------------------ shrinking
-// Feature j takes part in the next outer iteration unless w_j = 0 and |g_j| < 1 - M / s (M the
-// largest |v_j|, s the number of samples): outer-iteration shrinking with LIBLINEAR's margin, from
-// the fresh gradient of the stopping test.
+// Feature j takes part in the next outer iteration unless w_j = 0 and |g_j| < l1 - M / s (g the
+// smooth part's gradient, M the largest |v_j|, s the number of samples; l1 = 1 in the paper):
+// outer-iteration shrinking with LIBLINEAR's margin, from the fresh gradient of the stopping test.
 __device__ __forceinline__ bool feature_active(double g, double wj, double bound) {
   return wj != 0.0 || fabs(g) >= bound;
 }
-__device__ __forceinline__ double shrink_bound(const unsigned long long* vmax, int64_t n_samples) {
-  return 1.0 - __longlong_as_double((long long)*vmax) / (double)n_samples;
+__device__ __forceinline__ double shrink_bound(const unsigned long long* vmax, int64_t n_samples, double l1) {
+  return l1 - __longlong_as_double((long long)*vmax) / (double)n_samples;
 }
 
 // out[0] += active features, out[1] += their nonzeros.
 __global__ void __launch_bounds__(kRedThreads) active_count_kernel(const double* g, const double* w, int64_t m,
                                                                    const int64_t* col_ptr,
                                                                    const unsigned long long* vmax, int64_t n_samples,
-                                                                   unsigned long long* out) {
+                                                                   double l1, unsigned long long* out) {
   __shared__ unsigned long long red[2][kRedThreads / 32];
-  const double bound = shrink_bound(vmax, n_samples);
+  const double bound = shrink_bound(vmax, n_samples, l1);
   unsigned long long cnt = 0, nz = 0;
   for (int64_t j = (int64_t)blockIdx.x * kRedThreads + threadIdx.x; j < m; j += (int64_t)gridDim.x * kRedThreads) {
     if (feature_active(g[j], w[j], bound)) {
@@ -792,8 +793,8 @@ __global__ void __launch_bounds__(kRedThreads) active_count_kernel(const double*
 
 // flags[k] = 1 when feature perm[k] is active (k < m), flags[m] = 0.
 __global__ void active_flags_kernel(const int32_t* perm, int64_t m, const double* g, const double* w,
-                                    const unsigned long long* vmax, int64_t n_samples, int64_t* flags) {
-  const double bound = shrink_bound(vmax, n_samples);
+                                    const unsigned long long* vmax, int64_t n_samples, double l1, int64_t* flags) {
+  const double bound = shrink_bound(vmax, n_samples, l1);
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k <= m; k += (int64_t)gridDim.x * blockDim.x) {
     if (k == m) { flags[k] = 0; continue; }
     const int32_t j = perm[k];
@@ -807,11 +808,16 @@ __global__ void compact_kernel(const int32_t* perm, int64_t m, const int64_t* fl
     if (flags[k]) out[pos[k]] = perm[k];
 }
 
-__global__ void abs_sum_kernel(const double* w, int64_t m, double* block_part) {
+// Block sums of the penalty l1 |w_j| + (l2/2) w_j^2.
+__global__ void abs_sum_kernel(const double* w, int64_t m, double l1, double l2, double* block_part) {
   __shared__ double red[kRedThreads];
   double acc = 0.0;
-  for (int64_t j = (int64_t)blockIdx.x * kRedThreads + threadIdx.x; j < m; j += (int64_t)gridDim.x * kRedThreads)
-    acc += fabs(w[j]);
+  for (int64_t j = (int64_t)blockIdx.x * kRedThreads + threadIdx.x; j < m; j += (int64_t)gridDim.x * kRedThreads) {
+    const double wj = w[j];
+    double r = l1 * fabs(wj);
+    if (l2 != 0.0) r += 0.5 * l2 * wj * wj;
+    acc += r;
+  }
   red[threadIdx.x] = acc;
   __syncthreads();
   for (int o = kRedThreads / 2; o > 0; o >>= 1) {
@@ -1050,15 +1056,17 @@ cudaError_t state_at_zero(int loss, int prec, const int8_t* y, int64_t n, double
 
 cudaError_t kkt_l1(int prec, const Item* items, int64_t n_items, const int64_t* item_ptr, const int32_t* perm,
                    int64_t npos, const int32_t* row_idx, const float* val, const void* rec, const double* w, double c,
-                   double* gpart, double* block_part, int grid, double* out, cudaStream_t s, int64_t* launches,
-                   double* g_out, unsigned long long* vmax) {
+                   double l1, double l2, double* gpart, double* block_part, int grid, double* out, cudaStream_t s,
+                   int64_t* launches, double* g_out, unsigned long long* vmax) {
   // the item pass writes one sum per item, no block partials: twice the blocks for more loads in flight
   if (prec == 0) kkt_item_kernel<0><<<2 * grid, kRedThreads, 0, s>>>(items, n_items, row_idx, val, rec, gpart);
   else kkt_item_kernel<1><<<2 * grid, kRedThreads, 0, s>>>(items, n_items, row_idx, val, rec, gpart);
   cudaError_t e = post(launches);
   if (e != cudaSuccess) return e;
-  if (prec == 0) kkt_col_kernel<0><<<grid, kRedThreads, 0, s>>>(item_ptr, perm, npos, gpart, w, c, block_part, g_out, vmax);
-  else kkt_col_kernel<1><<<grid, kRedThreads, 0, s>>>(item_ptr, perm, npos, gpart, w, c, block_part, g_out, vmax);
+  if (prec == 0)
+    kkt_col_kernel<0><<<grid, kRedThreads, 0, s>>>(item_ptr, perm, npos, gpart, w, c, l1, l2, block_part, g_out, vmax);
+  else
+    kkt_col_kernel<1><<<grid, kRedThreads, 0, s>>>(item_ptr, perm, npos, gpart, w, c, l1, l2, block_part, g_out, vmax);
   e = post(launches);
   if (e != cudaSuccess) return e;
   finish_sum_kernel<<<1, kRedThreads, 0, s>>>(block_part, grid, 1.0, nullptr, 0, out);
@@ -1066,16 +1074,17 @@ cudaError_t kkt_l1(int prec, const Item* items, int64_t n_items, const int64_t* 
 }
 
 cudaError_t active_count(const double* g, const double* w, int64_t m, const int64_t* col_ptr,
-                         const unsigned long long* vmax, int64_t n_samples, unsigned long long* out, cudaStream_t s,
-                         int64_t* launches) {
-  active_count_kernel<<<grid_for(m, kRedThreads, 1024), kRedThreads, 0, s>>>(g, w, m, col_ptr, vmax, n_samples, out);
+                         const unsigned long long* vmax, int64_t n_samples, double l1, unsigned long long* out,
+                         cudaStream_t s, int64_t* launches) {
+  active_count_kernel<<<grid_for(m, kRedThreads, 1024), kRedThreads, 0, s>>>(g, w, m, col_ptr, vmax, n_samples, l1,
+                                                                              out);
   return post(launches);
 }
 
 cudaError_t compact_active(const int32_t* perm, int64_t m, const double* g, const double* w,
-                           const unsigned long long* vmax, int64_t n_samples, int64_t* flags_ws, int64_t* pos_ws,
-                           int64_t* scan_ws, int32_t* out, cudaStream_t s, int64_t* launches) {
-  active_flags_kernel<<<grid_for(m + 1, 256), 256, 0, s>>>(perm, m, g, w, vmax, n_samples, flags_ws);
+                           const unsigned long long* vmax, int64_t n_samples, double l1, int64_t* flags_ws,
+                           int64_t* pos_ws, int64_t* scan_ws, int32_t* out, cudaStream_t s, int64_t* launches) {
+  active_flags_kernel<<<grid_for(m + 1, 256), 256, 0, s>>>(perm, m, g, w, vmax, n_samples, l1, flags_ws);
   cudaError_t e = post(launches);
   if (e != cudaSuccess) return e;
   e = scan_exclusive(flags_ws, pos_ws, m + 1, scan_ws, s, launches);
@@ -1084,9 +1093,9 @@ cudaError_t compact_active(const int32_t* perm, int64_t m, const double* g, cons
   return post(launches);
 }
 
-cudaError_t objective_finish(const double* loss_part, int nb, const double* w, int64_t m, double c, double* block_part,
-                             int grid, double* out, cudaStream_t s, int64_t* launches) {
-  abs_sum_kernel<<<grid, kRedThreads, 0, s>>>(w, m, block_part);
+cudaError_t objective_finish(const double* loss_part, int nb, const double* w, int64_t m, double c, double l1,
+                             double l2, double* block_part, int grid, double* out, cudaStream_t s, int64_t* launches) {
+  abs_sum_kernel<<<grid, kRedThreads, 0, s>>>(w, m, l1, l2, block_part);
   cudaError_t e = post(launches);
   if (e != cudaSuccess) return e;
   finish_sum_kernel<<<1, kRedThreads, 0, s>>>(loss_part, nb, c, block_part, grid, out);

@@ -90,24 +90,26 @@ cudaError_t rec_from_mq(int loss, int prec, const double* mq, const int8_t* y, i
 // Minimum-norm subgradient l1 norm from the coefficients in rec, over work items of all columns.
 // When g_out / vmax are given (shrinking): g_j of every feature into g_out[j], and the largest
 // |v_j| into *vmax (as the bits of the double; *vmax zeroed by the caller).
+// l1, l2: the penalty l1 ||w||_1 + (l2/2) ||w||^2 (g is the smooth part's gradient).
 cudaError_t kkt_l1(int prec, const Item* items, int64_t n_items, const int64_t* item_ptr, const int32_t* perm,
                    int64_t npos, const int32_t* row_idx, const float* val, const void* rec, const double* w,
-                   double c, double* gpart, double* block_part, int grid, double* out, cudaStream_t s,
-                   int64_t* launches, double* g_out = nullptr, unsigned long long* vmax = nullptr);
+                   double c, double l1, double l2, double* gpart, double* block_part, int grid, double* out,
+                   cudaStream_t s, int64_t* launches, double* g_out = nullptr, unsigned long long* vmax = nullptr);
 
 // ---- shrinking (between outer iterations) ------------------------------------------------------
-// A feature is active unless w_j = 0 and |g_j| < 1 - M / n_samples, M = *vmax (the largest |v_j|).
+// A feature is active unless w_j = 0 and |g_j| < l1 - M / n_samples, M = *vmax (the largest |v_j|).
 // out[0] += active features, out[1] += their nonzeros (out zeroed by the caller).
 cudaError_t active_count(const double* g, const double* w, int64_t m, const int64_t* col_ptr,
-                         const unsigned long long* vmax, int64_t n_samples, unsigned long long* out, cudaStream_t s,
-                         int64_t* launches);
+                         const unsigned long long* vmax, int64_t n_samples, double l1, unsigned long long* out,
+                         cudaStream_t s, int64_t* launches);
 // The active features of partition perm[0..m), in partition order, into out[0..count) (a stable
 // filter; flags_ws and pos_ws hold m + 1 entries each).
 cudaError_t compact_active(const int32_t* perm, int64_t m, const double* g, const double* w,
-                           const unsigned long long* vmax, int64_t n_samples, int64_t* flags_ws, int64_t* pos_ws,
-                           int64_t* scan_ws, int32_t* out, cudaStream_t s, int64_t* launches);
-// out = c * sum(loss_part[0..nb)) + sum_j |w_j|
-cudaError_t objective_finish(const double* loss_part, int nb, const double* w, int64_t m, double c,
-                             double* block_part, int grid, double* out, cudaStream_t s, int64_t* launches);
+                           const unsigned long long* vmax, int64_t n_samples, double l1, int64_t* flags_ws,
+                           int64_t* pos_ws, int64_t* scan_ws, int32_t* out, cudaStream_t s, int64_t* launches);
+// out = c * sum(loss_part[0..nb)) + sum_j (l1 |w_j| + (l2/2) w_j^2)
+cudaError_t objective_finish(const double* loss_part, int nb, const double* w, int64_t m, double c, double l1,
+                             double l2, double* block_part, int grid, double* out, cudaStream_t s,
+                             int64_t* launches);
 
 }  // namespace pcdn

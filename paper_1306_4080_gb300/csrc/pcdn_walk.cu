@@ -279,12 +279,17 @@ __device__ __forceinline__ void scatter_one(const WalkParams& p, int32_t r, Delt
   }
 }
 
-// g, h (sums without the factor c) -> the scaled g, h and d (Eq. 5; h <= 0 replaced by nu).
+// g, h (sums without the factor c) -> the smooth part's g, h (c times the loss's, h <= 0 replaced
+// by nu, plus l2 w_j and l2) and d (Eq. 5 with the penalty's l1).
 __device__ __forceinline__ double column_direction(const WalkParams& p, double& g, double& h, double wj) {
   g *= p.c;
   h *= p.c;
   if (h <= 0.0) h = p.nu;
-  return newton_direction(g, h, wj);
+  if (p.l2 != 0.0) {
+    g += p.l2 * wj;
+    h += p.l2;
+  }
+  return newton_direction(g, h, wj, p.l1);
 }
 
 // A column's direction (Eq. 5) from its sums g, h (without the factor c; h <= 0 replaced by nu)
@@ -305,14 +310,19 @@ __device__ __forceinline__ double finalize(const WalkParams& p, int32_t kl, GHT<
     h *= p.c_f;
     if (h <= 0.0f) h = p.nu_f;
     const float wf = (float)wj;
-    if (g + 1.0f <= h * wf) d = (double)(-(g + 1.0f) / h);
-    else if (g - 1.0f >= h * wf) d = (double)(-(g - 1.0f) / h);
+    if (p.l2 != 0.0) {
+      g += p.l2_f * wf;
+      h += p.l2_f;
+    }
+    const float l1 = p.l1_f;
+    if (g + l1 <= h * wf) d = (double)(-(g + l1) / h);
+    else if (g - l1 >= h * wf) d = (double)(-(g - l1) / h);
     else d = -wj;
     const float df = (float)d;
     t.gd = g * df;
     t.hdd = h * df * df;
   }
-  t.l1 = d != 0.0 ? (GHT<PREC>)(fabs(wj + d) - fabs(wj)) : GHT<PREC>(0);
+  t.l1 = d != 0.0 ? (GHT<PREC>)(p.l1 * (fabs(wj + d) - fabs(wj))) : GHT<PREC>(0);
   if (write) {
     p.gk[kl] = (double)g;
     p.hk[kl] = (double)h;
@@ -1125,9 +1135,10 @@ __global__ void __launch_bounds__(kWalkThreads, 2) walk_kernel(WalkParams p) {
           }
         }
       }
-      // the L1 change of each step over a slice of the bundle's positions; Delta's terms (and the
-      // L1 change of the full step, when it is the only one) come from the column pass
-      const bool full_only = q0 == 0 && K == 1;
+      // the penalty's change for each step over a slice of the bundle's positions; Delta's terms (and
+      // the L1 change of the full step, when it is the only one and there is no L2 term) come from
+      // the column pass
+      const bool full_only = q0 == 0 && K == 1 && p.l2 == 0.0;
       if (!full_only && wib < pos_warps) {
         Acc<PREC> pq[kMaxK];
         for (int64_t kl = k0 + wib * 32 + lane; kl < k1; kl += 32 * pos_warps) {
@@ -1136,14 +1147,28 @@ __global__ void __launch_bounds__(kWalkThreads, 2) walk_kernel(WalkParams p) {
           const double wj = p.w_pos[lo + kl];
           if constexpr (PREC == 0) {
 #pragma unroll
-            for (int q = 0; q < kMaxK; ++q)
-              if (q < K) pq[q].add(fabs(wj + alpha[q] * d) - fabs(wj));
+            for (int q = 0; q < kMaxK; ++q) {
+              if (q < K) {
+                const double t = alpha[q] * d;
+                double r = p.l1 * (fabs(wj + t) - fabs(wj));
+                if (p.l2 != 0.0) r += 0.5 * p.l2 * ((wj + t) * (wj + t) - wj * wj);
+                pq[q].add(r);
+              }
+            }
           } else {
-            // |w + a d| - |w| in double-float arithmetic (a is a power of two when beta = 1/2)
+            // l1 (|w + a d| - |w|) in double-float arithmetic (a is a power of two when beta = 1/2);
+            // the L2 change's first-order part a l2 w d is in a g^T d (g holds l2 w), its second-order
+            // part (l2/2) a^2 d^2 is added here
             const dfloat wd = df_make(wj), dd = df_make(d), aw = df_neg(df_abs(wd));
 #pragma unroll
-            for (int q = 0; q < kMaxK; ++q)
-              if (q < K) pq[q].v = df_add(pq[q].v, df_add(df_abs(df_add(wd, df_scale(dd, alpha_f[q]))), aw));
+            for (int q = 0; q < kMaxK; ++q) {
+              if (q < K) {
+                dfloat r = df_add(df_abs(df_add(wd, df_scale(dd, alpha_f[q]))), aw);
+                if (p.l1 != 1.0) r = df_scale(r, p.l1_f);
+                if (p.l2 != 0.0) r = df_add(r, df_make(0.5 * p.l2 * (alpha[q] * d) * (alpha[q] * d)));
+                pq[q].v = df_add(pq[q].v, r);
+              }
+            }
           }
         }
 #pragma unroll
