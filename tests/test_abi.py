@@ -198,3 +198,10 @@ def test_binding_structs_match_the_header_layout(pk, tmp_path):
         assert c_layout[(name, "size")] == ctypes.sizeof(cls), name
         for fname, _ in cls._fields_:
             assert c_layout[(name, fname)] == getattr(cls, fname).offset, (name, fname)
+
+
+def test_penalty_rejects_a_missing_problem(pk):
+    """pcdn_set_penalty validates on the host (no GPU needed for the error path)."""
+    lib = pk.load()
+    assert lib.pcdn_set_penalty(None, 1.0, 0.0) == pk.PCDN_EINVAL
+    assert "problem" in pk.pcdn_last_error()
