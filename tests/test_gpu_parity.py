@@ -1,6 +1,6 @@
 """GPU path vs the FP64 oracle, through the C ABI, on identical seeded inputs and partitions.
 
-Tolerances (spec bar: per-bundle d and step size within 1e-5 relative, final objective
+Tolerances (the bar: per-bundle d and step size within 1e-5 relative, final objective
 within 1e-6 relative):
   FP64 mode   g, h, d, Delta within 1e-9 of the bundle's largest magnitude; q and alpha equal;
               dF within 1e-7 relative (different reduction order over up to 10^5 rows).
