@@ -52,7 +52,7 @@ def test_splitmix64_matches_independent_python():
 
 @pytest.mark.parametrize("m", [1, 2, 7, 64, 1000])
 def test_partition_is_sorted_key_order(m):
-    # Algorithm 3 / Eq. 8: a random disjoint partition; this build draws it as the order of
+    # Algorithm 3 / Eq. 8: a random disjoint partition, drawn (the paper leaves the draw open) as the order of
     # per-feature splitmix64 keys (ties broken by feature index).
     for seed, epoch in [(0, 0), (0, 1), (12345, 7), (2**64 - 1, 3)]:
         perm = oracle.permutation(seed, epoch, m)
