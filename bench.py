@@ -244,9 +244,12 @@ def run_reference(args):
 
 
 def config_of(wl, prob, prec):
+    if wl.spec.kind == "zipf":
+        shape = f"Zipf {wl.spec.zipf_s} columns, tf-idf rows L2-normalised"
+    else:
+        shape = f"uniform density {wl.spec.density}, |N(0,1)| values, rows L2-normalised"
     return {"workload": f"{wl.name}: L1 {wl.loss}, n_samples={prob.n_samples}, n_features={prob.n_features}, "
-                        f"nnz={prob.nnz}, Zipf {wl.spec.zipf_s} columns, tf-idf rows L2-normalised, C={wl.C}, "
-                        f"P={wl.P}, eps={wl.eps}",
+                        f"nnz={prob.nnz}, {shape}, C={wl.C}, P={wl.P}, eps={wl.eps}",
             "n_samples": prob.n_samples, "n_features": prob.n_features, "nnz": prob.nnz, "loss": wl.loss,
             "C": wl.C, "P": wl.P, "eps": wl.eps, "precision": prec,
             "cache": "inputs larger than L2 (X alone is %.2f GB)" % (prob.nnz * 8 / 1e9)}
