@@ -318,8 +318,9 @@ void pcdn_server_destroy(pcdn_server* srv);
  * For callers that may not allocate device memory (an application that owns all GPU memory
  * through its own pool or budget, or a request loop that allows no allocator calls): the
  * objective F(w) = C * sum_i phi(w; x_i, y_i) + ||w||_1 from the caller's device buffers,
- * with no cudaMalloc, cudaFree or other allocating call.  The paper has no counterpart; the
- * value equals pcdn_objective's for the same X, y, C, loss and w (up to summation order).
+ * with no cudaMalloc, cudaFree or other allocating call (the paper's penalty, l1 = 1, l2 = 0).
+ * The paper has no counterpart; the value equals pcdn_objective's for the same X, y, C, loss and
+ * w on a problem with the default penalty (up to summation order).
  *
  * X's arrays, y (n_samples labels in {-1, +1}), w (n_features doubles) and F (one double,
  * written) are device pointers; the call only enqueues work on `stream` (a cudaStream_t, NULL =
