@@ -107,6 +107,17 @@ double probe_score(const pcdn_stats& st) {
   return st.walk_s / std::max(decades, 1e-3);
 }
 
+// A probe that got fewer walker blocks than it asked for (other solves held the shared budget) ran
+// slower than its path's solves will once they hold their blocks, which biases the choice toward
+// small bundles.  Its time is scaled to the blocks it wanted by the walker's per-bundle time law
+// in its block count, time ~ blocks^-0.56 (31, 42 and 67 us per bundle at 304, 152 and 76 blocks on
+// the 2M x 3M workload).  A probe that got its blocks keeps its measured time.
+double probe_score_for_blocks(const pcdn_stats& st, int wanted) {
+  double s = probe_score(st);
+  if (wanted > 1 && st.walk_grid > 0 && st.walk_grid < wanted) s *= std::pow((double)st.walk_grid / wanted, 0.56);
+  return s;
+}
+
 // The C a job's probes run at: the geometric middle of its path (the larger C values of a path
 // cost the most outer iterations, the smallest the fewest).
 double probe_C(const pcdn_batch_job& j) { return std::sqrt(j.C_path[0] * j.C_path[j.n_C - 1]); }
@@ -175,7 +186,7 @@ bool on_done(BatchShared& B, JobRun& r, SolveTask* t, int rc) {
       r.status = rr;
       return true;
     }
-    const double score = probe_score(st);
+    const double score = probe_score_for_blocks(st, walker_blocks_wanted(j.prob, r.cand[r.probe]));
     if (r.best_P == 0 || score < r.best_s) {
       r.best_s = score;
       r.best_P = r.cand[r.probe];
