@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--grid", type=int, default=0)
+    ap.add_argument("--layout", default="auto", choices=["auto", "scatter", "rows"],
+                    help="how d^T x reaches the samples (pcdn_opts.layout)")
     ap.add_argument("--batched", type=int, default=1, help="also run the batched workload (reported under 'batched')")
     ap.add_argument("--batch-jobs", type=int, default=64)
     ap.add_argument("--batch-scale", type=float, default=1.0)
@@ -473,7 +475,8 @@ def run_ours(args):
     P = pk.Problem.from_device(t_cp, t_ri, t_v, t_y, wl.C, wl.loss, stream=stream)
 
     def timed(prec, steps, warmup, shrink=0):
-        opts = pk.pcdn_default_opts(prec=prec, max_epochs=args.max_epochs, grid_ctas=args.grid, shrink=shrink)
+        opts = pk.pcdn_default_opts(prec=prec, max_epochs=args.max_epochs, grid_ctas=args.grid, shrink=shrink,
+                                    layout=args.layout)
         for _ in range(warmup):
             P.solve(wl.P, wl.eps, wl.solver_seed, opts, want_w=False)
         torch.cuda.synchronize()
@@ -532,7 +535,7 @@ def run_ours(args):
         ss = stss[-1]
         _, _, _, trs = P.solve(wl.P, wl.eps, wl.solver_seed,
                                pk.pcdn_default_opts(prec=args.prec, max_epochs=args.max_epochs, grid_ctas=args.grid,
-                                                    shrink=1), want_w=False, trace_epochs=200)
+                                                    shrink=1, layout=args.layout), want_w=False, trace_epochs=200)
         extra["shrinking"] = {"value": mss * 1e-3 / world, "unit": UNIT, "ms_per_step": mss,
                               "speedup_vs_plain": ms / mss, "epochs": ss["epochs"], "bundles": ss["bundles"],
                               "coord_updates": ss["coord_updates"], "nnz_visited": ss["nnz_visited"],
@@ -544,7 +547,8 @@ def run_ours(args):
     if not args.no_e2e:
         cp, ri, vv, yy = prob.col_ptr, prob.row_idx, prob.val, prob.y
         pin = [torch.from_numpy(a).pin_memory().numpy() for a in (cp, ri, vv, yy)]
-        opts = pk.pcdn_default_opts(prec=args.prec, max_epochs=args.max_epochs, grid_ctas=args.grid)
+        opts = pk.pcdn_default_opts(prec=args.prec, max_epochs=args.max_epochs, grid_ctas=args.grid,
+                                    layout=args.layout)
         times = []
         for i in range(args.e2e_steps + 1):
             torch.cuda.synchronize()

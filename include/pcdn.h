@@ -81,7 +81,19 @@ typedef struct {
   double kkt_ref;     /* > 0: relative KKT measured against this ||v||_1 instead of the start point's (default 0).
                          A solve stopped after k outer iterations resumes exactly with warm_start = 1 from its w,
                          epoch0 = k and kkt_ref = its stats.kkt0 */
+  int32_t layout;     /* how d^T x_i (Algorithm 4) reaches the samples: PCDN_LAYOUT_AUTO (default), _SCATTER or _ROWS */
 } pcdn_opts;
+
+/* PCDN_LAYOUT_ROWS: per outer iteration the entries of every bundle's columns are regrouped by
+ *   sample; the thread that owns a sample sums its d^T x_i in a fixed order, and the step's full
+ *   update is written before the step-size decision (two grid barriers per bundle on the usual
+ *   path).  Every sum has a fixed order: FP64 results repeat bit for bit for a given walker grid.
+ * PCDN_LAYOUT_SCATTER: each block adds d_j x_ij into a dense vector with atomic adds (results
+ *   repeat up to rounding); no regrouping pass.
+ * PCDN_LAYOUT_AUTO: rows for walkers of several thread blocks, scatter for one-block walkers. */
+#define PCDN_LAYOUT_AUTO 0
+#define PCDN_LAYOUT_SCATTER 1
+#define PCDN_LAYOUT_ROWS 2
 
 /* Per-solve statistics (written by pcdn_solve). */
 typedef struct {

@@ -28,6 +28,7 @@ PCDN_ENOTCONVERGED = 1
 
 LOSSES = {"logistic": 0, "l2svm": 1}
 PRECISIONS = {"fp64": 0, "mixed": 1}
+LAYOUTS = {"auto": 0, "scatter": 1, "rows": 2}
 
 SYMBOLS = ["pcdn_default_opts", "pcdn_create", "pcdn_create_device", "pcdn_solve", "pcdn_bundle_step",
            "pcdn_set_w", "pcdn_get_w", "pcdn_objective", "pcdn_kkt", "pcdn_permutation", "pcdn_memory",
@@ -54,7 +55,8 @@ class pcdn_opts(ctypes.Structure):
                 ("nu", ctypes.c_double), ("q_max", ctypes.c_int32), ("ls_batch", ctypes.c_int32),
                 ("max_epochs", ctypes.c_int64), ("prec", ctypes.c_int), ("warm_start", ctypes.c_int32),
                 ("grid_ctas", ctypes.c_int32), ("refresh", ctypes.c_int32), ("spin_limit", ctypes.c_uint32),
-                ("shrink", ctypes.c_int32), ("epoch0", ctypes.c_int64), ("kkt_ref", ctypes.c_double)]
+                ("shrink", ctypes.c_int32), ("epoch0", ctypes.c_int64), ("kkt_ref", ctypes.c_double),
+                ("layout", ctypes.c_int32)]
 
 
 class pcdn_stats(ctypes.Structure):
@@ -186,6 +188,8 @@ def pcdn_default_opts(**overrides) -> pcdn_opts:
     for k, v in overrides.items():
         if k == "prec" and isinstance(v, str):
             v = PRECISIONS[v]
+        if k == "layout" and isinstance(v, str):
+            v = LAYOUTS[v]
         setattr(o, k, v)
     return o
 

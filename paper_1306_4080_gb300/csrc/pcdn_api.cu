@@ -28,6 +28,9 @@ namespace pcdn {
 cudaError_t launch_walk(int loss, int prec, const WalkParams& p, int grid, cudaStream_t s, bool capturing);
 cudaError_t walk_max_blocks_per_sm(int loss, int prec, int* out);
 cudaError_t walk_configure(int loss, int prec);
+cudaError_t launch_walk_rows(int loss, int prec, const WalkParams& p, int grid, cudaStream_t s, bool capturing);
+cudaError_t walk_rows_max_blocks_per_sm(int loss, int prec, int* out);
+int walk_rows_max_grid();
 }  // namespace pcdn
 
 using namespace pcdn;
@@ -72,7 +75,9 @@ int fail(int code, const char* fmt, ...) {
     }                                                                                               \
   } while (0)
 
-constexpr uint32_t kDefaultSpin = 1u << 22;  // ~seconds of polling before a wait gives up
+// A device-side wait gives up after kDefaultWaitNs of the global timer (or after opts.spin_limit
+// polls when the caller sets one).
+constexpr uint64_t kDefaultWaitNs = uint64_t(10) * 1000000000ull;
 
 // Device memory comes from one stream-ordered pool per device, owned by the library for the life of
 // the process: allocations and frees are ordered on the problem's stream and never synchronise the
@@ -143,9 +148,8 @@ struct pcdn_problem {
   // state
   double* w = nullptr;
   double* w_pos = nullptr;  // w in the walk's position order
-  double* mq = nullptr;
-  void* rec = nullptr;  // sized for the FP64 pair
-  int rec_prec = 0;
+  SampleRec* st = nullptr;  // per-sample maintained quantity and coefficients (32-byte records)
+  int rec_prec = 0;         // precision of the coefficient pairs in st
   double* delta = nullptr;
   uint32_t* touched = nullptr;
   int64_t nwords = 0;
@@ -169,17 +173,29 @@ struct pcdn_problem {
   int64_t* item_off = nullptr;  // [max_items + 1]
   int64_t* plan = nullptr;
   int64_t plan_cap = 0;
-  // bundle scratch
+  // bundle scratch (gk, hk, dk, dkf: two halves of P_cap, by bundle parity)
   int32_t P_cap = 0;
   double* gk = nullptr;
   double* hk = nullptr;
   double* dk = nullptr;
+  float* dkf = nullptr;
   uint32_t* col_cnt = nullptr;
   double* part = nullptr;
+  // row-sorted layout (allocated by the first walk that uses it)
+  int32_t* entry_row = nullptr;  // row of every mirror entry
+  int32_t* br_row = nullptr;
+  int32_t* br_k = nullptr;
+  float* br_val = nullptr;
+  int64_t* br_ptr = nullptr;
+  int64_t br_ptr_cap = 0;
+  int64_t* br_plan = nullptr;
+  int64_t br_plan_cap = 0;
+  RowsWorkspace rws{};
+  double* lspart = nullptr;
   // reductions, barriers, flags
   double* lsacc = nullptr;
   int max_grid = 1;
-  uint32_t* sync = nullptr;  // [0] bar_count [1] bar_gen [4..5] barrier-1 counter (64-bit)
+  uint32_t* sync = nullptr;  // [0] bar_count [1] bar_gen [2..3] barrier-1 flag counts [4..5] barrier-1 counter (64-bit)
   int* err = nullptr;
   unsigned long long* counters = nullptr;
   double* red_part = nullptr;  // block partials
@@ -223,12 +239,15 @@ void free_all(pcdn_problem* p) {
     f(p->col_ptr); f(p->row_idx); f(p->val); f(p->y);
   }
   f(p->row_ptr); f(p->col_idx); f(p->rval); f(p->ylab);
-  f(p->w); f(p->w_pos); f(p->mq); f(p->rec); f(p->delta); f(p->touched);
+  f(p->w); f(p->w_pos); f(p->st); f(p->delta); f(p->touched);
   f(p->item_len); f(p->item_off); f(p->plan);
   f(p->id_perm); f(p->id_item_ptr); f(p->id_items);
   f(p->keys0); f(p->keys1); f(p->vals0); f(p->vals1); f(p->cnt); f(p->item_ptr); f(p->items);
   f(p->hist); f(p->scan_ws);
-  f(p->gk); f(p->hk); f(p->dk); f(p->col_cnt); f(p->part);
+  f(p->gk); f(p->hk); f(p->dk); f(p->dkf); f(p->col_cnt); f(p->part);
+  f(p->entry_row); f(p->br_row); f(p->br_k); f(p->br_val); f(p->br_ptr); f(p->br_plan);
+  f(p->rws.inv); f(p->rws.hist); f(p->rws.scan_ws); f(p->rws.k0); f(p->rws.k1); f(p->rws.v0); f(p->rws.v1);
+  f(p->rws.rhist); f(p->lspart);
   f(p->lsacc); f(p->sync); f(p->err); f(p->counters); f(p->red_part); f(p->red_out);
   f(p->tr_q); f(p->tr_alpha); f(p->tr_Delta); f(p->tr_dF); f(p->epoch_dev);
   f(p->gfull); f(p->shr);
@@ -415,8 +434,7 @@ int finish_create(pcdn_problem* p) {
   p->nwords = (n + 31) / 32;
   CUDA_TRY(palloc(p, &p->w, m));
   CUDA_TRY(palloc(p, &p->w_pos, m));
-  CUDA_TRY(palloc(p, &p->mq, n));
-  CUDA_TRY(palloc(p, (RecT<0>**)&p->rec, n));
+  CUDA_TRY(palloc(p, &p->st, n));
   CUDA_TRY(palloc(p, &p->delta, n));
   CUDA_TRY(palloc(p, &p->touched, p->nwords));
   CUDA_TRY(cudaMemsetAsync(p->w, 0, sizeof(double) * m, s));
@@ -450,14 +468,16 @@ int finish_create(pcdn_problem* p) {
                        &p->launches));
   CUDA_TRY(cudaMemcpyAsync(&p->n_id_items, p->id_item_ptr + m, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
 
-  int bps = 1;
-  CUDA_TRY(walk_max_blocks_per_sm(p->loss, 0, &bps));
-  int bps1 = 1;
-  CUDA_TRY(walk_max_blocks_per_sm(p->loss, 1, &bps1));
-  if (bps1 < bps) bps = bps1;
-  if (bps > 2) bps = 2;
+  int bps = 2;
+  for (int prec = 0; prec < 2; ++prec) {
+    int b = 1;
+    CUDA_TRY(walk_max_blocks_per_sm(p->loss, prec, &b));
+    bps = std::min(bps, b);
+    CUDA_TRY(walk_rows_max_blocks_per_sm(p->loss, prec, &b));
+    bps = std::min(bps, b);
+  }
   if (bps < 1) return fail(PCDN_ECUDA, "bundle walker cannot be resident on this device");
-  p->max_grid = p->sms * bps;
+  p->max_grid = std::min(p->sms * bps, walk_rows_max_grid());
   CUDA_TRY(palloc(p, &p->lsacc, 3 * kPartStride * kAccPad));
   CUDA_TRY(palloc(p, &p->sync, 8));
   CUDA_TRY(palloc(p, &p->err, 4));
@@ -482,13 +502,15 @@ int finish_create(pcdn_problem* p) {
 int ensure_bundle_scratch(pcdn_problem* p, int32_t P) {
   if (P <= p->P_cap) return PCDN_OK;
   auto f = [p](void* q) { dfree(q, p->stream); };
-  f(p->gk); f(p->hk); f(p->dk); f(p->col_cnt);
+  f(p->gk); f(p->hk); f(p->dk); f(p->dkf); f(p->col_cnt);
   p->gk = p->hk = p->dk = nullptr;
+  p->dkf = nullptr;
   p->col_cnt = nullptr;
   p->P_cap = 0;
-  CUDA_TRY(palloc(p, &p->gk, P));
-  CUDA_TRY(palloc(p, &p->hk, P));
-  CUDA_TRY(palloc(p, &p->dk, P));
+  CUDA_TRY(palloc(p, &p->gk, 2 * (int64_t)P));
+  CUDA_TRY(palloc(p, &p->hk, 2 * (int64_t)P));
+  CUDA_TRY(palloc(p, &p->dk, 2 * (int64_t)P));
+  CUDA_TRY(palloc(p, &p->dkf, 2 * (int64_t)P));
   CUDA_TRY(palloc(p, &p->col_cnt, 2 * P));
   CUDA_TRY(cudaMemsetAsync(p->col_cnt, 0, sizeof(uint32_t) * 2 * P, p->stream));
   p->P_cap = P;
@@ -503,6 +525,53 @@ int ensure_plan(pcdn_problem* p, int64_t entries) {
   CUDA_TRY(palloc(p, &p->plan, entries));
   p->plan_cap = entries;
   return PCDN_OK;
+}
+
+// The row-sorted layout's arrays for a walk of nb bundles on G blocks (allocated once, the bundle
+// pointers and block plan grown as needed; the radix-sort workspace only for more than kBins bundles).
+int ensure_rows(pcdn_problem* p, int64_t nb, int G) {
+  const int64_t nnz = p->nnz;
+  if (!p->entry_row) {
+    CUDA_TRY(rows_configure());
+    CUDA_TRY(palloc(p, &p->entry_row, nnz));
+    CUDA_TRY(palloc(p, &p->br_row, nnz));
+    CUDA_TRY(palloc(p, &p->br_k, nnz));
+    CUDA_TRY(palloc(p, &p->br_val, nnz));
+    CUDA_TRY(palloc(p, &p->rws.inv, p->m));
+    CUDA_TRY(palloc(p, &p->rws.hist, rows_hist_elems(nnz)));
+    CUDA_TRY(palloc(p, &p->rws.scan_ws, scan_workspace_elems(std::max(rows_hist_elems(nnz), radix_hist_elems(nnz)))));
+    CUDA_TRY(palloc(p, &p->lspart, 2 * (int64_t)kPartStride * p->max_grid));
+    if (nnz > 0) CUDA_TRY(entry_rows(p->row_ptr, p->n, p->entry_row, p->stream, &p->launches));
+  }
+  if (nb > kBins && !p->rws.k0) {
+    CUDA_TRY(palloc(p, &p->rws.k0, nnz));
+    CUDA_TRY(palloc(p, &p->rws.k1, nnz));
+    CUDA_TRY(palloc(p, &p->rws.v0, nnz));
+    CUDA_TRY(palloc(p, &p->rws.v1, nnz));
+    CUDA_TRY(palloc(p, &p->rws.rhist, radix_hist_elems(nnz)));
+  }
+  if (nb + 1 > p->br_ptr_cap) {
+    dfree(p->br_ptr, p->stream);
+    p->br_ptr = nullptr;
+    p->br_ptr_cap = 0;
+    CUDA_TRY(palloc(p, &p->br_ptr, nb + 1));
+    p->br_ptr_cap = nb + 1;
+  }
+  const int64_t pe = nb * (int64_t)(G + 1);
+  if (pe > p->br_plan_cap) {
+    dfree(p->br_plan, p->stream);
+    p->br_plan = nullptr;
+    p->br_plan_cap = 0;
+    CUDA_TRY(palloc(p, &p->br_plan, pe));
+    p->br_plan_cap = pe;
+  }
+  return PCDN_OK;
+}
+
+// The walker layout of a walk on `grid` blocks (reading of PCDN_LAYOUT_AUTO).
+int walk_layout(const pcdn_opts* o, int grid) {
+  if (o->layout == PCDN_LAYOUT_SCATTER || o->layout == PCDN_LAYOUT_ROWS) return o->layout;
+  return grid > 1 ? PCDN_LAYOUT_ROWS : PCDN_LAYOUT_SCATTER;
 }
 
 int ensure_trace(pcdn_problem* p, int64_t nb) {
@@ -557,9 +626,8 @@ int reset_scratch(pcdn_problem* p) {
 
 int do_refresh(pcdn_problem* p, int prec, bool write_state, bool with_loss) {
   // w_pos (position-order w, used only inside a walk) holds the mixed mode's split copy of w
-  CUDA_TRY(refresh(p->loss, prec, p->row_ptr, p->col_idx, p->rval, p->y, p->w, p->n, p->m, p->nnz, p->w_pos, p->mq,
-                   p->rec, write_state, with_loss ? p->red_part : nullptr, p->red_grid, p->err, p->stream,
-                   &p->launches));
+  CUDA_TRY(refresh(p->loss, prec, p->row_ptr, p->col_idx, p->rval, p->y, p->w, p->n, p->m, p->nnz, p->w_pos, p->st,
+                   write_state, with_loss ? p->red_part : nullptr, p->red_grid, p->err, p->stream, &p->launches));
   if (write_state) p->rec_prec = prec;
   return PCDN_OK;
 }
@@ -569,7 +637,7 @@ int do_refresh(pcdn_problem* p, int prec, bool write_state, bool with_loss) {
 // set directly (the values a refresh from z = Xw gives there, bit for bit) without the pass over X.
 int start_state(pcdn_problem* p, int prec, bool cold) {
   if (!cold) return do_refresh(p, prec, true, false);
-  CUDA_TRY(state_at_zero(p->loss, prec, p->y, p->n, p->mq, p->rec, p->stream, &p->launches));
+  CUDA_TRY(state_at_zero(p->loss, prec, p->y, p->n, p->st, p->stream, &p->launches));
   p->rec_prec = prec;
   return PCDN_OK;
 }
@@ -578,7 +646,8 @@ int start_state(pcdn_problem* p, int prec, bool cold) {
 // nonzeros of the features active in the next outer iteration (p->shr).
 int do_kkt(pcdn_problem* p, int slot, bool shrink = false) {
   if (shrink) CUDA_TRY(cudaMemsetAsync(p->shr, 0, sizeof(unsigned long long) * 3, p->stream));
-  CUDA_TRY(kkt_l1(p->rec_prec, p->id_items, p->n_id_items, p->id_item_ptr, p->id_perm, p->m, p->row_idx, p->val, p->rec,
+  CUDA_TRY(kkt_l1(p->loss, p->rec_prec, p->y, p->n, p->id_items, p->n_id_items, p->id_item_ptr, p->id_perm, p->m,
+                  p->row_idx, p->val, p->st,
                   p->w, p->c, p->l1, p->l2, p->part, p->red_part, p->red_grid, p->red_out + slot, p->stream,
                   &p->launches, shrink ? p->gfull : nullptr, shrink ? p->shr : nullptr));
   if (shrink)
@@ -623,6 +692,7 @@ int check_opts(const pcdn_opts* o) {
   if (o->epoch0 < 0) return fail(PCDN_EINVAL, "epoch0 must be >= 0");
   if (!(o->kkt_ref >= 0) || !std::isfinite(o->kkt_ref)) return fail(PCDN_EINVAL, "kkt_ref must be >= 0 and finite");
   if (o->shrink != 0 && o->shrink != 1) return fail(PCDN_EINVAL, "shrink must be 0 or 1");
+  if (o->layout < PCDN_LAYOUT_AUTO || o->layout > PCDN_LAYOUT_ROWS) return fail(PCDN_EINVAL, "unknown layout");
   return PCDN_OK;
 }
 
@@ -653,14 +723,14 @@ int run_walk(pcdn_problem* p, const pcdn_opts* o, const int32_t* perm, int64_t n
   WalkParams w{};
   w.n = p->n;
   w.m = p->m;
+  w.nnz = p->nnz;
   w.col_ptr = p->col_ptr;
   w.row_idx = p->row_idx;
   w.val = p->val;
   w.y = p->ylab;
   w.c = p->c;
   w.w_pos = p->w_pos;
-  w.mq = p->mq;
-  w.rec = p->rec;
+  w.st = p->st;
   w.delta = p->delta;
   w.touched = p->touched;
   w.nwords = p->nwords;
@@ -679,10 +749,12 @@ int run_walk(pcdn_problem* p, const pcdn_opts* o, const int32_t* perm, int64_t n
   w.col_cnt = p->col_cnt;
   w.anynz = nullptr;
   w.bar1 = reinterpret_cast<unsigned long long*>(p->sync + 4);
+  w.nzc = p->sync + 2;
   w.lsacc = p->lsacc;
   w.bar_count = p->sync;
   w.bar_gen = p->sync + 1;
-  w.spin_limit = o->spin_limit ? o->spin_limit : kDefaultSpin;
+  w.spin_limit = o->spin_limit ? o->spin_limit : 0xffffffffu;
+  w.wait_ns = kDefaultWaitNs;
   w.sigma = o->sigma;
   w.beta = o->beta;
   w.gamma = o->gamma;
@@ -708,13 +780,31 @@ int run_walk(pcdn_problem* p, const pcdn_opts* o, const int32_t* perm, int64_t n
   int rc = ensure_plan(p, nb * (grid + 1));
   if (rc) return rc;
   w.plan = p->plan;
+  w.P_cap = p->P_cap;
+  w.dkf = p->dkf;
+  w.x_vec = ((uintptr_t)p->row_idx % 16 == 0 && (uintptr_t)p->val % 16 == 0) ? 1 : 0;
+  const int layout = walk_layout(o, grid);
   CUDA_TRY(build_plan(p->items, p->max_items, p->item_ptr, npos, P, nb, grid, p->item_len, p->item_off, p->plan,
                       p->scan_ws, p->stream, &p->launches));
+  if (layout == PCDN_LAYOUT_ROWS) {
+    rc = ensure_rows(p, nb, grid);
+    if (rc) return rc;
+    CUDA_TRY(build_rows(perm, npos, p->m, P, nb, grid, p->col_idx, p->rval, p->entry_row, p->nnz, p->rws, p->br_row,
+                        p->br_k, p->br_val, p->br_ptr, p->br_plan, p->stream, &p->launches));
+    w.br_row = p->br_row;
+    w.br_k = p->br_k;
+    w.br_val = p->br_val;
+    w.br_ptr = p->br_ptr;
+    w.br_plan = p->br_plan;
+    w.br_vec = 1;
+    w.lspart = p->lspart;
+  }
   CUDA_TRY(gather_w(p->w, perm, npos, p->w_pos, p->stream, &p->launches));
   CUDA_TRY(cudaMemsetAsync(p->sync, 0, sizeof(uint32_t) * 8, p->stream));
   CUDA_TRY(cudaMemsetAsync(p->lsacc, 0, sizeof(double) * 3 * kPartStride * kAccPad, p->stream));
   CUDA_TRY(record(p->ev0, p));
-  CUDA_TRY(launch_walk(p->loss, (int)o->prec, w, grid, p->stream, p->capturing));
+  if (layout == PCDN_LAYOUT_ROWS) CUDA_TRY(launch_walk_rows(p->loss, (int)o->prec, w, grid, p->stream, p->capturing));
+  else CUDA_TRY(launch_walk(p->loss, (int)o->prec, w, grid, p->stream, p->capturing));
   ++p->launches;
   CUDA_TRY(record(p->ev1, p));
   CUDA_TRY(scatter_w(p->w_pos, perm, npos, p->w, p->stream, &p->launches));
@@ -821,9 +911,11 @@ int device_walker_capacity(int* out) {
       int b = 1;
       CUDA_TRY(walk_max_blocks_per_sm(loss, prec, &b));
       bps = std::min(bps, b);
+      CUDA_TRY(walk_rows_max_blocks_per_sm(loss, prec, &b));
+      bps = std::min(bps, b);
     }
   if (bps < 1) return fail(PCDN_ECUDA, "bundle walker cannot be resident on this device");
-  *out = sms * bps;
+  *out = std::min(sms * bps, walk_rows_max_grid());
   return PCDN_OK;
 }
 
@@ -1025,7 +1117,8 @@ int task_start(SolveTask* t, pcdn_problem* p, int32_t P, double eps, uint64_t se
   t->t0 = std::chrono::steady_clock::now();
   std::memset(t->cnt, 0, sizeof(t->cnt));
   if ((rc = ensure_bundle_scratch(p, P)) || (rc = ensure_trace(p, t->nb)) ||
-      (rc = ensure_plan(p, t->nb * (t->grid + 1))) || (rc = reset_scratch(p)) || (o.shrink && (rc = ensure_shrink(p))))
+      (rc = ensure_plan(p, t->nb * (t->grid + 1))) || (rc = reset_scratch(p)) || (o.shrink && (rc = ensure_shrink(p))) ||
+      (walk_layout(&o, t->grid) == PCDN_LAYOUT_ROWS && (rc = ensure_rows(p, t->nb, t->grid))))
     return end_task(t, rc);
   // from here every failure ends the task (which returns its walker blocks)
   cudaError_t e = cudaSuccess;
@@ -1148,7 +1241,7 @@ int64_t problem_bytes_estimate(int64_t n, int64_t m, int64_t nnz, int32_t P) {
   b += 8 * (m + 1) + 8 * nnz + n;                       // X by columns, labels
   b += (n + 15) / 16 * 16;                              // padded labels
   b += 8 * (n + 1) + 8 * nnz;                           // X by rows
-  b += 16 * m + 8 * n + (int64_t)sizeof(RecT<0>) * n + 8 * n + 4 * ((n + 31) / 32);  // w, w_pos, mq, rec, delta, bitmap
+  b += 16 * m + (int64_t)kStateBytes * n + 8 * n + 4 * ((n + 31) / 32);  // w, w_pos, sample records, delta, bitmap
   b += 16 * m + 8 * m + 16 * (m + 1) + (int64_t)sizeof(Item) * max_items;           // keys, values, cnt, item_ptr, items
   b += 8 * hm + 8 * scan_workspace_elems(scan_n) + 16 * max_items + 16 * (max_items + 1);
   b += 4 * m + 8 * (m + 1) + (int64_t)sizeof(Item) * max_items;                     // identity-order items
@@ -1179,6 +1272,7 @@ void pcdn_default_opts(pcdn_opts* o) {
   o->grid_ctas = 0;
   o->refresh = 1;
   o->spin_limit = 0;
+  o->layout = PCDN_LAYOUT_AUTO;
 }
 
 const char* pcdn_last_error(void) { return g_err.c_str(); }
@@ -1402,7 +1496,7 @@ int pcdn_bundle_step(pcdn_problem* p, const double* w_in, const int32_t* bundle,
     rc = do_refresh(p, prec, true, false);
     if (rc) return rc;
   } else if (p->rec_prec != prec) {
-    CUDA_TRY(rec_from_mq(p->loss, prec, p->mq, p->y, p->n, p->rec, p->stream, &p->launches));
+    CUDA_TRY(rec_from_mq(p->loss, prec, p->y, p->n, p->st, p->stream, &p->launches));
     p->rec_prec = prec;
   }
   rc = ensure_bundle_scratch(p, P);

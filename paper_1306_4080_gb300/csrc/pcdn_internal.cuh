@@ -56,6 +56,32 @@ template <int PREC> struct RecT;
 template <> struct __align__(16) RecT<0> { double cg, ch; };
 template <> struct __align__(8) RecT<1> { float cg, ch; };
 
+// Per-sample state: one 32-byte record per sample (one L2 sector), so that a pass over the touched
+// samples reads and writes each one with a single access:
+//   +0  mq   the maintained quantity (e^{w^T x_i}, or b_i = 1 - y_i w^T x_i)
+//   +8  bak  mq before the bundle's speculative update (row-sorted walker)
+//   +16 the column reductions' coefficient pair: RecT<0> (two doubles) or RecT<1> (two floats)
+struct __align__(32) SampleRec {
+  double mq;
+  double bak;
+  double c[2];
+};
+constexpr int kStateBytes = sizeof(SampleRec);
+__host__ __device__ __forceinline__ double* st_mq(void* st, int64_t i) {
+  return &reinterpret_cast<SampleRec*>(st)[i].mq;
+}
+__host__ __device__ __forceinline__ const double* st_mq(const void* st, int64_t i) {
+  return &reinterpret_cast<const SampleRec*>(st)[i].mq;
+}
+template <int PREC>
+__host__ __device__ __forceinline__ RecT<PREC>* st_rec(void* st, int64_t i) {
+  return reinterpret_cast<RecT<PREC>*>(reinterpret_cast<SampleRec*>(st)[i].c);
+}
+template <int PREC>
+__host__ __device__ __forceinline__ const RecT<PREC>* st_rec(const void* st, int64_t i) {
+  return reinterpret_cast<const RecT<PREC>*>(reinterpret_cast<const SampleRec*>(st)[i].c);
+}
+
 // Decision of a line-search pass, written by the last block to arrive.
 enum : int32_t { kDecAccept = 0, kDecContinue = 1, kDecCap = 2 };
 struct Decision {
@@ -74,7 +100,7 @@ constexpr int kAccPad = 16;  // doubles per line-search accumulator (128 bytes)
 
 struct WalkParams {
   // problem
-  int64_t n, m;
+  int64_t n, m, nnz;
   const int64_t* col_ptr;
   const int32_t* row_idx;
   const float* val;
@@ -82,8 +108,7 @@ struct WalkParams {
   double c;
   // state
   double* w_pos;            // w in position order (the partition's order) during the walk
-  double* mq;
-  void* rec;
+  void* st;                 // [n] SampleRec
   void* delta;              // [n] d^T x of the bundle per row: DeltaT<PREC> (double or float)
   uint32_t* touched;
   int64_t nwords;
@@ -107,7 +132,8 @@ struct WalkParams {
                             // pass mod 3 (FP64 atomic adds; each field on its own 128-byte line)
   uint32_t* bar_count;
   uint32_t* bar_gen;
-  uint32_t spin_limit;
+  uint32_t spin_limit;      // polls a wait may make before it gives up
+  uint64_t wait_ns;         // global-timer nanoseconds a wait may last before it gives up
   // Armijo
   double sigma, beta, gamma, nu;
   float c_f, nu_f;          // c and nu in FP32 (mixed mode's column directions)
@@ -122,8 +148,22 @@ struct WalkParams {
   double* tr_Delta;
   double* tr_dF;
   unsigned long long* counters;  // [8]: ls_steps, cap_hits, passes, nnz, rows, bundles, coord_updates, nonzero-d bundles
-  unsigned long long* bar1;      // barrier 1: low 32 bits arrivals, high 32 bits blocks with a nonzero direction
+  unsigned long long* bar1;      // barrier 1: arrivals
+  uint32_t* nzc;                 // [2] blocks that found a nonzero direction, by barrier-1 parity
   int* err;
+  // row-sorted layout (walk_rows_kernel): the entries of every bundle's columns grouped by row
+  // (rows ascending, columns ascending within a row); entry s of bundle t lies in
+  // [br_ptr[t], br_ptr[t+1]) and holds its row, its position k within the bundle and its value
+  const int32_t* br_row;
+  const int32_t* br_k;
+  const float* br_val;
+  const int64_t* br_ptr;    // [bundles + 1]
+  const int64_t* br_plan;   // [bundles * (gridDim.x + 1)]: first entry of each block, at a row start
+  double* lspart;           // [2][kPartStride][gridDim.x] per-block partial sums, by bundle parity
+  float* dkf;               // [2 * P_cap] d in FP32 (mixed mode), by bundle parity
+  int64_t P_cap;            // stride of the parity halves of gk, hk, dk, dkf
+  int x_vec;                // row_idx and val are 16-byte aligned: 16-byte copies
+  int br_vec;               // br_row, br_k, br_val are 16-byte aligned
 };
 
 // ---------------------------------------------------------------- memory-order helpers
@@ -163,6 +203,128 @@ __device__ __forceinline__ void red_add(double* p, double v) { red_add_f64(p, v)
 __device__ __forceinline__ void red_add(float* p, float v) { red_add_f32(p, v); }
 __device__ __forceinline__ void red_or_u32(uint32_t* p, uint32_t v) {
   asm volatile("red.global.or.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// ---------------------------------------------------------------- bounded waits
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ bool err_set(const WalkParams& p) { return ld_volatile_int(p.err) != 0; }
+
+// A wait between thread blocks gives up after p.spin_limit polls or p.wait_ns nanoseconds of the
+// global timer, whichever comes first (the time bound keeps a legitimate wait on a GPU shared with
+// many other kernels from giving up early; the poll bound lets a test make a wait run out).
+// poll() returns 0 to keep waiting, 1 when the wait gave up (kErrTimeout recorded), 2 when another
+// block recorded an error.
+struct Waiter {
+  uint32_t spins = 0;
+  uint64_t t0 = 0;
+  __device__ __forceinline__ int poll(const WalkParams& p) {
+    ++spins;
+    if (spins > p.spin_limit) {
+      atomicOr(p.err, kErrTimeout);
+      return 1;
+    }
+    if ((spins & 255u) == 0) {
+      if (err_set(p)) return 2;
+      const uint64_t t = global_ns();
+      if (t0 == 0) t0 = t;
+      else if (t - t0 > p.wait_ns) {
+        atomicOr(p.err, kErrTimeout);
+        return 1;
+      }
+    }
+    return 0;
+  }
+};
+
+// ---------------------------------------------------------------- grid barriers
+// The shared-memory struct SH of a walker holds: int abort, has_nz, nonzero; int scan_tot[].
+
+// Plain barrier over the grid.  Returns false when the launch must end (a wait gave up, or a
+// block recorded an error while this one waited).  With one block, a GPU-scope fence stands in for
+// the release/acquire pair, so that the block's atomics (performed in L2) are seen by its later
+// loads.
+template <class SH>
+__device__ bool grid_barrier(const WalkParams& p, uint32_t& idx, SH& sh) {
+  __syncthreads();
+  if (gridDim.x == 1 && threadIdx.x == 0) __threadfence();
+  if (gridDim.x > 1) {
+    if (threadIdx.x == 0) {
+      const uint32_t target = (idx + 1) * gridDim.x;
+      red_release_add_u32(p.bar_count, 1u);
+      Waiter wt;
+      int abort = 0;
+      while (ld_acquire_u32(p.bar_count) < target) {
+        if (wt.poll(p)) { abort = 1; break; }
+      }
+      sh.abort = abort;
+    }
+  }
+  ++idx;
+  __syncthreads();
+  return !sh.abort;
+}
+
+// Split-phase form of grid_barrier: work between arrive and wait must neither write what other
+// blocks read after the barrier nor read what they write before it.
+__device__ __forceinline__ void grid_arrive(const WalkParams& p) {
+  __syncthreads();
+  if (gridDim.x > 1 && threadIdx.x == 0) red_release_add_u32(p.bar_count, 1u);
+}
+template <class SH>
+__device__ bool grid_wait(const WalkParams& p, uint32_t& idx, SH& sh) {
+  if (gridDim.x == 1 && threadIdx.x == 0) __threadfence();
+  if (gridDim.x > 1 && threadIdx.x == 0) {
+    const uint32_t target = (idx + 1) * gridDim.x;
+    Waiter wt;
+    int abort = 0;
+    while (ld_acquire_u32(p.bar_count) < target) {
+      if (wt.poll(p)) { abort = 1; break; }
+    }
+    sh.abort = abort;
+  }
+  ++idx;
+  __syncthreads();
+  return !sh.abort;
+}
+
+// Barrier 1: each block arrives on its own counter (bar1) and, when it found a nonzero direction,
+// first adds 1 to the flag counter of the barrier's parity (nzc[n1 & 1]); the waiters learn whether
+// any block did by comparing that counter with its value at the barrier of the same parity two
+// barriers earlier (seen[0..1]).  A block that runs ahead can only reach the next barrier 1 of the
+// same parity after every block has passed the one in between, so every block reads the same value.
+template <class SH>
+__device__ bool grid_barrier_flag(const WalkParams& p, uint32_t& n1, uint32_t& seen0, uint32_t& seen1, SH& sh) {
+  __syncthreads();
+  if (gridDim.x > 1) {
+    const int par = (int)(n1 & 1);
+    if (threadIdx.x == 0) {
+      const uint64_t target = (uint64_t)(n1 + 1) * gridDim.x;
+      if (sh.has_nz) atomicAdd(p.nzc + par, 1u);
+      red_release_add_u64(p.bar1, 1ull);
+      Waiter wt;
+      int abort = 0;
+      while (ld_acquire_u64(p.bar1) < target) {
+        if (wt.poll(p)) { abort = 1; break; }
+      }
+      const uint32_t v = ld_acquire_u32(p.nzc + par);
+      sh.nonzero = v != (par ? seen1 : seen0);
+      sh.abort = abort;
+      sh.scan_tot[0] = (int)v;
+    }
+    __syncthreads();
+    if (par) seen1 = (uint32_t)sh.scan_tot[0];
+    else seen0 = (uint32_t)sh.scan_tot[0];
+  } else if (threadIdx.x == 0) {
+    __threadfence();
+    sh.nonzero = sh.has_nz;
+  }
+  ++n1;
+  __syncthreads();
+  return !sh.abort;
 }
 
 // Streaming loads of X (ld.global.cs: read about once per bundle step, so evicted first and the
@@ -252,7 +414,7 @@ template <> struct RowCoef<0, 1> {
 template <> struct RowCoef<1, 0> {
   static __device__ __forceinline__ RecT<0> make(double b, int y) {
     RecT<0> r;
-    r.cg = b > 0.0 ? -2.0 * (double)y * b : 0.0;
+    r.cg = b > 0.0 ? -2.0 * (double)y * b : (y > 0 ? -0.0 : 0.0);
     r.ch = b > 0.0 ? 2.0 : 0.0;
     return r;
   }
@@ -260,11 +422,16 @@ template <> struct RowCoef<1, 0> {
 template <> struct RowCoef<1, 1> {
   static __device__ __forceinline__ RecT<1> make(double b, int y) {
     RecT<1> r;
-    r.cg = b > 0.0 ? (float)(-2.0 * (double)y * b) : 0.0f;
+    const float bf = (float)b;
+    r.cg = b > 0.0 ? (y > 0 ? -2.0f * bf : 2.0f * bf) : (y > 0 ? -0.0f : 0.0f);
     r.ch = b > 0.0 ? 2.0f : 0.0f;
     return r;
   }
 };
+// Every coefficient pair carries its sample's label in the sign bit of cg: set for y = +1 (cg is
+// -s <= 0 for the logistic loss, -2 b for the L2-SVM, -0 when zero), clear for y = -1.
+__device__ __forceinline__ int label_from_cg(double cg) { return __double_as_longlong(cg) < 0 ? 1 : -1; }
+__device__ __forceinline__ int label_from_cg(float cg) { return __float_as_int(cg) < 0 ? 1 : -1; }
 
 // Maintained quantity is usable: finite, and for the logistic loss E = e^{w^T x} in [2^-1009,
 // 2^1010), i.e. |w^T x| below about 699.  Tested on the bits (sign and exponent), which keeps the
@@ -374,6 +541,136 @@ __device__ __forceinline__ float warp_sum_f(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
+}
+
+// ---------------------------------------------------------------- exact sums
+// A sum carried exactly as an integer in units of 2^-88, in three signed limbs of 42 bits,
+// v = l2 2^84 + l1 2^42 + l0 (l2 unbounded, l0 and l1 in [0, 2^42) after fx_norm), plus flags for a
+// term that is not finite or whose magnitude reaches 2^59 (1: positive, 2: negative, 4: NaN).
+// Terms are truncated toward zero below 2^-88.  Integer additions are associative, so the sum does
+// not depend on the order in which terms, lanes, warps or blocks are added: results repeat bit for
+// bit whatever the order of atomic additions, on the integer pipes (this part's FP64 pipe runs at a
+// small fraction of its FP32 and integer rates).
+struct Fx {
+  long long l0 = 0, l1 = 0, l2 = 0;
+  unsigned fl = 0;
+};
+constexpr long long kFxMask = (1ll << 42) - 1;
+
+__device__ __forceinline__ void fx_norm(Fx& a) {
+  long long c = a.l0 >> 42;  // arithmetic shift: floor division
+  a.l0 -= c << 42;
+  a.l1 += c;
+  c = a.l1 >> 42;
+  a.l1 -= c << 42;
+  a.l2 += c;
+}
+__device__ __forceinline__ void fx_add(Fx& a, const Fx& b) {
+  a.l0 += b.l0;
+  a.l1 += b.l1;
+  a.l2 += b.l2;
+  a.fl |= b.fl;
+}
+// adds (or subtracts) m 2^s (units of 2^-88; m < 2^53, s <= 122 and m 2^s < 2^147)
+__device__ __forceinline__ void fx_add_bits(Fx& a, unsigned long long m, int s, bool neg) {
+  if (s < 0) {
+    if (s <= -53) return;
+    m >>= -s;
+    s = 0;
+  }
+  long long p0, p1, p2;
+  if (s >= 84) {
+    p0 = 0;
+    p1 = 0;
+    p2 = (long long)(m << (s - 84));
+  } else {
+    const int k = s >= 42 ? 1 : 0, r = s - 42 * k;
+    const long long lo = (long long)((m << r) & (unsigned long long)kFxMask);
+    const unsigned long long hi = r == 0 ? (m >> 42) : (m >> (42 - r));
+    if (k == 0) {
+      p0 = lo;
+      p1 = (long long)(hi & (unsigned long long)kFxMask);
+      p2 = (long long)(hi >> 42);
+    } else {
+      p0 = 0;
+      p1 = lo;
+      p2 = (long long)hi;
+    }
+  }
+  if (neg) {
+    a.l0 -= p0;
+    a.l1 -= p1;
+    a.l2 -= p2;
+  } else {
+    a.l0 += p0;
+    a.l1 += p1;
+    a.l2 += p2;
+  }
+}
+__device__ __forceinline__ void fx_add_f(Fx& a, float x) {
+  const unsigned u = __float_as_uint(x);
+  const int e = (int)((u >> 23) & 0xffu);
+  const bool neg = (u >> 31) != 0;
+  if (e == 0xff) {
+    a.fl |= (u & 0x7fffffu) ? 4u : (neg ? 2u : 1u);
+    return;
+  }
+  if (e > 185) {  // |x| >= 2^59
+    a.fl |= neg ? 2u : 1u;
+    return;
+  }
+  if (e == 0) return;  // below 2^-126: far below the unit
+  fx_add_bits(a, (unsigned long long)((u & 0x7fffffu) | 0x800000u), e - 62, neg);
+}
+__device__ __forceinline__ void fx_add_d(Fx& a, double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((u >> 52) & 0x7ffu);
+  const bool neg = (u >> 63) != 0;
+  if (e == 0x7ff) {
+    a.fl |= (u & 0xfffffffffffffull) ? 4u : (neg ? 2u : 1u);
+    return;
+  }
+  if (e > 1081) {  // |x| >= 2^59
+    a.fl |= neg ? 2u : 1u;
+    return;
+  }
+  if (e == 0) return;
+  fx_add_bits(a, (u & 0xfffffffffffffull) | (1ull << 52), e - 987, neg);
+}
+__device__ __forceinline__ Fx fx_warp_sum(Fx a) {
+  fx_norm(a);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a.l0 += __shfl_xor_sync(0xffffffffu, a.l0, o);
+    a.l1 += __shfl_xor_sync(0xffffffffu, a.l1, o);
+    a.l2 += __shfl_xor_sync(0xffffffffu, a.l2, o);
+  }
+  a.fl = __reduce_or_sync(0xffffffffu, a.fl);
+  fx_norm(a);
+  return a;
+}
+// the sum rounded to FP64 (the limbs normalised first; l0, l1 convert exactly)
+__device__ __forceinline__ double fx_value(Fx a) {
+  if (a.fl & 4u || (a.fl & 3u) == 3u) return __longlong_as_double(0x7ff8000000000000ll);
+  if (a.fl & 1u) return __longlong_as_double(0x7ff0000000000000ll);
+  if (a.fl & 2u) return __longlong_as_double((long long)0xfff0000000000000ull);
+  fx_norm(a);
+  return fma((double)a.l2, 0x1p-4, fma((double)a.l1, 0x1p-46, (double)a.l0 * 0x1p-88));
+}
+// global accumulator of 4 words: limbs, flags
+__device__ __forceinline__ void fx_red_global(long long* g, const Fx& a) {
+  asm volatile("red.global.add.u64 [%0], %1;" ::"l"(g), "l"(a.l0) : "memory");
+  asm volatile("red.global.add.u64 [%0], %1;" ::"l"(g + 1), "l"(a.l1) : "memory");
+  asm volatile("red.global.add.u64 [%0], %1;" ::"l"(g + 2), "l"(a.l2) : "memory");
+  if (a.fl) asm volatile("red.global.or.b64 [%0], %1;" ::"l"(g + 3), "l"((long long)a.fl) : "memory");
+}
+__device__ __forceinline__ Fx fx_load_global(const long long* g) {
+  Fx a;
+  a.l0 = __ldcg(g);
+  a.l1 = __ldcg(g + 1);
+  a.l2 = __ldcg(g + 2);
+  a.fl = (unsigned)__ldcg(g + 3);
+  return a;
 }
 
 __device__ __forceinline__ void kahan_add(float& s, float& comp, float x) {

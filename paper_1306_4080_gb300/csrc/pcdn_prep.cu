@@ -459,7 +459,7 @@ __device__ __forceinline__ double row_loss(int loss, double z, int y) {
 template <int LOSS, int PREC>
 __global__ void __launch_bounds__(kRedThreads) refresh_kernel(const int64_t* row_ptr, const int32_t* col_idx,
                                                               const float* rval, const int8_t* y, const double* w,
-                                                              int64_t n, double* mq, void* rec, int write_state,
+                                                              int64_t n, void* st, int write_state,
                                                               double* loss_part, int* err) {
   __shared__ double wsum[kRedThreads];
   double lsum = 0.0;
@@ -492,8 +492,8 @@ __global__ void __launch_bounds__(kRedThreads) refresh_kernel(const int64_t* row
       } else {
         v = 1.0 - (double)yi * z;
       }
-      mq[i] = v;
-      ((RecT<PREC>*)rec)[i] = RowCoef<LOSS, PREC>::make(v, yi);
+      *st_mq(st, i) = v;
+      *st_rec<PREC>(st, i) = RowCoef<LOSS, PREC>::make(v, yi);
     }
   }
   if (loss_part) {
@@ -526,7 +526,7 @@ __global__ void split_w_kernel(const double* w, int64_t m, float2* w2) {
 template <int LOSS, int T>
 __global__ void __launch_bounds__(kRedThreads) refresh_df_kernel(const int64_t* row_ptr, const int32_t* col_idx,
                                                                  const float* rval, const int8_t* y, const float2* w2,
-                                                                 int64_t n, double* mq, void* rec, int write_state,
+                                                                 int64_t n, void* st, int write_state,
                                                                  double* loss_part, int* err) {
   __shared__ double wsum[kRedThreads];
   __shared__ float2 zs[kRedThreads / 32][32];
@@ -590,8 +590,8 @@ __global__ void __launch_bounds__(kRedThreads) refresh_df_kernel(const int64_t* 
         } else {
           mv = 1.0 - (double)yi * z;
         }
-        mq[i] = mv;
-        ((RecT<1>*)rec)[i] = RowCoef<LOSS, 1>::make(mv, yi);
+        *st_mq(st, i) = mv;
+        *st_rec<1>(st, i) = RowCoef<LOSS, 1>::make(mv, yi);
       }
     }
     __syncwarp();
@@ -609,47 +609,60 @@ __global__ void __launch_bounds__(kRedThreads) refresh_df_kernel(const int64_t* 
 
 template <int LOSS>
 cudaError_t launch_refresh_df(int T, int grid, cudaStream_t s, const int64_t* row_ptr, const int32_t* col_idx,
-                              const float* rval, const int8_t* y, const float2* w2, int64_t n, double* mq, void* rec,
+                              const float* rval, const int8_t* y, const float2* w2, int64_t n, void* st,
                               int ws, double* loss_part, int* err) {
   if (T <= 8)
-    refresh_df_kernel<LOSS, 8><<<grid, kRedThreads, 0, s>>>(row_ptr, col_idx, rval, y, w2, n, mq, rec, ws, loss_part, err);
+    refresh_df_kernel<LOSS, 8><<<grid, kRedThreads, 0, s>>>(row_ptr, col_idx, rval, y, w2, n, st, ws, loss_part, err);
   else if (T <= 16)
-    refresh_df_kernel<LOSS, 16><<<grid, kRedThreads, 0, s>>>(row_ptr, col_idx, rval, y, w2, n, mq, rec, ws, loss_part, err);
+    refresh_df_kernel<LOSS, 16><<<grid, kRedThreads, 0, s>>>(row_ptr, col_idx, rval, y, w2, n, st, ws, loss_part, err);
   else
-    refresh_df_kernel<LOSS, 32><<<grid, kRedThreads, 0, s>>>(row_ptr, col_idx, rval, y, w2, n, mq, rec, ws, loss_part, err);
+    refresh_df_kernel<LOSS, 32><<<grid, kRedThreads, 0, s>>>(row_ptr, col_idx, rval, y, w2, n, st, ws, loss_part, err);
   return cudaGetLastError();
 }
 
 template <int LOSS, int PREC>
-__global__ void rec_from_mq_kernel(const double* mq, const int8_t* y, int64_t n, void* rec) {
+__global__ void rec_from_mq_kernel(const int8_t* y, int64_t n, void* st) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    ((RecT<PREC>*)rec)[i] = RowCoef<LOSS, PREC>::make(mq[i], y[i]);
+    *st_rec<PREC>(st, i) = RowCoef<LOSS, PREC>::make(*st_mq(st, i), y[i]);
+}
+
+// Mixed precision's stopping test (Section 5.1 reading): the gradient's per-sample coefficient cg in
+// FP64 (as FP64 mode computes it from the maintained quantity), kept as a pair of FP32 numbers
+// hi + lo in the record's last 8 bytes (mixed mode stores its FP32 coefficient pair in the 8 before),
+// so that the KKT column sums run in double-float arithmetic on the FP32 pipe at FP64-grade accuracy.
+template <int LOSS>
+__global__ void kkt_coef_kernel(const int8_t* y, int64_t n, void* st) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double cg = RowCoef<LOSS, 0>::make(*st_mq(st, i), y[i]).cg;
+    const float hi = (float)cg;
+    reinterpret_cast<float2*>(reinterpret_cast<SampleRec*>(st)[i].c)[1] = make_float2(hi, (float)(cg - (double)hi));
+  }
 }
 
 // At w = 0: z = 0, so E = e^0 = 1 (logistic) and b = 1 - y 0 = 1 (L2-SVM), exactly what a refresh
 // from z = Xw gives there.
 template <int LOSS, int PREC>
-__global__ void state_at_zero_kernel(const int8_t* y, int64_t n, double* mq, void* rec) {
+__global__ void state_at_zero_kernel(const int8_t* y, int64_t n, void* st) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    mq[i] = 1.0;
-    ((RecT<PREC>*)rec)[i] = RowCoef<LOSS, PREC>::make(1.0, y[i]);
+    *st_mq(st, i) = 1.0;
+    *st_rec<PREC>(st, i) = RowCoef<LOSS, PREC>::make(1.0, y[i]);
   }
 }
 
 // ------------------------------------------------------------------------------------ KKT
 template <int PREC>
 __global__ void __launch_bounds__(kRedThreads) kkt_item_kernel(const Item* items, int64_t n_items, const int32_t* row_idx,
-                                                               const float* val, const void* recp, double* gpart) {
+                                                               const float* val, const void* st, double* gpart) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t warps = (int64_t)gridDim.x * (kRedThreads / 32);
-  const RecT<PREC>* rec = (const RecT<PREC>*)recp;
+  const SampleRec* rec = reinterpret_cast<const SampleRec*>(st);
   constexpr int U = 4;  // entries per lane in flight: U index/value loads, then U gathers
   for (int64_t i = (int64_t)blockIdx.x * (kRedThreads / 32) + wid; i < n_items; i += warps) {
     const Item it = items[i];
     const int64_t end = it.start + it.len;
     // each lane sums its entries e = start + lane, + 32, ... in that order
-    using Acc = typename std::conditional<PREC == 0, double, float>::type;
-    Acc acc = Acc(0);
+    double acc = 0.0;  // FP64 mode
+    dfloat dacc = {0.0f, 0.0f};  // mixed mode: x (hi + lo) as an error-free product plus x lo
     for (int64_t e0 = it.start + lane; e0 < end; e0 += 32 * U) {
       int32_t r[U];
       float v[U];
@@ -659,23 +672,35 @@ __global__ void __launch_bounds__(kRedThreads) kkt_item_kernel(const Item* items
         r[u] = e < end ? row_idx[e] : -1;
         v[u] = e < end ? val[e] : 0.0f;
       }
-      Acc cg[U];
+      if constexpr (PREC == 0) {
+        double cg[U];
 #pragma unroll
-      for (int u = 0; u < U; ++u) cg[u] = r[u] >= 0 ? (Acc)rec[r[u]].cg : Acc(0);
+        for (int u = 0; u < U; ++u) cg[u] = r[u] >= 0 ? rec[r[u]].c[0] : 0.0;
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        if (r[u] < 0) break;
-        if constexpr (PREC == 0) acc = fma((double)v[u], cg[u], acc);
-        else acc = fmaf(v[u], cg[u], acc);
+        for (int u = 0; u < U; ++u) {
+          if (r[u] < 0) break;
+          acc = fma((double)v[u], cg[u], acc);
+        }
+      } else {
+        float2 cg[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          cg[u] = r[u] >= 0 ? reinterpret_cast<const float2*>(rec[r[u]].c)[1] : make_float2(0.0f, 0.0f);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if (r[u] < 0) break;
+          const float ph = v[u] * cg[u].x;
+          const float pl = fmaf(v[u], cg[u].y, fmaf(v[u], cg[u].x, -ph));
+          dacc = df_add(dacc, dfloat{ph, pl});
+        }
       }
     }
     if constexpr (PREC == 0) {
       const double g = warp_sum(acc);
       if (lane == 0) gpart[i] = g;
     } else {
-      // FP32 sums (this mode's column sums), stored as float; the column kernel widens them
-      acc = warp_sum_f(acc);
-      if (lane == 0) reinterpret_cast<float*>(gpart)[i] = acc;
+      dacc = df_warp_sum(dacc);
+      if (lane == 0) gpart[i] = df_value(dacc);
     }
   }
 }
@@ -691,7 +716,7 @@ __global__ void __launch_bounds__(kRedThreads) kkt_col_kernel(const int64_t* ite
   __shared__ double red[kRedThreads];
   double acc = 0.0, vm = 0.0;
   const int lane = threadIdx.x & 31;
-  auto part = [&](int64_t i) { return PREC == 0 ? gpart[i] : (double)reinterpret_cast<const float*>(gpart)[i]; };
+  auto part = [&](int64_t i) { return gpart[i]; };
   // a thread per feature; a feature of more than kLongItems items (a Zipf head column cut into
   // thousands of chunks) is summed by its whole warp, lane-strided and then a fixed butterfly
   constexpr int64_t kLongItems = 64;
@@ -1005,7 +1030,7 @@ cudaError_t validate_device(const int64_t* col_ptr, const int32_t* row_idx, cons
 
 cudaError_t refresh(int loss, int prec, const int64_t* row_ptr, const int32_t* col_idx, const float* rval,
                     const int8_t* y, const double* w, int64_t n, int64_t m, int64_t nnz, void* w2_scratch,
-                    double* mq, void* rec, bool write_state, double* loss_part, int grid, int* err, cudaStream_t s,
+                    void* st, bool write_state, double* loss_part, int grid, int* err, cudaStream_t s,
                     int64_t* launches) {
   const int ws = write_state ? 1 : 0;
   // without per-block loss partials any block count works: twice the blocks for more loads in flight
@@ -1018,50 +1043,54 @@ cudaError_t refresh(int loss, int prec, const int64_t* row_ptr, const int32_t* c
     // lanes per row from the mean row length: about 4-8 nonzeros per lane
     const double mean = n > 0 ? (double)nnz / (double)n : 0.0;
     const int T = mean < 64.0 ? 8 : (mean < 256.0 ? 16 : 32);
-    if (loss == 0) e = launch_refresh_df<0>(T, grid, s, row_ptr, col_idx, rval, y, w2, n, mq, rec, ws, loss_part, err);
-    else e = launch_refresh_df<1>(T, grid, s, row_ptr, col_idx, rval, y, w2, n, mq, rec, ws, loss_part, err);
+    if (loss == 0) e = launch_refresh_df<0>(T, grid, s, row_ptr, col_idx, rval, y, w2, n, st, ws, loss_part, err);
+    else e = launch_refresh_df<1>(T, grid, s, row_ptr, col_idx, rval, y, w2, n, st, ws, loss_part, err);
     if (launches) ++*launches;
     return e;
   }
   if (loss == 0 && prec == 0)
-    refresh_kernel<0, 0><<<grid, kRedThreads, 0, s>>>(row_ptr, col_idx, rval, y, w, n, mq, rec, ws, loss_part, err);
+    refresh_kernel<0, 0><<<grid, kRedThreads, 0, s>>>(row_ptr, col_idx, rval, y, w, n, st, ws, loss_part, err);
   else if (loss == 0)
-    refresh_kernel<0, 1><<<grid, kRedThreads, 0, s>>>(row_ptr, col_idx, rval, y, w, n, mq, rec, ws, loss_part, err);
+    refresh_kernel<0, 1><<<grid, kRedThreads, 0, s>>>(row_ptr, col_idx, rval, y, w, n, st, ws, loss_part, err);
   else if (prec == 0)
-    refresh_kernel<1, 0><<<grid, kRedThreads, 0, s>>>(row_ptr, col_idx, rval, y, w, n, mq, rec, ws, loss_part, err);
+    refresh_kernel<1, 0><<<grid, kRedThreads, 0, s>>>(row_ptr, col_idx, rval, y, w, n, st, ws, loss_part, err);
   else
-    refresh_kernel<1, 1><<<grid, kRedThreads, 0, s>>>(row_ptr, col_idx, rval, y, w, n, mq, rec, ws, loss_part, err);
+    refresh_kernel<1, 1><<<grid, kRedThreads, 0, s>>>(row_ptr, col_idx, rval, y, w, n, st, ws, loss_part, err);
   return post(launches);
 }
 
-cudaError_t rec_from_mq(int loss, int prec, const double* mq, const int8_t* y, int64_t n, void* rec, cudaStream_t s,
-                        int64_t* launches) {
+cudaError_t rec_from_mq(int loss, int prec, const int8_t* y, int64_t n, void* st, cudaStream_t s, int64_t* launches) {
   const unsigned g = grid_for(n, 256);
-  if (loss == 0 && prec == 0) rec_from_mq_kernel<0, 0><<<g, 256, 0, s>>>(mq, y, n, rec);
-  else if (loss == 0) rec_from_mq_kernel<0, 1><<<g, 256, 0, s>>>(mq, y, n, rec);
-  else if (prec == 0) rec_from_mq_kernel<1, 0><<<g, 256, 0, s>>>(mq, y, n, rec);
-  else rec_from_mq_kernel<1, 1><<<g, 256, 0, s>>>(mq, y, n, rec);
+  if (loss == 0 && prec == 0) rec_from_mq_kernel<0, 0><<<g, 256, 0, s>>>(y, n, st);
+  else if (loss == 0) rec_from_mq_kernel<0, 1><<<g, 256, 0, s>>>(y, n, st);
+  else if (prec == 0) rec_from_mq_kernel<1, 0><<<g, 256, 0, s>>>(y, n, st);
+  else rec_from_mq_kernel<1, 1><<<g, 256, 0, s>>>(y, n, st);
   return post(launches);
 }
 
-cudaError_t state_at_zero(int loss, int prec, const int8_t* y, int64_t n, double* mq, void* rec, cudaStream_t s,
-                          int64_t* launches) {
+cudaError_t state_at_zero(int loss, int prec, const int8_t* y, int64_t n, void* st, cudaStream_t s, int64_t* launches) {
   const unsigned g = grid_for(n, 256);
-  if (loss == 0 && prec == 0) state_at_zero_kernel<0, 0><<<g, 256, 0, s>>>(y, n, mq, rec);
-  else if (loss == 0) state_at_zero_kernel<0, 1><<<g, 256, 0, s>>>(y, n, mq, rec);
-  else if (prec == 0) state_at_zero_kernel<1, 0><<<g, 256, 0, s>>>(y, n, mq, rec);
-  else state_at_zero_kernel<1, 1><<<g, 256, 0, s>>>(y, n, mq, rec);
+  if (loss == 0 && prec == 0) state_at_zero_kernel<0, 0><<<g, 256, 0, s>>>(y, n, st);
+  else if (loss == 0) state_at_zero_kernel<0, 1><<<g, 256, 0, s>>>(y, n, st);
+  else if (prec == 0) state_at_zero_kernel<1, 0><<<g, 256, 0, s>>>(y, n, st);
+  else state_at_zero_kernel<1, 1><<<g, 256, 0, s>>>(y, n, st);
   return post(launches);
 }
 
-cudaError_t kkt_l1(int prec, const Item* items, int64_t n_items, const int64_t* item_ptr, const int32_t* perm,
-                   int64_t npos, const int32_t* row_idx, const float* val, const void* rec, const double* w, double c,
-                   double l1, double l2, double* gpart, double* block_part, int grid, double* out, cudaStream_t s,
-                   int64_t* launches, double* g_out, unsigned long long* vmax) {
+cudaError_t kkt_l1(int loss, int prec, const int8_t* y, int64_t n, const Item* items, int64_t n_items,
+                   const int64_t* item_ptr, const int32_t* perm, int64_t npos, const int32_t* row_idx, const float* val,
+                   void* st, const double* w, double c, double l1, double l2, double* gpart, double* block_part,
+                   int grid, double* out, cudaStream_t s, int64_t* launches, double* g_out, unsigned long long* vmax) {
+  cudaError_t e;
+  if (prec == 1) {  // the FP64 coefficients the mixed-precision item pass reads
+    if (loss == 0) kkt_coef_kernel<0><<<grid_for(n, 256), 256, 0, s>>>(y, n, st);
+    else kkt_coef_kernel<1><<<grid_for(n, 256), 256, 0, s>>>(y, n, st);
+    if ((e = post(launches)) != cudaSuccess) return e;
+  }
   // the item pass writes one sum per item, no block partials: twice the blocks for more loads in flight
-  if (prec == 0) kkt_item_kernel<0><<<2 * grid, kRedThreads, 0, s>>>(items, n_items, row_idx, val, rec, gpart);
-  else kkt_item_kernel<1><<<2 * grid, kRedThreads, 0, s>>>(items, n_items, row_idx, val, rec, gpart);
-  cudaError_t e = post(launches);
+  if (prec == 0) kkt_item_kernel<0><<<2 * grid, kRedThreads, 0, s>>>(items, n_items, row_idx, val, st, gpart);
+  else kkt_item_kernel<1><<<2 * grid, kRedThreads, 0, s>>>(items, n_items, row_idx, val, st, gpart);
+  e = post(launches);
   if (e != cudaSuccess) return e;
   if (prec == 0)
     kkt_col_kernel<0><<<grid, kRedThreads, 0, s>>>(item_ptr, perm, npos, gpart, w, c, l1, l2, block_part, g_out, vmax);

@@ -67,34 +67,61 @@ cudaError_t copy_keys_u32(const int32_t* src, uint32_t* dst, int64_t n, cudaStre
 cudaError_t gather_csr(const int32_t* order, const int32_t* entry_col, const float* val, int64_t nnz,
                        int32_t* col_idx, float* rval, cudaStream_t s, int64_t* launches);
 
+// ---- row-sorted bundle layout (pcdn_rows.cu) ---------------------------------------------------
+// Row of every entry of the row-major mirror.
+cudaError_t entry_rows(const int64_t* row_ptr, int64_t n, int32_t* entry_row, cudaStream_t s, int64_t* launches);
+// Bundle counts up to kBins use one counting sort; more use a radix sort.
+constexpr int kBins = 1024;
+struct RowsWorkspace {
+  int32_t* inv;       // [m] position of each feature in the walk, -1 outside it
+  int64_t* hist;      // [rows_hist_elems(nnz)] (counting sort)
+  int64_t* scan_ws;   // scan workspace for max(rows_hist_elems, radix_hist_elems) elements
+  uint32_t* k0;       // radix sort keys and values [nnz] each (only for more than kBins bundles)
+  uint32_t* k1;
+  int32_t* v0;
+  int32_t* v1;
+  int64_t* rhist;     // [radix_hist_elems(nnz)]
+};
+cudaError_t rows_configure();
+int64_t rows_tiles(int64_t nnz);
+int64_t rows_hist_elems(int64_t nnz);
+// The walk's entries by bundle, grouped by row (see pcdn_rows.cu): br_row/br_k/br_val[nnz],
+// br_ptr[nb + 1], br_plan[nb * (G + 1)].
+cudaError_t build_rows(const int32_t* perm, int64_t npos, int64_t m, int32_t P, int64_t nb, int G,
+                       const int32_t* col_idx, const float* rval, const int32_t* entry_row, int64_t nnz,
+                       const RowsWorkspace& ws, int32_t* br_row, int32_t* br_k, float* br_val, int64_t* br_ptr,
+                       int64_t* br_plan, cudaStream_t s, int64_t* launches);
+
 // ---- validation (device-resident input) -------------------------------------------------------
 cudaError_t validate_device(const int64_t* col_ptr, const int32_t* row_idx, const float* val, const int8_t* y,
                             int64_t n, int64_t m, int64_t nnz, int* flag, cudaStream_t s, int64_t* launches);
 
 // ---- maintained quantities --------------------------------------------------------------------
-// z = Xw by rows; mq and rec from z (write_state), optional per-block loss partial sums.
+// z = Xw by rows; each sample's maintained quantity and coefficients (SampleRec) from z (write_state),
+// optional per-block loss partial sums.
 // FP64 (prec 0, or no scratch): one lane per row, separate multiply and add in column order.
 // Mixed (prec 1 with w2_scratch, 8 bytes per feature): double-float sums on the FP32 pipe.
 cudaError_t refresh(int loss, int prec, const int64_t* row_ptr, const int32_t* col_idx, const float* rval,
                     const int8_t* y, const double* w, int64_t n, int64_t m, int64_t nnz, void* w2_scratch,
-                    double* mq, void* rec, bool write_state, double* loss_part, int grid, int* err, cudaStream_t s,
+                    void* st, bool write_state, double* loss_part, int grid, int* err, cudaStream_t s,
                     int64_t* launches);
 // The maintained quantities and coefficients at w = 0 (mq = 1 for both losses), without reading X.
-cudaError_t state_at_zero(int loss, int prec, const int8_t* y, int64_t n, double* mq, void* rec, cudaStream_t s,
-                          int64_t* launches);
-// rec from the current mq (precision switch without recomputing z).
-cudaError_t rec_from_mq(int loss, int prec, const double* mq, const int8_t* y, int64_t n, void* rec, cudaStream_t s,
-                        int64_t* launches);
+cudaError_t state_at_zero(int loss, int prec, const int8_t* y, int64_t n, void* st, cudaStream_t s, int64_t* launches);
+// The coefficients from the current mq (precision switch without recomputing z).
+cudaError_t rec_from_mq(int loss, int prec, const int8_t* y, int64_t n, void* st, cudaStream_t s, int64_t* launches);
 
 // ---- reductions -------------------------------------------------------------------------------
-// Minimum-norm subgradient l1 norm from the coefficients in rec, over work items of all columns.
+// Minimum-norm subgradient l1 norm from the samples' coefficients, over work items of all columns:
+// FP64 mode from the FP64 coefficient pair; mixed mode from the FP64 coefficient recomputed from mq
+// and summed in double-float arithmetic (kkt_coef_kernel).
 // When g_out / vmax are given (shrinking): g_j of every feature into g_out[j], and the largest
 // |v_j| into *vmax (as the bits of the double; *vmax zeroed by the caller).
 // l1, l2: the penalty l1 ||w||_1 + (l2/2) ||w||^2 (g is the smooth part's gradient).
-cudaError_t kkt_l1(int prec, const Item* items, int64_t n_items, const int64_t* item_ptr, const int32_t* perm,
-                   int64_t npos, const int32_t* row_idx, const float* val, const void* rec, const double* w,
-                   double c, double l1, double l2, double* gpart, double* block_part, int grid, double* out,
-                   cudaStream_t s, int64_t* launches, double* g_out = nullptr, unsigned long long* vmax = nullptr);
+cudaError_t kkt_l1(int loss, int prec, const int8_t* y, int64_t n, const Item* items, int64_t n_items,
+                   const int64_t* item_ptr, const int32_t* perm, int64_t npos, const int32_t* row_idx, const float* val,
+                   void* st, const double* w, double c, double l1, double l2, double* gpart, double* block_part,
+                   int grid, double* out, cudaStream_t s, int64_t* launches, double* g_out = nullptr,
+                   unsigned long long* vmax = nullptr);
 
 // ---- shrinking (between outer iterations) ------------------------------------------------------
 // A feature is active unless w_j = 0 and |g_j| < l1 - M / n_samples, M = *vmax (the largest |v_j|).

@@ -157,91 +157,6 @@ template <> struct Acc<1> {
   __device__ __forceinline__ double value() const { return df_value(v); }
 };
 
-// ---------------------------------------------------------------- barriers
-__device__ __forceinline__ bool err_set(const WalkParams& p) { return ld_volatile_int(p.err) != 0; }
-
-// Plain barrier over the grid.  Returns false when the launch must end (a wait gave up, or a
-// block recorded an error while this one waited).  With one block, a GPU-scope fence stands in for
-// the release/acquire pair, so that the block's atomics (performed in L2) are seen by its later
-// loads.
-template <class SH>
-__device__ bool grid_barrier(const WalkParams& p, uint32_t& idx, SH& sh) {
-  __syncthreads();
-  if (gridDim.x == 1 && threadIdx.x == 0) __threadfence();
-  if (gridDim.x > 1) {
-    if (threadIdx.x == 0) {
-      const uint32_t target = (idx + 1) * gridDim.x;
-      red_release_add_u32(p.bar_count, 1u);
-      uint32_t spins = 0;
-      int abort = 0;
-      while (ld_acquire_u32(p.bar_count) < target) {
-        if (++spins > p.spin_limit) { atomicOr(p.err, kErrTimeout); abort = 1; break; }
-        if ((spins & 1023u) == 0 && err_set(p)) { abort = 1; break; }
-      }
-      sh.abort = abort;
-    }
-  }
-  ++idx;
-  __syncthreads();
-  return !sh.abort;
-}
-
-// Split-phase form of grid_barrier: work between arrive and wait must neither write what other
-// blocks read after the barrier nor read what they write before it.
-__device__ __forceinline__ void grid_arrive(const WalkParams& p) {
-  __syncthreads();
-  if (gridDim.x > 1 && threadIdx.x == 0) red_release_add_u32(p.bar_count, 1u);
-}
-template <class SH>
-__device__ bool grid_wait(const WalkParams& p, uint32_t& idx, SH& sh) {
-  if (gridDim.x == 1 && threadIdx.x == 0) __threadfence();
-  if (gridDim.x > 1 && threadIdx.x == 0) {
-    const uint32_t target = (idx + 1) * gridDim.x;
-    uint32_t spins = 0;
-    int abort = 0;
-    while (ld_acquire_u32(p.bar_count) < target) {
-      if (++spins > p.spin_limit) { atomicOr(p.err, kErrTimeout); abort = 1; break; }
-      if ((spins & 1023u) == 0 && err_set(p)) { abort = 1; break; }
-    }
-    sh.abort = abort;
-  }
-  ++idx;
-  __syncthreads();
-  return !sh.abort;
-}
-
-// Barrier 1: each block adds 1 (arrival) + (has_nz << 32); the waiters also learn whether any
-// block found a nonzero direction.  `seen` is the high word at the previous barrier 1.
-template <class SH>
-__device__ bool grid_barrier_flag(const WalkParams& p, uint32_t& n1, uint32_t& seen, SH& sh) {
-  __syncthreads();
-  if (gridDim.x > 1) {
-    if (threadIdx.x == 0) {
-      const uint64_t target = (uint64_t)(n1 + 1) * gridDim.x;
-      red_release_add_u64(p.bar1, 1ull + ((unsigned long long)(sh.has_nz ? 1 : 0) << 32));
-      uint32_t spins = 0;
-      int abort = 0;
-      uint64_t v;
-      while (((v = ld_acquire_u64(p.bar1)) & 0xffffffffull) < target) {
-        if (++spins > p.spin_limit) { atomicOr(p.err, kErrTimeout); abort = 1; break; }
-        if ((spins & 1023u) == 0 && err_set(p)) { abort = 1; break; }
-      }
-      const uint32_t hi = (uint32_t)(v >> 32);
-      sh.nonzero = hi != seen;
-      sh.abort = abort;
-      sh.scan_tot[0] = (int)hi;
-    }
-    __syncthreads();
-    seen = (uint32_t)sh.scan_tot[0];
-  } else if (threadIdx.x == 0) {
-    __threadfence();
-    sh.nonzero = sh.has_nz;
-  }
-  ++n1;
-  __syncthreads();
-  return !sh.abort;
-}
-
 // ---------------------------------------------------------------- phase A helpers
 template <int PREC>
 struct ColAcc;
@@ -357,10 +272,9 @@ __device__ __forceinline__ int block_scan_incl(SH& sh, int v) {
 // Waits (one thread) until all nch chunks of a column have published; false on timeout or another
 // block's error.
 __device__ __forceinline__ bool split_wait(const WalkParams& p, const uint32_t* cnt, int nch) {
-  uint32_t spins = 0;
+  Waiter wt;
   while (ld_acquire_u32(cnt) != (uint32_t)nch) {
-    if (++spins > p.spin_limit) { atomicOr(p.err, kErrTimeout); return false; }
-    if ((spins & 1023u) == 0 && err_set(p)) return false;
+    if (wt.poll(p)) return false;
   }
   return true;
 }
@@ -511,7 +425,6 @@ __device__ void column_pass(const WalkParams& p, SharedWalk<PREC>& sh, int64_t l
                             uint32_t* col_cnt) {
   const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
   StageA<PREC>& st = sh.u.a;
-  const RecT<PREC>* rec = (const RecT<PREC>*)p.rec;
   if (tid == 0) {
     sh.n_split = 0;
     sh.apart[0] = sh.apart[1] = sh.apart[2] = Acc<PREC>().store();
@@ -539,8 +452,8 @@ __device__ void column_pass(const WalkParams& p, SharedWalk<PREC>& sh, int64_t l
     }
     // the rows' coefficient pairs
     for (int v = tid; v < eb; v += kWalkThreads) {
-      if constexpr (PREC == 0) cp_async16(&st.rec[v], rec + sh.row[v]);
-      else cp_async8(&st.rec[v], rec + sh.row[v]);
+      if constexpr (PREC == 0) cp_async16(&st.rec[v], st_rec<0>(p.st, sh.row[v]));
+      else cp_async8(&st.rec[v], st_rec<1>(p.st, sh.row[v]));
     }
     cp_async_commit();
     // chunks of split columns processed by this batch, listed in item order for the deferred
@@ -895,8 +808,8 @@ __device__ __forceinline__ void row_update(const WalkParams& p, int32_t r, const
     else mq = mq - alpha * (double)(rv.y > 0 ? rv.dl : -rv.dl);
   }
   if (!mq_ok<LOSS>(mq)) atomicOr(p.err, kErrRange);
-  p.mq[r] = mq;
-  ((RecT<PREC>*)p.rec)[r] = RowCoef<LOSS, PREC>::make(mq, rv.y);
+  *st_mq(p.st, r) = mq;
+  *st_rec<PREC>(p.st, r) = RowCoef<LOSS, PREC>::make(mq, rv.y);
 }
 
 // ---------------------------------------------------------------- phases B and C: the touched rows
@@ -968,8 +881,8 @@ __device__ __forceinline__ void stage_rows(const WalkParams& p, RowStage<PREC>& 
     const int32_t r = rs.row[i];
     if constexpr (PREC == 0) cp_async8(&rs.dl[i], static_cast<const double*>(p.delta) + r);
     else cp_async4(&rs.dl[i], static_cast<const float*>(p.delta) + r);
-    cp_async8(&rs.mq[i], p.mq + r);
-    if constexpr (PREC == 1 && LOSS == 0) cp_async8(&rs.rc[i], static_cast<const RecT<1>*>(p.rec) + r);
+    cp_async8(&rs.mq[i], st_mq(p.st, r));
+    if constexpr (PREC == 1 && LOSS == 0) cp_async8(&rs.rc[i], st_rec<1>(p.st, r));
     cp_async4(&rs.yw[i], p.y + (r & ~3));
   }
   cp_async_commit();
@@ -1031,7 +944,7 @@ __global__ void __launch_bounds__(kWalkThreads, 2) walk_kernel(WalkParams p) {
   const int lane = tid & 31;
   const int wib = tid >> 5;
   const int G = (int)gridDim.x;
-  uint32_t bar = 0, n1 = 0, seen = 0, npass = 0;
+  uint32_t bar = 0, n1 = 0, seen0 = 0, seen1 = 0, npass = 0;
   if (tid == 0) {
     sh.abort = 0;
     sh.has_nz = 0;
@@ -1064,7 +977,7 @@ __global__ void __launch_bounds__(kWalkThreads, 2) walk_kernel(WalkParams p) {
       const int64_t* pl = p.plan + t * (int64_t)(G + 1) + blockIdx.x;
       column_pass<LOSS, PREC>(p, sh, lo, pl[0], pl[1], p.col_cnt + (t & 1) * (int64_t)p.P);
     }
-    if (!grid_barrier_flag(p, n1, seen, sh)) return;  // no copies in flight: the column pass waited
+    if (!grid_barrier_flag(p, n1, seen0, seen1, sh)) return;  // no copies in flight: the column pass waited
     if (tid == 0) sh.has_nz = 0;  // read by the barrier above; next written in the next column pass
     const int64_t kpb = (Pt + G - 1) / G;  // bundle positions per block
     const int64_t k0 = min((int64_t)Pt, (int64_t)blockIdx.x * kpb), k1 = min((int64_t)Pt, k0 + kpb);

@@ -84,14 +84,15 @@ def test_permutation_bitwise(pk, name):
 CASES = [("lr_2k_10k", 64), ("svm_20k_100k", 1024), ("svm_20k_100k", 8), ("ragged_lr", 100), ("ragged_svm", 97)]
 
 
+@pytest.mark.parametrize("layout", ["scatter", "rows"])
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("grid", [1, 0])
 @pytest.mark.parametrize("name,Pb", CASES)
-def test_bundle_step_parity(pk, name, Pb, grid, prec):
+def test_bundle_step_parity(pk, name, Pb, grid, prec, layout):
     wl, p = problem(name)
     orc = oracle.Oracle.from_problem(p, wl.C, wl.loss)
     P = pk.Problem.from_csc(p.col_ptr, p.row_idx, p.val, p.y, wl.C, wl.loss)
-    opts = pk.pcdn_default_opts(prec=prec, grid_ctas=(grid if grid else 100000))
+    opts = pk.pcdn_default_opts(prec=prec, grid_ctas=(grid if grid else 100000), layout=layout)
     armijo = oracle.Armijo()
     tol = 1e-9 if prec == "fp64" else 1e-5
     try:
@@ -125,16 +126,17 @@ def test_bundle_step_parity(pk, name, Pb, grid, prec):
         P.close()
 
 
+@pytest.mark.parametrize("layout", ["scatter", "rows"])
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("name,Pb,grid", [("lr_2k_10k", 64, 0), ("lr_2k_10k", 64, 100000), ("svm_20k_100k", 256, 0),
                                           ("svm_20k_100k", 1024, 0), ("ragged_svm", 97, 100000)])
-def test_solve_parity(pk, name, Pb, grid, prec):
+def test_solve_parity(pk, name, Pb, grid, prec, layout):
     wl, p = problem(name)
     orc = oracle.Oracle.from_problem(p, wl.C, wl.loss)
     wo, so = orc.solve(Pb, eps=wl.eps, seed=wl.solver_seed, trace=True, max_epochs=200)
     P = pk.Problem.from_csc(p.col_ptr, p.row_idx, p.val, p.y, wl.C, wl.loss)
     try:
-        opts = pk.pcdn_default_opts(prec=prec, grid_ctas=grid, max_epochs=200)
+        opts = pk.pcdn_default_opts(prec=prec, grid_ctas=grid, max_epochs=200, layout=layout)
         nb = so["bundles"] + 8
         rc, w, st, tr = P.solve(Pb, wl.eps, wl.solver_seed, opts, trace_bundles=int(nb), trace_epochs=200)
         assert st["converged"] and so["converged"]
