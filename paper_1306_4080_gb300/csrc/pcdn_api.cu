@@ -1496,7 +1496,7 @@ int pcdn_bundle_step(pcdn_problem* p, const double* w_in, const int32_t* bundle,
     rc = do_refresh(p, prec, true, false);
     if (rc) return rc;
   } else if (p->rec_prec != prec) {
-    CUDA_TRY(rec_from_mq(p->loss, prec, p->y, p->n, p->st, p->stream, &p->launches));
+    CUDA_TRY(convert_state(p->loss, prec, p->y, p->n, p->st, p->stream, &p->launches));
     p->rec_prec = prec;
   }
   rc = ensure_bundle_scratch(p, P);

@@ -362,6 +362,11 @@ __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
 __device__ __forceinline__ int warp_sum_int(int v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -375,121 +380,6 @@ __device__ __forceinline__ double newton_direction(double g, double h, double w,
   if (g + l1 <= h * w) return -(g + l1) / h;
   if (g - l1 >= h * w) return -(g - l1) / h;
   return -w;
-}
-
-// ---------------------------------------------------------------- per-sample coefficients
-// Logistic (Eq. 11): with E = e^{z}, s = 1/(1+E), p = E/(1+E):
-//   (tau(y z) - 1) y = -s (y = +1) or p (y = -1);  tau (1 - tau) = p s.
-// L2-SVM (Appendix A, proof of Lemma 1(b)): b = 1 - y z; cg = -2 y max(b, 0), ch = 2 [b > 0].
-template <int LOSS, int PREC> struct RowCoef;
-
-template <> struct RowCoef<0, 0> {
-  static __device__ __forceinline__ RecT<0> make(double E, int y) {
-    double s = 1.0 / (1.0 + E);
-    double p = E * s;
-    RecT<0> r;
-    r.cg = y > 0 ? -s : p;
-    r.ch = p * s;
-    return r;
-  }
-};
-template <> struct RowCoef<0, 1> {
-  static __device__ __forceinline__ RecT<1> make(double E, int y) {
-    float e = (float)E;
-    float p, s;
-    if (e <= 1.0f) {
-      s = 1.0f / (1.0f + e);
-      p = e * s;
-    } else {
-      float r = 1.0f / e;  // e may be +inf when E > FLT_MAX: r = 0, p = 1, s = 0
-      p = 1.0f / (1.0f + r);
-      s = r * p;
-    }
-    RecT<1> o;
-    o.cg = y > 0 ? -s : p;
-    o.ch = p * s;
-    return o;
-  }
-};
-template <> struct RowCoef<1, 0> {
-  static __device__ __forceinline__ RecT<0> make(double b, int y) {
-    RecT<0> r;
-    r.cg = b > 0.0 ? -2.0 * (double)y * b : (y > 0 ? -0.0 : 0.0);
-    r.ch = b > 0.0 ? 2.0 : 0.0;
-    return r;
-  }
-};
-template <> struct RowCoef<1, 1> {
-  static __device__ __forceinline__ RecT<1> make(double b, int y) {
-    RecT<1> r;
-    const float bf = (float)b;
-    r.cg = b > 0.0 ? (y > 0 ? -2.0f * bf : 2.0f * bf) : (y > 0 ? -0.0f : 0.0f);
-    r.ch = b > 0.0 ? 2.0f : 0.0f;
-    return r;
-  }
-};
-// Every coefficient pair carries its sample's label in the sign bit of cg: set for y = +1 (cg is
-// -s <= 0 for the logistic loss, -2 b for the L2-SVM, -0 when zero), clear for y = -1.
-__device__ __forceinline__ int label_from_cg(double cg) { return __double_as_longlong(cg) < 0 ? 1 : -1; }
-__device__ __forceinline__ int label_from_cg(float cg) { return __float_as_int(cg) < 0 ? 1 : -1; }
-
-// Maintained quantity is usable: finite, and for the logistic loss E = e^{w^T x} in [2^-1009,
-// 2^1010), i.e. |w^T x| below about 699.  Tested on the bits (sign and exponent), which keeps the
-// test off the FP64 pipe.
-template <int LOSS>
-__device__ __forceinline__ bool mq_ok(double v) {
-  const uint32_t se = (uint32_t)((unsigned long long)__double_as_longlong(v) >> 52);  // sign and exponent
-  if (LOSS == 0) return se >= 14u && se <= 2032u;
-  return (se & 0x7ffu) != 0x7ffu;
-}
-
-// ---------------------------------------------------------------- line-search row terms
-// Mixed precision, logistic: the loss change of a row splits into a first-order part (summed
-// exactly as alpha * g^T d over the bundle) and the remainder
-//   R(v; a) = log(1 + a (e^v - 1)) - a v >= 0,  a = min(p, s) in [0, 1/2], v = +/- alpha d^T x_i,
-// the cumulant generating function of a Bernoulli(a) variable minus its first cumulant.  For
-// |v| <= 1/8 it is summed as the cumulant series up to order 7 (truncation below 1e-9 relative);
-// beyond, evaluated directly (cancellation at most a factor 32).
-__device__ __forceinline__ float lr_remainder(float a, float v) {
-  if (a <= 0.0f) return 0.0f;
-  float av = fabsf(v);
-  if (!(av <= 3.0e38f)) return __int_as_float(0x7f800000);  // an infinite trial step: +inf, rejected
-  if (av <= 0.125f) {
-    float b = 1.0f - a, ab = a * b, t = b - a;
-    float k2 = ab, k3 = ab * t, k4 = ab * (1.0f - 6.0f * ab), k5 = ab * t * (1.0f - 12.0f * ab);
-    float k6 = ab * (1.0f - 30.0f * ab + 120.0f * ab * ab);
-    float k7 = ab * t * (1.0f - 60.0f * ab + 360.0f * ab * ab);
-    float s = k6 * (1.0f / 720.0f) + v * (k7 * (1.0f / 5040.0f));
-    s = k5 * (1.0f / 120.0f) + v * s;
-    s = k4 * (1.0f / 24.0f) + v * s;
-    s = k3 * (1.0f / 6.0f) + v * s;
-    s = k2 * 0.5f + v * s;
-    return v * v * s;
-  }
-  float r;
-  if (v > 20.0f) {
-    // 1 + a (e^v - 1) = a e^v (1 + (1 - a) e^{-v} / a)
-    r = v + logf(a) + log1pf((1.0f - a) * expf(-v) / a) - a * v;
-  } else {
-    r = log1pf(a * expm1f(v)) - a * v;
-  }
-  return fmaxf(r, 0.0f);
-}
-
-// Mixed precision, L2-SVM: remainder of max(0, b - v)^2 - max(0, b)^2 after its first-order
-// part 2 max(b, 0) v (summed exactly as alpha g^T d / c).  v = alpha y_i d^T x_i.  The case
-// split compares b with v: FP32 decides unless the rounded values tie, then FP64.
-// b_pos = (b > 0) decided once per row in FP64; v = alpha y_i d^T x_i formed in FP32 (alpha is a
-// power of two for beta = 1/2, so the product is exact); ties of the rounded b and v fall back to
-// an FP64 comparison.
-__device__ __forceinline__ float svm_remainder(double b, float bf, bool b_pos, float vf, double alpha, double yd) {
-  const bool bn_pos = (bf != vf) ? (bf > vf) : (b > alpha * yd);
-  if (b_pos) return bn_pos ? vf * vf : bf * (2.0f * vf - bf);
-  if (bn_pos) {
-    const float t = bf - vf;
-    return t * t;
-  }
-  return 0.0f;
 }
 
 // ---------------------------------------------------------------- double-float sums
@@ -537,10 +427,175 @@ __device__ __forceinline__ dfloat df_warp_sum(dfloat a) {
   for (int o = 16; o > 0; o >>= 1) a = df_add(a, df_shfl_xor(a, o));
   return a;
 }
-__device__ __forceinline__ float warp_sum_f(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
+// ---------------------------------------------------------------- per-sample coefficients
+// Logistic (Eq. 11): with E = e^{z}, s = 1/(1+E), p = E/(1+E):
+//   (tau(y z) - 1) y = -s (y = +1) or p (y = -1);  tau (1 - tau) = p s.
+// L2-SVM (Appendix A, proof of Lemma 1(b)): b = 1 - y z; cg = -2 y max(b, 0), ch = 2 [b > 0].
+template <int LOSS, int PREC> struct RowCoef;
+
+template <> struct RowCoef<0, 0> {
+  static __device__ __forceinline__ RecT<0> make(double E, int y) {
+    double s = 1.0 / (1.0 + E);
+    double p = E * s;
+    RecT<0> r;
+    r.cg = y > 0 ? -s : p;
+    r.ch = p * s;
+    return r;
+  }
+};
+// Mixed precision keeps the maintained quantity as a double-float pair in the record's 8-byte slot:
+// the margin z = w^T x_i for the logistic loss (the paper's maintained e^{w^T x_i} is e^z) and
+// b = 1 - y w^T x_i for the L2-SVM.  An update adds the FP32 step alpha d^T x_i to the pair
+// (error-free, on the FP32 pipe), so no per-sample work of this mode runs on the FP64 pipe, and the
+// pair carries about 48 significant bits.
+__device__ __forceinline__ dfloat slot_df(double s) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(s);
+  return dfloat{__uint_as_float((unsigned)u), __uint_as_float((unsigned)(u >> 32))};
+}
+__device__ __forceinline__ double df_slot(dfloat v) {
+  return __longlong_as_double((long long)((unsigned long long)__float_as_uint(v.hi) |
+                                          ((unsigned long long)__float_as_uint(v.lo) << 32)));
+}
+// double-float of a double (the FP64 conversions of a once-per-outer-iteration pass)
+__device__ __forceinline__ dfloat df_of(double v) {
+  dfloat r;
+  r.hi = (float)v;
+  r.lo = (float)(v - (double)r.hi);
+  return r;
+}
+__device__ __forceinline__ double df_to_double(dfloat v) { return (double)v.hi + (double)v.lo; }
+__device__ __forceinline__ bool df_pos(dfloat v) { return v.hi > 0.0f || (v.hi == 0.0f && v.lo > 0.0f); }
+
+template <> struct RowCoef<0, 1> {
+  // from the margin z: e^z in FP32 on whichever side keeps it at most 1
+  static __device__ __forceinline__ RecT<1> make(dfloat z, int y) {
+    const float zf = z.hi;
+    float p, s;
+    if (zf <= 0.0f) {  // 1 + e in [1, 2]: the fast reciprocal is accurate to 2 ulp
+      const float e = expf(zf);
+      s = __fdividef(1.0f, 1.0f + e);
+      p = e * s;
+    } else {
+      const float r = expf(-zf);
+      p = __fdividef(1.0f, 1.0f + r);
+      s = r * p;
+    }
+    RecT<1> o;
+    o.cg = y > 0 ? -s : p;
+    o.ch = p * s;
+    return o;
+  }
+};
+template <> struct RowCoef<1, 0> {
+  static __device__ __forceinline__ RecT<0> make(double b, int y) {
+    RecT<0> r;
+    r.cg = b > 0.0 ? -2.0 * (double)y * b : (y > 0 ? -0.0 : 0.0);
+    r.ch = b > 0.0 ? 2.0 : 0.0;
+    return r;
+  }
+};
+template <> struct RowCoef<1, 1> {
+  static __device__ __forceinline__ RecT<1> make(dfloat b, int y) {
+    RecT<1> r;
+    const bool pos = df_pos(b);
+    r.cg = pos ? (y > 0 ? -2.0f * b.hi : 2.0f * b.hi) : (y > 0 ? -0.0f : 0.0f);
+    r.ch = pos ? 2.0f : 0.0f;
+    return r;
+  }
+};
+// Every coefficient pair carries its sample's label in the sign bit of cg: set for y = +1 (cg is
+// -s <= 0 for the logistic loss, -2 b for the L2-SVM, -0 when zero), clear for y = -1.
+__device__ __forceinline__ int label_from_cg(double cg) { return __double_as_longlong(cg) < 0 ? 1 : -1; }
+__device__ __forceinline__ int label_from_cg(float cg) { return __float_as_int(cg) < 0 ? 1 : -1; }
+
+// Maintained quantity is usable: finite, and for the logistic loss E = e^{w^T x} in [2^-1009,
+// 2^1010), i.e. |w^T x| below about 699.  Tested on the bits (sign and exponent), which keeps the
+// test off the FP64 pipe.
+template <int LOSS>
+__device__ __forceinline__ bool mq_ok(double v) {
+  const uint32_t se = (uint32_t)((unsigned long long)__double_as_longlong(v) >> 52);  // sign and exponent
+  if (LOSS == 0) return se >= 14u && se <= 2032u;
+  return (se & 0x7ffu) != 0x7ffu;
+}
+// the same for mixed precision's pair: |z| below 699 (logistic), finite (L2-SVM)
+template <int LOSS>
+__device__ __forceinline__ bool mq_ok(dfloat v) {
+  if (LOSS == 0) return fabsf(v.hi) < 699.0f;
+  return isfinite(v.hi) && isfinite(v.lo);
+}
+
+// The coefficient pair and usability of a record's state slot (a double in FP64 mode, a
+// double-float pair in mixed mode).
+template <int LOSS, int PREC>
+__device__ __forceinline__ RecT<PREC> slot_coef(double slot, int y) {
+  if constexpr (PREC == 0) return RowCoef<LOSS, 0>::make(slot, y);
+  else return RowCoef<LOSS, 1>::make(slot_df(slot), y);
+}
+template <int LOSS, int PREC>
+__device__ __forceinline__ bool slot_ok(double slot) {
+  if constexpr (PREC == 0) return mq_ok<LOSS>(slot);
+  else return mq_ok<LOSS>(slot_df(slot));
+}
+// The state slot at a sample's z = w^T x_i (refresh): FP64 e^z or 1 - y z; mixed the pair of z or 1 - y z.
+template <int LOSS, int PREC>
+__device__ __forceinline__ double slot_from_z(double z, int y) {
+  if constexpr (PREC == 0) return LOSS == 0 ? exp(z) : 1.0 - (double)y * z;
+  else return df_slot(df_of(LOSS == 0 ? z : 1.0 - (double)y * z));
+}
+// The maintained quantity of the slot as a double: FP64 e^z or b; mixed e^z (from z) or b.
+template <int LOSS, int PREC>
+__device__ __forceinline__ double slot_value(double slot) {
+  if constexpr (PREC == 0) return slot;
+  else return LOSS == 0 ? exp(df_to_double(slot_df(slot))) : df_to_double(slot_df(slot));
+}
+
+// ---------------------------------------------------------------- line-search row terms
+// Mixed precision, logistic: the loss change of a row splits into a first-order part (summed
+// exactly as alpha * g^T d over the bundle) and the remainder
+//   R(v; a) = log(1 + a (e^v - 1)) - a v >= 0,  a = min(p, s) in [0, 1/2], v = +/- alpha d^T x_i,
+// the cumulant generating function of a Bernoulli(a) variable minus its first cumulant.  For
+// |v| <= 1/8 it is summed as the cumulant series up to order 7 (truncation below 1e-9 relative);
+// beyond, evaluated directly (cancellation at most a factor 32).
+__device__ __forceinline__ float lr_remainder(float a, float v) {
+  if (a <= 0.0f) return 0.0f;
+  float av = fabsf(v);
+  if (!(av <= 3.0e38f)) return __int_as_float(0x7f800000);  // an infinite trial step: +inf, rejected
+  if (av <= 0.125f) {
+    float b = 1.0f - a, ab = a * b, t = b - a;
+    float k2 = ab, k3 = ab * t, k4 = ab * (1.0f - 6.0f * ab), k5 = ab * t * (1.0f - 12.0f * ab);
+    float k6 = ab * (1.0f - 30.0f * ab + 120.0f * ab * ab);
+    float k7 = ab * t * (1.0f - 60.0f * ab + 360.0f * ab * ab);
+    float s = k6 * (1.0f / 720.0f) + v * (k7 * (1.0f / 5040.0f));
+    s = k5 * (1.0f / 120.0f) + v * s;
+    s = k4 * (1.0f / 24.0f) + v * s;
+    s = k3 * (1.0f / 6.0f) + v * s;
+    s = k2 * 0.5f + v * s;
+    return v * v * s;
+  }
+  float r;
+  if (v > 20.0f) {
+    // 1 + a (e^v - 1) = a e^v (1 + (1 - a) e^{-v} / a)
+    r = v + logf(a) + log1pf((1.0f - a) * expf(-v) / a) - a * v;
+  } else {
+    r = log1pf(a * expm1f(v)) - a * v;
+  }
+  return fmaxf(r, 0.0f);
+}
+
+// Mixed precision, L2-SVM: remainder of max(0, b - v)^2 - max(0, b)^2 after its first-order part
+// 2 max(b, 0) v (summed exactly as alpha g^T d / c), v = alpha y_i d^T x_i formed in FP32 (exact
+// for beta = 1/2).  The sign of b - v is exact: the pair's high part decides unless it equals v,
+// then its low part.
+__device__ __forceinline__ float svm_remainder(dfloat b, float vf) {
+  const float bf = b.hi;
+  const bool b_pos = df_pos(b);
+  const bool bn_pos = (bf != vf) ? (bf > vf) : (b.lo > 0.0f);
+  if (b_pos) return bn_pos ? vf * vf : bf * (2.0f * vf - bf);
+  if (bn_pos) {
+    const float t = bf - vf;
+    return t * t;
+  }
+  return 0.0f;
 }
 
 // ---------------------------------------------------------------- exact sums

@@ -485,15 +485,10 @@ __global__ void __launch_bounds__(kRedThreads) refresh_kernel(const int64_t* row
     const int yi = y[i];
     if (loss_part) lsum += row_loss(LOSS, z, yi);
     if (write_state) {
-      double v;
-      if (LOSS == 0) {
-        if (fabs(z) > 700.0) atomicOr(err, kErrRefresh);
-        v = exp(z);
-      } else {
-        v = 1.0 - (double)yi * z;
-      }
+      if (LOSS == 0 && fabs(z) > 700.0) atomicOr(err, kErrRefresh);
+      const double v = slot_from_z<LOSS, PREC>(z, yi);
       *st_mq(st, i) = v;
-      *st_rec<PREC>(st, i) = RowCoef<LOSS, PREC>::make(v, yi);
+      *st_rec<PREC>(st, i) = slot_coef<LOSS, PREC>(v, yi);
     }
   }
   if (loss_part) {
@@ -583,15 +578,12 @@ __global__ void __launch_bounds__(kRedThreads) refresh_df_kernel(const int64_t* 
       const int yi = y[i];
       if (loss_part) lsum += row_loss(LOSS, z, yi);
       if (write_state) {
-        double mv;
-        if (LOSS == 0) {
-          if (fabs(z) > 700.0) atomicOr(err, kErrRefresh);
-          mv = exp(z);
-        } else {
-          mv = 1.0 - (double)yi * z;
-        }
-        *st_mq(st, i) = mv;
-        *st_rec<1>(st, i) = RowCoef<LOSS, 1>::make(mv, yi);
+        // the pair of z itself (logistic) or of 1 - y z (L2-SVM), without a round trip through FP64
+        if (LOSS == 0 && fabs(z) > 700.0) atomicOr(err, kErrRefresh);
+        const dfloat zd = {zz.x, zz.y};
+        const dfloat v = LOSS == 0 ? zd : df_add_f(yi > 0 ? df_neg(zd) : zd, 1.0f);
+        *st_mq(st, i) = df_slot(v);
+        *st_rec<1>(st, i) = RowCoef<LOSS, 1>::make(v, yi);
       }
     }
     __syncwarp();
@@ -623,7 +615,7 @@ cudaError_t launch_refresh_df(int T, int grid, cudaStream_t s, const int64_t* ro
 template <int LOSS, int PREC>
 __global__ void rec_from_mq_kernel(const int8_t* y, int64_t n, void* st) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    *st_rec<PREC>(st, i) = RowCoef<LOSS, PREC>::make(*st_mq(st, i), y[i]);
+    *st_rec<PREC>(st, i) = slot_coef<LOSS, PREC>(*st_mq(st, i), y[i]);
 }
 
 // Mixed precision's stopping test (Section 5.1 reading): the gradient's per-sample coefficient cg in
@@ -633,9 +625,23 @@ __global__ void rec_from_mq_kernel(const int8_t* y, int64_t n, void* st) {
 template <int LOSS>
 __global__ void kkt_coef_kernel(const int8_t* y, int64_t n, void* st) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const double cg = RowCoef<LOSS, 0>::make(*st_mq(st, i), y[i]).cg;
+    const double cg = RowCoef<LOSS, 0>::make(slot_value<LOSS, 1>(*st_mq(st, i)), y[i]).cg;
     const float hi = (float)cg;
     reinterpret_cast<float2*>(reinterpret_cast<SampleRec*>(st)[i].c)[1] = make_float2(hi, (float)(cg - (double)hi));
+  }
+}
+
+// A state slot from one precision's form to the other's (FP64: e^z or b; mixed: the pair of z or
+// b), then the coefficients.
+template <int LOSS, int TO>
+__global__ void convert_state_kernel(const int8_t* y, int64_t n, void* st) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double s = *st_mq(st, i);
+    double v;
+    if constexpr (TO == 1) v = df_slot(df_of(LOSS == 0 ? log(s) : s));
+    else v = slot_value<LOSS, 1>(s);
+    *st_mq(st, i) = v;
+    *st_rec<TO>(st, i) = slot_coef<LOSS, TO>(v, y[i]);
   }
 }
 
@@ -644,8 +650,9 @@ __global__ void kkt_coef_kernel(const int8_t* y, int64_t n, void* st) {
 template <int LOSS, int PREC>
 __global__ void state_at_zero_kernel(const int8_t* y, int64_t n, void* st) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    *st_mq(st, i) = 1.0;
-    *st_rec<PREC>(st, i) = RowCoef<LOSS, PREC>::make(1.0, y[i]);
+    const double v = slot_from_z<LOSS, PREC>(0.0, y[i]);
+    *st_mq(st, i) = v;
+    *st_rec<PREC>(st, i) = slot_coef<LOSS, PREC>(v, y[i]);
   }
 }
 
@@ -1065,6 +1072,16 @@ cudaError_t rec_from_mq(int loss, int prec, const int8_t* y, int64_t n, void* st
   else if (loss == 0) rec_from_mq_kernel<0, 1><<<g, 256, 0, s>>>(y, n, st);
   else if (prec == 0) rec_from_mq_kernel<1, 0><<<g, 256, 0, s>>>(y, n, st);
   else rec_from_mq_kernel<1, 1><<<g, 256, 0, s>>>(y, n, st);
+  return post(launches);
+}
+
+cudaError_t convert_state(int loss, int to_prec, const int8_t* y, int64_t n, void* st, cudaStream_t s,
+                          int64_t* launches) {
+  const unsigned g = grid_for(n, 256);
+  if (loss == 0 && to_prec == 0) convert_state_kernel<0, 0><<<g, 256, 0, s>>>(y, n, st);
+  else if (loss == 0) convert_state_kernel<0, 1><<<g, 256, 0, s>>>(y, n, st);
+  else if (to_prec == 0) convert_state_kernel<1, 0><<<g, 256, 0, s>>>(y, n, st);
+  else convert_state_kernel<1, 1><<<g, 256, 0, s>>>(y, n, st);
   return post(launches);
 }
 

@@ -107,8 +107,12 @@ cudaError_t refresh(int loss, int prec, const int64_t* row_ptr, const int32_t* c
                     int64_t* launches);
 // The maintained quantities and coefficients at w = 0 (mq = 1 for both losses), without reading X.
 cudaError_t state_at_zero(int loss, int prec, const int8_t* y, int64_t n, void* st, cudaStream_t s, int64_t* launches);
-// The coefficients from the current mq (precision switch without recomputing z).
+// The coefficients from the current state slot (of precision prec).
 cudaError_t rec_from_mq(int loss, int prec, const int8_t* y, int64_t n, void* st, cudaStream_t s, int64_t* launches);
+// The state slots converted to precision to_prec's form (FP64: e^z or b; mixed: a double-float pair
+// of z or b) and their coefficients (a precision switch without recomputing z = Xw).
+cudaError_t convert_state(int loss, int to_prec, const int8_t* y, int64_t n, void* st, cudaStream_t s,
+                          int64_t* launches);
 
 // ---- reductions -------------------------------------------------------------------------------
 // Minimum-norm subgradient l1 norm from the samples' coefficients, over work items of all columns:

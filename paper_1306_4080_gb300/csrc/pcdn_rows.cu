@@ -91,6 +91,7 @@ __global__ void __launch_bounds__(kTileWarps * 32) rows_count_kernel(const int32
 struct PlaceSmem {
   int cnt[kTileWarps][kBins];  // per-warp counts, then per-warp offsets within the bundle's run
   int tloc[kBins + 1];         // start of each bundle's run in the tile
+  int dst[kBins];              // each bundle's run: its first slot in the output
   int scan[kTileWarps];
   int32_t row[kTile];
   int32_t k[kTile];
@@ -123,6 +124,11 @@ __global__ void __launch_bounds__(kTileWarps * 32) rows_place_kernel(const int32
   constexpr int kPerT = kBins / (kTileWarps * 32);
   int len[kPerT];
   int tsum = 0;
+#pragma unroll
+  for (int u = 0; u < kPerT; ++u) {
+    const int b = tid * kPerT + u;
+    if (b < nb) sm.dst[b] = (int)off[(int64_t)b * tiles + blockIdx.x];  // all loads of the tile in flight
+  }
 #pragma unroll
   for (int u = 0; u < kPerT; ++u) {
     const int b = tid * kPerT + u;
@@ -159,12 +165,21 @@ __global__ void __launch_bounds__(kTileWarps * 32) rows_place_kernel(const int32
   __syncthreads();
   // ranks, then the entries into their runs in shared memory (eight steps' loads in flight)
   const unsigned lt = (1u << lane) - 1u;
+  int nbits = 1;
+  while ((1 << nbits) < nb) ++nbits;
   int slot[kTileSteps];
 #pragma unroll
   for (int s = 0; s < kTileSteps; ++s) {
     const int32_t ps = pos[s];
     const int b = ps >= 0 ? bundle_of(ps, P, invP) : -1;
-    const unsigned peers = __match_any_sync(0xffffffffu, b);
+    // lanes holding the same bundle index: one ballot per bit of the index (and one for validity)
+    unsigned peers = __ballot_sync(0xffffffffu, b >= 0);
+    if (b < 0) peers = ~peers;
+    for (int bit = 0; bit < nbits; ++bit) {
+      const bool on = (b >> bit) & 1;
+      const unsigned m = __ballot_sync(0xffffffffu, on);
+      peers &= on ? m : ~m;
+    }
     const int c0 = b >= 0 ? sm.cnt[w][b] : 0;
     __syncwarp();
     slot[s] = -1;
@@ -201,7 +216,7 @@ __global__ void __launch_bounds__(kTileWarps * 32) rows_place_kernel(const int32
   for (int b = w; b < nb; b += kTileWarps) {
     const int lo = sm.tloc[b], hi = sm.tloc[b + 1];
     if (lo == hi) continue;
-    const int64_t dst = off[(int64_t)b * tiles + blockIdx.x] - lo;
+    const int64_t dst = (int64_t)sm.dst[b] - lo;
     for (int i = lo + lane; i < hi; i += 32) {
       br_row[dst + i] = sm.row[i];
       br_k[dst + i] = sm.k[i];

@@ -768,15 +768,11 @@ struct LsAcc<LOSS, 1> {
       for (int q = 0; q < kMaxK; ++q)
         if (q < K) kahan_add(s[q], cmp[q], lr_remainder(a, alpha_f[q] * vf));
     } else {
-      const double mq = rv.mq;
-      const int y = rv.y;
-      const float ydf = y > 0 ? dlf : -dlf;
-      const double yd = (double)ydf;
-      const float bf = (float)mq;
-      const bool b_pos = mq > 0.0;
+      const dfloat b = slot_df(rv.mq);
+      const float ydf = rv.y > 0 ? dlf : -dlf;
 #pragma unroll
       for (int q = 0; q < kMaxK; ++q)
-        if (q < K) kahan_add(s[q], cmp[q], svm_remainder(mq, bf, b_pos, alpha_f[q] * ydf, alpha[q], yd));
+        if (q < K) kahan_add(s[q], cmp[q], svm_remainder(b, alpha_f[q] * ydf));
     }
   }
   __device__ __forceinline__ Acc<1> get(int q) const {
@@ -793,23 +789,17 @@ template <int LOSS, int PREC>
 __device__ __forceinline__ void row_update(const WalkParams& p, int32_t r, const RowVals<PREC>& rv, double alpha,
                                            float alpha_f) {
   double mq = rv.mq;
-  if constexpr (LOSS == 0) {
-    if constexpr (PREC == 0) {
-      mq = mq * exp(alpha * rv.dl);
-    } else {
-      // E e^u = E + E (e^u - 1) with FP32 expm1 where that is accurate to FP32 relative to e^u
-      // (u >= -1/2, so 1 + expm1(u) >= 0.6, and below FP32 overflow); FP64 exp elsewhere
-      const float uf = alpha_f * rv.dl;
-      if (uf >= -0.5f && uf < 80.0f) mq = fma(mq, (double)expm1f(uf), mq);
-      else mq = mq * exp(alpha * (double)rv.dl);
-    }
+  if constexpr (PREC == 0) {
+    if constexpr (LOSS == 0) mq = mq * exp(alpha * rv.dl);
+    else mq = mq - alpha * (double)rv.y * rv.dl;
   } else {
-    if constexpr (PREC == 0) mq = mq - alpha * (double)rv.y * rv.dl;
-    else mq = mq - alpha * (double)(rv.y > 0 ? rv.dl : -rv.dl);
+    // the pair of z (logistic) or b (L2-SVM) plus the FP32 step alpha d^T x_i
+    const float step = alpha_f * rv.dl;
+    mq = df_slot(df_add_f(slot_df(mq), LOSS == 0 ? step : (rv.y > 0 ? -step : step)));
   }
-  if (!mq_ok<LOSS>(mq)) atomicOr(p.err, kErrRange);
+  if (!slot_ok<LOSS, PREC>(mq)) atomicOr(p.err, kErrRange);
   *st_mq(p.st, r) = mq;
-  *st_rec<PREC>(p.st, r) = RowCoef<LOSS, PREC>::make(mq, rv.y);
+  *st_rec<PREC>(p.st, r) = slot_coef<LOSS, PREC>(mq, rv.y);
 }
 
 // ---------------------------------------------------------------- phases B and C: the touched rows

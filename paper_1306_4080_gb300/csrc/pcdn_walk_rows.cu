@@ -453,6 +453,36 @@ template <int LOSS> struct Row<LOSS, 0> {
     if constexpr (LOSS == 0) return mq * exp(a * dl);
     else return mq - a * (double)y * dl;
   }
+  // The first pass: the term at the full step and the state after it.  Logistic: one expm1 serves
+  // both (e^u = 1 + m for E <= 1; e^u = 1 / (1 + m) with m = expm1(-u) for E > 1), and the
+  // coefficient p or s comes from the sample's stored cg (-s for y = +1, p for y = -1; p = E s, and
+  // s = 1 - p is exact for p >= 1/2) instead of a division.
+  static __device__ __forceinline__ double term_step(Fx& acc, double mq, int y, double dl, double cg) {
+    if constexpr (LOSS == 0) {
+      const double u = dl;
+      if (fabs(u) < 700.0) {
+        double l, nq;
+        if (mq <= 1.0) {
+          const double pp = y > 0 ? mq * -cg : cg;
+          const double m = expm1(u);
+          l = log1p(pp * m) - (y > 0 ? u : 0.0);
+          nq = fma(mq, m, mq);
+        } else {
+          const double ss = y > 0 ? -cg : 1.0 - cg;
+          const double m = expm1(-u);
+          l = log1p(m * ss) + (y < 0 ? u : 0.0);
+          nq = mq / (1.0 + m);
+        }
+        fx_add_d(acc, l);
+        return nq;
+      }
+      fx_add_d(acc, lr_change_lse(mq, y, u));
+      return mq * exp(u);
+    } else {
+      term(acc, mq, y, dl, RecT<1>{0.0f, 0.0f}, 1.0, 1.0f);
+      return step(mq, y, dl, 1.0, 1.0f);
+    }
+  }
 };
 
 // Mixed mode: the FP32 remainder after the first-order part (summed exactly as alpha g^T d over the
@@ -464,32 +494,25 @@ template <int LOSS> struct Row<LOSS, 1> {
       // p = E/(1+E) and s = 1/(1+E) from the FP32 coefficient pair: |cg| is s (y = +1) or p
       // (y = -1), ch = p s; the other one is 1 - |cg| when |cg| <= 1/2, else ch / |cg|
       const float known = fabsf(rc.cg);
-      const float other = known <= 0.5f ? 1.0f - known : rc.ch / known;
+      const float other = known <= 0.5f ? 1.0f - known : __fdividef(rc.ch, known);
       const float pp = y > 0 ? other : known, ss = y > 0 ? known : other;
       const bool use_p = pp <= ss;
       fx_add_f(acc, lr_remainder(use_p ? pp : ss, af * (use_p ? dlf : -dlf)));
     } else {
-      const float ydf = y > 0 ? dlf : -dlf;
-      fx_add_f(acc, svm_remainder(mq, (float)mq, mq > 0.0, af * ydf, a, (double)ydf));
+      fx_add_f(acc, svm_remainder(slot_df(mq), af * (y > 0 ? dlf : -dlf)));
     }
   }
-  static __device__ __forceinline__ double step(double mq, int y, float dlf, double a, float af) {
-    if constexpr (LOSS == 0) {
-      // E e^u = E + E (e^u - 1) with FP32 expm1 where that is accurate to FP32 relative to e^u
-      // (u >= -1/2, below FP32 overflow); FP64 exp elsewhere
-      const float uf = af * dlf;
-      if (uf >= -0.5f && uf < 80.0f) return fma(mq, (double)expm1f(uf), mq);
-      return mq * exp(a * (double)dlf);
-    } else {
-      return mq - a * (double)(y > 0 ? dlf : -dlf);
-    }
+  // the pair of z (logistic) or b (L2-SVM) plus the FP32 step alpha d^T x_i, on the FP32 pipe
+  static __device__ __forceinline__ double step(double mq, int y, float dlf, double, float af) {
+    const float s = af * dlf;
+    return df_slot(df_add_f(slot_df(mq), LOSS == 0 ? s : (y > 0 ? -s : s)));
   }
 };
 
-// A pass over the block's samples at one step size.
+// A pass over the block's samples at one step size.  Its mode (a template parameter) is kFirst:
+// terms from the current state, then the full step's state written; kEval: terms from the kept
+// state; kApply: the final state from the kept state.
 struct RowCtx {
-  int mode;        // kFirst: terms from the current state, then the full step's state written
-                   // kEval: terms from the kept state; kApply: the final state from the kept state
   double a;        // the step size of the terms (kFirst, kEval) or the accepted step (kApply)
   float af;
   bool accept;     // kApply: a step was accepted (else the kept state is restored)
@@ -530,33 +553,38 @@ __device__ __forceinline__ void rec_words(const RecT<1>& r, unsigned long long& 
 }
 
 // Line-search term and state writes of sample r with d^T x_i = dl (nonzero).
-template <int LOSS, int PREC>
+template <int LOSS, int PREC, int MODE>
 __device__ __forceinline__ void row_work(const WalkParams& p, const RowCtx& c, int32_t r,
                                          typename Row<LOSS, PREC>::DT dl, RowState st, Fx& acc, unsigned& bad) {
-  if (c.mode == kFirst) {
-    RecT<1> rc;
-    rc.cg = __uint_as_float((unsigned)st.c0);
-    rc.ch = __uint_as_float((unsigned)(st.c0 >> 32));
-    Row<LOSS, PREC>::term(acc, st.mq, st.y, dl, rc, c.a, c.af);
-    // the state after the full step alpha = 1, written now; the old value is kept for the case
-    // that the line search rejects the full step
-    const double nq = Row<LOSS, PREC>::step(st.mq, st.y, dl, 1.0, 1.0f);
-    if (!mq_ok<LOSS>(nq)) bad = 1u;
+  if constexpr (MODE == kFirst) {
+    // the term at the full step alpha = 1 and the state after it, written now; the old value is
+    // kept for the case that the line search rejects the full step
+    double nq;
+    if constexpr (PREC == 0) {
+      nq = Row<LOSS, 0>::term_step(acc, st.mq, st.y, dl, __longlong_as_double((long long)st.c0));
+    } else {
+      RecT<1> rc;
+      rc.cg = __uint_as_float((unsigned)st.c0);
+      rc.ch = __uint_as_float((unsigned)(st.c0 >> 32));
+      Row<LOSS, 1>::term(acc, st.mq, st.y, dl, rc, 1.0, 1.0f);
+      nq = Row<LOSS, 1>::step(st.mq, st.y, dl, 1.0, 1.0f);
+    }
+    if (!slot_ok<LOSS, PREC>(nq)) bad = 1u;
     unsigned long long c0 = st.c0, c1 = st.c1;
-    rec_words(RowCoef<LOSS, PREC>::make(nq, st.y), c0, c1);
+    rec_words(slot_coef<LOSS, PREC>(nq, st.y), c0, c1);
     store_state(p, r, nq, st.mq, c0, c1);
-  } else if (c.mode == kEval) {
+  } else if constexpr (MODE == kEval) {
     RecT<1> rc{0.0f, 0.0f};
-    if constexpr (PREC == 1 && LOSS == 0) rc = RowCoef<0, 1>::make(st.bak, st.y);
+    if constexpr (PREC == 1 && LOSS == 0) rc = RowCoef<0, 1>::make(slot_df(st.bak), st.y);
     Row<LOSS, PREC>::term(acc, st.bak, st.y, dl, rc, c.a, c.af);
   } else {
     double nq = st.bak;
     if (c.accept) {
       nq = Row<LOSS, PREC>::step(st.bak, st.y, dl, c.a, c.af);
-      if (!mq_ok<LOSS>(nq)) atomicOr(p.err, kErrRange);
+      if (!slot_ok<LOSS, PREC>(nq)) atomicOr(p.err, kErrRange);
     }
     unsigned long long c0 = st.c0, c1 = st.c1;
-    rec_words(RowCoef<LOSS, PREC>::make(nq, st.y), c0, c1);
+    rec_words(slot_coef<LOSS, PREC>(nq, st.y), c0, c1);
     store_state(p, r, nq, st.bak, c0, c1);
   }
 }
@@ -595,7 +623,7 @@ __device__ __forceinline__ void stage_round_async(const WalkParams& p, Shared<PR
 // A sample whose segment in this bundle is longer than a round: d^T x_i by the whole block straight
 // from global memory (thread t sums entries t, t + 256, ... in order; lane trees; warps in order),
 // then its work by thread 0.  Returns the end of the segment.
-template <int LOSS, int PREC>
+template <int LOSS, int PREC, int MODE>
 __device__ __forceinline__ int64_t long_row(const WalkParams& p, Shared<PREC>& sh, int par, int64_t cur, int64_t e1,
                                             const RowCtx& c, Fx& acc, unsigned& bad) {
   using DT = typename Row<LOSS, PREC>::DT;
@@ -641,19 +669,19 @@ __device__ __forceinline__ int64_t long_row(const WalkParams& p, Shared<PREC>& s
     double s = 0.0;
     for (int w = 0; w < kWalkWarps; ++w) s += sh.dred[w];
     const DT dl = (DT)s;
-    if (dl != DT(0)) row_work<LOSS, PREC>(p, c, r, dl, load_state<PREC>(p, r), acc, bad);
+    if (dl != DT(0)) row_work<LOSS, PREC, MODE>(p, c, r, dl, load_state<PREC>(p, r), acc, bad);
   }
   __syncthreads();
   return end;
 }
 
-constexpr int kRowsPer = 2;  // samples whose state a thread loads at once
+constexpr int kRowsPer = 3;  // samples whose state a thread loads at once
 
 // Every sample the block owns in this bundle, once, in rounds of at most kBCap entries cut at row
 // starts (the first round may already be staged: sh.b_cur == e0).  Per round: the row starts (a
 // block scan), then every entry's d (Eq. 5) gathered into shared memory while each thread loads the
 // state of its samples, then per sample d^T x_i in entry order and its work.
-template <int LOSS, int PREC>
+template <int LOSS, int PREC, int MODE>
 __device__ __forceinline__ void rows_pass(const WalkParams& p, Shared<PREC>& sh, int par, int64_t e0, int64_t e1,
                                           const RowCtx& c, Fx& acc, unsigned& bad) {
   using DT = typename Row<LOSS, PREC>::DT;
@@ -670,6 +698,15 @@ __device__ __forceinline__ void rows_pass(const WalkParams& p, Shared<PREC>& sh,
     __syncthreads();
     const int head = sh.b_head, n = sh.b_n;
     const bool complete = cur + n >= e1;
+    // d of every staged entry (Eq. 5), gathered while the row starts are found
+    {
+      const int64_t o = (int64_t)par * p.P_cap;
+      for (int v = tid; v < n; v += kWalkThreads) {
+        if constexpr (PREC == 0) cp_async8(&sh.u.dv[v], p.dk + o + sh.b_k[head + v]);
+        else cp_async4(&sh.u.dv[v], p.dkf + o + sh.b_k[head + v]);
+      }
+      cp_async_commit();
+    }
     // row starts of the round: each thread flags a contiguous run of kPer entries
     constexpr int kPer = kBCap / kWalkThreads;
     int cnt = 0;
@@ -701,48 +738,58 @@ __device__ __forceinline__ void rows_pass(const WalkParams& p, Shared<PREC>& sh,
     for (int w = 0; w < kWalkWarps; ++w) Rt += sh.scan_tot[w];
     __syncthreads();  // every thread has read the totals and written its row starts
     if (!complete && Rt == 1) {
-      cur = long_row<LOSS, PREC>(p, sh, par, cur, e1, c, acc, bad);
+      cur = long_row<LOSS, PREC, MODE>(p, sh, par, cur, e1, c, acc, bad);
       continue;
     }
     const int Ru = complete ? Rt : Rt - 1;  // the last row of an incomplete round may go on
     if (complete && tid == 0) sh.rstart[Rt] = n;
     __syncthreads();
     const int ne = sh.rstart[Ru];
-    // d of every entry of the round's complete rows
-    {
-      const int64_t o = (int64_t)par * p.P_cap;
-      for (int v = tid; v < ne; v += kWalkThreads) {
-        if constexpr (PREC == 0) cp_async8(&sh.u.dv[v], p.dk + o + sh.b_k[head + v]);
-        else cp_async4(&sh.u.dv[v], p.dkf + o + sh.b_k[head + v]);
-      }
-      cp_async_commit();
-    }
-    for (int base = 0; base < Ru; base += kRowsPer * kWalkThreads) {
-      RowState st[kRowsPer];
-#pragma unroll
-      for (int u = 0; u < kRowsPer; ++u) {
-        const int rr = base + tid + u * kWalkThreads;
-        if (rr < Ru) st[u] = load_state<PREC>(p, sh.b_row[head + sh.rstart[rr]]);
-      }
-      if (base == 0) {
-        cp_async_wait_all();
-        __syncthreads();
-      }
-#pragma unroll
-      for (int u = 0; u < kRowsPer; ++u) {
-        const int rr = base + tid + u * kWalkThreads;
-        if (rr >= Ru) continue;
-        const int a = sh.rstart[rr], b = sh.rstart[rr + 1];
-        DT dl = DT(0);
-        for (int v = a; v < b; ++v) {
-          const DT d = sh.u.dv[v];
-          if constexpr (PREC == 0) {
-            if (d != 0.0) dl = __dadd_rn(dl, __dmul_rn(d, (double)sh.b_val[head + v]));
-          } else {
-            if (d != 0.0f) dl = fmaf(d, sh.b_val[head + v], dl);
-          }
+    cp_async_wait_all();
+    __syncthreads();
+    // d^T x_i of each complete row, in entry order, kept in place of the row's first d; the rows
+    // with a nonzero sum listed in row order (in b_k, idle once the d are gathered)
+    int nzc = 0;
+    for (int rr = tid; rr < Ru; rr += kWalkThreads) {
+      const int a = sh.rstart[rr], b = sh.rstart[rr + 1];
+      DT dl = DT(0);
+      for (int v = a; v < b; ++v) {
+        const DT d = sh.u.dv[v];
+        if constexpr (PREC == 0) {
+          if (d != 0.0) dl = __dadd_rn(dl, __dmul_rn(d, (double)sh.b_val[head + v]));
+        } else {
+          if (d != 0.0f) dl = fmaf(d, sh.b_val[head + v], dl);
         }
-        if (dl != DT(0)) row_work<LOSS, PREC>(p, c, sh.b_row[head + a], dl, st[u], acc, bad);
+      }
+      sh.u.dv[a] = dl;
+      nzc += dl != DT(0) ? 1 : 0;
+    }
+    {
+      const int incl2 = block_scan_incl(sh, nzc);
+      int at = incl2 - nzc;
+      for (int rr = tid; rr < Ru; rr += kWalkThreads)
+        if (sh.u.dv[sh.rstart[rr]] != DT(0)) sh.b_k[at++] = rr;
+      if (tid == 0) sh.b_cur = -1;  // the staged round no longer holds its positions: a later pass restages
+    }
+    int Rn = 0;
+    for (int w = 0; w < kWalkWarps; ++w) Rn += sh.scan_tot[w];
+    __syncthreads();
+    // the listed rows: every state load of a chunk in flight, then the work
+    for (int base = 0; base < Rn; base += kRowsPer * kWalkThreads) {
+      RowState st[kRowsPer];
+      int32_t rrow[kRowsPer];
+#pragma unroll
+      for (int u = 0; u < kRowsPer; ++u) {
+        const int i = base + tid + u * kWalkThreads;
+        if (i < Rn) {
+          rrow[u] = sh.b_row[head + sh.rstart[sh.b_k[i]]];
+          st[u] = load_state<PREC>(p, rrow[u]);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kRowsPer; ++u) {
+        const int i = base + tid + u * kWalkThreads;
+        if (i < Rn) row_work<LOSS, PREC, MODE>(p, c, rrow[u], sh.u.dv[sh.rstart[sh.b_k[i]]], st[u], acc, bad);
       }
     }
     cur += complete ? n : ne;
@@ -782,76 +829,98 @@ __device__ __forceinline__ void block_fields_to_global(const WalkParams& p, Shar
   fx_red_global(reinterpret_cast<long long*>(p.lsacc) + ((int64_t)buf * kPartStride + f) * kAccPad, a);
 }
 
-// One line-search pass of the block: the position fields (Delta's parts on the first pass, the
-// penalty change of each step), then the loss sum of each step over the block's samples; the
-// block's sums added to accumulator buffer `buf`.
+// Penalty change and Delta's terms of one position (FP64) into the thread's sums.
+template <int PREC>
+__device__ __forceinline__ void position_terms(const WalkParams& p, const Shared<PREC>& sh, double d, double g, double h,
+                                               double wj, int q0, int K, bool first, double& gd, double& hdd,
+                                               double& l1s, double* pen) {
+  if (d == 0.0) return;
+  if (first) {
+    gd += g * d;
+    hdd += h * d * d;
+    l1s += p.l1 * (fabs(wj + d) - fabs(wj));
+  }
+#pragma unroll
+  for (int q = 0; q < kMaxK; ++q) {
+    if (q < K) {
+      const double t = sh.atab[min(q0 + q, kAlphaTab - 1)] * d;
+      double r = p.l1 * (fabs(wj + t) - fabs(wj));
+      if (p.l2 != 0.0) {
+        // FP64 mode: the whole L2 change; mixed mode: its second-order part (the first-order part
+        // a l2 w d is inside a g^T d, g holding l2 w)
+        if constexpr (PREC == 0) r += 0.5 * p.l2 * ((wj + t) * (wj + t) - wj * wj);
+        else r += 0.5 * p.l2 * t * t;
+      }
+      pen[q] += r;
+    }
+  }
+}
+
+// One line-search pass of the block: the loss sum of each step over the block's samples, Delta's
+// parts (first pass) and the penalty change of each step over the block's positions; the block's
+// sums added to accumulator buffer `buf`.  The positions' values are loaded before the samples are
+// walked, so that their latency overlaps that work.
 template <int LOSS, int PREC>
 __device__ __forceinline__ void ls_pass(const WalkParams& p, Shared<PREC>& sh, int par, int64_t lo, int64_t k0,
-                                        int64_t k1, int64_t e0, int64_t e1, int q0, int K, bool first, int buf) {
+                                        int64_t k1, int64_t e0, int64_t e1, int q0, int K, bool first, int buf,
+                                        int64_t nx0, int nx_load) {
   const int tid = threadIdx.x, wib = tid >> 5;
-  // positions: FP64 per position, each thread's sums then added exactly
   const int npos = (int)(k1 - k0);
   const int pos_warps = min(kWalkWarps, (npos + kWarp - 1) / kWarp);
-  if (wib < pos_warps) {
-    double gd = 0.0, hdd = 0.0, l1s = 0.0, pen[kMaxK];
-#pragma unroll
-    for (int q = 0; q < kMaxK; ++q) pen[q] = 0.0;
-    const int64_t o = (int64_t)par * p.P_cap;
-    for (int64_t kl = k0 + tid; kl < k1; kl += kWalkThreads) {
-      const double d = __ldcg(p.dk + o + kl);
-      if (d == 0.0) continue;
-      const double wj = p.w_pos[lo + kl];
-      if (first) {
-        gd += __ldcg(p.gk + o + kl) * d;
-        hdd += __ldcg(p.hk + o + kl) * d * d;
-        l1s += p.l1 * (fabs(wj + d) - fabs(wj));
-      }
-#pragma unroll
-      for (int q = 0; q < kMaxK; ++q) {
-        if (q < K) {
-          const double t = sh.atab[min(q0 + q, kAlphaTab - 1)] * d;
-          double r = p.l1 * (fabs(wj + t) - fabs(wj));
-          if (p.l2 != 0.0) {
-            // FP64 mode: the whole L2 change; mixed mode: its second-order part (the first-order
-            // part a l2 w d is inside a g^T d, g holding l2 w)
-            if constexpr (PREC == 0) r += 0.5 * p.l2 * ((wj + t) * (wj + t) - wj * wj);
-            else r += 0.5 * p.l2 * t * t;
-          }
-          pen[q] += r;
-        }
-      }
-    }
-    if (first) {
-      Fx a;
-      fx_add_d(a, gd);
-      warp_field(sh, 0, a);
-      Fx b;
-      fx_add_d(b, hdd);
-      warp_field(sh, 1, b);
-      Fx c;
-      fx_add_d(c, l1s);
-      warp_field(sh, 2, c);
-    }
-#pragma unroll
-    for (int q = 0; q < kMaxK; ++q) {
-      if (q < K) {
-        Fx a;
-        fx_add_d(a, pen[q]);
-        warp_field(sh, 3 + q, a);
-      }
-    }
+  const int64_t o = (int64_t)par * p.P_cap;
+  double d0 = 0.0, g0 = 0.0, h0 = 0.0, w0 = 0.0;
+  if (tid < npos) {
+    const int64_t kl = k0 + tid;
+    d0 = __ldcg(p.dk + o + kl);
+    g0 = __ldcg(p.gk + o + kl);
+    h0 = __ldcg(p.hk + o + kl);
+    w0 = p.w_pos[lo + kl];
   }
   // samples: one rows pass per step size (the first pass writes the full step's state on q = 0)
   unsigned bad = 0u;
   for (int q = 0; q < K; ++q) {
     RowCtx c;
-    c.mode = (first && q == 0) ? kFirst : kEval;
     c.a = sh.atab[min(q0 + q, kAlphaTab - 1)];
     c.af = sh.atab_f[min(q0 + q, kAlphaTab - 1)];
     c.accept = false;
     Fx acc;
-    rows_pass<LOSS, PREC>(p, sh, par, e0, e1, c, acc, bad);
+    if (first && q == 0) rows_pass<LOSS, PREC, kFirst>(p, sh, par, e0, e1, c, acc, bad);
+    else rows_pass<LOSS, PREC, kEval>(p, sh, par, e0, e1, c, acc, bad);
     warp_field(sh, 3 + kMaxK + q, acc);
+    // the next bundle's first batch of items, copied while the pass finishes (phase A's staging
+    // area is idle here)
+    if (q == 0 && nx_load > 0) stage_items_async(p, sh, nx0, nx_load);
+  }
+  // positions: FP64 per position, each thread's sums then added exactly
+  if (wib < pos_warps) {
+    double gd = 0.0, hdd = 0.0, l1s = 0.0, pen[kMaxK];
+#pragma unroll
+    for (int q = 0; q < kMaxK; ++q) pen[q] = 0.0;
+    position_terms<PREC>(p, sh, d0, g0, h0, w0, q0, K, first, gd, hdd, l1s, pen);
+    for (int64_t kl = k0 + tid + kWalkThreads; kl < k1; kl += kWalkThreads)
+      position_terms<PREC>(p, sh, __ldcg(p.dk + o + kl), __ldcg(p.gk + o + kl), __ldcg(p.hk + o + kl),
+                           p.w_pos[lo + kl], q0, K, first, gd, hdd, l1s, pen);
+    // FP64 warp sums (a fixed tree), then each warp's sum added exactly
+    auto field = [&](int f, double v) {
+      v = warp_sum(v);
+      Fx a;
+      if ((tid & 31) == 0) {
+        fx_add_d(a, v);
+        FxSlot& sl = sh.fxs[wib][f];
+        sl.l0 = a.l0;
+        sl.l1 = a.l1;
+        sl.l2 = a.l2;
+        sl.fl = a.fl;
+      }
+    };
+    if (first) {
+      field(0, gd);
+      field(1, hdd);
+      field(2, l1s);
+    }
+#pragma unroll
+    for (int q = 0; q < kMaxK; ++q)
+      if (q < K) field(3 + q, pen[q]);
   }
   bad = __syncthreads_or(bad);
   // the block's sums to the pass's accumulators, one thread per field
@@ -963,7 +1032,6 @@ __global__ void __launch_bounds__(kWalkThreads, 2) walk_rows_kernel(WalkParams p
       nx1 = pl[(G + 1) + blockIdx.x + 1];
     }
     const int nx_load = (int)min((int64_t)kICap, nx1 - nx0);
-    if (nx_load > 0) stage_items_async(p, sh, nx0, nx_load);
 
     // ---------------- B: line search passes
     int q0 = 0;
@@ -972,7 +1040,7 @@ __global__ void __launch_bounds__(kWalkThreads, 2) walk_rows_kernel(WalkParams p
     for (;;) {
       const int K = first ? p.K1 : p.K;
       const int buf = (int)(npass % 3);
-      ls_pass<LOSS, PREC>(p, sh, par, lo, k0, k1, e0, e1, q0, K, first, buf);
+      ls_pass<LOSS, PREC>(p, sh, par, lo, k0, k1, e0, e1, q0, K, first, buf, first ? nx0 : 0, first ? nx_load : 0);
       // the next bundle's first batch: its nonzeros, once its items are in
       if (first && nx_load > 0) {
         cp_async_wait_all();
@@ -1088,13 +1156,12 @@ __global__ void __launch_bounds__(kWalkThreads, 2) walk_rows_kernel(WalkParams p
       }
       if (!(was_first && accept && dec.q == 0)) {
         RowCtx ca;
-        ca.mode = kApply;
         ca.a = dec.alpha;
         ca.af = dec.alpha_f;
         ca.accept = accept;
         Fx none;
         unsigned nb = 0u;
-        rows_pass<LOSS, PREC>(p, sh, par, e0, e1, ca, none, nb);
+        rows_pass<LOSS, PREC, kApply>(p, sh, par, e0, e1, ca, none, nb);
         if (!grid_barrier(p, bar, sh)) {
           cp_async_wait_all();
           return;
