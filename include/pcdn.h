@@ -90,7 +90,7 @@ typedef struct {
  *   path).  Every sum has a fixed order: FP64 results repeat bit for bit for a given walker grid.
  * PCDN_LAYOUT_SCATTER: each block adds d_j x_ij into a dense vector with atomic adds (results
  *   repeat up to rounding); no regrouping pass.
- * PCDN_LAYOUT_AUTO: rows for walkers of several thread blocks, scatter for one-block walkers. */
+ * PCDN_LAYOUT_AUTO: rows for FP64 solves whose walker spans several thread blocks, scatter otherwise. */
 #define PCDN_LAYOUT_AUTO 0
 #define PCDN_LAYOUT_SCATTER 1
 #define PCDN_LAYOUT_ROWS 2

@@ -93,9 +93,10 @@ struct Decision {
   float alpha_f;  // alpha in FP32
 };
 
-// Per-block partial record: [0] sum g d, [1] sum h d^2, [2] sum |w+d|-|w|,
-// [3, 3+K) sum |w + a_q d| - |w|, [3+K, 3+2K) line-search sums, [3+2K] touched rows
-constexpr int kPartStride = 3 + 2 * kMaxK + 1;
+// Per-pass sums: [0] sum g d, [1] sum h d^2, [2] sum |w+d|-|w|, [3, 3+K) sum |w + a_q d| - |w|,
+// [3+K, 3+2K) line-search sums, [3+2K] a speculative state left the usable range, [3+2K+1] warps that
+// could not write the full step's state in the line-search pass
+constexpr int kPartStride = 3 + 2 * kMaxK + 2;
 constexpr int kAccPad = 16;  // doubles per line-search accumulator (128 bytes)
 
 struct WalkParams {

@@ -96,6 +96,7 @@ struct PlaceSmem {
   int32_t row[kTile];
   int32_t k[kTile];
   float val[kTile];
+  int16_t bun[kTile];  // each staged entry's bundle
 };
 
 __global__ void __launch_bounds__(kTileWarps * 32) rows_place_kernel(const int32_t* __restrict__ col_idx,
@@ -168,6 +169,7 @@ __global__ void __launch_bounds__(kTileWarps * 32) rows_place_kernel(const int32
   int nbits = 1;
   while ((1 << nbits) < nb) ++nbits;
   int slot[kTileSteps];
+  int bun[kTileSteps];
 #pragma unroll
   for (int s = 0; s < kTileSteps; ++s) {
     const int32_t ps = pos[s];
@@ -183,6 +185,7 @@ __global__ void __launch_bounds__(kTileWarps * 32) rows_place_kernel(const int32
     const int c0 = b >= 0 ? sm.cnt[w][b] : 0;
     __syncwarp();
     slot[s] = -1;
+    bun[s] = b;
     if (b >= 0) {
       if ((peers & lt) == 0) sm.cnt[w][b] = c0 + __popc(peers);
       slot[s] = sm.tloc[b] + c0 + __popc(peers & lt);
@@ -208,20 +211,21 @@ __global__ void __launch_bounds__(kTileWarps * 32) rows_place_kernel(const int32
         sm.row[d] = rr[u];
         sm.k[d] = pos[g + u];
         sm.val[d] = vv[u];
+        sm.bun[d] = (int16_t)bun[g + u];
       }
     }
   }
   __syncthreads();
-  // each bundle's run to its slots in the output, one warp per bundle
-  for (int b = w; b < nb; b += kTileWarps) {
-    const int lo = sm.tloc[b], hi = sm.tloc[b + 1];
-    if (lo == hi) continue;
-    const int64_t dst = (int64_t)sm.dst[b] - lo;
-    for (int i = lo + lane; i < hi; i += 32) {
-      br_row[dst + i] = sm.row[i];
-      br_k[dst + i] = sm.k[i];
-      br_val[dst + i] = sm.val[i];
-    }
+  // the staged entries to the output in order: an entry's slot is its bundle's run start plus its
+  // offset in the run (runs are contiguous in both, so consecutive threads write consecutive words
+  // within a run)
+  const int total = sm.tloc[nb];
+  for (int i = tid; i < total; i += kTileWarps * 32) {
+    const int b = sm.bun[i];
+    const int64_t d = (int64_t)sm.dst[b] + (i - sm.tloc[b]);
+    br_row[d] = sm.row[i];
+    br_k[d] = sm.k[i];
+    br_val[d] = sm.val[i];
   }
 }
 

@@ -82,6 +82,10 @@ struct SharedWalk {
   int abort;
   int has_nz;
   int nonzero;
+  int64_t dko;  // this bundle's half of gk, hk, dk (bundle parity times P_cap)
+  int spec_bad;  // a warp's speculative state left the usable range (this bundle)
+  int nospec;    // warps of this block whose rows did not fit one staging round
+  int all_spec;  // every warp of the grid wrote the full step's state in the first pass
   int n_split;
   int split_ok;
   double split_d;
@@ -213,7 +217,7 @@ __device__ __forceinline__ double column_direction(const WalkParams& p, double& 
 // but for |w + d| - |w| (FP64, to keep its cancellation exact) and keeps d = -w exact, so that a
 // coordinate set to zero is zero: FP64 instructions are costly on this part.
 template <int PREC>
-__device__ __forceinline__ double finalize(const WalkParams& p, int32_t kl, GHT<PREC> g, GHT<PREC> h, double wj, bool write,
+__device__ __forceinline__ double finalize(const WalkParams& p, int64_t kl, GHT<PREC> g, GHT<PREC> h, double wj, bool write,
                                            ColTerms<PREC>& t) {
   double d;
   if constexpr (PREC == 0) {
@@ -351,7 +355,7 @@ __device__ __forceinline__ void split_combine_block(const double* part, int nch,
 // for the other holders, so that each column counts once); the holder of chunk 0 also writes gk,
 // hk, dk.
 template <int PREC>
-__device__ __forceinline__ double split_finalize(const WalkParams& p, int32_t kl, bool chunk0, double g, double h, double wj,
+__device__ __forceinline__ double split_finalize(const WalkParams& p, int64_t kl, bool chunk0, double g, double h, double wj,
                                                  ColTerms<PREC>& t) {
   const double d = finalize<PREC>(p, kl, (GHT<PREC>)g, (GHT<PREC>)h, wj, chunk0, t);
   if (!chunk0) t = ColTerms<PREC>{0, 0, 0};
@@ -500,7 +504,7 @@ __device__ void column_pass(const WalkParams& p, SharedWalk<PREC>& sh, int64_t l
         const Item it = sh.items[tid];
         double d = 0.0;
         if (it.nch == 1) {
-          d = finalize<PREC>(p, (int32_t)(it.pos - lo), st.g[tid], st.h[tid], it.w, true, ct);
+          d = finalize<PREC>(p, sh.dko + (it.pos - lo), st.g[tid], st.h[tid], it.w, true, ct);
           if (d != 0.0) sh.has_nz = 1;
         }
         st.d[tid] = d;
@@ -582,7 +586,7 @@ __device__ void column_pass(const WalkParams& p, SharedWalk<PREC>& sh, int64_t l
       }
       split_combine_warp(p.part + 2 * (sh.split_items[k] - sh.s_chunk[k]), sh.s_nch[k], g, h);
       if (lane == 0) {
-        const double dj = split_finalize<PREC>(p, sh.s_kl[k], sh.s_chunk[k] == 0, g, h, sh.s_w[k], sh.s_terms[sh.s_col[k]]);
+        const double dj = split_finalize<PREC>(p, sh.dko + sh.s_kl[k], sh.s_chunk[k] == 0, g, h, sh.s_w[k], sh.s_terms[sh.s_col[k]]);
         if (dj != 0.0) sh.has_nz = 1;
         sh.s_d[sh.s_col[k]] = dj;
       }
@@ -597,7 +601,7 @@ __device__ void column_pass(const WalkParams& p, SharedWalk<PREC>& sh, int64_t l
       double g, h;
       split_combine_block(p.part + 2 * (sh.split_items[k] - sh.s_chunk[k]), sh.s_nch[k], sh, g, h);
       if (tid == 0) {
-        const double dj = split_finalize<PREC>(p, sh.s_kl[k], sh.s_chunk[k] == 0, g, h, sh.s_w[k], sh.s_terms[sh.s_col[k]]);
+        const double dj = split_finalize<PREC>(p, sh.dko + sh.s_kl[k], sh.s_chunk[k] == 0, g, h, sh.s_w[k], sh.s_terms[sh.s_col[k]]);
         if (dj != 0.0) sh.has_nz = 1;
         sh.s_d[sh.s_col[k]] = dj;
       }
@@ -652,7 +656,7 @@ __device__ void column_pass(const WalkParams& p, SharedWalk<PREC>& sh, int64_t l
       }
       if (tid == 0) {
         ColTerms<PREC> ct;
-        const double dj = split_finalize<PREC>(p, kl, it.chunk == 0, g, h, it.w, ct);
+        const double dj = split_finalize<PREC>(p, sh.dko + kl, it.chunk == 0, g, h, it.w, ct);
         if (dj != 0.0) sh.has_nz = 1;
         sh.split_d = dj;
         if (it.chunk == 0) {
@@ -802,6 +806,31 @@ __device__ __forceinline__ void row_update(const WalkParams& p, int32_t r, const
   *st_rec<PREC>(p.st, r) = slot_coef<LOSS, PREC>(mq, rv.y);
 }
 
+// The full step's (alpha = 1) state of a touched row, written during the first line-search pass
+// (the old values stay staged in shared memory for the case that the step is rejected).  A state
+// outside the usable range is reported in `bad`, and an error only if the full step is taken.
+template <int LOSS, int PREC>
+__device__ __forceinline__ void spec_update(const WalkParams& p, int32_t r, const RowVals<PREC>& rv, int& bad) {
+  double mq = rv.mq;
+  if constexpr (PREC == 0) {
+    if constexpr (LOSS == 0) mq = mq * exp(1.0 * rv.dl);
+    else mq = mq - 1.0 * (double)rv.y * rv.dl;
+  } else {
+    mq = df_slot(df_add_f(slot_df(mq), LOSS == 0 ? rv.dl : (rv.y > 0 ? -rv.dl : rv.dl)));
+  }
+  if (!slot_ok<LOSS, PREC>(mq)) bad = 1;
+  *st_mq(p.st, r) = mq;
+  *st_rec<PREC>(p.st, r) = slot_coef<LOSS, PREC>(mq, rv.y);
+  static_cast<DeltaT<PREC>*>(p.delta)[r] = DeltaT<PREC>(0);
+}
+
+// The old state of a row written back (the full step, written speculatively, was not taken).
+template <int LOSS, int PREC>
+__device__ __forceinline__ void spec_restore(const WalkParams& p, int32_t r, const RowVals<PREC>& rv) {
+  *st_mq(p.st, r) = rv.mq;
+  *st_rec<PREC>(p.st, r) = slot_coef<LOSS, PREC>(rv.mq, rv.y);
+}
+
 // ---------------------------------------------------------------- phases B and C: the touched rows
 // Warp w of the grid owns the bitmap words [w0, w1) (equal contiguous shares).  It lists its touched
 // rows (lane l reads word l of each group of 32), copies each listed row's delta, maintained
@@ -813,6 +842,7 @@ struct WarpRows {
   int32_t w0, w1;  // n_samples < 2^31: at most 2^26 words
   int n;           // rows listed (cached)
   bool cached;
+  bool spec;       // the rows fit one staging round: the first pass writes the full step's state
   uint32_t word;   // this lane's bitmap word (cached)
 };
 
@@ -825,6 +855,7 @@ __device__ __forceinline__ WarpRows warp_rows_range(const WalkParams& p) {
   wr.w1 = (int32_t)min(p.nwords, (int64_t)wr.w0 + per);
   wr.n = 0;
   wr.cached = false;
+  wr.spec = false;
   wr.word = 0u;
   return wr;
 }
@@ -909,6 +940,7 @@ __device__ __forceinline__ void warp_rows(const WalkParams& p, RowStage<PREC>& r
     uint32_t word;
     int off;
     const int n = scan_group(p, base, wr.w1, word, off);
+    if (!clear) wr.spec = single && n <= kWarpRowCap;  // decided before the rows are visited
     for (int i0 = 0; i0 < n; i0 += kWarpRowCap) {
       const int cnt = min(kWarpRowCap, n - i0);
       list_window(rs, base, word, off, i0);
@@ -939,6 +971,8 @@ __global__ void __launch_bounds__(kWalkThreads, 2) walk_kernel(WalkParams p) {
     sh.abort = 0;
     sh.has_nz = 0;
     sh.pf_ready = 0;
+    sh.spec_bad = 0;
+    sh.nospec = 0;
     sh.halving = p.beta == 0.5;
     double a = 1.0;
     for (int q = 0; q < kAlphaTab; ++q) {
@@ -953,6 +987,7 @@ __global__ void __launch_bounds__(kWalkThreads, 2) walk_kernel(WalkParams p) {
     const int64_t lo = t * (int64_t)p.P;
     const int64_t hi = min(p.npos, lo + (int64_t)p.P);
     const int32_t Pt = (int32_t)(hi - lo);
+    const int64_t dko = (t & 1) * p.P_cap;  // this bundle's half of gk, hk, dk
 
     // the next bundle's item range (its first batch is copied in during phases B and C)
     int64_t nx0 = 0, nx1 = 0;
@@ -963,6 +998,7 @@ __global__ void __launch_bounds__(kWalkThreads, 2) walk_kernel(WalkParams p) {
     }
 
     // ---------------- A: column reductions, directions, scatter
+    if (tid == 0) sh.dko = (t & 1) * p.P_cap;  // read after column_pass's first barrier
     {
       const int64_t* pl = p.plan + t * (int64_t)(G + 1) + blockIdx.x;
       column_pass<LOSS, PREC>(p, sh, lo, pl[0], pl[1], p.col_cnt + (t & 1) * (int64_t)p.P);
@@ -1022,10 +1058,22 @@ __global__ void __launch_bounds__(kWalkThreads, 2) walk_kernel(WalkParams p) {
       LsAcc<LOSS, PREC> acc;
       acc.zero();
       int nrows = 0;
-      warp_rows<LOSS, PREC>(p, rs, wr, false, [&](int32_t, const RowVals<PREC>& v) {
+      int bad = 0;
+      const bool spec_pass = q0 == 0;
+      warp_rows<LOSS, PREC>(p, rs, wr, false, [&](int32_t r, const RowVals<PREC>& v) {
         acc.row(v, alpha, alpha_f, K, halving);
         ++nrows;
+        if (spec_pass && wr.spec) spec_update<LOSS, PREC>(p, r, v, bad);
       });
+      if (spec_pass) {
+        // speculating warps clear their bitmap words now (their rows stay staged); the others count
+        if (wr.spec && wr.word != 0u) p.touched[wr.w0 + lane] = 0u;
+        bad = __any_sync(0xffffffffu, bad != 0) ? 1 : 0;
+        if (lane == 0) {
+          if (bad) atomicOr(&sh.spec_bad, 1);
+          if (!wr.spec) atomicAdd(&sh.nospec, 1);
+        }
+      }
       // line-search sums of this warp
       {
         nrows = warp_sum_int(nrows);
@@ -1045,7 +1093,7 @@ __global__ void __launch_bounds__(kWalkThreads, 2) walk_kernel(WalkParams p) {
       if (!full_only && wib < pos_warps) {
         Acc<PREC> pq[kMaxK];
         for (int64_t kl = k0 + wib * 32 + lane; kl < k1; kl += 32 * pos_warps) {
-          const double d = p.dk[kl];
+          const double d = p.dk[dko + kl];
           if (d == 0.0) continue;
           const double wj = p.w_pos[lo + kl];
           if constexpr (PREC == 0) {
@@ -1090,6 +1138,10 @@ __global__ void __launch_bounds__(kWalkThreads, 2) walk_kernel(WalkParams p) {
         for (int wv = 0; wv < kWalkWarps; ++wv) s += sh.nrows[wv];
         atomicAdd(p.counters + 4, (unsigned long long)s);
       }
+      if (q0 == 0 && tid == 3 + 2 * kMaxK && sh.spec_bad)
+        red_add_f64(p.lsacc + ((npass % 3) * kPartStride + 3 + 2 * kMaxK) * kAccPad, 1.0);
+      if (q0 == 0 && tid == 4 + 2 * kMaxK && sh.nospec)
+        red_add_f64(p.lsacc + ((npass % 3) * kPartStride + 4 + 2 * kMaxK) * kAccPad, (double)sh.nospec);
       if (tid < 3 + 2 * kMaxK) {
         const int f = tid;
         {
@@ -1120,9 +1172,9 @@ __global__ void __launch_bounds__(kWalkThreads, 2) walk_kernel(WalkParams p) {
         return;
       }
       {
-        if (tid < 3 + 2 * kMaxK) {
+        if (tid < kPartStride) {
           const int f = tid;
-          const bool used = f < 3 + K || (f >= 3 + kMaxK && f < 3 + kMaxK + K);
+          const bool used = f < 3 + K || (f >= 3 + kMaxK && f < 3 + kMaxK + K) || (qbase == 0 && f >= 3 + 2 * kMaxK);
           if (used) sh.tot[f] = __ldcg(p.lsacc + ((npass % 3) * kPartStride + f) * kAccPad);
           if (blockIdx.x == 0) p.lsacc[(((npass + 2) % 3) * kPartStride + f) * kAccPad] = 0.0;
         }
@@ -1174,7 +1226,11 @@ __global__ void __launch_bounds__(kWalkThreads, 2) walk_kernel(WalkParams p) {
               dd.alpha_f = 0.0f;
               dd.dF = 0.0;
             }
+            if (qbase == 0) sh.all_spec = tot[4 + 2 * kMaxK] == 0.0;
             if (blockIdx.x == 0) {
+              // the full step was taken with some sample's speculative state outside the usable range
+              if (qbase == 0 && dd.state == kDecAccept && dd.q == 0 && tot[3 + 2 * kMaxK] != 0.0)
+                atomicOr(p.err, kErrRange);
               atomicAdd(p.counters + 2, 1ull);
               if (dd.state != kDecContinue) {
                 atomicAdd(p.counters + 0, (unsigned long long)(dd.state == kDecAccept ? dd.q + 1 : p.q_max));
@@ -1199,20 +1255,55 @@ __global__ void __launch_bounds__(kWalkThreads, 2) walk_kernel(WalkParams p) {
       q0 = dec.q;
     }
 
-    // ---------------- C: update w_B, the touched rows, clear scratch
+    // ---------------- C: update w_B; the touched rows unless the full step's state is in place
     const double a = dec.alpha;
     const bool accept = dec.state == kDecAccept;
     if (accept) {
       for (int64_t kl = k0 + tid; kl < k1; kl += kWalkThreads) {
-        const double d = p.dk[kl];
+        const double d = p.dk[dko + kl];
         if (d != 0.0) p.w_pos[lo + kl] += a * d;
       }
     }
+    const bool full_step = accept && dec.q == 0;
+    if (full_step && sh.all_spec) {
+      // every warp wrote the full step's state and cleared its scratch during the line search:
+      // the next bundle may start without a third barrier (its column pass reads the new states
+      // after barrier 2; gk, hk, dk alternate halves by bundle)
+      if (nx_load > 0) {
+        cp_async_wait_all();
+        __syncthreads();
+        int nb, eb;
+        plan_batch(sh, nx_load, nb, eb);
+        stage_entries_async(p, sh, nb);
+        if (tid == 0) {
+          sh.pf_nb = nb;
+          sh.pf_eb = eb;
+          sh.pf_ready = 1;
+        }
+      }
+      if (tid == 0) {
+        sh.spec_bad = 0;
+        sh.nospec = 0;
+      }
+      __syncthreads();
+      continue;
+    }
     const float a_f = dec.alpha_f;
+    const bool spec_rows = wr.spec;  // this warp's rows hold the full step's state
     warp_rows<LOSS, PREC>(p, rs, wr, true, [&](int32_t r, const RowVals<PREC>& v) {
+      if (spec_rows) {
+        if (full_step) return;
+        if (accept) row_update<LOSS, PREC>(p, r, v, a, a_f);
+        else spec_restore<LOSS, PREC>(p, r, v);
+        return;
+      }
       if (accept) row_update<LOSS, PREC>(p, r, v, a, a_f);
       static_cast<DeltaT<PREC>*>(p.delta)[r] = DeltaT<PREC>(0);
     });
+    if (tid == 0) {
+      sh.spec_bad = 0;
+      sh.nospec = 0;
+    }
     // barrier 3, with the next bundle's first batch planned and its nonzero copies issued between
     // arriving and waiting (X and the plan are read-only)
     grid_arrive(p);
