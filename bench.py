@@ -65,7 +65,7 @@ def parse():
     ap.add_argument("--serve-rates", default="10,30,100,300,1000")
     ap.add_argument("--serve-seconds", type=float, default=4.0, help="arrival window per rate (requests = rate x this, capped)")
     ap.add_argument("--serve-max-requests", type=int, default=200)
-    ap.add_argument("--batch-plain-every", type=int, default=4,
+    ap.add_argument("--batch-plain-every", type=int, default=1,
                     help="one-at-a-time comparison on every k-th job (batched again on the same jobs); 1 = all")
     ap.add_argument("--serve-seq", type=int, default=40, help="requests timed through the sequential plain loop")
     ap.add_argument("--main", type=int, default=1, help="run the 2M x 3M solve (the headline metric)")
@@ -322,10 +322,15 @@ def run_batched(args, pk, pool):
                               "walk_us_per_bundle": walk / bund * 1e6 if bund else 0.0})
         crit = sorted(jobs_diag, key=lambda d: -d["path_s"])
         n_solves = sum(len(j.C_path) for j, _ in pool)
+        # throughput counts the solves that reached the tolerance, nothing else
+        n_conv = sum(1 for r in res for st in r["stats"] if st["converged"])
         n_sub = sum(len(pool[k][0].C_path) for k in sub)
         nnz = [p.nnz for _, p in pool]
         return ({"metric": "solves/s (whole C paths, relative KKT 1e-3)", "unit": "solves/s",
-                 "value": n_solves / t_batch, "batch_s": t_batch, "solves": n_solves, "status": rc,
+                 "value": n_conv / t_batch, "batch_s": t_batch, "solves": n_solves, "solves_converged": n_conv,
+                 "status": rc, "job_statuses": {str(s_): sum(1 for r in res if r["status"] == s_)
+                                                for s_ in sorted({r["status"] for r in res})},
+                 "retries": bs["retries"],
                  "probe_solves": bs["probe_solves"], "epochs_batched": bs["epochs"], "gpu_launches": int(launches),
                  "graph_solves": bs["graph_solves"],
                  "vs_plain": {"jobs": len(sub), "solves": n_sub, "batched_s": t_sub, "plain_s": t_plain,
@@ -386,8 +391,18 @@ def run_serving(args, pk, pool, P_of):
             solve = np.array([r[2]["t_done"] - r[2]["t_start"] for r in res])
             first = min(r[2]["t_submit"] for r in res)
             last = max(r[2]["t_done"] for r in res)
-            ok = sum(1 for r in res if r[0] in (pk.PCDN_OK, pk.PCDN_ENOTCONVERGED))
-            out["rates"].append({"rate_per_s": rate, "requests": R, "ok": ok, "solves_per_s": R / (last - first),
+            ok = sum(1 for r in res if r[0] == pk.PCDN_OK)  # converged to the tolerance, nothing else
+            statuses = {}
+            for r in res:
+                statuses[str(r[0])] = statuses.get(str(r[0]), 0) + 1
+            errors = sorted({r[2].get("message", "") for r in res if r[0] < 0})[:5]
+            failed = [{"request": k, "problem": int(picks[k]), "C": float(Cs[k]), "loss": pool[picks[k]][0].loss,
+                       "status": int(res[k][0])} for k in range(R) if res[k][0] != pk.PCDN_OK][:8]
+            retried = sum(1 for r in res if r[2].get("retries", 0) > 0)
+            out["rates"].append({"rate_per_s": rate, "requests": R, "ok": ok, "statuses": statuses, "errors": errors,
+                                 "failed": failed, "retried_smaller_P": retried,
+                                 "not_converged": sum(1 for r in res if r[0] == pk.PCDN_ENOTCONVERGED),
+                                 "solves_per_s": ok / (last - first),
                                  "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
                                  "max_s": float(lat.max()),
                                  "mean_s": float(lat.mean()), "mean_queue_s": float(queue.mean()),

@@ -33,7 +33,10 @@ extern "C" {
 #define PCDN_EINVAL (-1)        /* bad argument: malformed CSC, label not +/-1, C <= 0, P out of [1, n_features], ... */
 #define PCDN_ENOMEM (-2)        /* a device or host allocation failed */
 #define PCDN_ECUDA (-3)         /* a CUDA call failed (no device, launch error, ...) */
-#define PCDN_ENUMERIC (-4)      /* a non-finite gradient, Hessian, objective change or maintained quantity */
+#define PCDN_ENUMERIC (-4)      /* a non-finite gradient, Hessian, objective change or maintained quantity;
+                                   FP64 mode keeps e^{w^T x_i} (Algorithm 4) and so also fails once some
+                                   |w^T x_i| passes about 699, where mixed precision (which keeps w^T x_i)
+                                   goes on */
 #define PCDN_ETIMEOUT (-5)      /* a device-side wait between thread blocks gave up (bounded spin) */
 #define PCDN_ENOTCONVERGED 1    /* max_epochs reached before the tolerance; outputs are still written */
 
@@ -131,7 +134,8 @@ typedef struct {
 
 typedef struct pcdn_problem pcdn_problem;
 
-/* Default options (see field comments). */
+/* Default options (see field comments; the Armijo parameters are Section 5.1's sigma = 0.01,
+ * beta = 0.5, gamma = 0). */
 void pcdn_default_opts(pcdn_opts* opts);
 
 /* Copy X (host CSC), y (host, n_samples entries in {-1, +1}) to the device and
@@ -141,7 +145,7 @@ void pcdn_default_opts(pcdn_opts* opts);
  * non-finite value, label not +/-1, C <= 0), PCDN_ENOMEM, PCDN_ECUDA. */
 int pcdn_create(const pcdn_csc* X, const int8_t* y, double C, pcdn_loss loss, pcdn_problem** out);
 
-/* As pcdn_create, but X's arrays and y are device pointers (e.g. from PyTorch)
+/* The problem of Eq. 1 as pcdn_create, but X's arrays and y are device pointers (e.g. from PyTorch)
  * that the caller keeps alive and unchanged until pcdn_destroy; they are read,
  * never written.  `stream` (a cudaStream_t, may be NULL = the library's own
  * stream) orders the library's work after the caller's producers. Validation
@@ -171,7 +175,8 @@ int pcdn_bundle_step(pcdn_problem* prob, const double* w_in, const int32_t* bund
                      const pcdn_opts* opts, double* g, double* h, double* d, double* Delta, int32_t* q,
                      double* alpha, double* dF);
 
-/* Set w (host, n_features entries) and recompute the maintained quantities. */
+/* Set w (host, n_features entries) and recompute the maintained quantities of Section 3.1
+ * (e^{w^T x_i} for the logistic loss, b_i = 1 - y_i w^T x_i for the L2-SVM) from z = Xw. */
 int pcdn_set_w(pcdn_problem* prob, const double* w);
 /* Change the loss weight c of Eq. 1 (C > 0, finite).  w and the maintained quantities are kept
  * (neither depends on c), so a following pcdn_solve with opts.warm_start = 1 continues from the
@@ -187,16 +192,19 @@ int pcdn_set_C(pcdn_problem* prob, double C);
  * (shrinking's bound becomes l1 - M/n_samples).  w and the maintained quantities are kept.
  * Errors: PCDN_EINVAL (l1 or l2 negative or not finite, both zero). */
 int pcdn_set_penalty(pcdn_problem* prob, double l1, double l2);
-/* Copy the current w to the host (n_features entries). */
+/* Copy the current w, the iterate of Algorithm 3, to the host (n_features entries); library
+ * management, no passage of its own. */
 int pcdn_get_w(pcdn_problem* prob, double* w);
 /* Objective F(w) (Eq. 1, with the problem's penalty) at the current w, from z = Xw. */
 int pcdn_objective(pcdn_problem* prob, double* F);
-/* ||v(w)||_1 of the minimum-norm subgradient at the current w (fresh gradient). */
+/* ||v(w)||_1 of the minimum-norm subgradient at the current w (fresh gradient): the quantity of
+ * the stopping test (Section 5.1 names newGLMNET's outer condition; this library's reading is the
+ * relative l1 norm of the minimum-norm subgradient). */
 int pcdn_kkt(pcdn_problem* prob, double* kkt_l1);
 /* The feature order of outer iteration `epoch` (host, n_features entries), as
- * pcdn_solve draws it on the device. */
+ * pcdn_solve draws it on the device: the random partition of Eq. 8 and Algorithm 3. */
 int pcdn_permutation(pcdn_problem* prob, uint64_t seed, int64_t epoch, int32_t* perm);
-/* Device-resident sizes (bytes) held by the problem. */
+/* Device-resident sizes (bytes) held by the problem; library management, no passage. */
 int pcdn_memory(pcdn_problem* prob, int64_t* bytes);
 
 /* ---- many solves on one GPU ----------------------------------------------------------------
@@ -244,24 +252,32 @@ typedef struct {
   int64_t coord_updates;  /* features visited by the path solves */
   double bytes_model;     /* algorithmic bytes of the path solves' bundle steps */
   int64_t graph_solves;   /* path solves whose outer iterations replayed a captured CUDA graph */
+  int64_t retries;        /* path solves of autotuned jobs repeated with a smaller bundle size after
+                             reaching max_epochs (counted in solves once, with their last attempt) */
 } pcdn_batch_stats;
 
-/* Defaults: max_inflight 0, threads 0, probe_eps 0.1, probe_epochs 3, default candidates. */
+/* Defaults: max_inflight 0, threads 0, probe_eps 0.1, probe_epochs 3, default candidates.  No
+ * passage: the paper solves one problem at a time (Algorithm 3). */
 void pcdn_default_batch_opts(pcdn_batch_opts* bopts);
 
-/* Solve every job's path (opts, may be NULL = defaults, apply to every solve; grid_ctas is
+/* Algorithm 3 on many problems at once (no passage: the paper solves one problem at a time; each
+ * solve is exactly pcdn_solve's).  Solve every job's path (opts, may be NULL = defaults, apply to every solve; grid_ctas is
  * ignored: each solve's walker is one thread block, or several from the shared block budget when
  * its bundles hold more than about 2048 nonzeros).  A job with P = 0 first runs a short probe solve
  * from w = 0 at the geometric middle of its C path for each candidate bundle size (to probe_eps, at
  * most probe_epochs outer iterations) and keeps the one with the least walker device time per
- * decade of KKT reduction; it then needs opts->warm_start = 0.  Jobs run concurrently, up to max_inflight at a time.  Returns the
+ * decade of KKT reduction; it then needs opts->warm_start = 0.  When a solve of such a job reaches
+ * max_epochs, its C is solved again from the w reached, with the next smaller candidate (and the
+ * job keeps that size for the rest of its path; P_used reports it): a bundle size probed at the
+ * path's middle can stall at its largest C, where the coordinates couple more strongly.  Jobs run concurrently, up to max_inflight at a time.  Returns the
  * first error of any job (with its message), else PCDN_ENOTCONVERGED if some solve reached
  * max_epochs, else PCDN_OK; every job's status is written.  Errors: PCDN_EINVAL (bad job, two jobs
  * on one problem), PCDN_ECUDA, and the solve errors of pcdn_solve. */
 int pcdn_solve_batch(pcdn_batch_job* jobs, int32_t n_jobs, const pcdn_opts* opts, const pcdn_batch_opts* bopts,
                      pcdn_batch_stats* out);
 
-/* The bundle-size autotuner on one problem (at its current C): for each candidate P (NULL/0 = the
+/* The bundle-size autotuner (Section 5.1 and Table 3 choose P* empirically; this replaces that
+ * search) on one problem (at its current C): for each candidate P (NULL/0 = the
  * defaults above), a probe solve from w = 0 to probe_eps (at most probe_epochs outer iterations;
  * 0 = opts' cap) with a one-block walker; *P_best = the candidate with the least walker device
  * time per decade of relative-KKT reduction; probe_s (may be NULL, [n_candidates or the default count]) receives each score.  The
@@ -295,34 +311,45 @@ typedef struct {
   double t_start;       /* copied to the device, solve started */
   double t_done;        /* solved, w on the host */
   int64_t bytes;        /* device footprint used for admission */
-  pcdn_stats stats;
+  pcdn_stats stats;     /* of the last solve; kkt_rel and kkt0 measured from w = 0 */
+  int32_t P_used;       /* bundle size of the last solve */
+  int32_t retries;      /* solves repeated with a smaller bundle size (below) */
 } pcdn_request_info;
 
+/* Default server options.  No passage: serving is not in the paper (each request is one solve of
+ * Algorithm 3). */
 void pcdn_default_server_opts(pcdn_server_opts* opts);
-/* Start a server on the current device.  Errors: PCDN_EINVAL, PCDN_ENOMEM, PCDN_ECUDA. */
+/* Start a server on the current device (no passage, as above).  Errors: PCDN_EINVAL, PCDN_ENOMEM,
+ * PCDN_ECUDA. */
 int pcdn_server_create(const pcdn_server_opts* opts, pcdn_server** out);
-/* Queue one solve (as pcdn_create + pcdn_solve from w = 0).  X and y are host arrays, copied
+/* Queue one solve of Eq. 1 by Algorithm 3 (as pcdn_create + pcdn_solve from w = 0).  A solve that
+ * reaches max_epochs with P above 16 goes on from the w it reached with the next smaller of the
+ * bundle sizes 4096, 1024, 256, 64, 16 (its relative KKT target still measured from w = 0), so
+ * that a bundle size too large for the request's C stalls no request; info reports the size used.  X and y are host arrays, copied
  * before the call returns.  *ticket identifies the request.  Full validation of X and y happens at
  * admission; a malformed request then finishes with PCDN_EINVAL.  Errors: PCDN_EINVAL (sizes, C,
  * loss, P, eps), PCDN_ENOMEM. */
 int pcdn_server_submit(pcdn_server* srv, const pcdn_csc* X, const int8_t* y, double C, pcdn_loss loss, int32_t P,
                        double eps, uint64_t seed, int64_t* ticket);
-/* As pcdn_server_submit, but X's arrays and y are not copied: the caller keeps them valid and
+/* As pcdn_server_submit (one solve of Algorithm 3), but X's arrays and y are not copied: the caller keeps them valid and
  * unchanged until pcdn_server_wait has returned the request's result (a caller that already holds
  * its problems in host memory saves a copy per request). */
 int pcdn_server_submit_borrowed(pcdn_server* srv, const pcdn_csc* X, const int8_t* y, double C, pcdn_loss loss,
                                 int32_t P, double eps, uint64_t seed, int64_t* ticket);
-/* Wait up to timeout_s seconds (<= 0: no limit) for a request; then w_out (host, n_features
- * entries, may be NULL) and info (may be NULL) receive its result and the request is forgotten
- * (each ticket can be collected once).  Returns the request's status, PCDN_ETIMEOUT if it did not
- * finish in time (it can be waited for again), or PCDN_EINVAL for an unknown ticket. */
+/* Wait up to timeout_s seconds (<= 0: no limit) for a request (library management, no passage);
+ * then w_out (host, n_features entries, may be NULL) and info (may be NULL) receive its result and
+ * the request is forgotten (each ticket can be collected once).  Returns the request's status,
+ * PCDN_ETIMEOUT if it did not finish in time (it can be waited for again), or PCDN_EINVAL for an
+ * unknown ticket.  info is written only for a finished request: a caller that needs to tell a
+ * solve that itself ended with PCDN_ETIMEOUT from a wait that timed out sets info->status to a
+ * value no call returns before the call and checks it after. */
 int pcdn_server_wait(pcdn_server* srv, int64_t ticket, double timeout_s, double* w_out, pcdn_request_info* info);
-/* Counters: requests submitted and finished so far, requests holding device memory, and the
- * device bytes they were admitted with.  Any pointer may be NULL. */
+/* Counters (library management, no passage): requests submitted and finished so far, requests
+ * holding device memory, and the device bytes they were admitted with.  Any pointer may be NULL. */
 int pcdn_server_stats(pcdn_server* srv, int64_t* submitted, int64_t* finished, int32_t* in_flight,
                       int64_t* bytes_in_use);
-/* Stop the server: solves in flight end after their current stage, uncollected results and queued
- * requests are dropped, all device memory is released. */
+/* Stop the server (library management, no passage): solves in flight end after their current
+ * stage, uncollected results and queued requests are dropped, all device memory is released. */
 void pcdn_server_destroy(pcdn_server* srv);
 
 /* Objective without allocation.
@@ -338,18 +365,25 @@ void pcdn_server_destroy(pcdn_server* srv);
  * written) are device pointers; the call only enqueues work on `stream` (a cudaStream_t, NULL =
  * the legacy default stream) and returns: F is ready once that stream has reached this work.
  * Its scratch (z = Xw and per-block partial sums) is one fixed array of about 2 MiB inside the
- * library, held on every GPU that loads the library until the process exits; hence
+ * library, which a GPU holds from the first call on it until the process exits; hence
  * n_samples <= PCDN_NOALLOC_MAX_SAMPLES, larger problems return PCDN_EINVAL.  The first call
- * on a device looks up that array's device address (cudaGetSymbolAddress) and keeps it: make
- * that first call before any stream capture.  All calls share the array, so calls that may
- * run at the same time on the GPU race: order them (one stream, or events).  A row index
- * outside [0, n_samples) makes F NaN.  Errors: PCDN_EINVAL, PCDN_ECUDA. */
+ * on a device looks up that array's device address (cudaGetSymbolAddress) and keeps it; under
+ * CUDA's lazy module loading (the default) that first call also loads the library's module on
+ * the device and places the array there, the one allocation this entry point causes: make that
+ * first call at set-up, before any stream capture, and later calls allocate nothing.  After a
+ * cudaDeviceReset the kept address is stale: reload the library before calling again.  All
+ * calls share the array, so calls that may run at the same time on the GPU race: order them (one
+ * stream, or events).  A row index outside [0, n_samples), a column pointer outside [0, nnz) or
+ * decreasing, or a label other than +/-1 makes F NaN (nothing outside the arrays is read).
+ * Errors: PCDN_EINVAL, PCDN_ECUDA. */
 #define PCDN_NOALLOC_MAX_SAMPLES 262144
+/* F(w) of Eq. 1 without allocation (described above; the paper has no counterpart). */
 int pcdn_objective_noalloc(const pcdn_csc* X, const int8_t* y, double C, pcdn_loss loss, const double* w,
                            double* F, void* stream);
 
+/* Release the problem's device memory and stream (library management, no passage). */
 void pcdn_destroy(pcdn_problem* prob);
-/* Message of the last failed call on this thread ("" if none). */
+/* Message of the last failed call on this thread ("" if none; library management, no passage). */
 const char* pcdn_last_error(void);
 
 #ifdef __cplusplus

@@ -39,6 +39,9 @@ SYMBOLS = ["pcdn_default_opts", "pcdn_create", "pcdn_create_device", "pcdn_solve
 PCDN_NOALLOC_MAX_SAMPLES = 262144
 
 
+_NOT_FINISHED = -12345  # a status no call returns
+
+
 class PcdnError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"pcdn error {code}: {msg}")
@@ -89,7 +92,7 @@ class pcdn_batch_opts(ctypes.Structure):
 class pcdn_batch_stats(ctypes.Structure):
     _fields_ = [("wall_s", ctypes.c_double), ("solves", ctypes.c_int64), ("probe_solves", ctypes.c_int64),
                 ("epochs", ctypes.c_int64), ("coord_updates", ctypes.c_int64), ("bytes_model", ctypes.c_double),
-                ("graph_solves", ctypes.c_int64)]
+                ("graph_solves", ctypes.c_int64), ("retries", ctypes.c_int64)]
 
 
 class pcdn_server_opts(ctypes.Structure):
@@ -99,7 +102,7 @@ class pcdn_server_opts(ctypes.Structure):
 class pcdn_request_info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double),
                 ("t_start", ctypes.c_double), ("t_done", ctypes.c_double), ("bytes", ctypes.c_int64),
-                ("stats", pcdn_stats)]
+                ("stats", pcdn_stats), ("P_used", ctypes.c_int32), ("retries", ctypes.c_int32)]
 
 
 _lib = None
@@ -313,6 +316,15 @@ def pcdn_objective_noalloc(col_ptr, row_idx, val, y, C: float, loss: str, w, F, 
     """F(w) into the one-element device tensor F from device tensors, allocating nothing on the
     device (see include/pcdn.h).  Enqueues on ``stream`` (torch.cuda.Stream, raw handle or None)."""
     lib = load()
+    for t, dt, name in ((col_ptr, "torch.int64", "col_ptr"), (row_idx, "torch.int32", "row_idx"),
+                        (val, "torch.float32", "val"), (y, "torch.int8", "y"), (w, "torch.float64", "w"),
+                        (F, "torch.float64", "F")):
+        # the C side receives raw device pointers and cannot check them: every tensor is checked here
+        if not (getattr(t, "is_cuda", False) and str(t.dtype) == dt and t.is_contiguous()):
+            raise PcdnError(PCDN_EINVAL, f"{name} must be a contiguous CUDA tensor of {dt}")
+    if int(w.numel()) != int(col_ptr.numel()) - 1 or int(F.numel()) < 1 or int(row_idx.numel()) != int(val.numel()):
+        raise PcdnError(PCDN_EINVAL, "w must hold n_features = col_ptr.numel() - 1 values, F at least one, "
+                                     "row_idx and val the same count")
     X = pcdn_csc(int(y.shape[0]), int(col_ptr.shape[0] - 1), int(row_idx.shape[0]), col_ptr.data_ptr(),
                  row_idx.data_ptr(), val.data_ptr())
     s = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
@@ -427,14 +439,17 @@ class Server:
         nf = self._nf[ticket]
         w = np.empty(nf, dtype=np.float64)
         info = pcdn_request_info()
+        info.status = _NOT_FINISHED  # written by the library only for a finished request
         rc = load().pcdn_server_wait(self.handle, int(ticket), float(timeout_s), w.ctypes.data, ctypes.byref(info))
-        if rc == PCDN_ETIMEOUT:
+        if rc == PCDN_ETIMEOUT and info.status == _NOT_FINISHED:  # the wait timed out (not the solve)
             raise PcdnError(rc, pcdn_last_error())
+        msg = pcdn_last_error() if rc < 0 else ""
         del self._nf[ticket]
         self._keep.pop(ticket, None)
         d = dict(status=info.status, t_submit=info.t_submit, t_admit=info.t_admit, t_start=info.t_start,
                  t_done=info.t_done,
-                 bytes=info.bytes, stats=_stats_dict(info.stats))
+                 bytes=info.bytes, stats=_stats_dict(info.stats), P_used=info.P_used, retries=info.retries,
+                 message=msg)
         return rc, w, d
 
     def stats(self):

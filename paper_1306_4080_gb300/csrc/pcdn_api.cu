@@ -527,10 +527,17 @@ int ensure_plan(pcdn_problem* p, int64_t entries) {
   return PCDN_OK;
 }
 
+// The row-sorted walker's exact sums take fewer than 2^24 terms each (one per sample and per
+// position at most): larger problems take the scatter layout.
+constexpr int64_t kRowsMaxTerms = 1ll << 24;
+
 // The row-sorted layout's arrays for a walk of nb bundles on G blocks (allocated once, the bundle
 // pointers and block plan grown as needed; the radix-sort workspace only for more than kBins bundles).
 int ensure_rows(pcdn_problem* p, int64_t nb, int G) {
   const int64_t nnz = p->nnz;
+  if (p->n + p->m >= kRowsMaxTerms)
+    return fail(PCDN_EINVAL, "the row-sorted layout needs n_samples + n_features below 2^24 (its exact sums take "
+                             "fewer than 2^24 terms); use the scatter layout");
   if (!p->entry_row) {
     CUDA_TRY(rows_configure());
     CUDA_TRY(palloc(p, &p->entry_row, nnz));
@@ -572,9 +579,10 @@ int ensure_rows(pcdn_problem* p, int64_t nb, int G) {
 // layout for FP64 solves on several blocks (repeatable bit for bit, and its solve measured within a
 // few percent of the scatter layout's on the 2M x 3M workload), the scatter layout otherwise (mixed
 // precision: the per-outer-iteration regrouping costs more than its walker saves).
-int walk_layout(const pcdn_opts* o, int grid) {
+int walk_layout(const pcdn_problem* p, const pcdn_opts* o, int grid) {
   if (o->layout == PCDN_LAYOUT_SCATTER || o->layout == PCDN_LAYOUT_ROWS) return o->layout;
-  return (grid > 1 && o->prec == PCDN_PREC_FP64) ? PCDN_LAYOUT_ROWS : PCDN_LAYOUT_SCATTER;
+  return (grid > 1 && o->prec == PCDN_PREC_FP64 && p->n + p->m < kRowsMaxTerms) ? PCDN_LAYOUT_ROWS
+                                                                                : PCDN_LAYOUT_SCATTER;
 }
 
 int ensure_trace(pcdn_problem* p, int64_t nb) {
@@ -612,8 +620,12 @@ int device_status(pcdn_problem* p) {
 int status_from_flags(int h) {
   if (h & kErrTimeout) return fail(PCDN_ETIMEOUT, "a device-side wait between thread blocks timed out");
   if (h & kErrNumeric) return fail(PCDN_ENUMERIC, "non-finite gradient, Hessian diagonal or direction");
-  if (h & kErrRange) return fail(PCDN_ENUMERIC, "maintained quantity out of range after an update (|w^T x| above about 699)");
-  if (h & kErrRefresh) return fail(PCDN_ENUMERIC, "|w^T x| > 700 when recomputing from z = Xw");
+  if (h & kErrRange)
+    return fail(PCDN_ENUMERIC, "maintained quantity out of range (FP64 keeps e^{w^T x}, which holds |w^T x| up "
+                               "to about 699; mixed precision keeps w^T x itself and has no such limit)");
+  if (h & kErrRefresh)
+    return fail(PCDN_ENUMERIC, "w^T x out of range when recomputing from z = Xw (FP64: |w^T x| > 700; "
+                               "mixed: not finite)");
   return PCDN_OK;
 }
 
@@ -786,7 +798,7 @@ int run_walk(pcdn_problem* p, const pcdn_opts* o, const int32_t* perm, int64_t n
   w.P_cap = p->P_cap;
   w.dkf = p->dkf;
   w.x_vec = ((uintptr_t)p->row_idx % 16 == 0 && (uintptr_t)p->val % 16 == 0) ? 1 : 0;
-  const int layout = walk_layout(o, grid);
+  const int layout = walk_layout(p, o, grid);
   CUDA_TRY(build_plan(p->items, p->max_items, p->item_ptr, npos, P, nb, grid, p->item_len, p->item_off, p->plan,
                       p->scan_ws, p->stream, &p->launches));
   if (layout == PCDN_LAYOUT_ROWS) {
@@ -1121,7 +1133,7 @@ int task_start(SolveTask* t, pcdn_problem* p, int32_t P, double eps, uint64_t se
   std::memset(t->cnt, 0, sizeof(t->cnt));
   if ((rc = ensure_bundle_scratch(p, P)) || (rc = ensure_trace(p, t->nb)) ||
       (rc = ensure_plan(p, t->nb * (t->grid + 1))) || (rc = reset_scratch(p)) || (o.shrink && (rc = ensure_shrink(p))) ||
-      (walk_layout(&o, t->grid) == PCDN_LAYOUT_ROWS && (rc = ensure_rows(p, t->nb, t->grid))))
+      (walk_layout(p, &o, t->grid) == PCDN_LAYOUT_ROWS && (rc = ensure_rows(p, t->nb, t->grid))))
     return end_task(t, rc);
   // from here every failure ends the task (which returns its walker blocks)
   cudaError_t e = cudaSuccess;
@@ -1499,8 +1511,11 @@ int pcdn_bundle_step(pcdn_problem* p, const double* w_in, const int32_t* bundle,
     rc = do_refresh(p, prec, true, false);
     if (rc) return rc;
   } else if (p->rec_prec != prec) {
-    CUDA_TRY(convert_state(p->loss, prec, p->y, p->n, p->st, p->stream, &p->launches));
+    CUDA_TRY(cudaMemsetAsync(p->err, 0, sizeof(int), p->stream));
+    CUDA_TRY(convert_state(p->loss, prec, p->y, p->n, p->st, p->err, p->stream, &p->launches));
     p->rec_prec = prec;
+    rc = device_status(p);
+    if (rc) return rc;
   }
   rc = ensure_bundle_scratch(p, P);
   if (rc) return rc;

@@ -32,8 +32,8 @@ constexpr int kWarpChunks = 256;   // split columns of at most this many chunks 
 
 constexpr int kErrTimeout = 1;
 constexpr int kErrNumeric = 2;       // non-finite g, h or d
-constexpr int kErrRange = 4;         // maintained quantity out of range after an update
-constexpr int kErrRefresh = 8;       // |w^T x| > 700 when recomputing from z = Xw
+constexpr int kErrRange = 4;         // maintained quantity out of range (FP64's e^{w^T x} past about e^699)
+constexpr int kErrRefresh = 8;       // z = Xw out of range on a recompute (FP64 |z| > 700, mixed not finite)
 
 // One column work item: nonzeros [start, start+len) of the feature at permutation position pos,
 // chunk `chunk` of `nch` chunks of that column.
@@ -382,6 +382,18 @@ __device__ __forceinline__ double newton_direction(double g, double h, double w,
   if (g - l1 >= h * w) return -(g - l1) / h;
   return -w;
 }
+// The same in FP32 (mixed mode), keeping d = -w exact.  A quotient past FP32's range (h near nu
+// against a large g, as when every sample of the column has |w^T x_i| beyond about 90, where the
+// logistic's FP32 curvature underflows) is formed in FP64 instead, so that d stays finite; its FP32
+// copy is then infinite and the line search rejects each trial step.
+__device__ __forceinline__ double newton_direction_f(float g, float h, float wf, double w, float l1) {
+  float num;
+  if (g + l1 <= h * wf) num = -(g + l1);
+  else if (g - l1 >= h * wf) num = -(g - l1);
+  else return -w;
+  const float q = num / h;
+  return isinf(q) ? (double)num / (double)h : (double)q;
+}
 
 // ---------------------------------------------------------------- double-float sums
 // A sum carried as an unevaluated pair hi + lo of FP32 numbers (error-free TwoSum, Knuth), about
@@ -518,10 +530,10 @@ __device__ __forceinline__ bool mq_ok(double v) {
   if (LOSS == 0) return se >= 14u && se <= 2032u;
   return (se & 0x7ffu) != 0x7ffu;
 }
-// the same for mixed precision's pair: |z| below 699 (logistic), finite (L2-SVM)
+// Mixed precision's pair (the margin z itself for the logistic loss, b for the L2-SVM) is usable
+// whenever it is finite: every coefficient it yields is formed with e^{-|z|}, which never overflows.
 template <int LOSS>
 __device__ __forceinline__ bool mq_ok(dfloat v) {
-  if (LOSS == 0) return fabsf(v.hi) < 699.0f;
   return isfinite(v.hi) && isfinite(v.lo);
 }
 
@@ -537,6 +549,31 @@ __device__ __forceinline__ bool slot_ok(double slot) {
   if constexpr (PREC == 0) return mq_ok<LOSS>(slot);
   else return mq_ok<LOSS>(slot_df(slot));
 }
+// FP64 coefficients of a mixed-precision slot.  Logistic: p = 1/(1+e^{-z}) and s = 1/(1+e^{z}) with
+// the exponential taken on whichever side keeps it at most 1 (the same values as from E = e^z, for
+// any finite z); L2-SVM: from b as in FP64 mode.
+template <int LOSS>
+__device__ __forceinline__ RecT<0> coef64_of_mixed(double slot, int y) {
+  const double v = df_to_double(slot_df(slot));
+  if constexpr (LOSS == 1) {
+    return RowCoef<1, 0>::make(v, y);
+  } else {
+    double p, s;
+    if (v <= 0.0) {
+      const double e = exp(v);
+      s = 1.0 / (1.0 + e);
+      p = e * s;
+    } else {
+      const double r = exp(-v);
+      p = 1.0 / (1.0 + r);
+      s = r * p;
+    }
+    RecT<0> o;
+    o.cg = y > 0 ? -s : p;
+    o.ch = p * s;
+    return o;
+  }
+}
 // The state slot at a sample's z = w^T x_i (refresh): FP64 e^z or 1 - y z; mixed the pair of z or 1 - y z.
 template <int LOSS, int PREC>
 __device__ __forceinline__ double slot_from_z(double z, int y) {
@@ -551,15 +588,19 @@ __device__ __forceinline__ double slot_value(double slot) {
 }
 
 // ---------------------------------------------------------------- line-search row terms
-// Mixed precision, logistic: the loss change of a row splits into a first-order part (summed
-// exactly as alpha * g^T d over the bundle) and the remainder
-//   R(v; a) = log(1 + a (e^v - 1)) - a v >= 0,  a = min(p, s) in [0, 1/2], v = +/- alpha d^T x_i,
+// Mixed precision, logistic: the loss change of a row at u = alpha d^T x_i is its first-order part
+// cg u (cg the row's gradient coefficient) plus the remainder
+//   R(v; a) = log(1 + a (e^v - 1)) - a v >= 0,  a = min(p, s) = 1/(1 + e^{|z|}) in [0, 1/2],
+//   v = +/- alpha d^T x_i (z = w^T x_i),
 // the cumulant generating function of a Bernoulli(a) variable minus its first cumulant.  For
 // |v| <= 1/8 it is summed as the cumulant series up to order 7 (truncation below 1e-9 relative);
-// beyond, evaluated directly (cancellation at most a factor 32).
-__device__ __forceinline__ float lr_remainder(float a, float v) {
-  if (a <= 0.0f) return 0.0f;
-  float av = fabsf(v);
+// beyond, evaluated directly (cancellation at most a factor 32).  For v > 20 it is taken from |z|:
+// 1 + a (e^v - 1) = (e^{|z|} + e^v) / (1 + e^{|z|}), so with t = v - |z|
+//   R = max(t, 0) + log1p(e^{-|t|}) - log1p(e^{-|z|}) - a v,
+// which stays exact where a underflows FP32 (|z| beyond about 87: a confidently classified
+// sample that a large trial step would flip, whose change is then about t, not 0).
+__device__ __forceinline__ float lr_remainder(float a, float v, float az) {
+  const float av = fabsf(v);
   if (!(av <= 3.0e38f)) return __int_as_float(0x7f800000);  // an infinite trial step: +inf, rejected
   if (av <= 0.125f) {
     float b = 1.0f - a, ab = a * b, t = b - a;
@@ -575,8 +616,8 @@ __device__ __forceinline__ float lr_remainder(float a, float v) {
   }
   float r;
   if (v > 20.0f) {
-    // 1 + a (e^v - 1) = a e^v (1 + (1 - a) e^{-v} / a)
-    r = v + logf(a) + log1pf((1.0f - a) * expf(-v) / a) - a * v;
+    const float t = v - az;
+    r = fmaxf(t, 0.0f) + log1pf(expf(-fabsf(t))) - log1pf(expf(-az)) - a * v;
   } else {
     r = log1pf(a * expm1f(v)) - a * v;
   }
@@ -584,8 +625,8 @@ __device__ __forceinline__ float lr_remainder(float a, float v) {
 }
 
 // Mixed precision, L2-SVM: remainder of max(0, b - v)^2 - max(0, b)^2 after its first-order part
-// 2 max(b, 0) v (summed exactly as alpha g^T d / c), v = alpha y_i d^T x_i formed in FP32 (exact
-// for beta = 1/2).  The sign of b - v is exact: the pair's high part decides unless it equals v,
+// -2 max(b, 0) v (= cg alpha d^T x_i), v = alpha y_i d^T x_i formed in FP32 (exact for
+// beta = 1/2).  The sign of b - v is exact: the pair's high part decides unless it equals v,
 // then its low part.
 __device__ __forceinline__ float svm_remainder(dfloat b, float vf) {
   const float bf = b.hi;
@@ -601,9 +642,12 @@ __device__ __forceinline__ float svm_remainder(dfloat b, float vf) {
 
 // ---------------------------------------------------------------- exact sums
 // A sum carried exactly as an integer in units of 2^-88, in three signed limbs of 42 bits,
-// v = l2 2^84 + l1 2^42 + l0 (l2 unbounded, l0 and l1 in [0, 2^42) after fx_norm), plus flags for a
-// term that is not finite or whose magnitude reaches 2^59 (1: positive, 2: negative, 4: NaN).
-// Terms are truncated toward zero below 2^-88.  Integer additions are associative, so the sum does
+// v = l2 2^84 + l1 2^42 + l0 (l2 a signed 64-bit word, l0 and l1 in [0, 2^42) after fx_norm), plus
+// flags for a term that is not finite or whose magnitude reaches 2^35 (1: positive, 2: negative,
+// 4: NaN); a flagged sum reads as +-inf or NaN, which fails the line-search test.  Capped terms keep
+// any sum of fewer than 2^24 of them inside l2's range (|v| < 2^59), so the limbs never wrap.  A
+// line-search term that large is a trial step the test rejects anyway (an increase of the loss
+// beyond what all samples' losses could give back).  Terms are truncated toward zero below 2^-88.  Integer additions are associative, so the sum does
 // not depend on the order in which terms, lanes, warps or blocks are added: results repeat bit for
 // bit whatever the order of atomic additions, on the integer pipes (this part's FP64 pipe runs at a
 // small fraction of its FP32 and integer rates).
@@ -671,7 +715,7 @@ __device__ __forceinline__ void fx_add_f(Fx& a, float x) {
     a.fl |= (u & 0x7fffffu) ? 4u : (neg ? 2u : 1u);
     return;
   }
-  if (e > 185) {  // |x| >= 2^59
+  if (e > 161) {  // |x| >= 2^35
     a.fl |= neg ? 2u : 1u;
     return;
   }
@@ -686,7 +730,7 @@ __device__ __forceinline__ void fx_add_d(Fx& a, double x) {
     a.fl |= (u & 0xfffffffffffffull) ? 4u : (neg ? 2u : 1u);
     return;
   }
-  if (e > 1081) {  // |x| >= 2^59
+  if (e > 1057) {  // |x| >= 2^35
     a.fl |= neg ? 2u : 1u;
     return;
   }

@@ -10,9 +10,14 @@
 //
 // The first call on a device looks up that array's device address with cudaGetSymbolAddress
 // (the name is only a host-side stand-in; passing it to a kernel would be wrong) and remembers
-// it for later calls on that device.  Every call shares the one array: z is cleared at the start
-// of each call, and calls that overlap on the GPU (on different streams, or from several host
-// threads without ordering) race on it.
+// it for later calls on that device.  With CUDA's lazy module loading (the default), that first
+// call is also when the library's module is loaded on the device and the array is placed there:
+// the one allocation this entry point ever causes happens then, so a caller that may not allocate
+// on its request path makes one call at set-up (outside any stream capture).  A cudaDeviceReset
+// discards the array and the remembered address; after a reset, call pcdn_objective_noalloc only
+// after reloading the library.  Every call shares the one array: z is cleared at the start of each
+// call, and calls that overlap on the GPU (on different streams, or from several host threads
+// without ordering) race on it.
 //
 // The paper has no counterpart to this entry point.
 
@@ -53,15 +58,23 @@ __global__ void noalloc_zero(double* z, int64_t n, double* flag) {
   if (blockIdx.x == 0 && threadIdx.x == 0) *flag = 0.0;
 }
 
-// z = X w over the columns with w_j != 0 (one warp per column)
+// z = X w over the columns with w_j != 0 (one warp per column).  Every column's range is clamped to
+// [0, nnz): a column pointer outside it, or one that decreases, sets the flag instead of being read
+// past the arrays.
 __global__ void noalloc_xw(const int64_t* col_ptr, const int32_t* row_idx, const float* val, const double* w, int64_t n,
-                           int64_t m, double* z, double* flag) {
+                           int64_t m, int64_t nnz, double* z, double* flag) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
   for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; j < m; j += warps) {
     const double wj = w[j];
     if (wj == 0.0) continue;
-    for (int64_t e = col_ptr[j] + lane; e < col_ptr[j + 1]; e += 32) {
+    int64_t a = col_ptr[j], b = col_ptr[j + 1];
+    if (a < 0 || b > nnz || b < a) {
+      if (lane == 0) *flag = 1.0;
+      a = a < 0 ? 0 : (a > nnz ? nnz : a);
+      b = b < a ? a : (b > nnz ? nnz : b);
+    }
+    for (int64_t e = a + lane; e < b; e += 32) {
       const int32_t r = row_idx[e];
       if (r < 0 || r >= n) {
         *flag = 1.0;
@@ -72,12 +85,14 @@ __global__ void noalloc_xw(const int64_t* col_ptr, const int32_t* row_idx, const
   }
 }
 
-// per-block sums of the losses phi(z_i) (Eq. 2 or Eq. 3) and of |w_j|, each in a fixed order
+// per-block sums of the losses phi(z_i) (Eq. 2 or Eq. 3) and of |w_j|, each in a fixed order; a
+// label other than +1 or -1 sets the flag
 __global__ void noalloc_partials(const double* z, const int8_t* y, int64_t n, int loss, const double* w, int64_t m,
-                                 double* part_loss, double* part_w) {
+                                 double* part_loss, double* part_w, double* flag) {
   __shared__ double red[kNoallocThreads];
   double a = 0.0, b = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * kNoallocThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kNoallocThreads) {
+    if (y[i] != 1 && y[i] != -1) *flag = 1.0;
     const double yz = (double)y[i] * z[i];
     if (loss == PCDN_LOSS_LOGISTIC) a += yz > 0 ? log1p(exp(-yz)) : (-yz + log1p(exp(yz)));
     else a += (1.0 - yz) > 0 ? (1.0 - yz) * (1.0 - yz) : 0.0;
@@ -177,8 +192,8 @@ extern "C" int pcdn_objective_noalloc(const pcdn_csc* X, const int8_t* y, double
   noalloc_zero<<<gz, kNoallocThreads, 0, s>>>(z, n, flag);
   int gx = (int)((m * 32 + kNoallocThreads - 1) / kNoallocThreads);
   if (gx > 4096) gx = 4096;
-  noalloc_xw<<<gx, kNoallocThreads, 0, s>>>(X->col_ptr, X->row_idx, X->val, w, n, m, z, flag);
-  noalloc_partials<<<kNoallocBlocks, kNoallocThreads, 0, s>>>(z, y, n, (int)loss, w, m, part_loss, part_w);
+  noalloc_xw<<<gx, kNoallocThreads, 0, s>>>(X->col_ptr, X->row_idx, X->val, w, n, m, X->nnz, z, flag);
+  noalloc_partials<<<kNoallocBlocks, kNoallocThreads, 0, s>>>(z, y, n, (int)loss, w, m, part_loss, part_w, flag);
   noalloc_finish<<<1, kNoallocThreads, 0, s>>>(part_loss, part_w, kNoallocBlocks, C, flag, F);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return noalloc_fail(PCDN_ECUDA, cudaGetErrorString(e));

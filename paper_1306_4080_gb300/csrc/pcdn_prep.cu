@@ -485,7 +485,8 @@ __global__ void __launch_bounds__(kRedThreads) refresh_kernel(const int64_t* row
     const int yi = y[i];
     if (loss_part) lsum += row_loss(LOSS, z, yi);
     if (write_state) {
-      if (LOSS == 0 && fabs(z) > 700.0) atomicOr(err, kErrRefresh);
+      // FP64 keeps e^z (Algorithm 4), which holds |z| up to about 700; mixed keeps z itself
+      if (PREC == 0 ? (LOSS == 0 && fabs(z) > 700.0) : !isfinite(z)) atomicOr(err, kErrRefresh);
       const double v = slot_from_z<LOSS, PREC>(z, yi);
       *st_mq(st, i) = v;
       *st_rec<PREC>(st, i) = slot_coef<LOSS, PREC>(v, yi);
@@ -579,7 +580,7 @@ __global__ void __launch_bounds__(kRedThreads) refresh_df_kernel(const int64_t* 
       if (loss_part) lsum += row_loss(LOSS, z, yi);
       if (write_state) {
         // the pair of z itself (logistic) or of 1 - y z (L2-SVM), without a round trip through FP64
-        if (LOSS == 0 && fabs(z) > 700.0) atomicOr(err, kErrRefresh);
+        if (!isfinite(z)) atomicOr(err, kErrRefresh);
         const dfloat zd = {zz.x, zz.y};
         const dfloat v = LOSS == 0 ? zd : df_add_f(yi > 0 ? df_neg(zd) : zd, 1.0f);
         *st_mq(st, i) = df_slot(v);
@@ -625,21 +626,26 @@ __global__ void rec_from_mq_kernel(const int8_t* y, int64_t n, void* st) {
 template <int LOSS>
 __global__ void kkt_coef_kernel(const int8_t* y, int64_t n, void* st) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const double cg = RowCoef<LOSS, 0>::make(slot_value<LOSS, 1>(*st_mq(st, i)), y[i]).cg;
+    const double cg = coef64_of_mixed<LOSS>(*st_mq(st, i), y[i]).cg;
     const float hi = (float)cg;
     reinterpret_cast<float2*>(reinterpret_cast<SampleRec*>(st)[i].c)[1] = make_float2(hi, (float)(cg - (double)hi));
   }
 }
 
 // A state slot from one precision's form to the other's (FP64: e^z or b; mixed: the pair of z or
-// b), then the coefficients.
+// b), then the coefficients.  A margin that FP64's e^z cannot hold (|z| above about 699) sets the
+// range flag.
 template <int LOSS, int TO>
-__global__ void convert_state_kernel(const int8_t* y, int64_t n, void* st) {
+__global__ void convert_state_kernel(const int8_t* y, int64_t n, void* st, int* err) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const double s = *st_mq(st, i);
     double v;
-    if constexpr (TO == 1) v = df_slot(df_of(LOSS == 0 ? log(s) : s));
-    else v = slot_value<LOSS, 1>(s);
+    if constexpr (TO == 1) {
+      v = df_slot(df_of(LOSS == 0 ? log(s) : s));
+    } else {
+      v = slot_value<LOSS, 1>(s);
+      if (!mq_ok<LOSS>(v)) atomicOr(err, kErrRange);
+    }
     *st_mq(st, i) = v;
     *st_rec<TO>(st, i) = slot_coef<LOSS, TO>(v, y[i]);
   }
@@ -1075,13 +1081,13 @@ cudaError_t rec_from_mq(int loss, int prec, const int8_t* y, int64_t n, void* st
   return post(launches);
 }
 
-cudaError_t convert_state(int loss, int to_prec, const int8_t* y, int64_t n, void* st, cudaStream_t s,
+cudaError_t convert_state(int loss, int to_prec, const int8_t* y, int64_t n, void* st, int* err, cudaStream_t s,
                           int64_t* launches) {
   const unsigned g = grid_for(n, 256);
-  if (loss == 0 && to_prec == 0) convert_state_kernel<0, 0><<<g, 256, 0, s>>>(y, n, st);
-  else if (loss == 0) convert_state_kernel<0, 1><<<g, 256, 0, s>>>(y, n, st);
-  else if (to_prec == 0) convert_state_kernel<1, 0><<<g, 256, 0, s>>>(y, n, st);
-  else convert_state_kernel<1, 1><<<g, 256, 0, s>>>(y, n, st);
+  if (loss == 0 && to_prec == 0) convert_state_kernel<0, 0><<<g, 256, 0, s>>>(y, n, st, err);
+  else if (loss == 0) convert_state_kernel<0, 1><<<g, 256, 0, s>>>(y, n, st, err);
+  else if (to_prec == 0) convert_state_kernel<1, 0><<<g, 256, 0, s>>>(y, n, st, err);
+  else convert_state_kernel<1, 1><<<g, 256, 0, s>>>(y, n, st, err);
   return post(launches);
 }
 

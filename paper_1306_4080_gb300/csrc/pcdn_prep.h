@@ -110,8 +110,9 @@ cudaError_t state_at_zero(int loss, int prec, const int8_t* y, int64_t n, void* 
 // The coefficients from the current state slot (of precision prec).
 cudaError_t rec_from_mq(int loss, int prec, const int8_t* y, int64_t n, void* st, cudaStream_t s, int64_t* launches);
 // The state slots converted to precision to_prec's form (FP64: e^z or b; mixed: a double-float pair
-// of z or b) and their coefficients (a precision switch without recomputing z = Xw).
-cudaError_t convert_state(int loss, int to_prec, const int8_t* y, int64_t n, void* st, cudaStream_t s,
+// of z or b) and their coefficients (a precision switch without recomputing z = Xw); a margin too
+// large for FP64's e^z sets kErrRange in *err.
+cudaError_t convert_state(int loss, int to_prec, const int8_t* y, int64_t n, void* st, int* err, cudaStream_t s,
                           int64_t* launches);
 
 // ---- reductions -------------------------------------------------------------------------------

@@ -135,6 +135,10 @@ struct JobRun {
   // path
   int32_t P = 0;
   int32_t ci = 0;
+  bool warm = false;  // the next solve continues from the problem's current w
+  // repeated solves of one C: the product of the earlier attempts' relative KKT values and the
+  // first attempt's starting KKT value, so that the target stays eps times the latter
+  double kkt_scale = 1.0, kkt0 = 0.0;
   int status = PCDN_OK;
 };
 
@@ -148,7 +152,7 @@ struct BatchShared {
   bool use_graphs = true;
   std::vector<int32_t> cand;
   std::atomic<int32_t> next{0};
-  std::atomic<int64_t> solves{0}, probes{0}, epochs{0}, coord{0}, graphs{0};
+  std::atomic<int64_t> solves{0}, probes{0}, epochs{0}, coord{0}, graphs{0}, retries{0};
   std::mutex acc_mu;
   double bytes_model = 0.0;
   FirstError err;
@@ -167,11 +171,11 @@ int start_next(BatchShared& B, JobRun& r, SolveTask* t) {
     task_set_blocks(t, &B.budget, walker_blocks_wanted(j.prob, r.cand[r.probe]));
     return task_start(t, j.prob, r.cand[r.probe], B.probe_eps, j.seed, &o, 1);
   }
-  if (r.ci > 0) o.warm_start = 1;
+  if (r.ci > 0 || r.warm) o.warm_start = 1;
   int rc = pcdn_set_C(j.prob, j.C_path[r.ci]);
   if (rc) return rc;
   task_set_blocks(t, &B.budget, walker_blocks_wanted(j.prob, r.P));
-  return task_start(t, j.prob, r.P, j.eps, j.seed, &o, 1);
+  return task_start(t, j.prob, r.P, j.eps / r.kkt_scale, j.seed, &o, 1);
 }
 
 // A solve of the job ended on task t (status rc): record it and start the next one.
@@ -203,17 +207,37 @@ bool on_done(BatchShared& B, JobRun& r, SolveTask* t, int rc) {
       r.status = rr < 0 ? rr : rc;
       return true;
     }
-    if (j.stats) j.stats[r.ci] = st;
-    if (rr == PCDN_ENOTCONVERGED) r.status = PCDN_ENOTCONVERGED;
-    B.solves.fetch_add(1);
-    if (task_used_graph(t)) B.graphs.fetch_add(1);
     B.epochs.fetch_add(st.epochs);
     B.coord.fetch_add(st.coord_updates);
     {
       std::lock_guard<std::mutex> lock(B.acc_mu);
       B.bytes_model += st.bytes_model;
     }
-    if (++r.ci >= j.n_C) return true;
+    if (task_used_graph(t)) B.graphs.fetch_add(1);
+    int32_t smaller = 0;
+    if (rr == PCDN_ENOTCONVERGED && j.P == 0)
+      for (int32_t c : r.cand)
+        if (c < r.P && c > smaller) smaller = c;
+    if (smaller > 0) {
+      // stalled at this C with the autotuned size: solve it again from here with the next smaller
+      // one, its relative tolerance measured from this C's first start
+      B.retries.fetch_add(1);
+      if (r.kkt_scale == 1.0) r.kkt0 = st.kkt0;
+      r.kkt_scale *= st.kkt_rel;
+      r.P = smaller;
+      j.P_used = smaller;
+      r.warm = true;
+    } else {
+      if (r.kkt_scale != 1.0) {
+        st.kkt_rel *= r.kkt_scale;
+        st.kkt0 = r.kkt0;
+        r.kkt_scale = 1.0;
+      }
+      if (j.stats) j.stats[r.ci] = st;
+      if (rr == PCDN_ENOTCONVERGED) r.status = PCDN_ENOTCONVERGED;
+      B.solves.fetch_add(1);
+      if (++r.ci >= j.n_C) return true;
+    }
   }
   int s = start_next(B, r, t);
   if (s < 0) {
@@ -340,6 +364,8 @@ struct Request {
   std::string msg;
   std::vector<double> w;
   pcdn_stats stats{};
+  int32_t retries = 0;    // solves repeated with a smaller bundle size after reaching max_epochs
+  double kkt_scale = 1.0, kkt0 = 0.0;  // as JobRun's, for those repeats
 };
 
 }  // namespace
@@ -509,6 +535,27 @@ void drive_loop(pcdn_server* s) {
       pcdn_stats st;
       std::memset(&st, 0, sizeof(st));
       int rr = rc < 0 ? rc : task_result(tasks[k], w.data(), &st);
+      int32_t smaller = 0;
+      if (rr == PCDN_ENOTCONVERGED)
+        for (int32_t c : default_candidates(r->m))
+          if (c < r->P && c > smaller) smaller = c;
+      if (smaller > 0) {
+        // stalled with the requested bundle size: go on from the w reached with the next smaller
+        // default size, the relative tolerance still measured from w = 0
+        if (r->kkt_scale == 1.0) r->kkt0 = st.kkt0;
+        r->kkt_scale *= st.kkt_rel;
+        r->P = smaller;
+        r->retries += 1;
+        pcdn_opts o = s->opts;
+        o.warm_start = 1;
+        task_set_blocks(tasks[k], &s->blocks, walker_blocks_wanted(r->prob, r->P));
+        rr = task_start(tasks[k], r->prob, r->P, r->eps / r->kkt_scale, r->seed, &o, 1);
+        if (rr >= 0) continue;
+      }
+      if (rr >= 0 && r->kkt_scale != 1.0) {
+        st.kkt_rel *= r->kkt_scale;
+        st.kkt0 = r->kkt0;
+      }
       std::string msg = rr < 0 ? pcdn_last_error() : "";
       std::lock_guard<std::mutex> lock(s->mu);
       r->w.swap(w);
@@ -629,6 +676,7 @@ int pcdn_solve_batch(pcdn_batch_job* jobs, int32_t n_jobs, const pcdn_opts* opts
     out->wall_s = std::chrono::duration<double>(Clock::now() - t0).count();
     out->solves = B.solves.load();
     out->probe_solves = B.probes.load();
+    out->retries = B.retries.load();
     out->epochs = B.epochs.load();
     out->coord_updates = B.coord.load();
     out->bytes_model = B.bytes_model;
@@ -820,6 +868,8 @@ int pcdn_server_wait(pcdn_server* s, int64_t ticket, double timeout_s, double* w
     info->t_done = r->t_done;
     info->bytes = r->bytes;
     info->stats = r->stats;
+    info->P_used = r->P;
+    info->retries = r->retries;
   }
   const int status = r->status;
   if (status < 0) set_last_error(r->msg.c_str());

@@ -63,7 +63,7 @@ template <int PREC> using GHT = typename std::conditional<PREC == 0, double, flo
 // A column's terms of Delta (Eq. 7): g d, h d^2, |w + d| - |w| (zero when d = 0).
 template <int PREC>
 struct ColTerms {
-  GHT<PREC> gd, hdd, l1;
+  double gd, hdd, l1;  // FP64 in both modes (one product per coordinate)
 };
 
 // Phase A scratch that phases B and C reuse for their row lists.
@@ -233,15 +233,11 @@ __device__ __forceinline__ double finalize(const WalkParams& p, int64_t kl, GHT<
       g += p.l2_f * wf;
       h += p.l2_f;
     }
-    const float l1 = p.l1_f;
-    if (g + l1 <= h * wf) d = (double)(-(g + l1) / h);
-    else if (g - l1 >= h * wf) d = (double)(-(g - l1) / h);
-    else d = -wj;
-    const float df = (float)d;
-    t.gd = g * df;
-    t.hdd = h * df * df;
+    d = newton_direction_f(g, h, wf, wj, p.l1_f);
+    t.gd = (double)g * d;
+    t.hdd = (double)h * d * d;
   }
-  t.l1 = d != 0.0 ? (GHT<PREC>)(p.l1 * (fabs(wj + d) - fabs(wj))) : GHT<PREC>(0);
+  t.l1 = d != 0.0 ? p.l1 * (fabs(wj + d) - fabs(wj)) : 0.0;
   if (write) {
     p.gk[kl] = (double)g;
     p.hk[kl] = (double)h;
@@ -511,9 +507,9 @@ __device__ void column_pass(const WalkParams& p, SharedWalk<PREC>& sh, int64_t l
       }
       if (wib * kWarp < nb) {
         Acc<PREC> a0, a1, a2;
-        a0.add_t(ct.gd);
-        a1.add_t(ct.hdd);
-        a2.add_t(ct.l1);
+        a0.add(ct.gd);
+        a1.add(ct.hdd);
+        a2.add(ct.l1);
         a0.warp_reduce();
         a1.warp_reduce();
         a2.warp_reduce();
@@ -612,9 +608,9 @@ __device__ void column_pass(const WalkParams& p, SharedWalk<PREC>& sh, int64_t l
       Acc<PREC> a0 = Acc<PREC>::load(sh.apart[0]), a1 = Acc<PREC>::load(sh.apart[1]), a2 = Acc<PREC>::load(sh.apart[2]);
       const int ncol = sh.s_col[ns - 1] + 1;
       for (int c = 0; c < ncol; ++c) {
-        a0.add_t(sh.s_terms[c].gd);
-        a1.add_t(sh.s_terms[c].hdd);
-        a2.add_t(sh.s_terms[c].l1);
+        a0.add(sh.s_terms[c].gd);
+        a1.add(sh.s_terms[c].hdd);
+        a2.add(sh.s_terms[c].l1);
       }
       sh.apart[0] = a0.store();
       sh.apart[1] = a1.store();
@@ -661,9 +657,9 @@ __device__ void column_pass(const WalkParams& p, SharedWalk<PREC>& sh, int64_t l
         sh.split_d = dj;
         if (it.chunk == 0) {
           Acc<PREC> a0 = Acc<PREC>::load(sh.apart[0]), a1 = Acc<PREC>::load(sh.apart[1]), a2 = Acc<PREC>::load(sh.apart[2]);
-          a0.add_t(ct.gd);
-          a1.add_t(ct.hdd);
-          a2.add_t(ct.l1);
+          a0.add(ct.gd);
+          a1.add(ct.hdd);
+          a2.add(ct.l1);
           sh.apart[0] = a0.store();
           sh.apart[1] = a1.store();
           sh.apart[2] = a2.store();
@@ -748,7 +744,10 @@ struct LsAcc<LOSS, 0> {
   __device__ __forceinline__ Acc<0> get(int q) const { Acc<0> a; a.v = s[q]; return a; }
 };
 
-// Mixed: FP32 remainder terms (non-negative), compensated FP32 sums per lane.
+// Mixed: each row's loss change in FP32, its first-order part cg u plus the remainder at the very
+// u = alpha d^T x_i its state moves by (one rounding), compensated FP32 sums per lane.  Summing the
+// first-order part per row rather than as alpha g^T d from the column sums keeps the FP32 error of
+// each coordinate's g_j away from large opposite d_j whose effects cancel within each x_i^T d.
 template <int LOSS>
 struct LsAcc<LOSS, 1> {
   float s[kMaxK], cmp[kMaxK];
@@ -766,17 +765,25 @@ struct LsAcc<LOSS, 1> {
       const float other = known <= 0.5f ? 1.0f - known : rv.rc.ch / known;
       const float pp = rv.y > 0 ? other : known, ss = rv.y > 0 ? known : other;
       const bool use_p = pp <= ss;
-      const float a = use_p ? pp : ss;
-      const float vf = use_p ? dlf : -dlf;
+      const float a = use_p ? pp : ss, az = fabsf(slot_df(rv.mq).hi);
 #pragma unroll
-      for (int q = 0; q < kMaxK; ++q)
-        if (q < K) kahan_add(s[q], cmp[q], lr_remainder(a, alpha_f[q] * vf));
+      for (int q = 0; q < kMaxK; ++q) {
+        if (q < K) {
+          const float u = alpha_f[q] * dlf;
+          kahan_add(s[q], cmp[q], fmaf(rv.rc.cg, u, lr_remainder(a, use_p ? u : -u, az)));
+        }
+      }
     } else {
+      // the L2-SVM's coefficient from b (its records are not staged): -2 y max(b, 0)
       const dfloat b = slot_df(rv.mq);
-      const float ydf = rv.y > 0 ? dlf : -dlf;
+      const float cg = RowCoef<1, 1>::make(b, rv.y).cg;
 #pragma unroll
-      for (int q = 0; q < kMaxK; ++q)
-        if (q < K) kahan_add(s[q], cmp[q], svm_remainder(b, alpha_f[q] * ydf));
+      for (int q = 0; q < kMaxK; ++q) {
+        if (q < K) {
+          const float u = alpha_f[q] * dlf;
+          kahan_add(s[q], cmp[q], fmaf(cg, u, svm_remainder(b, rv.y > 0 ? u : -u)));
+        }
+      }
     }
   }
   __device__ __forceinline__ Acc<1> get(int q) const {
@@ -1107,16 +1114,18 @@ __global__ void __launch_bounds__(kWalkThreads, 2) walk_kernel(WalkParams p) {
               }
             }
           } else {
-            // l1 (|w + a d| - |w|) in double-float arithmetic (a is a power of two when beta = 1/2);
-            // the L2 change's first-order part a l2 w d is in a g^T d (g holds l2 w), its second-order
-            // part (l2/2) a^2 d^2 is added here
+            // l1 (|w + a d| - |w|) in double-float arithmetic (a is a power of two when beta = 1/2),
+            // plus the L2 change (l2/2) ((w + a d)^2 - w^2)
             const dfloat wd = df_make(wj), dd = df_make(d), aw = df_neg(df_abs(wd));
 #pragma unroll
             for (int q = 0; q < kMaxK; ++q) {
               if (q < K) {
                 dfloat r = df_add(df_abs(df_add(wd, df_scale(dd, alpha_f[q]))), aw);
                 if (p.l1 != 1.0) r = df_scale(r, p.l1_f);
-                if (p.l2 != 0.0) r = df_add(r, df_make(0.5 * p.l2 * (alpha[q] * d) * (alpha[q] * d)));
+                if (p.l2 != 0.0) {
+                  const double t = alpha[q] * d;
+                  r = df_add(r, df_make(0.5 * p.l2 * ((wj + t) * (wj + t) - wj * wj)));
+                }
                 pq[q].v = df_add(pq[q].v, r);
               }
             }
@@ -1183,7 +1192,10 @@ __global__ void __launch_bounds__(kWalkThreads, 2) walk_kernel(WalkParams p) {
         if (wib == 0) {
           const double* tot = sh.tot;
           const double gd = tot[0], hdd = tot[1], l1 = tot[2];
-          const double Delta = gd + p.gamma * hdd + l1;
+          double Delta = gd + p.gamma * hdd + l1;
+          // Delta <= (gamma - 1) d^T H d <= 0 (Eq. 7 with Eq. 5's d); mixed mode's FP32 g can leave
+          // a small positive rounding residue, which would let a step that raises F pass
+          if (PREC == 1 && Delta > 0.0) Delta = 0.0;
           double a = alpha[0];
 #pragma unroll
           for (int q = 1; q < kMaxK; ++q)
@@ -1191,10 +1203,10 @@ __global__ void __launch_bounds__(kWalkThreads, 2) walk_kernel(WalkParams p) {
           double dF = 0.0;
           bool pass = false;
           if (lane < K && qbase + lane < p.q_max) {
-            if constexpr (PREC == 0) dF = p.c * tot[3 + kMaxK + lane] + tot[3 + lane];
-            else dF = a * gd + p.c * tot[3 + kMaxK + lane] + tot[3 + lane];
-            // a NaN change (an overflowing trial step) fails the test, as in Eq. 6 read literally
-            pass = dF <= p.sigma * a * Delta;
+            dF = p.c * tot[3 + kMaxK + lane] + tot[3 + lane];
+            // Delta and the change are finite in exact arithmetic (Delta <= 0): a sum that overflowed
+            // (a huge direction or trial step) fails the test instead of passing as inf <= inf
+            pass = isfinite(Delta) && isfinite(dF) && dF <= p.sigma * a * Delta;
           }
           const uint32_t m = __ballot_sync(0xffffffffu, pass);
           const int qa = m ? __ffs(m) - 1 : 0;

@@ -180,10 +180,7 @@ __device__ __forceinline__ double finalize(const WalkParams& p, int par, int32_t
       g += p.l2_f * wf;
       h += p.l2_f;
     }
-    const float l1 = p.l1_f;
-    if (g + l1 <= h * wf) d = (double)(-(g + l1) / h);
-    else if (g - l1 >= h * wf) d = (double)(-(g - l1) / h);
-    else d = -wj;
+    d = newton_direction_f(g, h, wf, wj, p.l1_f);
   }
   const int64_t o = (int64_t)par * p.P_cap + kl;
   p.gk[o] = (double)g;
@@ -485,11 +482,16 @@ template <int LOSS> struct Row<LOSS, 0> {
   }
 };
 
-// Mixed mode: the FP32 remainder after the first-order part (summed exactly as alpha g^T d over the
-// bundle).
+// Mixed mode: the sample's loss change at u = alpha d^T x_i in FP32 as its first-order part cg u
+// plus the remainder, one rounding; each sample's change is formed from the very u its state moves
+// by, so the sum is the objective change of the step taken up to FP32 rounding of each term, with
+// no cancellation between coordinates (a first-order part taken from the column sums, alpha g^T d,
+// errs by about 2^-24 |d_j| sum_i |x_ij cg_i| per coordinate, which a bundle of large opposite d_j
+// whose effects cancel in each x_i^T d turns into a spurious decrease).
 template <int LOSS> struct Row<LOSS, 1> {
   using DT = float;
   static __device__ __forceinline__ void term(Fx& acc, double mq, int y, float dlf, RecT<1> rc, double a, float af) {
+    const float u = af * dlf;
     if constexpr (LOSS == 0) {
       // p = E/(1+E) and s = 1/(1+E) from the FP32 coefficient pair: |cg| is s (y = +1) or p
       // (y = -1), ch = p s; the other one is 1 - |cg| when |cg| <= 1/2, else ch / |cg|
@@ -497,9 +499,9 @@ template <int LOSS> struct Row<LOSS, 1> {
       const float other = known <= 0.5f ? 1.0f - known : __fdividef(rc.ch, known);
       const float pp = y > 0 ? other : known, ss = y > 0 ? known : other;
       const bool use_p = pp <= ss;
-      fx_add_f(acc, lr_remainder(use_p ? pp : ss, af * (use_p ? dlf : -dlf)));
+      fx_add_f(acc, fmaf(rc.cg, u, lr_remainder(use_p ? pp : ss, use_p ? u : -u, fabsf(slot_df(mq).hi))));
     } else {
-      fx_add_f(acc, svm_remainder(slot_df(mq), af * (y > 0 ? dlf : -dlf)));
+      fx_add_f(acc, fmaf(rc.cg, u, svm_remainder(slot_df(mq), y > 0 ? u : -u)));
     }
   }
   // the pair of z (logistic) or b (L2-SVM) plus the FP32 step alpha d^T x_i, on the FP32 pipe
@@ -574,8 +576,9 @@ __device__ __forceinline__ void row_work(const WalkParams& p, const RowCtx& c, i
     rec_words(slot_coef<LOSS, PREC>(nq, st.y), c0, c1);
     store_state(p, r, nq, st.mq, c0, c1);
   } else if constexpr (MODE == kEval) {
+    // mixed: the record holds the full step's coefficients by now; the kept state's are recomputed
     RecT<1> rc{0.0f, 0.0f};
-    if constexpr (PREC == 1 && LOSS == 0) rc = RowCoef<0, 1>::make(slot_df(st.bak), st.y);
+    if constexpr (PREC == 1) rc = RowCoef<LOSS, 1>::make(slot_df(st.bak), st.y);
     Row<LOSS, PREC>::term(acc, st.bak, st.y, dl, rc, c.a, c.af);
   } else {
     double nq = st.bak;
@@ -845,12 +848,7 @@ __device__ __forceinline__ void position_terms(const WalkParams& p, const Shared
     if (q < K) {
       const double t = sh.atab[min(q0 + q, kAlphaTab - 1)] * d;
       double r = p.l1 * (fabs(wj + t) - fabs(wj));
-      if (p.l2 != 0.0) {
-        // FP64 mode: the whole L2 change; mixed mode: its second-order part (the first-order part
-        // a l2 w d is inside a g^T d, g holding l2 w)
-        if constexpr (PREC == 0) r += 0.5 * p.l2 * ((wj + t) * (wj + t) - wj * wj);
-        else r += 0.5 * p.l2 * t * t;
-      }
+      if (p.l2 != 0.0) r += 0.5 * p.l2 * ((wj + t) * (wj + t) - wj * wj);
       pen[q] += r;
     }
   }
@@ -1081,15 +1079,18 @@ __global__ void __launch_bounds__(kWalkThreads, 2) walk_rows_kernel(WalkParams p
         }
         __syncwarp();
         const double gd = sh.dparts[0], hdd = sh.dparts[1], l1 = sh.dparts[2];
-        const double Delta = gd + p.gamma * hdd + l1;
+        double Delta = gd + p.gamma * hdd + l1;
+        // Delta <= (gamma - 1) d^T H d <= 0 (Eq. 7 with Eq. 5's d); mixed mode's FP32 g can leave a
+        // small positive rounding residue, which would let a step that raises F pass
+        if (PREC == 1 && Delta > 0.0) Delta = 0.0;
         const double a = alpha_of(p, sh, q0 + (lane < K ? lane : 0));
         double dF = 0.0;
         bool pass = false;
         if (lane < K && q0 + lane < p.q_max) {
-          if constexpr (PREC == 0) dF = p.c * tot[3 + kMaxK + lane] + tot[3 + lane];
-          else dF = a * gd + p.c * tot[3 + kMaxK + lane] + tot[3 + lane];
-          // a NaN change (an overflowing trial step) fails the test, as in Eq. 6 read literally
-          pass = dF <= p.sigma * a * Delta;
+          dF = p.c * tot[3 + kMaxK + lane] + tot[3 + lane];
+          // Delta and the change are finite in exact arithmetic (Delta <= 0): a sum that overflowed
+          // (a huge direction or trial step) fails the test instead of passing as inf <= inf
+          pass = isfinite(Delta) && isfinite(dF) && dF <= p.sigma * a * Delta;
         }
         const uint32_t m = __ballot_sync(0xffffffffu, pass);
         const int qa = m ? __ffs(m) - 1 : 0;

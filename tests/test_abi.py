@@ -205,3 +205,26 @@ def test_penalty_rejects_a_missing_problem(pk):
     lib = pk.load()
     assert lib.pcdn_set_penalty(None, 1.0, 0.0) == pk.PCDN_EINVAL
     assert "problem" in pk.pcdn_last_error()
+
+
+def test_every_declaration_cites_its_passage():
+    """Each entry point of include/pcdn.h is preceded by a comment that cites the paper's passage
+    defining the operation (Section, Eq., Algorithm, Appendix, Table, Lemma, Theorem), or says that
+    it is library management with no passage, or that the paper has no counterpart."""
+    import re
+    with open(os.path.join(ROOT, "include", "pcdn.h")) as f:
+        lines = f.read().split("\n")
+    decl = re.compile(r"^(int|void|const char\*|int64_t)\s+(pcdn_\w+)\(")
+    cite = re.compile(r"Section|Eq\.|Algorithm|Appendix|Table|Lemma|Theorem|no passage|no counterpart")
+    seen = []
+    for i, line in enumerate(lines):
+        m = decl.match(line)
+        if not m:
+            continue
+        j, block = i - 1, []
+        while j >= 0 and (lines[j].strip().startswith(("/*", "*", "//")) or lines[j].strip().endswith("*/")):
+            block.append(lines[j])
+            j -= 1
+        assert cite.search(" ".join(block)), m.group(2)
+        seen.append(m.group(2))
+    assert "pcdn_create" in seen and "pcdn_kkt" in seen and len(seen) >= 20

@@ -327,3 +327,59 @@ def test_server_error_paths(pk):
         assert q.solve(8, 1e-3, 0)[2]["converged"]
     finally:
         q.close()
+
+
+def test_server_burst_all_ok_and_matching_the_oracle(pk):
+    """A burst of 120 requests submitted at once (ten problems of uneven sizes, both losses, two C
+    values each, every pair six times) into a server with the default slots, in mixed precision:
+    every request returns PCDN_OK, and its objective is within 1e-6 of the FP64 oracle's at the same
+    tolerance (the bar of the single solves); the copies of one pair agree with each other."""
+    items = batch(10, seed=11, scale=0.05, n_C=1, C_range=(1.0, 1.0))
+    P, eps, seed = 32, 1e-3, 3
+    combos = [(k, C) for k in range(len(items)) for C in (0.3, 3.0)]
+    opts = pk.pcdn_default_opts(prec="mixed", max_epochs=1000)
+    srv = pk.Server(opts=opts)
+    try:
+        tickets = []
+        for rep in range(6):
+            for k, C in combos:
+                job, p = items[k]
+                tickets.append(((k, C), srv.submit(p.col_ptr, p.row_idx, p.val, p.y, C, job.loss,
+                                                   min(P, p.n_features), eps, seed, borrow=True)))
+        out = [(kc, srv.wait(t, 600)) for kc, t in tickets]
+    finally:
+        srv.close()
+    bad = [(kc, r[0], r[2]["message"]) for kc, r in out if r[0] != pk.PCDN_OK]
+    assert not bad, bad
+    F_or = {}
+    for k, C in combos:
+        job, p = items[k]
+        orc = oracle.Oracle.from_problem(p, C, job.loss)
+        _, so = orc.solve(min(P, p.n_features), eps=eps, seed=seed, max_epochs=1000)
+        assert so["converged"]
+        F_or[(k, C)] = so["F_final"]
+    for kc, (rc, w, info) in out:
+        F = info["stats"]["F_final"]
+        assert abs(F - F_or[kc]) <= 1e-6 * abs(F_or[kc]), (kc, F, F_or[kc])
+
+
+def test_server_request_that_stalls_goes_on_with_a_smaller_bundle(pk):
+    """A request whose solve reaches max_epochs with P above 16 is continued from the w it reached
+    with the next smaller default bundle size (256 -> 64 -> 16): info reports the retries and the
+    size used, and its relative KKT value is still measured from w = 0 (checked against the
+    oracle's KKT measure at the returned w)."""
+    job, p = batch(1, seed=5, scale=0.2, n_C=1, C_range=(2.0, 2.0))[0]
+    P0 = 256
+    assert p.n_features > P0
+    srv = pk.Server(slots=1, opts=pk.pcdn_default_opts(max_epochs=2))
+    try:
+        t = srv.submit(p.col_ptr, p.row_idx, p.val, p.y, 2.0, job.loss, P0, 1e-9, 0)
+        rc, w, info = srv.wait(t, 300)
+    finally:
+        srv.close()
+    assert rc == pk.PCDN_ENOTCONVERGED  # 1e-9 is out of reach in 2 outer iterations per size
+    assert info["retries"] == 2 and info["P_used"] == 16
+    orc = oracle.Oracle.from_problem(p, 2.0, job.loss)
+    k0 = orc.kkt_l1(np.zeros(p.n_features))
+    assert info["stats"]["kkt0"] == pytest.approx(k0, rel=1e-9)
+    assert info["stats"]["kkt_rel"] == pytest.approx(orc.kkt_l1(w) / k0, rel=1e-6)
