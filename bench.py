@@ -88,22 +88,32 @@ def measured_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def walker_source_hash():
-    """Hash of the walker's sources (the kernel and the header with its constants)."""
+def walker_source_hash(layout: str = "scatter"):
+    """Hash of a walker's sources (its kernel and the header with its constants)."""
     h = hashlib.sha256()
-    for f in ("pcdn_walk.cu", "pcdn_internal.cuh"):
+    for f in ({"scatter": "pcdn_walk.cu", "rows": "pcdn_walk_rows.cu"}[layout], "pcdn_internal.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1306_4080_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
-def walker_traffic():
-    """DRAM bytes per walker launch from the committed ncu summary, if it was taken on the
-    current walker sources; else None."""
+WALKERS = {"scatter": "pcdn::walk_kernel", "rows": "pcdn::rows::walk_rows_kernel"}
+
+
+def walker_layout(requested: str, prec: str, grid: int) -> str:
+    """The walker a solve ran: the requested layout, else the library's default (row-sorted for
+    FP64 on more than one block, scatter otherwise)."""
+    if requested in WALKERS:
+        return requested
+    return "rows" if (prec == "fp64" and grid > 1) else "scatter"
+
+
+def walker_traffic(layout: str):
+    """DRAM bytes per walker launch from the committed ncu summary of that walker, if it was taken
+    on the current walker sources; else None."""
     path = os.path.join(ROOT, "profiles", "walk_traffic.json")
     try:
-        d = json.load(open(path))
-        h = walker_source_hash()
-        if d.get("walk_source_sha256_16") != h:
+        d = json.load(open(path)).get(layout)
+        if not d or d.get("walk_source_sha256_16") != walker_source_hash(layout):
             return None
         return d
     except Exception:
@@ -340,7 +350,7 @@ def run_batched(args, pk, pool):
                               "how": f"every {every}-th job; plain = pcdn_solve one solve at a time, same bundle sizes, "
                                      "its own choice of walker blocks"},
                  "P_chosen": {str(P): Ps.count(P) for P in sorted(set(Ps))},
-                 "critical_jobs": crit[:4], "sum_path_s": sum(d["path_s"] for d in jobs_diag),
+                 "critical_jobs": crit[:2], "sum_path_s": sum(d["path_s"] for d in jobs_diag),
                  "config": {"workload": f"{len(pool)} problems, n_samples log-uniform [1k, 50k] x {args.batch_scale:g}, "
                                         f"n_features log-uniform [5k, 200k] x {args.batch_scale:g}, density U[0.1%, 1%], "
                                         "Zipf 1.1 columns, tf-idf rows L2-normalised, losses alternating logistic / "
@@ -522,13 +532,17 @@ def run_ours(args):
     launches = sum(s["kernel_launches"] for s in sts)
     peak, peak_src = measured_peak()
     achieved = bytes_model / walk_s / 1e9 if walk_s > 0 else 0.0
-    tr = walker_traffic()
+    layout = walker_layout(args.layout, args.prec, int(st0["walk_grid"]))
+    tr = walker_traffic(layout)
+    ms_launch = walk_s / walk_launches * 1e3
+    traffic = (tr["dram_bytes_per_launch"] * (bytes_model / walk_launches) / tr["bytes_model_per_launch"]) if tr else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": (tr["dram_bytes_per_launch"] * (bytes_model / walk_launches) / tr["bytes_model_per_launch"])
-            if tr else None,
-            "kernel": "pcdn::walk_kernel (one launch per outer iteration)",
+            "traffic": traffic,
+            # DRAM bytes the kernel really moved (ncu, scaled to this launch) per launch time, of peak
+            "dram_frac": (traffic / (ms_launch * 1e-3) / 1e9 / peak) if traffic else None,
+            "kernel": WALKERS[layout] + " (one launch per outer iteration)", "layout": layout,
             "peak_source": f"{peak_src} HBM copy bandwidth",
-            "bytes_per_launch": bytes_model / walk_launches, "ms_per_launch": walk_s / walk_launches * 1e3,
+            "bytes_per_launch": bytes_model / walk_launches, "ms_per_launch": ms_launch,
             "walk_share_of_step": walk_s / (ms * 1e-3 * len(sts))}
     if tr:
         roof["traffic_source"] = tr.get("source")
@@ -537,11 +551,14 @@ def run_ours(args):
     if args.also_fp64 and args.prec != "fp64":
         ms64, sts64, clk64 = timed("fp64", max(1, min(args.steps, 3)), 1)
         s64 = sts64[-1]
-        extra["fp64"] = {"value": ms64 * 1e-3 / world, "ms_per_step": ms64, "epochs": s64["epochs"],
-                         "F_final": s64["F_final"], "kkt_rel": s64["kkt_rel"],
+        lay64 = walker_layout(args.layout, "fp64", int(s64["walk_grid"]))
+        ach64 = sum(s["bytes_model"] for s in sts64) / sum(s["walk_s"] for s in sts64) / 1e9
+        extra["fp64"] = {"value": ms64 * 1e-3 / world, "unit": UNIT, "ms_per_step": ms64, "epochs": s64["epochs"],
+                         "F_final": s64["F_final"], "kkt_rel": s64["kkt_rel"], "layout": lay64,
+                         "kernel": WALKERS[lay64],
                          "walk_ms_per_launch": sum(s["walk_s"] for s in sts64) / sum(s["epochs"] for s in sts64) * 1e3,
-                         "achieved_GBps": sum(s["bytes_model"] for s in sts64) / sum(s["walk_s"] for s in sts64) / 1e9,
-                         "clocks": clk64}
+                         "achieved_GBps": ach64, "frac": ach64 / peak, "clocks": clk64,
+                         "note": "like-for-like with the FP64 reference arm: every quantity in FP64"}
 
     if args.also_shrink:
         # the same solve with shrinking between outer iterations (an option; the headline solve visits
@@ -554,7 +571,7 @@ def run_ours(args):
         extra["shrinking"] = {"value": mss * 1e-3 / world, "unit": UNIT, "ms_per_step": mss,
                               "speedup_vs_plain": ms / mss, "epochs": ss["epochs"], "bundles": ss["bundles"],
                               "coord_updates": ss["coord_updates"], "nnz_visited": ss["nnz_visited"],
-                              "features_per_outer_iteration": [int(x) for x in trs["epoch_features"]],
+                              "features_first_outer_iterations": [int(x) for x in trs["epoch_features"][:6]],
                               "F_final": ss["F_final"], "F_plain": st0["F_final"], "kkt_rel": ss["kkt_rel"],
                               "walk_ms": ss["walk_s"] * 1e3, "clocks": clks}
 
@@ -595,13 +612,16 @@ def run_ours(args):
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32/f64 mixed" if args.prec == "mixed" else "f64",
                 "data": "synthetic (seeded generator, shapes of the paper's sparse text workloads)",
-                "config": config_of(wl, prob, args.prec), "roofline": roof, "cpu_baseline": cpu,
-                "cpu_baseline_openmp": cpu_omp, "e2e": e2e,
-                "gpu_launches": int(launches), "clocks": clocks,
-                "solve": {"epochs": st0["epochs"], "bundles": st0["bundles"], "F_final": st0["F_final"],
-                          "kkt_rel": st0["kkt_rel"], "coord_updates_per_s": st0["coord_updates"] / (ms * 1e-3),
-                          "ls_steps": st0["ls_steps"], "ls_cap_hits": st0["ls_cap_hits"],
-                          "rows_touched": st0["rows_touched"]}}
+                "config": config_of(wl, prob, args.prec)}
+        # the FP64 solve right after the headline, so that both precisions lead the line
+        if "fp64" in extra:
+            line["fp64"] = extra.pop("fp64")
+        line.update({"roofline": roof, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
+                     "cpu_baseline": cpu, "cpu_baseline_openmp": cpu_omp,
+                     "solve": {"epochs": st0["epochs"], "bundles": st0["bundles"], "F_final": st0["F_final"],
+                               "kkt_rel": st0["kkt_rel"], "coord_updates_per_s": st0["coord_updates"] / (ms * 1e-3),
+                               "ls_steps": st0["ls_steps"], "ls_cap_hits": st0["ls_cap_hits"],
+                               "rows_touched": st0["rows_touched"]}})
         line.update(extra)
         if world == 1:
             add_extra_legs(args, pk, line)

@@ -55,6 +55,37 @@ def rel_err(a, b):
     return float(np.max(np.abs(np.asarray(a) - np.asarray(b)))) / scale if np.size(b) else 0.0
 
 
+def armijo_margin(orc, p, w, mq, B, d, Delta, q_lo, q_hi, armijo):
+    """The smallest relative Armijo margin |dF(a) - sigma a Delta| / scale over q in [q_lo, q_hi],
+    dF(a) in the oracle's maintained form (Eq. 10 per sample plus the penalty change), scale =
+    c sum_i |change_i| + sum_j |penalty change_j| + |sigma a Delta|: the size of the rounding that
+    any order of summation leaves."""
+    dx = np.zeros(p.n_samples)
+    for k, j in enumerate(B):
+        a, b = p.col_ptr[j], p.col_ptr[j + 1]
+        dx[p.row_idx[a:b]] += p.val[a:b].astype(np.float64) * d[k]
+    rows = np.flatnonzero(dx)
+    best = np.inf
+    for q in range(q_lo, q_hi + 1):
+        a = armijo.beta ** q
+        ch = np.array([orc.row_loss_change(mq[i], int(p.y[i]), a * dx[i]) for i in rows])
+        pen = np.abs(w[B] + a * d) - np.abs(w[B])
+        dF = orc.c * ch.sum() + pen.sum()
+        thr = armijo.sigma * a * Delta
+        best = min(best, abs(dF - thr) / (orc.c * np.abs(ch).sum() + np.abs(pen).sum() + abs(thr)))
+    return best
+
+
+def oracle_state_at(orc, m, Pb, seed, t):
+    """The oracle's w after t bundles of its solve (Algorithm 3 from w = 0, no shrinking) and the
+    bundle it takes next."""
+    nb = (m + Pb - 1) // Pb
+    w, _ = orc.solve(Pb, eps=1e-300, seed=seed, max_epochs=t // nb + 1, bundle_limit=t)
+    k, i = divmod(t, nb)
+    perm = oracle.permutation(seed, k, m)
+    return w, perm[i * Pb:(i + 1) * Pb].astype(np.int32)
+
+
 def margin_small(orc, w, ro, bundle, q_gpu, q_or, armijo, tol):
     """True when, at every step size between the two accepted ones, the oracle's objective change
     F(w + a d) - F(w) is within tol of the Armijo threshold sigma a Delta (Eq. 6)."""
@@ -146,12 +177,24 @@ def test_solve_parity(pk, name, Pb, grid, prec, layout):
             assert st["epochs"] == so["epochs"]
             n = min(len(tr["q"]), len(so["q"]))
             assert n == so["bundles"]
-            assert np.mean(tr["q"][:n] == so["q"][:n]) >= 0.999
+            # a differing accepted step is a near-tie: at the oracle's state there, the Armijo test
+            # (Eq. 6) is within 1e-10 of equality at some step size between the two choices
+            mism = np.flatnonzero(tr["q"][:n] != so["q"][:n])
+            assert mism.size <= max(2, n // 500), (mism.size, n)
+            armijo = oracle.Armijo()
+            for t in mism:
+                wt, B = oracle_state_at(orc, p.n_features, Pb, wl.solver_seed, int(t))
+                mq = orc.maintained(wt)
+                _, _, ro = orc.bundle_step(wt, mq, B, armijo=armijo)
+                mg = armijo_margin(orc, p, wt, mq, B, ro["d"], ro["Delta"], int(min(tr["q"][t], ro["q"])),
+                                   int(max(tr["q"][t], ro["q"])), armijo)
+                assert mg <= 1e-10, (int(t), int(tr["q"][t]), int(so["q"][t]), mg)
             np.testing.assert_allclose(tr["epoch_kkt"], so["epoch_kkt"], rtol=1e-6)
             np.testing.assert_allclose(w, wo, rtol=0, atol=1e-7 * max(1.0, np.abs(wo).max()))
         else:
-            assert abs(st["epochs"] - so["epochs"]) <= 1
-        assert st["bundles"] == so["bundles"] or prec == "mixed"
+            # mixed precision stops at the oracle's outer iteration: its stopping test is FP64-grade
+            assert st["epochs"] == so["epochs"], (st["epochs"], so["epochs"], st["kkt_rel"], so["kkt_rel"])
+        assert st["bundles"] == so["bundles"]
         # F is non-increasing bundle by bundle (Lemma 1(c)) on the GPU as well
         assert np.all(tr["dF"] <= 1e-9 * abs(so["F_final"]))
         assert st["kernel_launches"] > 0
@@ -180,7 +223,8 @@ def test_objective_and_kkt(pk, name):
 def test_mixed_mode_refresh(pk, name):
     """After a mixed-precision solve the problem refreshes z = Xw in double-float arithmetic on the
     FP32 pipe: the objective from it stays within 1e-12 of the oracle's FP64 one, also at large
-    margins; the KKT norm (FP32 column sums in this mode) within 1e-5."""
+    margins; the KKT norm (per-sample FP64 coefficients split into FP32 pairs, double-float column
+    sums) within 1e-9."""
     wl, p = problem(name)
     orc = oracle.Oracle.from_problem(p, wl.C, wl.loss)
     P = pk.Problem.from_csc(p.col_ptr, p.row_idx, p.val, p.y, wl.C, wl.loss)
@@ -191,9 +235,32 @@ def test_mixed_mode_refresh(pk, name):
             w = rng.normal(0, scale, p.n_features) * (rng.random(p.n_features) < 0.05)
             P.set_w(w)
             assert P.objective() == pytest.approx(orc.objective(w), rel=1e-12)
-            assert P.kkt() == pytest.approx(orc.kkt_l1(w), rel=1e-5)
+            assert P.kkt() == pytest.approx(orc.kkt_l1(w), rel=1e-9)
     finally:
         P.close()
+
+
+@pytest.mark.parametrize("name,Pb", [("svm_20k_100k", 1024), ("lr_2k_10k", 64), ("ragged_svm", 97)])
+def test_fp64_rows_layout_repeats_bit_for_bit(pk, name, Pb):
+    """FP64 with the row-sorted layout on the largest walker grid: every sum of the path is formed in
+    a fixed order or exactly (integer limbs), so two solves give the same w, bit for bit, and the
+    same trajectory."""
+    wl, p = problem(name)
+    runs = []
+    for _ in range(2):
+        P = pk.Problem.from_csc(p.col_ptr, p.row_idx, p.val, p.y, wl.C, wl.loss)
+        try:
+            opts = pk.pcdn_default_opts(prec="fp64", grid_ctas=100000, layout="rows", max_epochs=200)
+            rc, w, st, tr = P.solve(Pb, wl.eps, wl.solver_seed, opts, trace_bundles=100000, trace_epochs=200)
+            assert st["walk_grid"] > 1
+            runs.append((w, st, tr))
+        finally:
+            P.close()
+    (w1, s1, t1), (w2, s2, t2) = runs
+    assert np.array_equal(w1.view(np.uint64), w2.view(np.uint64))
+    assert s1["epochs"] == s2["epochs"] and s1["bundles"] == s2["bundles"] and s1["F_final"] == s2["F_final"]
+    for k in ("q", "alpha", "Delta", "dF"):
+        assert np.array_equal(t1[k], t2[k]), k
 
 
 @pytest.mark.parametrize("long_row", [False, True])
