@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libpcdn.so")
-SOURCES = ["pcdn_walk.cu", "pcdn_walk_rows.cu", "pcdn_rows.cu", "pcdn_prep.cu", "pcdn_api.cu", "pcdn_noalloc.cu",
+SOURCES = ["pcdn_walk.cu", "pcdn_walk_rows.cu", "pcdn_rows.cu", "pcdn_mirror.cu", "pcdn_prep.cu", "pcdn_api.cu", "pcdn_noalloc.cu",
            "pcdn_sched.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

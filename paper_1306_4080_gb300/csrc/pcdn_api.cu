@@ -338,45 +338,6 @@ int check_host_entries(const pcdn_csc* X, const int8_t* y) {
   return PCDN_OK;
 }
 
-// The row mirror by a stable LSD radix sort of all entries by row (any row lengths); row_ptr is
-// already set.
-int mirror_by_sort(pcdn_problem* p) {
-  cudaStream_t s = p->stream;
-  const int64_t n = p->n, m = p->m, nnz = p->nnz;
-  int32_t* entry_col = nullptr;
-  uint32_t *k0 = nullptr, *k1 = nullptr;
-  int32_t *v0 = nullptr, *v1 = nullptr;
-  int64_t *hist = nullptr, *ws = nullptr;
-  const int64_t hn = radix_hist_elems(nnz);
-  cudaError_t e = cudaSuccess;
-  auto cleanup = [&]() {
-    dfree(entry_col, s); dfree(k0, s); dfree(k1, s); dfree(v0, s); dfree(v1, s);
-    dfree(hist, s); dfree(ws, s);
-  };
-  if ((e = dalloc(&entry_col, nnz, s)) || (e = dalloc(&k0, nnz, s)) || (e = dalloc(&k1, nnz, s)) ||
-      (e = dalloc(&v0, nnz, s)) || (e = dalloc(&v1, nnz, s)) || (e = dalloc(&hist, hn, s)) ||
-      (e = dalloc(&ws, scan_workspace_elems(hn > n + 1 ? hn : n + 1), s))) {
-    cleanup();
-    return fail(e == cudaErrorMemoryAllocation ? PCDN_ENOMEM : PCDN_ECUDA, "mirror workspace: %s", cudaGetErrorString(e));
-  }
-  int key_bits = 1;
-  while ((int64_t(1) << key_bits) < n) ++key_bits;
-  uint32_t* ko = nullptr;
-  int32_t* vo = nullptr;
-  if (nnz > 0) {
-    if ((e = entry_columns(p->col_ptr, m, nnz, entry_col, s, &p->launches)) ||
-        (e = copy_keys_u32(p->row_idx, k0, nnz, s, &p->launches)) || (e = iota_i32(v0, nnz, s, &p->launches)) ||
-        (e = radix_sort_u32(k0, v0, k1, v1, nnz, key_bits, hist, ws, &ko, &vo, s, &p->launches)) ||
-        (e = gather_csr(vo, entry_col, p->val, nnz, p->col_idx, p->rval, s, &p->launches)) ||
-        (e = cudaStreamSynchronize(s))) {
-      cleanup();
-      return fail(PCDN_ECUDA, "mirror build: %s", cudaGetErrorString(e));
-    }
-  }
-  cleanup();
-  return PCDN_OK;
-}
-
 // Everything after X and y are on the device: mirror, state, workspaces.
 int finish_create(pcdn_problem* p) {
   cudaStream_t s = p->stream;
@@ -391,43 +352,43 @@ int finish_create(pcdn_problem* p) {
   }
 
   // ---- row-major mirror: the CSC entries in row order, columns ascending within each row (the order
-  // of the FP64 refresh's sums).  Rows of at most kRowSortCap entries: scatter by row through atomic
-  // cursors, then sort each row by column.  Longer rows: a stable radix sort of all entries by row.
+  // of the FP64 refresh's sums): row pointers from the row counts, entries by a stable counting sort
+  // on the row index.  Every write stays inside the arrays whatever the entries hold, so this may
+  // run while the host still checks them.
   CUDA_TRY(palloc(p, &p->row_ptr, n + 1));
   CUDA_TRY(palloc(p, &p->col_idx, nnz));
   CUDA_TRY(palloc(p, &p->rval, nnz));
   {
+    const MirrorSizes z = mirror_sizes(n, nnz);
+    MirrorWorkspace mw{};
     int64_t *counts = nullptr, *ws = nullptr;
-    unsigned long long* mx = nullptr;
+    int32_t* ecol = nullptr;
     cudaError_t e = cudaSuccess;
-    auto cleanup = [&]() { dfree(counts, s); dfree(ws, s); dfree(mx, s); };
-    if ((e = dalloc(&counts, n + 1, s)) || (e = dalloc(&ws, scan_workspace_elems(n + 1), s)) || (e = dalloc(&mx, 1, s))) {
+    auto cleanup = [&]() {
+      dfree(counts, s); dfree(ws, s); dfree(ecol, s); dfree(mw.hist, s); dfree(mw.off, s); dfree(mw.scan_ws, s);
+      for (int t = 0; t < 2; ++t) { dfree(mw.row[t], s); dfree(mw.col[t], s); dfree(mw.val[t], s); }
+    };
+    if ((e = dalloc(&counts, n + 1, s)) || (e = dalloc(&ws, scan_workspace_elems(n + 1), s)) ||
+        (e = dalloc(&ecol, std::max<int64_t>(nnz, 1), s)) || (e = dalloc(&mw.hist, z.hist, s)) ||
+        (e = dalloc(&mw.off, z.hist, s)) || (e = dalloc(&mw.scan_ws, scan_workspace_elems(z.hist), s))) {
       cleanup();
       return fail(e == cudaErrorMemoryAllocation ? PCDN_ENOMEM : PCDN_ECUDA, "mirror workspace: %s", cudaGetErrorString(e));
     }
-    unsigned long long longest = 0;
-    if ((e = cudaMemsetAsync(counts, 0, sizeof(int64_t) * (n + 1), s)) ||
-        (nnz > 0 && (e = row_counts(p->row_idx, nnz, counts, s, &p->launches))) ||
-        (e = scan_exclusive(counts, p->row_ptr, n + 1, ws, s, &p->launches)) ||
-        (e = max_count(counts, n, mx, s, &p->launches)) ||
-        (e = cudaMemcpyAsync(&longest, mx, sizeof(longest), cudaMemcpyDeviceToHost, s)) || (e = cudaStreamSynchronize(s))) {
-      cleanup();
-      return fail(PCDN_ECUDA, "mirror row pointers: %s", cudaGetErrorString(e));
-    }
-    if (longest <= (unsigned long long)kRowSortCap) {
-      // the counts are no longer needed: they become the per-row cursors
-      if ((e = mirror_by_rows(p->col_ptr, m, p->row_idx, p->val, nnz, p->row_ptr, n,
-                              reinterpret_cast<unsigned long long*>(counts), p->col_idx, p->rval, s, &p->launches)) ||
-          (e = cudaStreamSynchronize(s))) {
+    for (int t = 0; t < z.tmp_triples; ++t)
+      if ((e = dalloc(&mw.row[t], nnz, s)) || (e = dalloc(&mw.col[t], nnz, s)) || (e = dalloc(&mw.val[t], nnz, s))) {
         cleanup();
-        return fail(PCDN_ECUDA, "mirror build: %s", cudaGetErrorString(e));
+        return fail(e == cudaErrorMemoryAllocation ? PCDN_ENOMEM : PCDN_ECUDA, "mirror workspace: %s",
+                    cudaGetErrorString(e));
       }
+    if ((e = mirror_configure()) || (e = cudaMemsetAsync(counts, 0, sizeof(int64_t) * (n + 1), s)) ||
+        (e = mirror_row_counts(p->row_idx, nnz, n, counts, s, &p->launches)) ||
+        (e = scan_exclusive(counts, p->row_ptr, n + 1, ws, s, &p->launches)) ||
+        (nnz > 0 && (e = entry_columns(p->col_ptr, m, nnz, ecol, s, &p->launches))) ||
+        (e = build_mirror(p->row_idx, ecol, p->val, nnz, n, mw, p->col_idx, p->rval, s, &p->launches))) {
       cleanup();
-    } else {
-      cleanup();
-      int rc = mirror_by_sort(p);
-      if (rc) return rc;
+      return fail(PCDN_ECUDA, "mirror build: %s", cudaGetErrorString(e));
     }
+    cleanup();
   }
 
   // ---- state
@@ -464,9 +425,6 @@ int finish_create(pcdn_problem* p) {
   CUDA_TRY(palloc(p, &p->id_item_ptr, m + 1));
   CUDA_TRY(palloc(p, &p->id_items, p->max_items));
   CUDA_TRY(cudaError_t(iota_i32(p->id_perm, m, s, &p->launches)));
-  CUDA_TRY(build_items(p->id_perm, m, p->col_ptr, nullptr, p->cnt, p->id_item_ptr, p->id_items, p->scan_ws, s,
-                       &p->launches));
-  CUDA_TRY(cudaMemcpyAsync(&p->n_id_items, p->id_item_ptr + m, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
 
   int bps = 2;
   for (int prec = 0; prec < 2; ++prec) {
@@ -495,6 +453,20 @@ int finish_create(pcdn_problem* p) {
   CUDA_TRY(cudaMemsetAsync(p->err, 0, sizeof(int) * 4, s));
   CUDA_TRY(cudaEventCreate(&p->ev0));
   CUDA_TRY(cudaEventCreate(&p->ev1));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return PCDN_OK;
+}
+
+// The work items of the identity order (the KKT and objective passes over the columns), and the
+// state at w = 0.  The items follow col_ptr: only for checked input.
+int finish_create_checked(pcdn_problem* p) {
+  cudaStream_t s = p->stream;
+  CUDA_TRY(build_items(p->id_perm, p->m, p->col_ptr, nullptr, p->cnt, p->id_item_ptr, p->id_items, p->scan_ws, s,
+                       &p->launches));
+  CUDA_TRY(cudaMemcpyAsync(&p->n_id_items, p->id_item_ptr + p->m, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  // w = 0: z = 0 for every sample, set directly (what a refresh from z = Xw gives there, bit for bit)
+  CUDA_TRY(state_at_zero(p->loss, 0, p->y, p->n, p->st, s, &p->launches));
+  p->rec_prec = 0;
   CUDA_TRY(cudaStreamSynchronize(s));
   return PCDN_OK;
 }
@@ -1262,9 +1234,11 @@ int64_t problem_bytes_estimate(int64_t n, int64_t m, int64_t nnz, int32_t P) {
   b += 4 * m + 8 * (m + 1) + (int64_t)sizeof(Item) * max_items;                     // identity-order items
   b += 8 * 3 * kPartStride * kAccPad + 4096;                                         // accumulators, flags, partials
   b += 32 * (int64_t)P + 28 * nb + 16 * nb;                                          // bundle scratch, trace, plan (1 block)
-  // the row mirror's build workspace, held while the problem is created
-  const int64_t hn = radix_hist_elems(nnz);
-  const int64_t transient = 20 * nnz + 8 * hn + 8 * scan_workspace_elems(std::max<int64_t>(hn, n + 1)) + 8 * (n + 1);
+  // the row mirror's build workspace, held while the problem is created: entry columns, the
+  // counting sort's (row, col, val) arrays between passes, histograms and offsets, row counts
+  const MirrorSizes z = mirror_sizes(n, nnz);
+  const int64_t transient = 4 * nnz + 12 * nnz * z.tmp_triples + 16 * z.hist + 8 * scan_workspace_elems(z.hist) +
+                            8 * (n + 1) + 8 * scan_workspace_elems(n + 1);
   return b + transient;
 }
 
@@ -1329,17 +1303,25 @@ int pcdn_create(const pcdn_csc* X, const int8_t* y, double C, pcdn_loss loss, pc
       (p->nnz > 0 && (e = cudaMemcpyAsync(p->val, X->val, sizeof(float) * p->nnz, cudaMemcpyHostToDevice, p->stream))) ||
       (e = cudaMemcpyAsync(p->y, y, p->n, cudaMemcpyHostToDevice, p->stream)))
     return bail(fail(PCDN_ECUDA, "input copy: %s", cudaGetErrorString(e)));
-  // every entry is checked on the host while the copies run (asynchronous from pinned memory);
-  // nothing reads the device copy before the check has passed
-  rc = check_host_entries(X, y);
-  if (rc) {
-    cudaStreamSynchronize(p->stream);  // the copies still read the caller's arrays
-    return bail(rc);
-  }
+  // every entry is checked on the host (its own thread) while the copies run and the device builds
+  // the row mirror and workspaces, whose writes stay inside their arrays for any entries; what
+  // follows col_ptr (the work items) waits for the check
+  int rc_check = PCDN_OK;
+  std::string check_msg;
+  std::thread checker([&]() {
+    rc_check = check_host_entries(X, y);
+    if (rc_check) check_msg = pcdn_last_error();
+  });
   rc = finish_create(p);
+  checker.join();
+  if (rc_check) {
+    cudaStreamSynchronize(p->stream);  // the copies still read the caller's arrays
+    bail(rc_check);
+    set_last_error(check_msg.c_str());
+    return rc_check;
+  }
   if (rc) return bail(rc);
-  rc = do_refresh(p, 0, true, false);
-  if (!rc) rc = device_status(p);
+  rc = finish_create_checked(p);
   if (rc) return bail(rc);
   *out = p;
   return PCDN_OK;
@@ -1391,9 +1373,7 @@ int pcdn_create_device(const pcdn_csc* X, const int8_t* y, double C, pcdn_loss l
   dfree(p->err, p->stream);
   p->err = nullptr;
   int rc = finish_create(p);
-  if (rc) return bail(rc);
-  rc = do_refresh(p, 0, true, false);
-  if (!rc) rc = device_status(p);
+  if (!rc) rc = finish_create_checked(p);
   if (rc) return bail(rc);
   *out = p;
   return PCDN_OK;

@@ -306,104 +306,9 @@ __global__ void entry_col_kernel(const int64_t* col_ptr, int64_t m, int64_t nnz,
   }
 }
 
-// ---- row mirror by scatter + per-row sort: entry e of column j goes to the next free slot of its
-// row (an atomic cursor per row); each row is then sorted by column.  (row, column) pairs are
-// unique, so the result equals the stable sort of the CSC entries by row.
-__global__ void max_count_kernel(const int64_t* counts, int64_t n, unsigned long long* out) {
-  unsigned long long mx = 0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    mx = max(mx, (unsigned long long)counts[i]);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if ((threadIdx.x & 31) == 0) atomicMax(out, mx);
-}
-
-__global__ void mirror_scatter_kernel(const int64_t* col_ptr, int64_t m, const int32_t* row_idx, const float* val,
-                                      int64_t nnz, unsigned long long* cursor, int32_t* col_idx, float* rval) {
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t * kSpan < nnz; t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t e0 = t * kSpan, e1 = min(nnz, e0 + kSpan);
-    int64_t j = column_of(col_ptr, m, e0);
-    int64_t next = col_ptr[j + 1];
-    for (int64_t e = e0; e < e1; ++e) {
-      while (e >= next && j + 1 < m) next = col_ptr[++j + 1];
-      const unsigned long long pos = atomicAdd(cursor + row_idx[e], 1ull);
-      col_idx[pos] = (int32_t)j;
-      rval[pos] = val[e];
-    }
-  }
-}
-
-constexpr int kRowSortWarps = 4;
-
-// One warp per row: the row's (column, value) pairs sorted by column in shared memory (bitonic
-// network over the next power of two, padded with the largest key).  Rows of at most kRowSortCap.
-__global__ void __launch_bounds__(kRowSortWarps * 32) row_sort_kernel(const int64_t* row_ptr, int64_t n,
-                                                                      int32_t* col_idx, float* rval) {
-  __shared__ int32_t sk[kRowSortWarps][kRowSortCap];
-  __shared__ float sv[kRowSortWarps][kRowSortCap];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  int32_t* K = sk[wid];
-  float* V = sv[wid];
-  for (int64_t i = (int64_t)blockIdx.x * kRowSortWarps + wid; i < n; i += (int64_t)gridDim.x * kRowSortWarps) {
-    const int64_t a = row_ptr[i];
-    const int L = (int)(row_ptr[i + 1] - a);
-    if (L <= 1) continue;
-    int N = 2;
-    while (N < L) N <<= 1;
-    for (int k = lane; k < N; k += 32) {
-      K[k] = k < L ? col_idx[a + k] : INT32_MAX;
-      V[k] = k < L ? rval[a + k] : 0.0f;
-    }
-    __syncwarp();
-    for (int size = 2; size <= N; size <<= 1) {
-      for (int stride = size >> 1; stride > 0; stride >>= 1) {
-        for (int k = lane; k < N; k += 32) {
-          const int partner = k ^ stride;
-          if (partner > k) {
-            const bool up = (k & size) == 0;
-            const int32_t x = K[k], y = K[partner];
-            if ((x > y) == up) {
-              K[k] = y;
-              K[partner] = x;
-              const float tv = V[k];
-              V[k] = V[partner];
-              V[partner] = tv;
-            }
-          }
-        }
-        __syncwarp();
-      }
-    }
-    for (int k = lane; k < L; k += 32) {
-      col_idx[a + k] = K[k];
-      rval[a + k] = V[k];
-    }
-    __syncwarp();
-  }
-}
-
-__global__ void row_count_kernel(const int32_t* row_idx, int64_t nnz, unsigned long long* counts) {
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x)
-    atomicAdd(counts + row_idx[e], 1ull);
-}
-
 __global__ void iota_kernel(int32_t* v, int64_t n) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
     v[e] = (int32_t)e;
-}
-
-__global__ void copy_keys_kernel(const int32_t* src, uint32_t* dst, int64_t n) {
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
-    dst[e] = (uint32_t)src[e];
-}
-
-__global__ void gather_csr_kernel(const int32_t* order, const int32_t* entry_col, const float* val, int64_t nnz,
-                                  int32_t* col_idx, float* rval) {
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t src = order[e];
-    col_idx[e] = entry_col[src];
-    rval[e] = val[src];
-  }
 }
 
 // ------------------------------------------------------------------------------------ validation
@@ -990,44 +895,8 @@ cudaError_t entry_columns(const int64_t* col_ptr, int64_t m, int64_t nnz, int32_
   return post(launches);
 }
 
-cudaError_t max_count(const int64_t* counts, int64_t n, unsigned long long* out, cudaStream_t s, int64_t* launches) {
-  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned long long), s);
-  if (e != cudaSuccess) return e;
-  max_count_kernel<<<grid_for(n, 256, 1024), 256, 0, s>>>(counts, n, out);
-  return post(launches);
-}
-
-cudaError_t mirror_by_rows(const int64_t* col_ptr, int64_t m, const int32_t* row_idx, const float* val, int64_t nnz,
-                           const int64_t* row_ptr, int64_t n, unsigned long long* cursor, int32_t* col_idx, float* rval,
-                           cudaStream_t s, int64_t* launches) {
-  if (nnz <= 0) return cudaSuccess;
-  cudaError_t e = cudaMemcpyAsync(cursor, row_ptr, sizeof(int64_t) * n, cudaMemcpyDeviceToDevice, s);
-  if (e != cudaSuccess) return e;
-  mirror_scatter_kernel<<<grid_for(cdiv(nnz, kSpan), 256), 256, 0, s>>>(col_ptr, m, row_idx, val, nnz, cursor, col_idx,
-                                                                         rval);
-  if ((e = post(launches)) != cudaSuccess) return e;
-  row_sort_kernel<<<grid_for(n, kRowSortWarps, 8192), kRowSortWarps * 32, 0, s>>>(row_ptr, n, col_idx, rval);
-  return post(launches);
-}
-
-cudaError_t row_counts(const int32_t* row_idx, int64_t nnz, int64_t* counts, cudaStream_t s, int64_t* launches) {
-  row_count_kernel<<<grid_for(nnz, 256), 256, 0, s>>>(row_idx, nnz, (unsigned long long*)counts);
-  return post(launches);
-}
-
 cudaError_t iota_i32(int32_t* v, int64_t n, cudaStream_t s, int64_t* launches) {
   iota_kernel<<<grid_for(n, 256), 256, 0, s>>>(v, n);
-  return post(launches);
-}
-
-cudaError_t copy_keys_u32(const int32_t* src, uint32_t* dst, int64_t n, cudaStream_t s, int64_t* launches) {
-  copy_keys_kernel<<<grid_for(n, 256), 256, 0, s>>>(src, dst, n);
-  return post(launches);
-}
-
-cudaError_t gather_csr(const int32_t* order, const int32_t* entry_col, const float* val, int64_t nnz, int32_t* col_idx,
-                       float* rval, cudaStream_t s, int64_t* launches) {
-  gather_csr_kernel<<<grid_for(nnz, 256), 256, 0, s>>>(order, entry_col, val, nnz, col_idx, rval);
   return post(launches);
 }
 

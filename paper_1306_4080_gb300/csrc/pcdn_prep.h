@@ -49,23 +49,34 @@ cudaError_t build_plan(const Item* items, int64_t n_items, const int64_t* item_p
 cudaError_t gather_w(const double* w, const int32_t* perm, int64_t npos, double* w_pos, cudaStream_t s, int64_t* launches);
 cudaError_t scatter_w(const double* w_pos, const int32_t* perm, int64_t npos, double* w, cudaStream_t s, int64_t* launches);
 
-// ---- row-major mirror -------------------------------------------------------------------------
+// ---- row-major mirror (pcdn_mirror.cu) ---------------------------------------------------------
+// Column of every CSC entry (bounded by m for any col_ptr).
 cudaError_t entry_columns(const int64_t* col_ptr, int64_t m, int64_t nnz, int32_t* entry_col, cudaStream_t s,
                           int64_t* launches);
-cudaError_t row_counts(const int32_t* row_idx, int64_t nnz, int64_t* counts, cudaStream_t s, int64_t* launches);
-// *out = max of counts[0..n) (device).
-cudaError_t max_count(const int64_t* counts, int64_t n, unsigned long long* out, cudaStream_t s, int64_t* launches);
-// Row mirror without a sort of all entries: each entry scattered to its row through an atomic
-// cursor (cursor: n words of scratch), then every row sorted by column; rows of at most
-// kRowSortCap entries.  The same arrays as the stable sort by row.  Inputs must be valid.
-constexpr int kRowSortCap = 1024;
-cudaError_t mirror_by_rows(const int64_t* col_ptr, int64_t m, const int32_t* row_idx, const float* val, int64_t nnz,
-                           const int64_t* row_ptr, int64_t n, unsigned long long* cursor, int32_t* col_idx, float* rval,
-                           cudaStream_t s, int64_t* launches);
 cudaError_t iota_i32(int32_t* v, int64_t n, cudaStream_t s, int64_t* launches);
-cudaError_t copy_keys_u32(const int32_t* src, uint32_t* dst, int64_t n, cudaStream_t s, int64_t* launches);
-cudaError_t gather_csr(const int32_t* order, const int32_t* entry_col, const float* val, int64_t nnz,
-                       int32_t* col_idx, float* rval, cudaStream_t s, int64_t* launches);
+// Entries per row into counts[0..n) (zeroed by the caller); indexes outside [0, n) are skipped.
+cudaError_t mirror_row_counts(const int32_t* row_idx, int64_t nnz, int64_t n, int64_t* counts, cudaStream_t s,
+                              int64_t* launches);
+struct MirrorSizes {
+  int passes;       // counting-sort passes (digits of at most 10 bits)
+  int64_t tiles;    // tiles of 4096 entries
+  int64_t hist;     // histogram elements per pass
+  int tmp_triples;  // (row, col, val) arrays of nnz entries between passes
+};
+MirrorSizes mirror_sizes(int64_t n, int64_t nnz);
+struct MirrorWorkspace {
+  int64_t* hist;     // [hist]
+  int64_t* off;      // [hist]
+  int64_t* scan_ws;  // [scan_workspace_elems(hist)]
+  int32_t* row[2];   // [nnz] each, tmp_triples of them
+  int32_t* col[2];
+  float* val[2];
+};
+cudaError_t mirror_configure();
+// col_idx/rval[nnz]: the entries (row_idx, entry_col, val) stably sorted by row.  Writes stay inside
+// the arrays for any row index (malformed input gives a wrong order, never a stray write).
+cudaError_t build_mirror(const int32_t* row_idx, const int32_t* entry_col, const float* val, int64_t nnz, int64_t n,
+                         const MirrorWorkspace& ws, int32_t* col_idx, float* rval, cudaStream_t s, int64_t* launches);
 
 // ---- row-sorted bundle layout (pcdn_rows.cu) ---------------------------------------------------
 // Row of every entry of the row-major mirror.
