@@ -1303,22 +1303,31 @@ int pcdn_create(const pcdn_csc* X, const int8_t* y, double C, pcdn_loss loss, pc
       (p->nnz > 0 && (e = cudaMemcpyAsync(p->val, X->val, sizeof(float) * p->nnz, cudaMemcpyHostToDevice, p->stream))) ||
       (e = cudaMemcpyAsync(p->y, y, p->n, cudaMemcpyHostToDevice, p->stream)))
     return bail(fail(PCDN_ECUDA, "input copy: %s", cudaGetErrorString(e)));
-  // every entry is checked on the host (its own thread) while the copies run and the device builds
-  // the row mirror and workspaces, whose writes stay inside their arrays for any entries; what
-  // follows col_ptr (the work items) waits for the check
-  int rc_check = PCDN_OK;
-  std::string check_msg;
-  std::thread checker([&]() {
-    rc_check = check_host_entries(X, y);
-    if (rc_check) check_msg = pcdn_last_error();
-  });
+  // every entry is checked on the device right after the copies (the same tests as the host check),
+  // while the row mirror and workspaces are built behind it (their writes stay inside their arrays
+  // for any entries); what follows col_ptr (the work items) waits for the verdict.  A rejected
+  // input is checked again on the host for a message that names the entry.
+  int* flag = nullptr;
+  if ((e = dalloc(&flag, 1, p->stream)) || (e = cudaMemsetAsync(flag, 0, sizeof(int), p->stream)) ||
+      (e = validate_device(p->col_ptr, p->row_idx, p->val, p->y, p->n, p->m, p->nnz, flag, p->stream, &p->launches)))
+    return bail(fail(PCDN_ECUDA, "validation launch: %s", cudaGetErrorString(e)));
   rc = finish_create(p);
-  checker.join();
-  if (rc_check) {
-    cudaStreamSynchronize(p->stream);  // the copies still read the caller's arrays
-    bail(rc_check);
-    set_last_error(check_msg.c_str());
-    return rc_check;
+  // the verdict, read once the stream is idle (a device-to-host copy into pageable memory in the
+  // middle of the stream would hold the host until the copies ahead of it finished)
+  cudaStreamSynchronize(p->stream);
+  int hflag = 0;
+  e = cudaMemcpy(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost);
+  dfree(flag, p->stream);
+  if (e != cudaSuccess) return bail(fail(PCDN_ECUDA, "validation: %s", cudaGetErrorString(e)));
+  if (hflag) {
+    const int rc_host = check_host_entries(X, y);
+    const std::string msg = rc_host ? pcdn_last_error() : "";
+    bail(PCDN_EINVAL);
+    if (rc_host) {
+      set_last_error(msg.c_str());
+      return rc_host;
+    }
+    return fail(PCDN_EINVAL, "CSC/labels invalid (flags 0x%x)", hflag);
   }
   if (rc) return bail(rc);
   rc = finish_create_checked(p);

@@ -861,8 +861,9 @@ __device__ __forceinline__ WarpRows warp_rows_range(const WalkParams& p) {
   wr.w0 = (int32_t)min(p.nwords, gw * per);
   wr.w1 = (int32_t)min(p.nwords, (int64_t)wr.w0 + per);
   wr.n = 0;
-  wr.cached = false;
-  wr.spec = false;
+  // a warp past the last bitmap word has no rows: nothing to stage, nothing to restore
+  wr.cached = wr.w1 <= wr.w0;
+  wr.spec = wr.w1 <= wr.w0;
   wr.word = 0u;
   return wr;
 }
