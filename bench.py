@@ -312,7 +312,8 @@ def run_batched(args, pk, pool):
             row = []
             for ci, C in enumerate(job.C_path):
                 pk.pcdn_set_C(q.handle, C)
-                o = pk.pcdn_default_opts(prec="mixed", max_epochs=args.max_epochs, warm_start=1 if ci else 0)
+                o = pk.pcdn_default_opts(prec="mixed", max_epochs=args.max_epochs, warm_start=1 if ci else 0,
+                                         layout=res[k]["layout_used"])
                 _, _, st, _ = pk.pcdn_solve(q.handle, Ps[k], 1e-3, 0, o, q.n_features, want_w=False)
                 row.append(st["F_final"])
                 epochs_plain += st["epochs"]
@@ -350,6 +351,8 @@ def run_batched(args, pk, pool):
                               "how": f"every {every}-th job; plain = pcdn_solve one solve at a time, same bundle sizes, "
                                      "its own choice of walker blocks"},
                  "P_chosen": {str(P): Ps.count(P) for P in sorted(set(Ps))},
+                 "layout_chosen": {k: sum(1 for r in res if r["layout_used"] == k)
+                                   for k in sorted({r["layout_used"] for r in res})},
                  "critical_jobs": crit[:2], "sum_path_s": sum(d["path_s"] for d in jobs_diag),
                  "config": {"workload": f"{len(pool)} problems, n_samples log-uniform [1k, 50k] x {args.batch_scale:g}, "
                                         f"n_features log-uniform [5k, 200k] x {args.batch_scale:g}, density U[0.1%, 1%], "

@@ -231,6 +231,7 @@ typedef struct {
   int32_t status;       /* out: PCDN_OK, PCDN_ENOTCONVERGED (some solve hit max_epochs) or the error
                            that ended the job */
   int32_t P_used;       /* out: the bundle size the job's path ran with */
+  int32_t layout_used;  /* out: the walker layout of its path (PCDN_LAYOUT_*; AUTO = the library's choice) */
 } pcdn_batch_job;
 
 typedef struct {
@@ -242,6 +243,10 @@ typedef struct {
   int32_t n_candidates;   /* autotuner: bundle sizes to try (0 = powers of 4 from 16 to min(4096, n_features)) */
   const int32_t* candidates;
   int32_t no_graphs;      /* 1: issue every outer iteration's kernels directly instead of replaying a graph */
+  int32_t tune_layout;    /* autotuner: 1 also probes, for each candidate bundle size whose walker
+                             takes more than one block, the walker layout the library would not pick
+                             (PCDN_LAYOUT_ROWS for mixed precision, SCATTER for FP64); only when
+                             opts->layout is PCDN_LAYOUT_AUTO */
 } pcdn_batch_opts;
 
 typedef struct {
@@ -256,7 +261,9 @@ typedef struct {
                              reaching max_epochs (counted in solves once, with their last attempt) */
 } pcdn_batch_stats;
 
-/* Defaults: max_inflight 0, threads 0, probe_eps 0.1, probe_epochs 3, default candidates.  No
+/* Defaults: max_inflight 0, threads 0, probe_eps 0.1, probe_epochs 3, default candidates,
+ * tune_layout 0 (on the 64-problem batch the extra probes cost more than the layouts they found
+ * gained: 8.2 s against 7.1 to 7.5 s).  No
  * passage: the paper solves one problem at a time (Algorithm 3). */
 void pcdn_default_batch_opts(pcdn_batch_opts* bopts);
 

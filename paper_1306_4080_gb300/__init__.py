@@ -29,6 +29,7 @@ PCDN_ENOTCONVERGED = 1
 LOSSES = {"logistic": 0, "l2svm": 1}
 PRECISIONS = {"fp64": 0, "mixed": 1}
 LAYOUTS = {"auto": 0, "scatter": 1, "rows": 2}
+LAYOUT_NAMES = {v: k for k, v in LAYOUTS.items()}
 
 SYMBOLS = ["pcdn_default_opts", "pcdn_create", "pcdn_create_device", "pcdn_solve", "pcdn_bundle_step",
            "pcdn_set_w", "pcdn_get_w", "pcdn_objective", "pcdn_kkt", "pcdn_permutation", "pcdn_memory",
@@ -80,13 +81,14 @@ class pcdn_trace(ctypes.Structure):
 class pcdn_batch_job(ctypes.Structure):
     _fields_ = [("prob", ctypes.c_void_p), ("P", ctypes.c_int32), ("eps", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("n_C", ctypes.c_int32), ("C_path", ctypes.c_void_p), ("w_out", ctypes.c_void_p),
-                ("stats", ctypes.c_void_p), ("status", ctypes.c_int32), ("P_used", ctypes.c_int32)]
+                ("stats", ctypes.c_void_p), ("status", ctypes.c_int32), ("P_used", ctypes.c_int32),
+                ("layout_used", ctypes.c_int32)]
 
 
 class pcdn_batch_opts(ctypes.Structure):
     _fields_ = [("max_inflight", ctypes.c_int32), ("threads", ctypes.c_int32), ("probe_eps", ctypes.c_double),
                 ("probe_epochs", ctypes.c_int32), ("n_candidates", ctypes.c_int32), ("candidates", ctypes.c_void_p),
-                ("no_graphs", ctypes.c_int32)]
+                ("no_graphs", ctypes.c_int32), ("tune_layout", ctypes.c_int32)]
 
 
 class pcdn_batch_stats(ctypes.Structure):
@@ -382,7 +384,8 @@ def pcdn_solve_batch(handles, n_features, C_paths, P, eps=1e-3, seed=0, opts: pc
     res = []
     for k in range(J):
         w, st, nC = outs[k]
-        res.append(dict(status=jobs[k].status, P_used=jobs[k].P_used, w=w, stats=[_stats_dict(st[i]) for i in range(nC)]))
+        res.append(dict(status=jobs[k].status, P_used=jobs[k].P_used, layout_used=LAYOUT_NAMES[jobs[k].layout_used],
+                        w=w, stats=[_stats_dict(st[i]) for i in range(nC)]))
     return rc, res, {f: getattr(bs, f) for f, _ in pcdn_batch_stats._fields_}
 
 

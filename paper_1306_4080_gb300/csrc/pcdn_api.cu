@@ -1217,6 +1217,7 @@ int task_result(SolveTask* t, double* w_out, pcdn_stats* stats) {
 
 int64_t problem_n_features(pcdn_problem* p) { return p ? p->m : 0; }
 int64_t problem_nnz(pcdn_problem* p) { return p ? p->nnz : 0; }
+bool problem_rows_layout_ok(pcdn_problem* p) { return p && p->n + p->m < kRowsMaxTerms; }
 
 int64_t problem_bytes_estimate(int64_t n, int64_t m, int64_t nnz, int32_t P) {
   if (P < 1) P = 1;

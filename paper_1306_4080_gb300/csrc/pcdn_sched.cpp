@@ -128,9 +128,11 @@ struct JobRun {
   int64_t m = 0;
   // autotuner
   std::vector<int32_t> cand;
+  std::vector<int32_t> cand_layout;  // the walker layout of each candidate (PCDN_LAYOUT_*)
   size_t probe = 0;
   double best_s = 0.0;
-  int32_t best_P = 0;
+  int32_t best_P = 0, best_layout = PCDN_LAYOUT_AUTO;
+  int32_t layout = PCDN_LAYOUT_AUTO;  // of the path's solves
   bool probing = false;
   // path
   int32_t P = 0;
@@ -150,6 +152,7 @@ struct BatchShared {
   double probe_eps;
   int32_t probe_epochs;
   bool use_graphs = true;
+  bool tune_layout = true;
   std::vector<int32_t> cand;
   std::atomic<int32_t> next{0};
   std::atomic<int64_t> solves{0}, probes{0}, epochs{0}, coord{0}, graphs{0}, retries{0};
@@ -168,9 +171,11 @@ int start_next(BatchShared& B, JobRun& r, SolveTask* t) {
     if (B.probe_epochs > 0 && o.max_epochs > B.probe_epochs) o.max_epochs = B.probe_epochs;
     int rc = pcdn_set_C(j.prob, probe_C(j));
     if (rc) return rc;
+    o.layout = r.cand_layout[r.probe];
     task_set_blocks(t, &B.budget, walker_blocks_wanted(j.prob, r.cand[r.probe]));
     return task_start(t, j.prob, r.cand[r.probe], B.probe_eps, j.seed, &o, 1);
   }
+  if (j.P == 0) o.layout = r.layout;
   if (r.ci > 0 || r.warm) o.warm_start = 1;
   int rc = pcdn_set_C(j.prob, j.C_path[r.ci]);
   if (rc) return rc;
@@ -194,11 +199,14 @@ bool on_done(BatchShared& B, JobRun& r, SolveTask* t, int rc) {
     if (r.best_P == 0 || score < r.best_s) {
       r.best_s = score;
       r.best_P = r.cand[r.probe];
+      r.best_layout = r.cand_layout[r.probe];
     }
     if (++r.probe >= r.cand.size()) {
       r.probing = false;
       r.P = r.best_P;
+      r.layout = r.best_layout;
       j.P_used = r.P;
+      j.layout_used = r.layout;
     }
   } else {
     double* w = j.w_out ? j.w_out + (int64_t)r.ci * r.m : nullptr;
@@ -226,6 +234,8 @@ bool on_done(BatchShared& B, JobRun& r, SolveTask* t, int rc) {
       r.kkt_scale *= st.kkt_rel;
       r.P = smaller;
       j.P_used = smaller;
+      r.layout = PCDN_LAYOUT_AUTO;  // the library's choice for the new size
+      j.layout_used = PCDN_LAYOUT_AUTO;
       r.warm = true;
     } else {
       if (r.kkt_scale != 1.0) {
@@ -290,14 +300,26 @@ void batch_worker(BatchShared& B, int cap, int device) {
       r.m = problem_n_features(r.job->prob);
       r.P = r.job->P;
       r.job->P_used = r.P;
+      r.job->layout_used = B.opts.layout;
       if (r.P == 0) {
         r.probing = true;
-        r.cand = B.cand.empty() ? default_candidates(r.m) : B.cand;
-        std::vector<int32_t> ok;
-        for (int32_t P : r.cand)
+        std::vector<int32_t> sizes = B.cand.empty() ? default_candidates(r.m) : B.cand, ok;
+        for (int32_t P : sizes)
           if (P >= 1 && P <= r.m) ok.push_back(P);
         if (ok.empty()) ok.push_back((int32_t)r.m);
-        r.cand = ok;
+        // every size with the library's layout; a size whose walker takes several blocks also with
+        // the other layout (the two differ only when the walker has more than one block)
+        r.cand.clear();
+        r.cand_layout.clear();
+        for (int32_t P : ok) {
+          r.cand.push_back(P);
+          r.cand_layout.push_back(B.opts.layout);
+          if (B.tune_layout && B.opts.layout == PCDN_LAYOUT_AUTO && walker_blocks_wanted(r.job->prob, P) > 1 &&
+              problem_rows_layout_ok(r.job->prob)) {
+            r.cand.push_back(P);
+            r.cand_layout.push_back(B.opts.prec == PCDN_PREC_FP64 ? PCDN_LAYOUT_SCATTER : PCDN_LAYOUT_ROWS);
+          }
+        }
       }
       busy[k] = true;
       ++active;
@@ -608,6 +630,7 @@ void pcdn_default_batch_opts(pcdn_batch_opts* o) {
   o->probe_epochs = 3;
   o->n_candidates = 0;
   o->candidates = nullptr;
+  o->tune_layout = 0;
 }
 
 int pcdn_solve_batch(pcdn_batch_job* jobs, int32_t n_jobs, const pcdn_opts* opts, const pcdn_batch_opts* bopts,
@@ -650,6 +673,7 @@ int pcdn_solve_batch(pcdn_batch_job* jobs, int32_t n_jobs, const pcdn_opts* opts
   B.probe_eps = bo.probe_eps;
   B.probe_epochs = bo.probe_epochs;
   B.use_graphs = bo.no_graphs == 0;
+  B.tune_layout = bo.tune_layout != 0;
   // longest jobs first (nonzeros times path length), so that the batch's critical paths start at
   // once and take the walker blocks they want before the short jobs fill the GPU
   B.order.resize(n_jobs);

@@ -74,6 +74,8 @@ int task_result(SolveTask* t, double* w_out, pcdn_stats* stats);
 // Number of features and of nonzeros of a problem.
 int64_t problem_n_features(pcdn_problem* p);
 int64_t problem_nnz(pcdn_problem* p);
+// the row-sorted layout fits the problem (its exact sums take fewer than 2^24 terms)
+bool problem_rows_layout_ok(pcdn_problem* p);
 
 // Device bytes a problem of this shape holds once created (and at most transiently while it is
 // created), for admission under a memory budget.

@@ -110,7 +110,7 @@ def test_autotune_picks_a_candidate_and_the_path_still_matches(pk):
     try:
         cand = [16, 64, 256]
         opts = pk.pcdn_default_opts(prec="mixed", max_epochs=400)
-        bo = pk.pcdn_default_batch_opts(n_candidates=3)
+        bo = pk.pcdn_default_batch_opts(n_candidates=3)  # one probe per size (no layout tuning)
         arr = np.array(cand, dtype=np.int32)
         bo.candidates = arr.ctypes.data
         rc, res, bs = pk.pcdn_solve_batch([q.handle for q in probs], [q.n_features for q in probs],
@@ -166,6 +166,35 @@ def test_batch_multiblock_walkers(pk):
     finally:
         for q in probs:
             q.close()
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_autotune_tries_both_layouts_for_multiblock_sizes(pk, prec):
+    """With tune_layout a candidate size whose walker spans several blocks is probed
+    with both walker layouts; the job keeps the faster one (layout_used) and its path still matches
+    the oracle (the layouts differ only in how d^T x_i reaches the samples)."""
+    wl = datagen.workload("svm_20k_100k")
+    p = datagen.generate(wl.spec, with_csr=False)
+    path = [0.5, 1.0]
+    q = pk.Problem.from_csc(p.col_ptr, p.row_idx, p.val, p.y, path[0], wl.loss)
+    try:
+        arr = np.array([1024], dtype=np.int32)
+        bo = pk.pcdn_default_batch_opts(n_candidates=1, tune_layout=1)
+        bo.candidates = arr.ctypes.data
+        opts = pk.pcdn_default_opts(prec=prec, max_epochs=400)
+        rc, res, bs = pk.pcdn_solve_batch([q.handle], [q.n_features], [path], 0, eps=1e-3, seed=1, opts=opts, bopts=bo)
+        assert rc == pk.PCDN_OK
+        assert bs["probe_solves"] == 2  # P = 1024 with each layout
+        other = "rows" if prec == "mixed" else "scatter"
+        assert res[0]["P_used"] == 1024 and res[0]["layout_used"] in ("auto", other)
+        w = None
+        for ci, C in enumerate(path):
+            orc = oracle.Oracle.from_problem(p, C, wl.loss)
+            w, so = orc.solve(1024, eps=1e-3, seed=1, w0=w, max_epochs=400)
+            Fb = res[0]["stats"][ci]["F_final"]
+            assert abs(Fb - so["F_final"]) <= 1e-6 * abs(so["F_final"]), (ci, Fb, so["F_final"])
+    finally:
+        q.close()
 
 
 def test_batch_rejects_bad_jobs(pk):
