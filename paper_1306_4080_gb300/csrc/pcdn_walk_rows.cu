@@ -776,6 +776,8 @@ __device__ __forceinline__ void rows_pass(const WalkParams& p, Shared<PREC>& sh,
     }
     int Rn = 0;
     for (int w = 0; w < kWalkWarps; ++w) Rn += sh.scan_tot[w];
+    // rows touched by the bundle, a statistic (the first pass counts each once)
+    if (MODE == kFirst && tid == 0 && Rn > 0) atomicAdd(p.counters + 4, (unsigned long long)Rn);
     __syncthreads();
     // the listed rows: every state load of a chunk in flight, then the work
     for (int base = 0; base < Rn; base += kRowsPer * kWalkThreads) {
