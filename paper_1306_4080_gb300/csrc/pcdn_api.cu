@@ -82,7 +82,8 @@ constexpr uint64_t kDefaultWaitNs = uint64_t(10) * 1000000000ull;
 // Device memory comes from one stream-ordered pool per device, owned by the library for the life of
 // the process: allocations and frees are ordered on the problem's stream and never synchronise the
 // device, so problems can be created and destroyed while other problems' solves run (the request
-// server does exactly that).  Up to kPoolKeep bytes of freed memory stay reserved for reuse.
+// server does exactly that).  Freed memory stays reserved for reuse up to kPoolKeep bytes or an
+// eighth of the device, whichever is more.
 constexpr uint64_t kPoolKeep = uint64_t(8) << 30;
 
 cudaError_t library_pool(cudaMemPool_t* out) {
@@ -101,7 +102,12 @@ cudaError_t library_pool(cudaMemPool_t* out) {
     props.location.id = dev;
     cudaMemPool_t pool = nullptr;
     if ((e = cudaMemPoolCreate(&pool, &props)) != cudaSuccess) return e;
-    uint64_t keep = kPoolKeep;
+    // freed memory kept reserved: 8 GiB, or an eighth of the device when that is more, so that a
+    // large problem's creation (transient buffers of up to about 40 bytes per nonzero) followed by
+    // its destruction and the next creation reuses mapped memory instead of mapping it again
+    size_t mem_free = 0, mem_total = 0;
+    if ((e = cudaMemGetInfo(&mem_free, &mem_total)) != cudaSuccess) return e;
+    uint64_t keep = std::max<uint64_t>(kPoolKeep, (uint64_t)mem_total / 8);
     if ((e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep)) != cudaSuccess) return e;
     // never make one problem's stream wait for another's to reuse memory freed there
     int no = 0;
@@ -366,7 +372,7 @@ int finish_create(pcdn_problem* p) {
     cudaError_t e = cudaSuccess;
     auto cleanup = [&]() {
       dfree(counts, s); dfree(ws, s); dfree(ecol, s); dfree(mw.hist, s); dfree(mw.off, s); dfree(mw.scan_ws, s);
-      for (int t = 0; t < 2; ++t) { dfree(mw.row[t], s); dfree(mw.col[t], s); dfree(mw.val[t], s); }
+      dfree(mw.row0, s); dfree(mw.trow, s); dfree(mw.tcol, s); dfree(mw.tval, s);
     };
     if ((e = dalloc(&counts, n + 1, s)) || (e = dalloc(&ws, scan_workspace_elems(n + 1), s)) ||
         (e = dalloc(&ecol, std::max<int64_t>(nnz, 1), s)) || (e = dalloc(&mw.hist, z.hist, s)) ||
@@ -374,12 +380,13 @@ int finish_create(pcdn_problem* p) {
       cleanup();
       return fail(e == cudaErrorMemoryAllocation ? PCDN_ENOMEM : PCDN_ECUDA, "mirror workspace: %s", cudaGetErrorString(e));
     }
-    for (int t = 0; t < z.tmp_triples; ++t)
-      if ((e = dalloc(&mw.row[t], nnz, s)) || (e = dalloc(&mw.col[t], nnz, s)) || (e = dalloc(&mw.val[t], nnz, s))) {
-        cleanup();
-        return fail(e == cudaErrorMemoryAllocation ? PCDN_ENOMEM : PCDN_ECUDA, "mirror workspace: %s",
-                    cudaGetErrorString(e));
-      }
+    if ((z.tmp_row && (e = dalloc(&mw.row0, nnz, s))) ||
+        (z.tmp_triple && ((e = dalloc(&mw.trow, nnz, s)) || (e = dalloc(&mw.tcol, nnz, s)) ||
+                          (e = dalloc(&mw.tval, nnz, s))))) {
+      cleanup();
+      return fail(e == cudaErrorMemoryAllocation ? PCDN_ENOMEM : PCDN_ECUDA, "mirror workspace: %s",
+                  cudaGetErrorString(e));
+    }
     if ((e = mirror_configure()) || (e = cudaMemsetAsync(counts, 0, sizeof(int64_t) * (n + 1), s)) ||
         (e = mirror_row_counts(p->row_idx, nnz, n, counts, s, &p->launches)) ||
         (e = scan_exclusive(counts, p->row_ptr, n + 1, ws, s, &p->launches)) ||
@@ -1238,7 +1245,8 @@ int64_t problem_bytes_estimate(int64_t n, int64_t m, int64_t nnz, int32_t P) {
   // the row mirror's build workspace, held while the problem is created: entry columns, the
   // counting sort's (row, col, val) arrays between passes, histograms and offsets, row counts
   const MirrorSizes z = mirror_sizes(n, nnz);
-  const int64_t transient = 4 * nnz + 12 * nnz * z.tmp_triples + 16 * z.hist + 8 * scan_workspace_elems(z.hist) +
+  const int64_t transient = 4 * nnz + 4 * nnz * z.tmp_row + 12 * nnz * z.tmp_triple + 16 * z.hist +
+                            8 * scan_workspace_elems(z.hist) +
                             8 * (n + 1) + 8 * scan_workspace_elems(n + 1);
   return b + transient;
 }

@@ -219,7 +219,8 @@ MirrorSizes mirror_sizes(int64_t n, int64_t nnz) {
   z.passes = passes;
   z.tiles = cdiv(nnz > 0 ? nnz : 1, kMTile);
   z.hist = (int64_t)(1 << bits) * z.tiles;
-  z.tmp_triples = passes >= 3 ? 2 : (passes == 2 ? 1 : 0);
+  z.tmp_row = passes >= 3 ? 1 : 0;
+  z.tmp_triple = passes >= 2 ? 1 : 0;
   return z;
 }
 
@@ -250,19 +251,25 @@ cudaError_t build_mirror(const int32_t* row_idx, const int32_t* entry_col, const
     if (e != cudaSuccess) return e;
     e = scan_exclusive(ws.hist, ws.off, (int64_t)nbins * tiles, ws.scan_ws, s, launches);
     if (e != cudaSuccess) return e;
-    const int t = pass & 1;
     if (last) {
       mirror_place_kernel<true><<<(unsigned)tiles, kMThreads, sizeof(MirrorSmem), s>>>(
           sr, sc, sv, nnz, shift, nbins, bits, tiles, ws.off, nullptr, col_idx, rval);
     } else {
+      // the pass before the last one writes the workspace's triple; a first pass of three writes
+      // its rows to the workspace and its columns and values to the output arrays (free until the
+      // last pass, which reads the triple)
+      const bool to_triple = pass == passes - 2;
+      int32_t* dr = to_triple ? ws.trow : ws.row0;
+      int32_t* dc = to_triple ? ws.tcol : col_idx;
+      float* dv = to_triple ? ws.tval : rval;
       mirror_place_kernel<false><<<(unsigned)tiles, kMThreads, sizeof(MirrorSmem), s>>>(
-          sr, sc, sv, nnz, shift, nbins, bits, tiles, ws.off, ws.row[t], ws.col[t], ws.val[t]);
+          sr, sc, sv, nnz, shift, nbins, bits, tiles, ws.off, dr, dc, dv);
+      sr = dr;
+      sc = dc;
+      sv = dv;
     }
     e = post(launches);
     if (e != cudaSuccess) return e;
-    sr = ws.row[t];
-    sc = ws.col[t];
-    sv = ws.val[t];
   }
   return cudaSuccess;
 }

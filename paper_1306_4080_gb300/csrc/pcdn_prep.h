@@ -58,19 +58,21 @@ cudaError_t iota_i32(int32_t* v, int64_t n, cudaStream_t s, int64_t* launches);
 cudaError_t mirror_row_counts(const int32_t* row_idx, int64_t nnz, int64_t n, int64_t* counts, cudaStream_t s,
                               int64_t* launches);
 struct MirrorSizes {
-  int passes;       // counting-sort passes (digits of at most 10 bits)
-  int64_t tiles;    // tiles of 4096 entries
-  int64_t hist;     // histogram elements per pass
-  int tmp_triples;  // (row, col, val) arrays of nnz entries between passes
+  int passes;      // counting-sort passes (digits of at most 10 bits)
+  int64_t tiles;   // tiles of 4096 entries
+  int64_t hist;    // histogram elements per pass
+  int tmp_row;     // 1: a row array of nnz entries (three passes)
+  int tmp_triple;  // 1: a (row, col, val) triple of nnz entries (two or three passes)
 };
 MirrorSizes mirror_sizes(int64_t n, int64_t nnz);
 struct MirrorWorkspace {
   int64_t* hist;     // [hist]
   int64_t* off;      // [hist]
   int64_t* scan_ws;  // [scan_workspace_elems(hist)]
-  int32_t* row[2];   // [nnz] each, tmp_triples of them
-  int32_t* col[2];
-  float* val[2];
+  int32_t* row0;     // [nnz] if tmp_row
+  int32_t* trow;     // [nnz] each if tmp_triple
+  int32_t* tcol;
+  float* tval;
 };
 cudaError_t mirror_configure();
 // col_idx/rval[nnz]: the entries (row_idx, entry_col, val) stably sorted by row.  Writes stay inside
