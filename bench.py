@@ -556,11 +556,16 @@ def run_ours(args):
         s64 = sts64[-1]
         lay64 = walker_layout(args.layout, "fp64", int(s64["walk_grid"]))
         ach64 = sum(s["bytes_model"] for s in sts64) / sum(s["walk_s"] for s in sts64) / 1e9
+        tr64 = walker_traffic(lay64)
+        bpl64 = sum(s["bytes_model"] for s in sts64) / sum(s["epochs"] for s in sts64)
+        mpl64 = sum(s["walk_s"] for s in sts64) / sum(s["epochs"] for s in sts64) * 1e3
+        traf64 = tr64["dram_bytes_per_launch"] * bpl64 / tr64["bytes_model_per_launch"] if tr64 else None
         extra["fp64"] = {"value": ms64 * 1e-3 / world, "unit": UNIT, "ms_per_step": ms64, "epochs": s64["epochs"],
                          "F_final": s64["F_final"], "kkt_rel": s64["kkt_rel"], "layout": lay64,
                          "kernel": WALKERS[lay64],
-                         "walk_ms_per_launch": sum(s["walk_s"] for s in sts64) / sum(s["epochs"] for s in sts64) * 1e3,
-                         "achieved_GBps": ach64, "frac": ach64 / peak, "clocks": clk64,
+                         "walk_ms_per_launch": mpl64,
+                         "achieved_GBps": ach64, "frac": ach64 / peak, "traffic": traf64,
+                         "dram_frac": (traf64 / (mpl64 * 1e-3) / 1e9 / peak) if traf64 else None, "clocks": clk64,
                          "note": "like-for-like with the FP64 reference arm: every quantity in FP64"}
 
     if args.also_shrink:
