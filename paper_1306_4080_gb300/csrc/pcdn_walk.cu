@@ -1148,10 +1148,16 @@ __global__ void __launch_bounds__(kWalkThreads, 2) walk_kernel(WalkParams p) {
         for (int wv = 0; wv < kWalkWarps; ++wv) s += sh.nrows[wv];
         atomicAdd(p.counters + 4, (unsigned long long)s);
       }
-      if (q0 == 0 && tid == 3 + 2 * kMaxK && sh.spec_bad)
-        red_add_f64(p.lsacc + ((npass % 3) * kPartStride + 3 + 2 * kMaxK) * kAccPad, 1.0);
-      if (q0 == 0 && tid == 4 + 2 * kMaxK && sh.nospec)
-        red_add_f64(p.lsacc + ((npass % 3) * kPartStride + 4 + 2 * kMaxK) * kAccPad, (double)sh.nospec);
+      // one block: its sums are the totals, kept in shared memory (no accumulator round trip)
+      if (q0 == 0 && tid == 3 + 2 * kMaxK) {
+        if (G == 1) sh.tot[tid] = sh.spec_bad ? 1.0 : 0.0;
+        else if (sh.spec_bad) red_add_f64(p.lsacc + ((npass % 3) * kPartStride + 3 + 2 * kMaxK) * kAccPad, 1.0);
+      }
+      if (q0 == 0 && tid == 4 + 2 * kMaxK) {
+        if (G == 1) sh.tot[tid] = (double)sh.nospec;
+        else if (sh.nospec)
+          red_add_f64(p.lsacc + ((npass % 3) * kPartStride + 4 + 2 * kMaxK) * kAccPad, (double)sh.nospec);
+      }
       if (tid < 3 + 2 * kMaxK) {
         const int f = tid;
         {
@@ -1169,7 +1175,9 @@ __global__ void __launch_bounds__(kWalkThreads, 2) walk_kernel(WalkParams p) {
             for (int wv = 0; wv < nw; ++wv) s.add_acc(Acc<PREC>::load(sh.red[wv][f]));
             out = s.store();
           }
-          red_add_f64(p.lsacc + ((npass % 3) * kPartStride + f) * kAccPad, Acc<PREC>::load(out).value());
+          const double v = Acc<PREC>::load(out).value();
+          if (G == 1) sh.tot[f] = v;  // = 0 + v, what the accumulator would hold
+          else red_add_f64(p.lsacc + ((npass % 3) * kPartStride + f) * kAccPad, v);
         }
       }
       const int qbase = q0;
@@ -1185,8 +1193,10 @@ __global__ void __launch_bounds__(kWalkThreads, 2) walk_kernel(WalkParams p) {
         if (tid < kPartStride) {
           const int f = tid;
           const bool used = f < 3 + K || (f >= 3 + kMaxK && f < 3 + kMaxK + K) || (qbase == 0 && f >= 3 + 2 * kMaxK);
-          if (used) sh.tot[f] = __ldcg(p.lsacc + ((npass % 3) * kPartStride + f) * kAccPad);
-          if (blockIdx.x == 0) p.lsacc[(((npass + 2) % 3) * kPartStride + f) * kAccPad] = 0.0;
+          if (G > 1) {
+            if (used) sh.tot[f] = __ldcg(p.lsacc + ((npass % 3) * kPartStride + f) * kAccPad);
+            if (blockIdx.x == 0) p.lsacc[(((npass + 2) % 3) * kPartStride + f) * kAccPad] = 0.0;
+          }
         }
         __syncthreads();
         // the decision (Eq. 6): lane q of warp 0 tests step size alpha_q, the first passing one wins
