@@ -1181,6 +1181,20 @@ __global__ void __launch_bounds__(kWalkThreads, 2) walk_kernel(WalkParams p) {
         }
       }
       const int qbase = q0;
+      // the next bundle's first batch of nonzeros, copied while barrier 2 and the decision run (X and
+      // the plan are read-only; the item and nonzero arrays are idle until the next column pass)
+      if (q0 == 0 && nx_load > 0) {
+        cp_async_wait_all();  // its items
+        __syncthreads();
+        int nb, eb;
+        plan_batch(sh, nx_load, nb, eb);
+        stage_entries_async(p, sh, nb);
+        if (tid == 0) {
+          sh.pf_nb = nb;
+          sh.pf_eb = eb;
+          sh.pf_ready = 1;
+        }
+      }
       // barrier 2; then every block reads the accumulated sums and takes the same decision.  The
       // accumulators rotate over three buffers by pass: after barrier 2 of pass k, block 0 clears the
       // buffer of pass k + 2 (last read in pass k - 1, before this barrier; next added to after
@@ -1291,19 +1305,7 @@ __global__ void __launch_bounds__(kWalkThreads, 2) walk_kernel(WalkParams p) {
     if (full_step && sh.all_spec) {
       // every warp wrote the full step's state and cleared its scratch during the line search:
       // the next bundle may start without a third barrier (its column pass reads the new states
-      // after barrier 2; gk, hk, dk alternate halves by bundle)
-      if (nx_load > 0) {
-        cp_async_wait_all();
-        __syncthreads();
-        int nb, eb;
-        plan_batch(sh, nx_load, nb, eb);
-        stage_entries_async(p, sh, nb);
-        if (tid == 0) {
-          sh.pf_nb = nb;
-          sh.pf_eb = eb;
-          sh.pf_ready = 1;
-        }
-      }
+      // after barrier 2; gk, hk, dk alternate halves by bundle; its first batch is in flight)
       if (tid == 0) {
         sh.spec_bad = 0;
         sh.nospec = 0;
@@ -1327,21 +1329,8 @@ __global__ void __launch_bounds__(kWalkThreads, 2) walk_kernel(WalkParams p) {
       sh.spec_bad = 0;
       sh.nospec = 0;
     }
-    // barrier 3, with the next bundle's first batch planned and its nonzero copies issued between
-    // arriving and waiting (X and the plan are read-only)
+    // barrier 3 (the next bundle's first batch was issued before barrier 2)
     grid_arrive(p);
-    if (nx_load > 0) {
-      cp_async_wait_all();
-      __syncthreads();
-      int nb, eb;
-      plan_batch(sh, nx_load, nb, eb);
-      stage_entries_async(p, sh, nb);
-      if (tid == 0) {
-        sh.pf_nb = nb;
-        sh.pf_eb = eb;
-        sh.pf_ready = 1;
-      }
-    }
     if (!grid_wait(p, bar, sh)) {
       cp_async_wait_all();  // the next bundle's nonzero copies
       return;
