@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--also-shrink", type=int, default=1,
                     help="also time solves that shrink between outer iterations (reported under 'shrinking')")
     ap.add_argument("--max-epochs", type=int, default=1000)
-    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=4)
     ap.add_argument("--cpu-bundles", type=int, default=0, help="oracle sample size in bundles (0 = auto)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -600,7 +600,8 @@ def run_ours(args):
             if i > 0:
                 times.append(t1 - t0)
         h2d = cp.nbytes + ri.nbytes + vv.nbytes + yy.nbytes
-        e2e = {"value": statistics.mean(times) / world, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+        e2e = {"value": statistics.mean(times) / world, "unit": UNIT, "min": min(times), "max": max(times),
+               "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(8 * prob.n_features + 8), "steps": len(times),
                "includes": "pcdn_create from pinned host CSC + row-mirror build + solve + w to host + destroy"}
 
