@@ -796,6 +796,8 @@ int run_walk(pcdn_problem* p, const pcdn_opts* o, const int32_t* perm, int64_t n
   CUDA_TRY(gather_w(p->w, perm, npos, p->w_pos, p->stream, &p->launches));
   CUDA_TRY(cudaMemsetAsync(p->sync, 0, sizeof(uint32_t) * 8, p->stream));
   CUDA_TRY(cudaMemsetAsync(p->lsacc, 0, sizeof(double) * 3 * kPartStride * kAccPad, p->stream));
+  // split-column partial slots start all ones (unpublished) for the scatter walker's polled combine
+  if (layout != PCDN_LAYOUT_ROWS) CUDA_TRY(cudaMemsetAsync(p->part, 0xFF, sizeof(double) * 2 * p->max_items, p->stream));
   CUDA_TRY(record(p->ev0, p));
   if (layout == PCDN_LAYOUT_ROWS) CUDA_TRY(launch_walk_rows(p->loss, (int)o->prec, w, grid, p->stream, p->capturing));
   else CUDA_TRY(launch_walk(p->loss, (int)o->prec, w, grid, p->stream, p->capturing));

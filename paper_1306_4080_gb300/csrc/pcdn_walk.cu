@@ -310,6 +310,44 @@ __device__ __forceinline__ void split_combine_warp(const double* part, int nch, 
   h = warp_sum(h);
 }
 
+// The same sum, polling the partial slots themselves instead of the column's counter: before each
+// walker launch the slots are filled with an all-ones pattern (a NaN payload that no arithmetic
+// produces), so a slot is published once its two words differ from it, and the warp has every
+// chunk's sums in one round trip when they are ready.  The order of the sum is split_combine_warp's.
+// false when the wait gave up (or another block recorded an error).
+__device__ __forceinline__ bool split_poll_combine_warp(const WalkParams& p, const double* part, int nch, double& g,
+                                                        double& h) {
+  const int lane = threadIdx.x & 31;
+  double2 v[kWarpChunks / kWarp];
+  Waiter wt;
+  for (;;) {
+    bool ready = true;
+#pragma unroll
+    for (int u = 0; u < kWarpChunks / kWarp; ++u) {
+      const int c = u * kWarp + lane;
+      v[u] = c < nch ? __ldcv(reinterpret_cast<const double2*>(part) + c) : make_double2(0.0, 0.0);
+      ready = ready && __double_as_longlong(v[u].x) != -1ll && __double_as_longlong(v[u].y) != -1ll;
+    }
+    if (__all_sync(0xffffffffu, ready)) break;
+    int stop = 0;
+    if (lane == 0) stop = wt.poll(p);
+    if (__shfl_sync(0xffffffffu, stop, 0)) return false;
+  }
+  g = v[0].x;
+  h = v[0].y;
+  const int nu = (nch + kWarp - 1) / kWarp;
+#pragma unroll
+  for (int u = 1; u < kWarpChunks / kWarp; ++u) {
+    if (u < nu) {
+      g += v[u].x;
+      h += v[u].y;
+    }
+  }
+  g = warp_sum(g);
+  h = warp_sum(h);
+  return true;
+}
+
 // Canonical sum for nch > kWarpChunks, by the whole block: thread s sums chunks s, s + 256, ...,
 // then each warp's lane tree, then the warps in order (result in thread 0).
 template <class SH>
@@ -556,7 +594,10 @@ __device__ void column_pass(const WalkParams& p, SharedWalk<PREC>& sh, int64_t l
     // the listed chunks (item order): their columns, one warp per column of at most kWarpChunks
     // chunks, then the block for each larger one
     if (tid < ns) {
-      const Item it = p.items[sh.split_items[tid]];
+      // the chunk's record: still staged when it belongs to the last batch (a block's whole share,
+      // usually), else from global memory
+      const int64_t gi = sh.split_items[tid];
+      const Item it = (gi >= last_i && gi < last_i + last_nb) ? sh.items[gi - last_i] : p.items[gi];
       sh.s_kl[tid] = (int32_t)(it.pos - lo);
       sh.s_nch[tid] = it.nch;
       sh.s_chunk[tid] = it.chunk;
@@ -576,11 +617,10 @@ __device__ void column_pass(const WalkParams& p, SharedWalk<PREC>& sh, int64_t l
       const bool start = k == 0 || sh.s_kl[k] != sh.s_kl[k - 1];
       if (!start || sh.s_nch[k] > kWarpChunks) continue;
       double g, h;
-      if (!split_wait_warp(p, col_cnt + sh.s_kl[k], sh.s_nch[k])) {
+      if (!split_poll_combine_warp(p, p.part + 2 * (sh.split_items[k] - sh.s_chunk[k]), sh.s_nch[k], g, h)) {
         if (lane == 0) sh.split_ok = 0;
         continue;
       }
-      split_combine_warp(p.part + 2 * (sh.split_items[k] - sh.s_chunk[k]), sh.s_nch[k], g, h);
       if (lane == 0) {
         const double dj = split_finalize<PREC>(p, sh.dko + sh.s_kl[k], sh.s_chunk[k] == 0, g, h, sh.s_w[k], sh.s_terms[sh.s_col[k]]);
         if (dj != 0.0) sh.has_nz = 1;
